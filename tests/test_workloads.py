@@ -1,0 +1,84 @@
+"""Pins of the synthetic beam inputs (Sec. 5 beam model) to closed forms."""
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as la
+
+from paper_1606_01216_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "cantilever_roots.txt")
+
+
+def _roots():
+    rows = [l.split() for l in open(GOLD) if l.strip() and not l.startswith("#")]
+    return [(int(k), float(a), float(b)) for k, a, b in rows]
+
+
+def _dense(b, which):
+    A = np.zeros((b.n, b.n))
+    rows = np.repeat(np.arange(b.n), np.diff(b.rowptr))
+    A[rows, b.col] = b.m_val if which == "m" else b.k_val
+    return A
+
+
+def test_bisection_matches_tabulated_roots():
+    for k, r5, r10 in _roots():
+        x = W.cantilever_beta_l(k)
+        assert abs(x - r10) < 1e-9
+        assert abs(x - r5) < 6e-5
+        assert abs(1 + math.cos(x) * math.cosh(x)) < 1e-9 * math.cosh(x)
+
+
+@pytest.mark.parametrize("scaling", ["unit", "literal"])
+@pytest.mark.parametrize("n_e", [10, 20, 50])
+def test_eigenfrequencies(n_e, scaling):
+    """Generalised eigenvalues of (K, M) give omega_k = (beta_k L)^2 / L^2
+    (EI = rho A = 1).  The Hermite-cubic FE error in beta_k L falls like h^4:
+    bound 2e-4 (k=3, n_e=10) scaled by (10/n_e)^4, with headroom; a floor of
+    2e-8 covers the dense eigensolver's own eps * kappa error at n_e = 50."""
+    b = W.beam(n_e, scaling)
+    L = n_e * b.h
+    ev = la.eigh(_dense(b, "k"), _dense(b, "m"), eigvals_only=True)[:3]
+    for (k, r5, r10), lam in zip(_roots(), ev):
+        bl = math.sqrt(math.sqrt(lam)) * L
+        tol = max({1: 1e-6, 2: 3e-5, 3: 3e-4}[k] * (10.0 / n_e) ** 4, 2e-8)
+        assert abs(bl - r10) / r10 < tol, (k, bl, r10)
+        if n_e >= 20:
+            assert abs(bl - r5) / r5 < 5e-5
+
+
+def test_h4_convergence():
+    errs = []
+    for n_e in (10, 20):
+        b = W.beam(n_e, "unit")
+        lam = la.eigh(_dense(b, "k"), _dense(b, "m"), eigvals_only=True)[2]
+        errs.append(abs(math.sqrt(math.sqrt(lam)) * n_e - _roots()[2][2]))
+    assert 12 < errs[0] / errs[1] < 20   # h halves -> error / 16
+
+
+def test_structure():
+    b = W.beam(7)
+    assert b.n == 14 and b.nnz == 7 * b.n - 12
+    for A in (_dense(b, "m"), _dense(b, "k")):
+        assert np.array_equal(A, A.T)
+        assert np.all(np.linalg.eigvalsh(A) > 0)
+        i, j = np.nonzero(A)
+        assert np.max(np.abs(i - j)) == 3
+
+
+def test_loads_and_shifts():
+    F = W.loads(10, 3, seed=4)
+    assert F.flags.f_contiguous and F.shape == (10, 3)
+    assert F[8, 0] == 1.0 and np.count_nonzero(F[:, 0]) == 1
+    assert np.array_equal(F, W.loads(10, 3, seed=4))
+    s = W.log_shifts(-1, 4, 8)
+    assert s[0] == pytest.approx(0.1) and s[-1] == pytest.approx(1e4)
+    assert np.allclose(np.diff(np.log10(s)), 5 / 7)
+    mid = W.midpoint_shifts(-1, 4, 16)
+    assert len(mid) == 16 and mid[0] > 0.1 and mid[-1] < 1e4
+    batch = W.batched_beams()
+    assert len(batch) == 32
+    assert all(5000 <= c["n_e"] <= 500000 and 4 <= len(c["shifts"]) <= 16 and c["m"] in (1, 4)
+               for c in batch)
