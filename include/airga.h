@@ -1,0 +1,219 @@
+/*
+ * airga.h — C ABI of libairga.so: the shifted-system SPAI-preconditioned CG
+ * path of "Preconditioned Iterative Solves in Model Reduction of Second Order
+ * Linear Dynamical Systems" (Singh, Ahuja, Fassbender; arXiv 1606.01216),
+ * written for one NVIDIA GB300 GPU (sm_103a).
+ *
+ * The path solves a sequence of shifted sparse SPD systems
+ *     K_i X = F,   K_i = s_i^2 M + s_i D + K,   D = alpha M + beta K
+ * (Eq. 1.1; coefficient matrix of Algorithm 3, Sec. 3.1) by preconditioned CG
+ * with a sparse approximate inverse P (Sec. 3.1, Eq. 3.1) built on a fixed
+ * sparsity pattern, and the SPAI update P_new = Q P_old of Sec. 3.2 applied as
+ * a chain of mat-vecs (Algorithm 5).
+ *
+ * General conventions
+ * -------------------
+ * - Every function is plain C; no CUDA or torch type appears.  A `stream`
+ *   argument is a cudaStream_t passed as void* (NULL = legacy default
+ *   stream).  Work is enqueued asynchronously on that stream unless a
+ *   function says it synchronises; results written to caller buffers are
+ *   valid after the stream has been synchronised.
+ * - Every raw pointer argument is a DEVICE pointer on the current CUDA
+ *   device, owned by the caller, unless stated otherwise.  Vectors and
+ *   multi-column blocks are FP64, column-major n x m with leading dimension n.
+ * - Handles (airga_mat, airga_precond) are owned by the library and released
+ *   with the matching *_free.  Their device storage comes from a
+ *   library-owned stream-ordered memory pool on the device that was current
+ *   at creation; it is released on the stream that created the handle, so
+ *   free a handle before destroying that stream.
+ * - Matrices are stored as band-7 diagonals ("DIA"): band[(d+3)*n + i] =
+ *   A(i, i+d) for d = -3..3, entries outside the matrix held as 0.
+ * - Return value: AIRGA_OK or an AIRGA_E_* code for argument, shape, CUDA or
+ *   allocation errors detected when the call is made.  Numerical outcomes of
+ *   a solve (converged, iteration cap, breakdown, barrier timeout) are written
+ *   per column to device memory (pcg_solve's `status`).  No call aborts the
+ *   process or traps the device.  airga_last_error() gives a message for the
+ *   last failing call on the calling host thread.
+ */
+#ifndef AIRGA_H
+#define AIRGA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes ---------------------------------------------------------- */
+#define AIRGA_OK 0
+#define AIRGA_E_INVALID_ARG 1   /* bad pointer, size, option or handle */
+#define AIRGA_E_SHAPE 2         /* operands of different sizes */
+#define AIRGA_E_BREAKDOWN 3     /* CG: (p, A p) <= 0 (A not SPD) or (r, z) zero / not finite */
+#define AIRGA_E_MAXIT 4         /* CG: iteration cap reached; X holds the last iterate */
+#define AIRGA_E_TIMEOUT 5       /* bounded grid barrier gave up; the solve stopped early */
+#define AIRGA_E_RANK 6          /* SPAI: a column least-squares block is rank deficient */
+#define AIRGA_E_CUDA 7          /* a CUDA runtime call failed */
+#define AIRGA_E_OOM 8           /* device allocation failed */
+#define AIRGA_E_NOT_BANDED 9    /* CSR input has an entry with |col - row| > 3 */
+
+/* SPAI modes */
+#define AIRGA_SPAI_QR 0         /* exact fixed-pattern least squares, Householder QR */
+#define AIRGA_SPAI_MR 1         /* the paper's minimal-residual iteration (Algorithms 2 / 4) */
+
+typedef struct airga_mat_s *airga_mat;
+typedef struct airga_precond_s *airga_precond;
+
+/* Options shared by the SPAI and CG calls.  Fill with airga_options_default
+ * and change fields; passing NULL where an options pointer is taken means
+ * the defaults. */
+typedef struct {
+    double tol;                 /* CG stops when ||r_k||_2 <= tol ||F(:,c)||_2 (default 1e-10) */
+    int32_t maxit;              /* CG iteration cap per column (default 20000) */
+    int32_t spai_mode;          /* AIRGA_SPAI_QR (default) or AIRGA_SPAI_MR */
+    double mr_tol;              /* MR: stop a column when ||r|| <= mr_tol ||b_j|| (default 0.01, Sec. 5) */
+    int32_t mr_kmax;            /* MR: step cap per column (default 50) */
+    int32_t symmetrize;         /* CG applies z = 1/2 (C + C^T) r instead of z = C r (default 1) */
+    int32_t pattern_hbw;        /* SPAI pattern: band |i - j| <= pattern_hbw, 0..3 (default 3) */
+    int32_t warm_start;         /* CG: nonzero = use X's content on entry as x_0 (default 0: x_0 = 0) */
+    int32_t barrier_timeout_ms; /* bound on any single grid-barrier wait (default 2000) */
+} airga_options;
+
+void airga_options_default(airga_options *opt);
+const char *airga_status_string(int status);
+const char *airga_last_error(void);
+int airga_version(void);        /* 100 * major + minor */
+
+/* ---------------------------------------------------------------------- */
+/* matrices                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* Import a square n x n CSR matrix (device arrays: rowptr[n+1] int64,
+ * col[nnz] int32, val[nnz] double) into band-7 storage.  Duplicate entries
+ * are summed.  Entries with |col - row| > 3 give AIRGA_E_NOT_BANDED, column
+ * indices outside [0, n) or a malformed rowptr give AIRGA_E_INVALID_ARG.
+ * SYNCHRONISES `stream` (to read back the validation flag).  n >= 1. */
+int airga_mat_from_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
+                       const double *val, void *stream, airga_mat *out);
+
+/* Import band-7 storage band[7*n] (layout above; entries outside the matrix
+ * must be 0).  The data are copied. */
+int airga_mat_from_band(int64_t n, const double *band, void *stream, airga_mat *out);
+
+/* Copy a matrix's band-7 storage into band[7*n]. */
+int airga_mat_to_band(airga_mat A, double *band, void *stream);
+
+/* Rows of a matrix (0 for NULL). */
+int64_t airga_mat_rows(airga_mat A);
+
+void airga_mat_free(airga_mat A);
+
+/* ---------------------------------------------------------------------- */
+/* the path                                                                */
+/* ---------------------------------------------------------------------- */
+
+/* K(s) = s^2 M + s D + K with D = alpha M + beta K (Eq. 1.1; K_i of
+ * Algorithms 3 and 5, Sec. 3).  M and K must have equal n.  *A_out is a new
+ * handle on the same band. */
+int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, double s,
+                           void *stream, airga_mat *A_out);
+
+/* Y = A X for m columns (X, Y: n x m column-major, distinct buffers). */
+int airga_spmv(airga_mat A, const double *X, double *Y, int32_t m, void *stream);
+
+/* SPAI of Sec. 3.1: P minimising ||I - A P||_F = sum_j ||e_j - A p_j||_2
+ * (Eq. 3.1) over matrices whose column j is supported on
+ * J_j = {k : |k - j| <= hbw}, hbw = opt->pattern_hbw (band-7 pattern of A for
+ * hbw = 3).  opt->spai_mode selects the exact per-column least-squares
+ * solution (Householder QR of the |I_j| x |J_j| block A(I_j, J_j)) or the
+ * paper's MR iteration of Algorithm 2 (initial P = alpha I, alpha =
+ * trace(A) / trace(A A^T); steps capped by opt->mr_kmax).  The new handle
+ * holds P and, for CG, P_sym = 1/2 (P + P^T) on the same band.  A rank
+ * deficient column block is reported through airga_precond_status. */
+int airga_spai_build(airga_mat A, const airga_options *opt, void *stream, airga_precond *P_out);
+
+/* SPAI update of Sec. 3.2 / Algorithm 4: Q minimising
+ * ||A_prev - A_next Q||_F = sum_j ||A_prev e_j - A_next q_j||_2 over the same
+ * kind of pattern, exact (QR) or by the MR iteration with the initial scaling
+ * alpha = 1/2 trace(A_prev^T A_next + A_next^T A_prev) / trace(A_next^T A_next).
+ * The new handle is the chain [P_prev's factors..., Q], i.e. the
+ * preconditioner Q P_prev of Algorithm 5, applied by mat-vecs and never
+ * formed.  The new handle keeps P_prev's factors alive (reference counted),
+ * so P_prev may be freed at any time. */
+int airga_spai_update(airga_precond P_prev, airga_mat A_prev, airga_mat A_next,
+                      const airga_options *opt, void *stream, airga_precond *P_out);
+
+/* z = 1/2 (C + C^T) r (symmetrize != 0) or z = C r, C = F_last ... F_0 the
+ * handle's chain.  r, z: n-vectors, distinct buffers. */
+int airga_precond_apply(airga_precond P, const double *r, double *z, int32_t symmetrize,
+                        void *stream);
+
+/* Number of factors in the chain (1 for a freshly built SPAI), 0 for NULL. */
+int32_t airga_precond_length(airga_precond P);
+
+/* Rows of the preconditioner (0 for NULL). */
+int64_t airga_precond_rows(airga_precond P);
+
+/* Copy factor k (0 = the built SPAI P, k >= 1 the update factors Q in
+ * order) into band[7*n]. */
+int airga_precond_factor(airga_precond P, int32_t k, double *band, void *stream);
+
+/* Build a chain handle from nfactors band-7 arrays (device pointers, each
+ * 7*n doubles, factor 0 first); the data are copied.  Together with
+ * airga_precond_factor this saves and restores a preconditioner. */
+int airga_precond_from_bands(int64_t n, int32_t nfactors, const double *const *bands,
+                             void *stream, airga_precond *P_out);
+
+/* Per-column results of the SPAI call that produced the newest factor:
+ * steps[n] (int32, MR steps; 0 in QR mode) and colres[n] (double,
+ * ||b_j - A m_j||_2 of the column least-squares problem); either may be
+ * NULL.  *status_out (host) is AIRGA_OK or AIRGA_E_RANK and SYNCHRONISES
+ * `stream` when status_out is not NULL. */
+int airga_precond_status(airga_precond P, int32_t *steps, double *colres, int *status_out,
+                         void *stream);
+
+void airga_precond_free(airga_precond P);
+
+/* Preconditioned CG (Hestenes-Stiefel) on A X = F for m right-hand sides,
+ * each column an independent recurrence (Alg. 3 line 5, Alg. 5 lines 7 and
+ * 11; CG chosen for SPD K_i, Sec. 5):
+ *   x_0 = 0 (or X on entry if opt->warm_start); r_0 = f - A x_0;
+ *   z = M r; p = z; for k = 1..maxit: q = A p; a = (r,z)/(p,q);
+ *   x += a p; r -= a q; stop if ||r|| <= tol ||f||; z = M r;
+ *   b = (r,z)_new / (r,z)_old; p = z + b p,
+ * with M = 1/2 (C + C^T) (opt->symmetrize) or C, C the chain of P.  P may
+ * be NULL (M = I).  Outputs (device): X[n*m]; iters[m] (int32, iterations
+ * done); status[m] (int32, AIRGA_OK / AIRGA_E_MAXIT / AIRGA_E_BREAKDOWN /
+ * AIRGA_E_TIMEOUT); true_relres[m] (||f - A x|| / ||f|| recomputed from X at
+ * exit); res_hist[(maxit+1)*m] (optional, may be NULL: column c holds
+ * ||r_k|| / ||f|| for k = 0..iters[c], the rest untouched).  A zero column f
+ * gives x = 0, iters = 0, status OK, true_relres 0.  Uses a per-call device
+ * workspace from the library pool (about 4 n doubles). */
+int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
+                    const airga_options *opt, double *X, double *res_hist, int32_t *iters,
+                    int32_t *status, double *true_relres, void *stream);
+
+/* relres[c] = ||F(:,c) - A X(:,c)||_2 / ||F(:,c)||_2 (0 when F(:,c) = 0),
+ * the FP64 acceptance residual of a solve. */
+int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m,
+                        double *relres, void *stream);
+
+/* Test hook for failure detection (no GPU fault involved): arm a fault for
+ * the next airga_pcg_solve call of this process.  AIRGA_FAULT_SKIP_ARRIVAL
+ * makes CTA 0 skip its arrival at the first iteration barrier of the first
+ * column, so every CTA's bounded barrier wait (opt->barrier_timeout_ms)
+ * expires, the kernel returns and that column's status is AIRGA_E_TIMEOUT;
+ * the CUDA context stays usable.  The fault is consumed by that call. */
+#define AIRGA_FAULT_NONE 0
+#define AIRGA_FAULT_SKIP_ARRIVAL 1
+int airga_debug_set_fault(int fault);
+
+/* Release the library's cached device memory (pool trim) on the current
+ * device; outstanding handles stay valid. */
+int airga_trim(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AIRGA_H */

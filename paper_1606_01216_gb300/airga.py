@@ -1,0 +1,362 @@
+"""ctypes binding of libairga.so (C ABI in include/airga.h).
+
+Argument marshalling only: every step of the path runs in the library's CUDA
+kernels.  PyTorch supplies device memory (tensors) and the current stream.
+Function names follow the C entry points without the ``airga_`` prefix.
+
+The library is loaded from this package directory; if it is missing the
+import of any compute function raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libairga.so")
+
+OK = 0
+E_INVALID_ARG, E_SHAPE, E_BREAKDOWN, E_MAXIT, E_TIMEOUT = 1, 2, 3, 4, 5
+E_RANK, E_CUDA, E_OOM, E_NOT_BANDED = 6, 7, 8, 9
+SPAI_QR, SPAI_MR = 0, 1
+
+# every symbol include/airga.h declares
+EXPORTS = (
+    "airga_options_default", "airga_status_string", "airga_last_error", "airga_version",
+    "airga_mat_from_csr", "airga_mat_from_band", "airga_mat_to_band", "airga_mat_rows",
+    "airga_mat_free", "airga_assemble_shifted", "airga_spmv", "airga_spai_build",
+    "airga_spai_update", "airga_precond_apply", "airga_precond_length", "airga_precond_rows",
+    "airga_precond_factor", "airga_precond_from_bands", "airga_precond_status",
+    "airga_precond_free", "airga_pcg_solve", "airga_true_residual", "airga_debug_set_fault",
+    "airga_trim",
+)
+
+
+class Options(C.Structure):
+    _fields_ = [
+        ("tol", C.c_double),
+        ("maxit", C.c_int32),
+        ("spai_mode", C.c_int32),
+        ("mr_tol", C.c_double),
+        ("mr_kmax", C.c_int32),
+        ("symmetrize", C.c_int32),
+        ("pattern_hbw", C.c_int32),
+        ("warm_start", C.c_int32),
+        ("barrier_timeout_ms", C.c_int32),
+    ]
+
+
+class AirgaError(RuntimeError):
+    def __init__(self, code, where, msg):
+        super().__init__("%s failed: %s (%s)" % (where, msg, status_string(code)))
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """Load libairga.so once; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libairga.so is not built (run paper_1606_01216_gb300.build.build())")
+    L = C.CDLL(LIB_PATH)
+    vp, dp, i64, i32 = C.c_void_p, C.c_void_p, C.c_int64, C.c_int32
+    sig = {
+        "airga_options_default": (None, [C.POINTER(Options)]),
+        "airga_status_string": (C.c_char_p, [C.c_int]),
+        "airga_last_error": (C.c_char_p, []),
+        "airga_version": (C.c_int, []),
+        "airga_mat_from_csr": (C.c_int, [i64, i64, vp, vp, vp, vp, C.POINTER(vp)]),
+        "airga_mat_from_band": (C.c_int, [i64, vp, vp, C.POINTER(vp)]),
+        "airga_mat_to_band": (C.c_int, [vp, vp, vp]),
+        "airga_mat_rows": (i64, [vp]),
+        "airga_mat_free": (None, [vp]),
+        "airga_assemble_shifted": (C.c_int, [vp, vp, C.c_double, C.c_double, C.c_double, vp,
+                                             C.POINTER(vp)]),
+        "airga_spmv": (C.c_int, [vp, vp, vp, i32, vp]),
+        "airga_spai_build": (C.c_int, [vp, C.POINTER(Options), vp, C.POINTER(vp)]),
+        "airga_spai_update": (C.c_int, [vp, vp, vp, C.POINTER(Options), vp, C.POINTER(vp)]),
+        "airga_precond_apply": (C.c_int, [vp, vp, vp, i32, vp]),
+        "airga_precond_length": (i32, [vp]),
+        "airga_precond_rows": (i64, [vp]),
+        "airga_precond_factor": (C.c_int, [vp, i32, vp, vp]),
+        "airga_precond_from_bands": (C.c_int, [i64, i32, C.POINTER(vp), vp, C.POINTER(vp)]),
+        "airga_precond_status": (C.c_int, [vp, vp, vp, C.POINTER(C.c_int), vp]),
+        "airga_precond_free": (None, [vp]),
+        "airga_pcg_solve": (C.c_int, [vp, vp, vp, i32, C.POINTER(Options), vp, vp, vp, vp, vp,
+                                      vp]),
+        "airga_true_residual": (C.c_int, [vp, vp, vp, i32, vp, vp]),
+        "airga_debug_set_fault": (C.c_int, [C.c_int]),
+        "airga_trim": (C.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def status_string(code: int) -> str:
+    return lib().airga_status_string(int(code)).decode()
+
+
+def last_error() -> str:
+    return lib().airga_last_error().decode()
+
+
+def _check(code, where):
+    if code != OK:
+        raise AirgaError(code, where, last_error())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t: torch.Tensor | None, dtype=None):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError("expected %s, got %s" % (dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def options(**kw) -> Options:
+    o = Options()
+    lib().airga_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+# ---------------------------------------------------------------------------
+# handles
+# ---------------------------------------------------------------------------
+
+class Mat:
+    """Owning wrapper of an airga_mat handle (band-7 matrix on the device)."""
+
+    def __init__(self, handle: int, n: int):
+        self.h = C.c_void_p(handle)
+        self.n = int(n)
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.airga_mat_free(self.h)
+            self.h = C.c_void_p(None)
+
+    def band(self, stream=None) -> torch.Tensor:
+        return mat_to_band(self, stream)
+
+
+class Precond:
+    """Owning wrapper of an airga_precond handle (SPAI / update chain)."""
+
+    def __init__(self, handle: int, n: int):
+        self.h = C.c_void_p(handle)
+        self.n = int(n)
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.airga_precond_free(self.h)
+            self.h = C.c_void_p(None)
+
+    def __len__(self):
+        return int(lib().airga_precond_length(self.h))
+
+
+# ---------------------------------------------------------------------------
+# matrices
+# ---------------------------------------------------------------------------
+
+def mat_from_csr(n: int, rowptr: torch.Tensor, col: torch.Tensor, val: torch.Tensor,
+                 stream=None) -> Mat:
+    out = C.c_void_p()
+    _check(lib().airga_mat_from_csr(int(n), int(col.numel()), _ptr(rowptr, torch.int64),
+                                    _ptr(col, torch.int32), _ptr(val, torch.float64),
+                                    _stream(stream), C.byref(out)), "mat_from_csr")
+    return Mat(out.value, n)
+
+
+def mat_from_band(band: torch.Tensor, stream=None) -> Mat:
+    n = band.numel() // 7
+    out = C.c_void_p()
+    _check(lib().airga_mat_from_band(n, _ptr(band, torch.float64), _stream(stream),
+                                     C.byref(out)), "mat_from_band")
+    return Mat(out.value, n)
+
+
+def mat_to_band(A: Mat, stream=None) -> torch.Tensor:
+    band = torch.empty(7 * A.n, dtype=torch.float64, device="cuda")
+    _check(lib().airga_mat_to_band(A.h, _ptr(band), _stream(stream)), "mat_to_band")
+    return band
+
+
+# ---------------------------------------------------------------------------
+# the path
+# ---------------------------------------------------------------------------
+
+def assemble_shifted(M: Mat, K: Mat, alpha: float, beta: float, s: float, stream=None) -> Mat:
+    out = C.c_void_p()
+    _check(lib().airga_assemble_shifted(M.h, K.h, float(alpha), float(beta), float(s),
+                                        _stream(stream), C.byref(out)), "assemble_shifted")
+    return Mat(out.value, M.n)
+
+
+def _colmajor(X: torch.Tensor) -> torch.Tensor:
+    """(m, n) contiguous view of an n-vector or a column-major n x m block."""
+    if X.dim() == 1:
+        return X.reshape(1, -1)
+    Xc = X.t()
+    if not Xc.is_contiguous():
+        raise ValueError("blocks must be column-major (the transpose of a contiguous (m, n) tensor)")
+    return Xc
+
+
+def spmv(A: Mat, X: torch.Tensor, Y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Y = A X for an n-vector or a column-major n x m block."""
+    Xc = _colmajor(X)
+    if Y is None:
+        Yc = torch.empty_like(Xc)
+        Y = Yc.reshape(-1) if X.dim() == 1 else Yc.t()
+    Yc = _colmajor(Y)
+    _check(lib().airga_spmv(A.h, _ptr(Xc, torch.float64), _ptr(Yc, torch.float64), Xc.shape[0],
+                            _stream(stream)), "spmv")
+    return Y
+
+
+def spai_build(A: Mat, opts: Options | None = None, stream=None) -> Precond:
+    out = C.c_void_p()
+    _check(lib().airga_spai_build(A.h, C.byref(opts) if opts else None, _stream(stream),
+                                  C.byref(out)), "spai_build")
+    return Precond(out.value, A.n)
+
+
+def spai_update(P_prev: Precond, A_prev: Mat, A_next: Mat, opts: Options | None = None,
+                stream=None) -> Precond:
+    out = C.c_void_p()
+    _check(lib().airga_spai_update(P_prev.h, A_prev.h, A_next.h,
+                                   C.byref(opts) if opts else None, _stream(stream),
+                                   C.byref(out)), "spai_update")
+    return Precond(out.value, A_next.n)
+
+
+def precond_apply(P: Precond, r: torch.Tensor, symmetrize: bool = True,
+                  z: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if z is None:
+        z = torch.empty_like(r)
+    _check(lib().airga_precond_apply(P.h, _ptr(r, torch.float64), _ptr(z, torch.float64),
+                                     1 if symmetrize else 0, _stream(stream)), "precond_apply")
+    return z
+
+
+def precond_factor(P: Precond, k: int, stream=None) -> torch.Tensor:
+    band = torch.empty(7 * P.n, dtype=torch.float64, device="cuda")
+    _check(lib().airga_precond_factor(P.h, int(k), _ptr(band), _stream(stream)),
+           "precond_factor")
+    return band
+
+
+def precond_from_bands(bands, stream=None) -> Precond:
+    bands = list(bands)
+    n = bands[0].numel() // 7
+    arr = (C.c_void_p * len(bands))(*[b.data_ptr() for b in bands])
+    for b in bands:
+        _ptr(b, torch.float64)
+    out = C.c_void_p()
+    _check(lib().airga_precond_from_bands(n, len(bands), arr, _stream(stream), C.byref(out)),
+           "precond_from_bands")
+    return Precond(out.value, n)
+
+
+def precond_status(P: Precond, stream=None):
+    """(steps int32[n], colres float64[n], status) of the newest factor."""
+    steps = torch.empty(P.n, dtype=torch.int32, device="cuda")
+    colres = torch.empty(P.n, dtype=torch.float64, device="cuda")
+    st = C.c_int(0)
+    _check(lib().airga_precond_status(P.h, _ptr(steps), _ptr(colres), C.byref(st),
+                                      _stream(stream)), "precond_status")
+    return steps, colres, st.value
+
+
+def pcg_solve(A: Mat, P: Precond | None, F: torch.Tensor, opts: Options | None = None,
+              X: torch.Tensor | None = None, want_hist: bool = False, stream=None):
+    """Solve A X = F (F: n or n x m column-major, i.e. a contiguous (m, n)
+    tensor transposed, or a contiguous n-vector).  Returns a dict with X,
+    iters, status, true_relres (device tensors) and res_hist if asked."""
+    if F.dim() == 1:
+        Fc = F.reshape(1, -1)
+    else:
+        Fc = F.t().contiguous() if not F.t().is_contiguous() else F.t()
+    m = Fc.shape[0]
+    o = opts if opts is not None else options()
+    if X is None:
+        Xc = torch.zeros_like(Fc)
+    else:
+        Xc = X.reshape(1, -1) if X.dim() == 1 else X.t()
+        if not Xc.is_contiguous():
+            raise ValueError("X must be column-major (a transposed contiguous (m, n) tensor)")
+    iters = torch.zeros(m, dtype=torch.int32, device="cuda")
+    status = torch.zeros(m, dtype=torch.int32, device="cuda")
+    relres = torch.zeros(m, dtype=torch.float64, device="cuda")
+    hist = torch.full((m, o.maxit + 1), float("nan"), dtype=torch.float64, device="cuda") \
+        if want_hist else None
+    _check(lib().airga_pcg_solve(A.h, P.h if P is not None else None, _ptr(Fc, torch.float64), m,
+                                 C.byref(o), _ptr(Xc, torch.float64), _ptr(hist), _ptr(iters),
+                                 _ptr(status), _ptr(relres), _stream(stream)), "pcg_solve")
+    out = dict(X=Xc.reshape(-1) if F.dim() == 1 else Xc.t(), iters=iters, status=status,
+               true_relres=relres)
+    if want_hist:
+        out["res_hist"] = hist
+    return out
+
+
+def true_residual(A: Mat, X: torch.Tensor, F: torch.Tensor, stream=None) -> torch.Tensor:
+    Xc = X.reshape(1, -1) if X.dim() == 1 else X.t()
+    Fc = F.reshape(1, -1) if F.dim() == 1 else F.t()
+    m = Fc.shape[0]
+    out = torch.empty(m, dtype=torch.float64, device="cuda")
+    _check(lib().airga_true_residual(A.h, _ptr(Xc, torch.float64), _ptr(Fc, torch.float64), m,
+                                     _ptr(out), _stream(stream)), "true_residual")
+    return out
+
+
+FAULT_NONE, FAULT_SKIP_ARRIVAL = 0, 1
+
+
+def debug_set_fault(fault: int):
+    _check(lib().airga_debug_set_fault(int(fault)), "debug_set_fault")
+
+
+def trim():
+    _check(lib().airga_trim(), "trim")
+
+
+# ---------------------------------------------------------------------------
+# convenience: beam inputs to device handles
+# ---------------------------------------------------------------------------
+
+def beam_mats(beam, stream=None):
+    """(M, K) device handles from a workloads.BeamCSR (CSR uploaded, then
+    converted to band storage by the library)."""
+    rp = torch.from_numpy(beam.rowptr).cuda()
+    ci = torch.from_numpy(beam.col).cuda()
+    mv = torch.from_numpy(beam.m_val).cuda()
+    kv = torch.from_numpy(beam.k_val).cuda()
+    M = mat_from_csr(beam.n, rp, ci, mv, stream)
+    K = mat_from_csr(beam.n, rp, ci, kv, stream)
+    return M, K

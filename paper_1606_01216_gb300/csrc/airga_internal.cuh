@@ -1,0 +1,153 @@
+// Internal declarations of libairga (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "../../include/airga.h"
+
+namespace airga {
+
+constexpr int kBand = 7;   // diagonals -3..+3
+constexpr int kHalf = 3;
+
+// ---------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define AIRGA_CUDA(call)                                   \
+    do {                                                   \
+        cudaError_t e_ = (call);                           \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// device memory: one stream-ordered pool per device, owned by the library
+// ---------------------------------------------------------------------------
+int dev_alloc(void **p, size_t bytes, cudaStream_t s);
+void dev_free(void *p, cudaStream_t s);
+
+// A band-7 array of 7*n doubles, freed on its creation stream.
+struct Band {
+    int64_t n = 0;
+    double *d = nullptr;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    ~Band();
+};
+using BandPtr = std::shared_ptr<Band>;
+int make_band(int64_t n, cudaStream_t s, BandPtr *out);
+
+}  // namespace airga
+
+struct airga_mat_s {
+    int64_t n = 0;
+    airga::BandPtr band;
+};
+
+struct airga_precond_s {
+    int64_t n = 0;
+    std::vector<airga::BandPtr> factors;  // factor 0 = built P, then Q_2, Q_3, ...
+    airga::BandPtr psym;                  // 1/2 (P + P^T) when factors.size() == 1
+    // per-column results of the SPAI call that made the newest factor
+    std::shared_ptr<void> col_steps;      // int32[n]
+    std::shared_ptr<void> col_res;        // double[n]
+    std::shared_ptr<void> rank_flag;      // int32[1]
+};
+
+namespace airga {
+
+// ---------------------------------------------------------------------------
+// kernel launchers (band_kernels.cu)
+// ---------------------------------------------------------------------------
+cudaError_t launch_csr_to_band(int64_t n, const int64_t *rowptr, const int32_t *col,
+                               const double *val, double *band, int32_t *flag, cudaStream_t s);
+cudaError_t launch_assemble(int64_t n, const double *M, const double *K, double alpha,
+                            double beta, double sh, double *A, cudaStream_t s);
+cudaError_t launch_spmv(int64_t n, const double *band, const double *X, double *Y, int32_t m,
+                        cudaStream_t s);
+cudaError_t launch_band_apply(int64_t n, const double *band, const double *x, double *y,
+                              bool transpose, cudaStream_t s);
+cudaError_t launch_symmetrize(int64_t n, const double *P, double *Psym, cudaStream_t s);
+cudaError_t launch_axpby(int64_t n, double a, const double *x, double b, double *y,
+                         cudaStream_t s);
+// relres[c] = ||F_c - A X_c|| / ||F_c||; `partial` holds 2 * nblk * m doubles
+cudaError_t launch_true_residual(int64_t n, const double *band, const double *X,
+                                 const double *F, int32_t m, double *relres, double *partial,
+                                 int nblk, cudaStream_t s);
+int true_residual_blocks(int64_t n);
+// Frobenius-type sums for the MR initial scaling: out[0] = sum a_ii (or
+// <A_old, A_new>_F), out[1] = ||A||_F^2 (or ||A_new||_F^2), then out[2] = alpha0
+cudaError_t launch_mr_alpha(int64_t n, const double *A, const double *A_old, double *partial,
+                            int nblk, double *out, cudaStream_t s);
+int mr_alpha_blocks(int64_t n);
+
+// ---------------------------------------------------------------------------
+// SPAI (spai_kernels.cu)
+// ---------------------------------------------------------------------------
+// QR mode: exact LS per column.  A_old == nullptr -> SPAI (b_j = e_j), else
+// update (b_j = A_old e_j).  Output band-7 factor F (entries outside the
+// pattern 0).  colres: ||b_j - A m_j|| per column.  rank_flag set on a
+// rank-deficient column block.
+cudaError_t launch_spai_qr(int64_t n, int hbw, const double *A, const double *A_old, double *F,
+                           double *colres, int32_t *rank_flag, cudaStream_t s);
+// MR mode (Algorithms 2 / 4); alpha0 read from device memory.
+cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_old,
+                           const double *alpha0, double tol, int kmax, double *F,
+                           int32_t *steps, double *colres, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// persistent PCG (pcg_kernel.cu)
+// ---------------------------------------------------------------------------
+constexpr int kMaxChain = 16;
+
+struct PcgPlan {
+    int grid = 0;          // CTAs (all co-resident)
+    int threads = 0;
+    int64_t rows = 0;      // rows per CTA (R)
+    int halo = 0;          // r window halo H
+    bool smem_state = false;
+    size_t smem_bytes = 0;
+    size_t scratch_doubles = 0;  // global workspace (doubles), excluding the control block
+};
+
+struct PcgArgs {
+    int64_t n;
+    const double *A;
+    int nf;                        // chain length (0 = identity preconditioner)
+    const double *fac[kMaxChain];  // factor bands, factor 0 first
+    const double *psym;            // precomputed symmetric factor (nf == 1 && symmetrize) or null
+    int symmetrize;
+    const double *b;
+    double *x;
+    double tol;
+    int maxit;
+    int warm;
+    double *hist;                  // (maxit+1) or null
+    int32_t *iters;
+    int32_t *status;
+    long long timeout_ns;
+    // workspace
+    double *pbuf;                  // n doubles (boundary rows of p)
+    double *rbuf;                  // 2 n doubles (boundary rows of r, double buffered)
+    double *state;                 // per-CTA window state when it is not in shared memory
+    double *partials;              // 2 slots x 4 values x grid
+    unsigned int *bar;             // barrier counter (zeroed before launch)
+    int *abort_flag;               // set by a CTA whose barrier wait timed out
+    int fault_skip_arrival;        // test injection: CTA 0 skips its first iteration barrier
+};
+
+// process-wide test fault consumed by the next pcg_solve (airga_debug_set_fault)
+int take_fault();
+
+int pcg_plan(int64_t n, int nf, bool psym_path, int device, PcgPlan *plan);
+cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
+
+}  // namespace airga

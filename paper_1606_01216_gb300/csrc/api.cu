@@ -1,0 +1,589 @@
+// Host side of the C ABI declared in include/airga.h: argument checks,
+// handle lifetime, the library's stream-ordered memory pool and kernel
+// launch sequencing.  No compute happens here.
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "airga_internal.cuh"
+
+namespace airga {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local std::string g_last_error;
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+
+int fail(int code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? AIRGA_E_OOM : AIRGA_E_CUDA;
+}
+
+// ---------------------------------------------------------------------------
+// one stream-ordered pool per device (memory is kept for reuse until trim)
+// ---------------------------------------------------------------------------
+static std::mutex g_pool_mu;
+static std::vector<cudaMemPool_t> g_pools;
+
+static int pool_for_current(cudaMemPool_t *out) {
+    int dev = 0;
+    AIRGA_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if ((int)g_pools.size() <= dev) g_pools.resize(dev + 1, nullptr);
+    if (!g_pools[dev]) {
+        cudaMemPoolProps props;
+        std::memset(&props, 0, sizeof(props));
+        props.allocType = cudaMemAllocationTypePinned;
+        props.handleTypes = cudaMemHandleTypeNone;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = dev;
+        cudaMemPool_t p;
+        AIRGA_CUDA(cudaMemPoolCreate(&p, &props));
+        uint64_t keep = ~0ull;
+        AIRGA_CUDA(cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep));
+        g_pools[dev] = p;
+    }
+    *out = g_pools[dev];
+    return AIRGA_OK;
+}
+
+int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
+    *p = nullptr;
+    cudaMemPool_t pool;
+    int st = pool_for_current(&pool);
+    if (st) return st;
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMallocFromPoolAsync(p, bytes, pool, s);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        return cuda_fail(e, "device allocation");
+    }
+    return AIRGA_OK;
+}
+
+void dev_free(void *p, cudaStream_t s) {
+    if (p) cudaFreeAsync(p, s);
+}
+
+Band::~Band() {
+    if (d) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != device) cudaSetDevice(device);
+        cudaFreeAsync(d, stream);
+        if (cur != device) cudaSetDevice(cur);
+    }
+}
+
+int make_band(int64_t n, cudaStream_t s, BandPtr *out) {
+    auto b = std::make_shared<Band>();
+    b->n = n;
+    b->stream = s;
+    cudaGetDevice(&b->device);
+    void *p = nullptr;
+    int st = dev_alloc(&p, sizeof(double) * (size_t)kBand * (size_t)n, s);
+    if (st) return st;
+    b->d = (double *)p;
+    *out = b;
+    return AIRGA_OK;
+}
+
+// shared_ptr<void> owning a pool allocation
+static int make_buf(size_t bytes, cudaStream_t s, std::shared_ptr<void> *out) {
+    void *p = nullptr;
+    int st = dev_alloc(&p, bytes, s);
+    if (st) return st;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    *out = std::shared_ptr<void>(p, [s, dev](void *q) {
+        int cur = 0;
+        cudaGetDevice(&cur);
+        if (cur != dev) cudaSetDevice(dev);
+        cudaFreeAsync(q, s);
+        if (cur != dev) cudaSetDevice(cur);
+    });
+    return AIRGA_OK;
+}
+
+static cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
+
+static std::atomic<int> g_fault{AIRGA_FAULT_NONE};
+
+int take_fault() { return g_fault.exchange(AIRGA_FAULT_NONE); }
+
+static int check_options(const airga_options *o) {
+    if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return fail(AIRGA_E_INVALID_ARG, "tol must be finite and >= 0");
+    if (o->maxit < 0) return fail(AIRGA_E_INVALID_ARG, "maxit must be >= 0");
+    if (o->spai_mode != AIRGA_SPAI_QR && o->spai_mode != AIRGA_SPAI_MR)
+        return fail(AIRGA_E_INVALID_ARG, "spai_mode must be AIRGA_SPAI_QR or AIRGA_SPAI_MR");
+    if (!(o->mr_tol >= 0.0)) return fail(AIRGA_E_INVALID_ARG, "mr_tol must be >= 0");
+    if (o->mr_kmax < 0) return fail(AIRGA_E_INVALID_ARG, "mr_kmax must be >= 0");
+    if (o->pattern_hbw < 0 || o->pattern_hbw > 3)
+        return fail(AIRGA_E_INVALID_ARG, "pattern_hbw must be in 0..3");
+    if (o->barrier_timeout_ms <= 0) return fail(AIRGA_E_INVALID_ARG, "barrier_timeout_ms must be > 0");
+    return AIRGA_OK;
+}
+
+static int check_mat(airga_mat A, const char *name) {
+    if (!A || !A->band || A->n < 1) return fail(AIRGA_E_INVALID_ARG, std::string(name) + " is not a valid matrix");
+    return AIRGA_OK;
+}
+
+// Build one SPAI / SPAI-update factor of A (b_j = e_j, or A_old e_j) into a
+// new band; per-column results into `out`'s status buffers.
+static int spai_factor(airga_mat A, airga_mat A_old, const airga_options &o, cudaStream_t s,
+                       airga_precond_s *out, BandPtr *F) {
+    const int64_t n = A->n;
+    int st = make_band(n, s, F);
+    if (st) return st;
+    st = make_buf(sizeof(int32_t) * (size_t)n, s, &out->col_steps);
+    if (st) return st;
+    st = make_buf(sizeof(double) * (size_t)n, s, &out->col_res);
+    if (st) return st;
+    st = make_buf(sizeof(int32_t), s, &out->rank_flag);
+    if (st) return st;
+    AIRGA_CUDA(cudaMemsetAsync(out->rank_flag.get(), 0, sizeof(int32_t), s));
+    const double *Aold = A_old ? A_old->band->d : nullptr;
+    if (o.spai_mode == AIRGA_SPAI_QR) {
+        AIRGA_CUDA(cudaMemsetAsync(out->col_steps.get(), 0, sizeof(int32_t) * (size_t)n, s));
+        AIRGA_CUDA(launch_spai_qr(n, o.pattern_hbw, A->band->d, Aold, (*F)->d,
+                                  (double *)out->col_res.get(), (int32_t *)out->rank_flag.get(), s));
+        return AIRGA_OK;
+    }
+    const int nblk = mr_alpha_blocks(n);
+    void *tmp = nullptr;
+    st = dev_alloc(&tmp, sizeof(double) * (size_t)(2 * nblk + 4), s);
+    if (st) return st;
+    double *partial = (double *)tmp, *alpha = partial + 2 * nblk;
+    cudaError_t e = launch_mr_alpha(n, A->band->d, Aold, partial, nblk, alpha, s);
+    if (e == cudaSuccess)
+        e = launch_spai_mr(n, o.pattern_hbw, A->band->d, Aold, alpha + 2, o.mr_tol, o.mr_kmax,
+                           (*F)->d, (int32_t *)out->col_steps.get(), (double *)out->col_res.get(), s);
+    dev_free(tmp, s);
+    if (e != cudaSuccess) return cuda_fail(e, "spai MR launch");
+    return AIRGA_OK;
+}
+
+}  // namespace airga
+
+using namespace airga;
+
+extern "C" {
+
+void airga_options_default(airga_options *o) {
+    if (!o) return;
+    o->tol = 1e-10;
+    o->maxit = 20000;
+    o->spai_mode = AIRGA_SPAI_QR;
+    o->mr_tol = 0.01;
+    o->mr_kmax = 50;
+    o->symmetrize = 1;
+    o->pattern_hbw = 3;
+    o->warm_start = 0;
+    o->barrier_timeout_ms = 2000;
+}
+
+const char *airga_status_string(int s) {
+    switch (s) {
+        case AIRGA_OK: return "ok";
+        case AIRGA_E_INVALID_ARG: return "invalid argument";
+        case AIRGA_E_SHAPE: return "shape mismatch";
+        case AIRGA_E_BREAKDOWN: return "CG breakdown (not SPD, or (r,z) zero / not finite)";
+        case AIRGA_E_MAXIT: return "iteration cap reached";
+        case AIRGA_E_TIMEOUT: return "grid barrier timed out";
+        case AIRGA_E_RANK: return "rank-deficient least-squares block";
+        case AIRGA_E_CUDA: return "CUDA error";
+        case AIRGA_E_OOM: return "out of device memory";
+        case AIRGA_E_NOT_BANDED: return "matrix has entries outside the band |i-j| <= 3";
+        default: return "unknown status";
+    }
+}
+
+const char *airga_last_error(void) { return g_last_error.c_str(); }
+
+int airga_version(void) { return 100; }
+
+// ---------------------------------------------------------------------------
+// matrices
+// ---------------------------------------------------------------------------
+int airga_mat_from_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
+                       const double *val, void *stream, airga_mat *out) {
+    if (!out) return fail(AIRGA_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > (int64_t)INT32_MAX) return fail(AIRGA_E_INVALID_ARG, "n must be in [1, 2^31)");
+    if (nnz < 0 || !rowptr || (nnz > 0 && (!col || !val)))
+        return fail(AIRGA_E_INVALID_ARG, "bad CSR arrays");
+    cudaStream_t s = S(stream);
+    BandPtr b;
+    int st = make_band(n, s, &b);
+    if (st) return st;
+    void *flag = nullptr;
+    st = dev_alloc(&flag, sizeof(int32_t), s);
+    if (st) return st;
+    int32_t hflag = 0;
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = launch_csr_to_band(n, rowptr, col, val, b->d, (int32_t *)flag, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    dev_free(flag, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "mat_from_csr");
+    if (hflag & 2) return fail(AIRGA_E_INVALID_ARG, "CSR column index out of range or rowptr decreasing");
+    if (hflag & 1) return fail(AIRGA_E_NOT_BANDED, "CSR entry with |col - row| > 3");
+    auto *m = new airga_mat_s;
+    m->n = n;
+    m->band = b;
+    *out = m;
+    return AIRGA_OK;
+}
+
+int airga_mat_from_band(int64_t n, const double *band, void *stream, airga_mat *out) {
+    if (!out) return fail(AIRGA_E_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 1 || n > (int64_t)INT32_MAX || !band) return fail(AIRGA_E_INVALID_ARG, "bad band input");
+    cudaStream_t s = S(stream);
+    BandPtr b;
+    int st = make_band(n, s, &b);
+    if (st) return st;
+    AIRGA_CUDA(cudaMemcpyAsync(b->d, band, sizeof(double) * kBand * (size_t)n,
+                               cudaMemcpyDeviceToDevice, s));
+    auto *m = new airga_mat_s;
+    m->n = n;
+    m->band = b;
+    *out = m;
+    return AIRGA_OK;
+}
+
+int airga_mat_to_band(airga_mat A, double *band, void *stream) {
+    int st = check_mat(A, "A");
+    if (st) return st;
+    if (!band) return fail(AIRGA_E_INVALID_ARG, "band is NULL");
+    AIRGA_CUDA(cudaMemcpyAsync(band, A->band->d, sizeof(double) * kBand * (size_t)A->n,
+                               cudaMemcpyDeviceToDevice, S(stream)));
+    return AIRGA_OK;
+}
+
+int64_t airga_mat_rows(airga_mat A) { return A ? A->n : 0; }
+
+void airga_mat_free(airga_mat A) { delete A; }
+
+// ---------------------------------------------------------------------------
+// the path
+// ---------------------------------------------------------------------------
+int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, double s,
+                           void *stream, airga_mat *A_out) {
+    if (!A_out) return fail(AIRGA_E_INVALID_ARG, "A_out is NULL");
+    *A_out = nullptr;
+    int st = check_mat(M, "M");
+    if (!st) st = check_mat(K, "K");
+    if (st) return st;
+    if (M->n != K->n) return fail(AIRGA_E_SHAPE, "M and K differ in size");
+    if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(s))
+        return fail(AIRGA_E_INVALID_ARG, "alpha, beta and s must be finite");
+    cudaStream_t cs = S(stream);
+    BandPtr b;
+    st = make_band(M->n, cs, &b);
+    if (st) return st;
+    AIRGA_CUDA(launch_assemble(M->n, M->band->d, K->band->d, alpha, beta, s, b->d, cs));
+    auto *m = new airga_mat_s;
+    m->n = M->n;
+    m->band = b;
+    *A_out = m;
+    return AIRGA_OK;
+}
+
+int airga_spmv(airga_mat A, const double *X, double *Y, int32_t m, void *stream) {
+    int st = check_mat(A, "A");
+    if (st) return st;
+    if (m < 0 || (m > 0 && (!X || !Y))) return fail(AIRGA_E_INVALID_ARG, "bad spmv operands");
+    if (m == 0) return AIRGA_OK;
+    AIRGA_CUDA(launch_spmv(A->n, A->band->d, X, Y, m, S(stream)));
+    return AIRGA_OK;
+}
+
+int airga_spai_build(airga_mat A, const airga_options *opt, void *stream, airga_precond *P_out) {
+    if (!P_out) return fail(AIRGA_E_INVALID_ARG, "P_out is NULL");
+    *P_out = nullptr;
+    int st = check_mat(A, "A");
+    if (st) return st;
+    airga_options o;
+    airga_options_default(&o);
+    if (opt) o = *opt;
+    st = check_options(&o);
+    if (st) return st;
+    cudaStream_t s = S(stream);
+    auto *P = new airga_precond_s;
+    P->n = A->n;
+    BandPtr F;
+    st = spai_factor(A, nullptr, o, s, P, &F);
+    if (!st) st = make_band(A->n, s, &P->psym);
+    if (!st) {
+        cudaError_t e = launch_symmetrize(A->n, F->d, P->psym->d, s);
+        if (e != cudaSuccess) st = cuda_fail(e, "symmetrize");
+    }
+    if (st) {
+        delete P;
+        return st;
+    }
+    P->factors.push_back(F);
+    *P_out = P;
+    return AIRGA_OK;
+}
+
+int airga_spai_update(airga_precond P_prev, airga_mat A_prev, airga_mat A_next,
+                      const airga_options *opt, void *stream, airga_precond *P_out) {
+    if (!P_out) return fail(AIRGA_E_INVALID_ARG, "P_out is NULL");
+    *P_out = nullptr;
+    if (!P_prev || P_prev->factors.empty()) return fail(AIRGA_E_INVALID_ARG, "P_prev is not a valid preconditioner");
+    int st = check_mat(A_prev, "A_prev");
+    if (!st) st = check_mat(A_next, "A_next");
+    if (st) return st;
+    if (A_prev->n != A_next->n || P_prev->n != A_next->n)
+        return fail(AIRGA_E_SHAPE, "P_prev, A_prev and A_next differ in size");
+    if ((int)P_prev->factors.size() + 1 > kMaxChain)
+        return fail(AIRGA_E_INVALID_ARG, "preconditioner chain longer than 16 factors");
+    airga_options o;
+    airga_options_default(&o);
+    if (opt) o = *opt;
+    st = check_options(&o);
+    if (st) return st;
+    cudaStream_t s = S(stream);
+    auto *P = new airga_precond_s;
+    P->n = A_next->n;
+    BandPtr Q;
+    st = spai_factor(A_next, A_prev, o, s, P, &Q);
+    if (st) {
+        delete P;
+        return st;
+    }
+    P->factors = P_prev->factors;
+    P->factors.push_back(Q);
+    *P_out = P;
+    return AIRGA_OK;
+}
+
+int airga_precond_apply(airga_precond P, const double *r, double *z, int32_t symmetrize,
+                        void *stream) {
+    if (!P || P->factors.empty() || !r || !z) return fail(AIRGA_E_INVALID_ARG, "bad apply operands");
+    cudaStream_t s = S(stream);
+    const int64_t n = P->n;
+    if (P->factors.size() == 1 && symmetrize && P->psym) {
+        AIRGA_CUDA(launch_band_apply(n, P->psym->d, r, z, false, s));
+        return AIRGA_OK;
+    }
+    void *tmp = nullptr;
+    int st = dev_alloc(&tmp, sizeof(double) * 3 * (size_t)n, s);
+    if (st) return st;
+    double *t1 = (double *)tmp, *t2 = t1 + n, *t3 = t2 + n;
+    cudaError_t e = cudaSuccess;
+    // C r
+    const double *src = r;
+    for (size_t f = 0; f < P->factors.size() && e == cudaSuccess; ++f) {
+        double *dst = (f & 1) ? t2 : t1;
+        e = launch_band_apply(n, P->factors[f]->d, src, dst, false, s);
+        src = dst;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(z, src, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    if (symmetrize && e == cudaSuccess) {
+        // C^T r = F_0^T ... F_last^T r
+        src = r;
+        size_t cnt = 0;
+        for (size_t q = P->factors.size(); q-- > 0 && e == cudaSuccess; ++cnt) {
+            double *dst = (cnt & 1) ? t3 : t1;
+            e = launch_band_apply(n, P->factors[q]->d, src, dst, true, s);
+            src = dst;
+        }
+        if (e == cudaSuccess) e = launch_axpby(n, 0.5, src, 0.5, z, s);
+    }
+    dev_free(tmp, s);
+    if (e != cudaSuccess) return cuda_fail(e, "precond apply");
+    return AIRGA_OK;
+}
+
+int32_t airga_precond_length(airga_precond P) { return P ? (int32_t)P->factors.size() : 0; }
+
+int64_t airga_precond_rows(airga_precond P) { return P ? P->n : 0; }
+
+int airga_precond_factor(airga_precond P, int32_t k, double *band, void *stream) {
+    if (!P || k < 0 || k >= (int32_t)P->factors.size() || !band)
+        return fail(AIRGA_E_INVALID_ARG, "bad factor request");
+    AIRGA_CUDA(cudaMemcpyAsync(band, P->factors[k]->d, sizeof(double) * kBand * (size_t)P->n,
+                               cudaMemcpyDeviceToDevice, S(stream)));
+    return AIRGA_OK;
+}
+
+int airga_precond_from_bands(int64_t n, int32_t nfactors, const double *const *bands,
+                             void *stream, airga_precond *P_out) {
+    if (!P_out) return fail(AIRGA_E_INVALID_ARG, "P_out is NULL");
+    *P_out = nullptr;
+    if (n < 1 || nfactors < 1 || nfactors > kMaxChain || !bands)
+        return fail(AIRGA_E_INVALID_ARG, "bad factor list");
+    cudaStream_t s = S(stream);
+    auto *P = new airga_precond_s;
+    P->n = n;
+    int st = AIRGA_OK;
+    for (int32_t k = 0; k < nfactors && !st; ++k) {
+        if (!bands[k]) { st = fail(AIRGA_E_INVALID_ARG, "NULL band"); break; }
+        BandPtr b;
+        st = make_band(n, s, &b);
+        if (st) break;
+        cudaError_t e = cudaMemcpyAsync(b->d, bands[k], sizeof(double) * kBand * (size_t)n,
+                                        cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) { st = cuda_fail(e, "copy factor"); break; }
+        P->factors.push_back(b);
+    }
+    if (!st && nfactors == 1) {
+        st = make_band(n, s, &P->psym);
+        if (!st) {
+            cudaError_t e = launch_symmetrize(n, P->factors[0]->d, P->psym->d, s);
+            if (e != cudaSuccess) st = cuda_fail(e, "symmetrize");
+        }
+    }
+    if (st) {
+        delete P;
+        return st;
+    }
+    *P_out = P;
+    return AIRGA_OK;
+}
+
+int airga_precond_status(airga_precond P, int32_t *steps, double *colres, int *status_out,
+                         void *stream) {
+    if (!P) return fail(AIRGA_E_INVALID_ARG, "P is NULL");
+    cudaStream_t s = S(stream);
+    const size_t n = (size_t)P->n;
+    if (steps) {
+        if (!P->col_steps) return fail(AIRGA_E_INVALID_ARG, "no per-column data (imported handle)");
+        AIRGA_CUDA(cudaMemcpyAsync(steps, P->col_steps.get(), sizeof(int32_t) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    if (colres) {
+        if (!P->col_res) return fail(AIRGA_E_INVALID_ARG, "no per-column data (imported handle)");
+        AIRGA_CUDA(cudaMemcpyAsync(colres, P->col_res.get(), sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    }
+    if (status_out) {
+        int32_t f = 0;
+        if (P->rank_flag) {
+            AIRGA_CUDA(cudaMemcpyAsync(&f, P->rank_flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+            AIRGA_CUDA(cudaStreamSynchronize(s));
+        }
+        *status_out = f ? AIRGA_E_RANK : AIRGA_OK;
+    }
+    return AIRGA_OK;
+}
+
+void airga_precond_free(airga_precond P) { delete P; }
+
+int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
+                    const airga_options *opt, double *X, double *res_hist, int32_t *iters,
+                    int32_t *status, double *true_relres, void *stream) {
+    int st = check_mat(A, "A");
+    if (st) return st;
+    if (m < 0) return fail(AIRGA_E_INVALID_ARG, "m must be >= 0");
+    if (m == 0) return AIRGA_OK;
+    if (!F || !X || !iters || !status || !true_relres)
+        return fail(AIRGA_E_INVALID_ARG, "F, X, iters, status and true_relres are required");
+    if (P && (P->n != A->n || P->factors.empty())) return fail(AIRGA_E_SHAPE, "P does not match A");
+    airga_options o;
+    airga_options_default(&o);
+    if (opt) o = *opt;
+    st = check_options(&o);
+    if (st) return st;
+    const int nf = P ? (int)P->factors.size() : 0;
+    if (nf > kMaxChain) return fail(AIRGA_E_INVALID_ARG, "chain too long");
+    int dev = 0;
+    AIRGA_CUDA(cudaGetDevice(&dev));
+    const int64_t n = A->n;
+    PcgPlan plan;
+    st = pcg_plan(n, nf, nf == 1 && o.symmetrize, dev, &plan);
+    if (st) return st;
+    cudaStream_t s = S(stream);
+
+    const int nblk = true_residual_blocks(n);
+    const size_t n_pbuf = (size_t)n;
+    const size_t n_part = (size_t)2 * 4 * plan.grid;
+    const size_t n_res = (size_t)2 * nblk * m;
+    const size_t doubles = n_pbuf + plan.scratch_doubles + n_part + n_res;
+    const size_t bytes = doubles * sizeof(double) + 256;
+    void *ws = nullptr;
+    st = dev_alloc(&ws, bytes, s);
+    if (st) return st;
+    double *base = (double *)ws;
+    PcgArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.n = n;
+    a.A = A->band->d;
+    a.nf = nf;
+    for (int f = 0; f < nf; ++f) a.fac[f] = P->factors[f]->d;
+    a.psym = (nf == 1 && o.symmetrize && P->psym) ? P->psym->d : nullptr;
+    a.symmetrize = o.symmetrize ? 1 : 0;
+    a.tol = o.tol;
+    a.maxit = o.maxit;
+    a.warm = o.warm_start ? 1 : 0;
+    a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
+    a.fault_skip_arrival = take_fault() == AIRGA_FAULT_SKIP_ARRIVAL ? 1 : 0;
+    a.pbuf = base;
+    a.state = base + n_pbuf;
+    a.partials = a.state + plan.scratch_doubles;
+    double *res_part = a.partials + n_part;
+    unsigned *ctl = (unsigned *)(res_part + n_res);
+    a.bar = ctl;
+    a.abort_flag = (int *)(ctl + 1);
+    cudaError_t e = cudaSuccess;
+    for (int32_t c = 0; c < m && e == cudaSuccess; ++c) {
+        a.b = F + (size_t)c * n;
+        a.x = X + (size_t)c * n;
+        a.hist = res_hist ? res_hist + (size_t)c * (o.maxit + 1) : nullptr;
+        a.iters = iters + c;
+        a.status = status + c;
+        e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
+        if (e == cudaSuccess) e = launch_pcg(plan, a, s);
+    }
+    if (e == cudaSuccess)
+        e = launch_true_residual(n, A->band->d, X, F, m, true_relres, res_part, nblk, s);
+    dev_free(ws, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pcg launch");
+    return AIRGA_OK;
+}
+
+int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m,
+                        double *relres, void *stream) {
+    int st = check_mat(A, "A");
+    if (st) return st;
+    if (m < 0 || (m > 0 && (!X || !F || !relres))) return fail(AIRGA_E_INVALID_ARG, "bad residual operands");
+    if (m == 0) return AIRGA_OK;
+    cudaStream_t s = S(stream);
+    const int nblk = true_residual_blocks(A->n);
+    void *tmp = nullptr;
+    st = dev_alloc(&tmp, sizeof(double) * 2 * (size_t)nblk * m, s);
+    if (st) return st;
+    cudaError_t e = launch_true_residual(A->n, A->band->d, X, F, m, relres, (double *)tmp, nblk, s);
+    dev_free(tmp, s);
+    if (e != cudaSuccess) return cuda_fail(e, "true residual");
+    return AIRGA_OK;
+}
+
+int airga_debug_set_fault(int fault) {
+    if (fault != AIRGA_FAULT_NONE && fault != AIRGA_FAULT_SKIP_ARRIVAL)
+        return fail(AIRGA_E_INVALID_ARG, "unknown fault");
+    g_fault.store(fault);
+    return AIRGA_OK;
+}
+
+int airga_trim(void) {
+    cudaMemPool_t pool;
+    int st = pool_for_current(&pool);
+    if (st) return st;
+    AIRGA_CUDA(cudaMemPoolTrimTo(pool, 0));
+    return AIRGA_OK;
+}
+
+}  // extern "C"

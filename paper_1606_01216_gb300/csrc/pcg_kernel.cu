@@ -1,0 +1,468 @@
+// Persistent preconditioned CG (one launch per right-hand side column).
+//
+// The CG recurrence is the standard Hestenes-Stiefel PCG of the paper's CG
+// solves (Alg. 3 line 5, Alg. 5 lines 7/11): q = A p; a = (r,z)/(p,q);
+// x += a p; r -= a q; z = M r; b = (r,z)_new/(r,z)_old; p = z + b p.
+//
+// GB300 layout of one iteration
+// -----------------------------
+// * One cooperative launch of G co-resident CTAs; CTA c owns the rows
+//   [lo, hi) = [c R, (c+1) R) for the whole solve.  Two grid barriers per
+//   iteration (after (p,q) and after (r,z),(r,r)), each also the only
+//   exchange point between CTAs.
+// * The vector state of the CTA's rows lives in shared memory when it fits
+//   (x: own rows, r: own +- H, p: own +- (H+3), z/q: own +- 3), so per
+//   iteration the only DRAM/L2 traffic is the two band-7 matrices A and
+//   P_sym (112 B per row) plus a few boundary rows.  When it does not fit,
+//   the same windows live in a per-CTA slice of a global workspace.
+// * Halo rows are recomputed redundantly instead of exchanged: r on the
+//   halo follows r_k = r_{k-1} - a (A p_k) with the same stencil code, and z
+//   on own +- 3 from r on own +- H; only p's outer halo is read from the
+//   owners (boundary rows written to `pbuf` before barrier 1).  Every CTA
+//   therefore holds bit-identical copies of the shared rows.
+// * Reductions: warp shuffles -> one partial per CTA -> after the barrier
+//   every CTA sums all G partials in the same fixed order, so all CTAs take
+//   identical convergence decisions and results are run-to-run deterministic.
+// * The barrier is a monotone arrival counter with a bounded wait (global
+//   timer); a CTA that gives up sets an abort flag that ends the others'
+//   waits, and the column's status becomes AIRGA_E_TIMEOUT.
+#include "airga_internal.cuh"
+
+namespace airga {
+namespace {
+
+constexpr int kPcgThreads = 512;
+constexpr int kMinRowsPerCta = 128;
+
+enum Mode { kIdentity = 0, kBand1 = 1, kChain = 2 };
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded grid barrier.  Returns false (in every thread) if this CTA gave up.
+// `arrive` is false only under the test fault injection (a CTA that never
+// arrives, so every wait runs into its bound).
+__device__ bool grid_barrier(unsigned *bar, int *abort_flag, unsigned target,
+                             long long timeout_ns, int *s_flag, bool arrive = true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (arrive) atomicAdd(bar, 1u);
+        int ok = 1;
+        unsigned long long t0 = global_ns();
+        unsigned spins = 0;
+        while (ld_acquire(bar) < target) {
+            if ((++spins & 63u) == 0) {
+                if (*(volatile int *)abort_flag) { ok = 0; break; }
+                if ((long long)(global_ns() - t0) > timeout_ns) {
+                    atomicExch(abort_flag, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-sum NV values; thread 0 writes them to partials[slot][v][cta].
+template <int NV>
+__device__ void block_partials(double (&v)[NV], double *red, double *partials, int slot,
+                               int grid) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[q * 32 + w] = v[q];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = l < nw ? red[q * 32 + l] : 0.0;
+            t = warp_sum(t);
+            if (l == 0) partials[(slot * 4 + q) * grid + blockIdx.x] = t;
+        }
+    }
+}
+
+// After a barrier: every CTA sums the G partials of `slot` in the same order.
+template <int NV>
+__device__ void grid_totals(const double *partials, int slot, int grid, double *red,
+                            double (&out)[NV]) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = 0.0;
+            for (int g = l; g < grid; g += 32) t += __ldcg(partials + (slot * 4 + q) * grid + g);
+            t = warp_sum(t);
+            if (l == 0) red[128 + q] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = red[128 + q];
+    __syncthreads();
+}
+
+// One row of (band) x from a window buffer holding rows [wbase, ...).
+__device__ __forceinline__ double stencil(const double *__restrict__ band, int64_t n, int64_t i,
+                                          const double *win, int64_t wbase) {
+    double acc = 0.0;
+#pragma unroll
+    for (int d = 0; d < kBand; ++d) {
+        const int64_t c = i + d - kHalf;
+        if (c >= 0 && c < n) acc = fma(__ldg(band + (int64_t)d * n + i), win[c - wbase], acc);
+    }
+    return acc;
+}
+
+// One row of (band)^T x: sum_d F(i+d, i) x_{i+d}, F(i+d, i) = band[(3-d) n + i + d].
+__device__ __forceinline__ double stencil_t(const double *__restrict__ band, int64_t n,
+                                            int64_t i, const double *win, int64_t wbase) {
+    double acc = 0.0;
+#pragma unroll
+    for (int d = -kHalf; d <= kHalf; ++d) {
+        const int64_t c = i + d;
+        if (c >= 0 && c < n)
+            acc = fma(__ldg(band + (int64_t)(kHalf - d) * n + c), win[c - wbase], acc);
+    }
+    return acc;
+}
+
+// z = M r on rows [lo-3, hi+3) (clipped to the matrix), written to zq.
+template <int MODE>
+__device__ void apply_precond(const PcgArgs &a, int64_t lo, int64_t hi, int H, double *rs,
+                              double *zq, double *t1, double *t2) {
+    const int64_t n = a.n;
+    const int64_t zlo = lo - 3 > 0 ? lo - 3 : 0, zhi = hi + 3 < n ? hi + 3 : n;
+    const int64_t rbase = lo - H, zbase = lo - 3;
+    if (MODE == kIdentity) {
+        for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x) zq[i - zbase] = rs[i - rbase];
+        return;
+    }
+    if (MODE == kBand1) {
+        const double *Pb = a.psym ? a.psym : a.fac[0];
+        for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x)
+            zq[i - zbase] = stencil(Pb, n, i, rs, rbase);
+        return;
+    }
+    // chain: C r with C = F_{nf-1} ... F_0, windows shrink by 3 per factor
+    const double *src = rs;
+    for (int f = 0; f < a.nf; ++f) {
+        const int h = H - 3 * (f + 1);
+        const int64_t wlo = lo - h > 0 ? lo - h : 0, whi = hi + h < n ? hi + h : n;
+        double *dst = (f & 1) ? t2 : t1;
+        for (int64_t i = wlo + threadIdx.x; i < whi; i += blockDim.x)
+            dst[i - rbase] = stencil(a.fac[f], n, i, src, rbase);
+        __syncthreads();
+        src = dst;
+    }
+    if (!a.symmetrize) {
+        for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x) zq[i - zbase] = src[i - rbase];
+        __syncthreads();
+        return;
+    }
+    for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x) zq[i - zbase] = src[i - rbase];
+    __syncthreads();
+    // C^T r = F_0^T ... F_{nf-1}^T r
+    src = rs;
+    for (int s = 0; s < a.nf; ++s) {
+        const int f = a.nf - 1 - s;
+        const int h = H - 3 * (s + 1);
+        const int64_t wlo = lo - h > 0 ? lo - h : 0, whi = hi + h < n ? hi + h : n;
+        double *dst = (s & 1) ? t2 : t1;
+        for (int64_t i = wlo + threadIdx.x; i < whi; i += blockDim.x)
+            dst[i - rbase] = stencil_t(a.fac[f], n, i, src, rbase);
+        __syncthreads();
+        src = dst;
+    }
+    for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x)
+        zq[i - zbase] = 0.5 * (zq[i - zbase] + src[i - rbase]);
+}
+
+template <bool SMEM, int MODE>
+__global__ void __launch_bounds__(kPcgThreads, 1)
+pcg_kernel(PcgArgs a, int64_t R, int H) {
+    extern __shared__ double smem[];
+    __shared__ double red[160];
+    __shared__ int s_flag;
+
+    const int G = gridDim.x;
+    const int64_t n = a.n;
+    const int64_t lo = (int64_t)blockIdx.x * R < n ? (int64_t)blockIdx.x * R : n;
+    const int64_t hi = lo + R < n ? lo + R : n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+
+    // window buffers (global row i of a window with base B sits at buf[i - B])
+    const int64_t lenX = R, lenR = R + 2 * H, lenP = R + 2 * H + 6, lenZ = R + 6;
+    double *base = SMEM ? smem : a.state + (size_t)blockIdx.x * (lenX + lenR + lenP + lenZ + 2 * lenR);
+    double *xs = base;
+    double *rs = xs + lenX;
+    double *ps = rs + lenR;
+    double *zq = ps + lenP;
+    double *t1 = SMEM ? nullptr : zq + lenZ;
+    double *t2 = SMEM ? nullptr : t1 + lenR;
+    const int64_t xbase = lo, rbase = lo - H, pbase = lo - H - 3, zbase = lo - 3;
+    const int64_t rlo = lo - H > 0 ? lo - H : 0, rhi = hi + H < n ? hi + H : n;
+    const int64_t plo3 = lo - 3 > 0 ? lo - 3 : 0, phi3 = hi + 3 < n ? hi + 3 : n;
+    const int64_t bw = (H + 3) < (hi - lo) ? (H + 3) : (hi - lo);   // boundary rows written
+
+    unsigned bar_no = 0;
+    const long long tmo = a.timeout_ns;
+    int status = AIRGA_E_MAXIT;
+    int iters = 0;
+
+    // ---- initial residual r_0 = b - A x_0 on own +- H, x_0 on own rows ----
+    for (int64_t i = lo + tid; i < hi; i += nt) xs[i - xbase] = a.warm ? a.x[i] : 0.0;
+    for (int64_t i = rlo + tid; i < rhi; i += nt) {
+        double v = a.b[i];
+        if (a.warm) {
+            double ax = 0.0;
+#pragma unroll
+            for (int d = 0; d < kBand; ++d) {
+                const int64_t c = i + d - kHalf;
+                if (c >= 0 && c < n) ax = fma(__ldg(a.A + (int64_t)d * n + i), a.x[c], ax);
+            }
+            v -= ax;
+        }
+        rs[i - rbase] = v;
+    }
+    __syncthreads();
+    apply_precond<MODE>(a, lo, hi, H, rs, zq, t1, t2);
+    __syncthreads();
+    {
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int64_t i = lo + tid; i < hi; i += nt) {
+            const double r = rs[i - rbase], bi = a.b[i];
+            v[0] = fma(r, zq[i - zbase], v[0]);
+            v[1] = fma(r, r, v[1]);
+            v[2] = fma(bi, bi, v[2]);
+        }
+        block_partials<3>(v, red, a.partials, bar_no & 1, G);
+    }
+    if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+        status = AIRGA_E_TIMEOUT;
+        goto finish;
+    }
+    double tot0[3];
+    grid_totals<3>(a.partials, bar_no & 1, G, red, tot0);
+    ++bar_no;
+    {
+        double rz = tot0[0];
+        const double nb = sqrt(tot0[2]);
+        double rn = sqrt(tot0[1]);
+        if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[0] = nb > 0.0 ? rn / nb : 0.0;
+        if (nb == 0.0) {
+            for (int64_t i = lo + tid; i < hi; i += nt) xs[i - xbase] = 0.0;
+            status = AIRGA_OK;
+            goto finish;
+        }
+        if (rn <= a.tol * nb) { status = AIRGA_OK; goto finish; }
+        if (!isfinite(rz) || rz == 0.0) { status = AIRGA_E_BREAKDOWN; goto finish; }
+
+        double beta = 0.0;
+        for (int k = 1; k <= a.maxit; ++k) {
+            // ---- phase 1: p = z + beta p on own +- 3; boundary rows out; q = A p ----
+            if (k == 1) {
+                for (int64_t i = plo3 + tid; i < phi3; i += nt) ps[i - pbase] = zq[i - zbase];
+            } else {
+                for (int64_t i = plo3 + tid; i < phi3; i += nt)
+                    ps[i - pbase] = fma(beta, ps[i - pbase], zq[i - zbase]);
+            }
+            __syncthreads();
+            for (int64_t t = tid; t < 2 * bw; t += nt) {
+                const int64_t i = t < bw ? lo + t : hi - bw + (t - bw);
+                a.pbuf[i] = ps[i - pbase];
+            }
+            double vq[1] = {0.0};
+            for (int64_t i = lo + tid; i < hi; i += nt) {
+                const double q = stencil(a.A, n, i, ps, pbase);
+                zq[i - zbase] = q;
+                vq[0] = fma(ps[i - pbase], q, vq[0]);
+            }
+            block_partials<1>(vq, red, a.partials, bar_no & 1, G);
+            const bool arrive = !(a.fault_skip_arrival && k == 1 && blockIdx.x == 0);
+            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
+                              arrive)) {
+                status = AIRGA_E_TIMEOUT;
+                iters = k - 1;
+                goto finish;
+            }
+            double pqt[1];
+            grid_totals<1>(a.partials, bar_no & 1, G, red, pqt);
+            ++bar_no;
+            const double pq = pqt[0];
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                status = AIRGA_E_BREAKDOWN;
+                iters = k - 1;
+                goto finish;
+            }
+            const double alpha = rz / pq;
+
+            // ---- phase 2: outer p halo in; x, r updates; z = M r ----
+            for (int64_t t = tid; t < 2 * (int64_t)H; t += nt) {
+                const int64_t i = t < H ? lo - H - 3 + t : hi + 3 + (t - H);
+                if (i < 0 || i >= n) continue;
+                ps[i - pbase] = __ldcg(a.pbuf + i);
+            }
+            for (int64_t i = lo + tid; i < hi; i += nt) {
+                xs[i - xbase] = fma(alpha, ps[i - pbase], xs[i - xbase]);
+                rs[i - rbase] = fma(-alpha, zq[i - zbase], rs[i - rbase]);
+            }
+            __syncthreads();
+            for (int64_t t = tid; t < 2 * (int64_t)H; t += nt) {
+                const int64_t i = t < H ? lo - H + t : hi + (t - H);
+                if (i < 0 || i >= n) continue;
+                rs[i - rbase] = fma(-alpha, stencil(a.A, n, i, ps, pbase), rs[i - rbase]);
+            }
+            __syncthreads();
+            apply_precond<MODE>(a, lo, hi, H, rs, zq, t1, t2);
+            __syncthreads();
+            double v2[2] = {0.0, 0.0};
+            for (int64_t i = lo + tid; i < hi; i += nt) {
+                const double r = rs[i - rbase];
+                v2[0] = fma(r, zq[i - zbase], v2[0]);
+                v2[1] = fma(r, r, v2[1]);
+            }
+            block_partials<2>(v2, red, a.partials, bar_no & 1, G);
+            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+                status = AIRGA_E_TIMEOUT;
+                iters = k;
+                goto finish;
+            }
+            double t2v[2];
+            grid_totals<2>(a.partials, bar_no & 1, G, red, t2v);
+            ++bar_no;
+            iters = k;
+            rn = sqrt(t2v[1]);
+            if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[k] = rn / nb;
+            if (rn <= a.tol * nb) { status = AIRGA_OK; break; }
+            const double rz_new = t2v[0];
+            if (!isfinite(rz_new) || rz_new == 0.0) { status = AIRGA_E_BREAKDOWN; break; }
+            beta = rz_new / rz;
+            rz = rz_new;
+        }
+    }
+finish:
+    __syncthreads();
+    for (int64_t i = lo + tid; i < hi; i += nt) a.x[i] = xs[i - xbase];
+    if (blockIdx.x == 0 && tid == 0) {
+        *a.iters = iters;
+        *a.status = status;
+    }
+}
+
+template <bool SMEM, int MODE>
+cudaError_t launch_mode(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
+    auto kern = pcg_kernel<SMEM, MODE>;
+    if (SMEM) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)plan.smem_bytes);
+        if (e != cudaSuccess) return e;
+    }
+    PcgArgs a = args;
+    int64_t R = plan.rows;
+    int H = plan.halo;
+    void *kargs[] = {(void *)&a, (void *)&R, (void *)&H};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(plan.grid), dim3(plan.threads),
+                                       kargs, SMEM ? plan.smem_bytes : 0, s);
+}
+
+int mode_of(int nf, bool psym_path) {
+    if (nf == 0) return kIdentity;
+    if (nf == 1) return kBand1;
+    (void)psym_path;
+    return kChain;
+}
+
+}  // namespace
+
+int pcg_plan(int64_t n, int nf, bool psym_path, int device, PcgPlan *plan) {
+    const int mode = mode_of(nf, psym_path);
+    int sms = 0, optin = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    const int H = mode == kIdentity ? 3 : (mode == kBand1 ? 6 : 3 + 3 * nf);
+    const size_t static_smem = 160 * sizeof(double) + 64;
+    // grid: one CTA per SM at most (the state fills shared memory), fewer for
+    // small n so that every CTA keeps at least kMinRowsPerCta rows
+    int64_t want = (n + kMinRowsPerCta - 1) / kMinRowsPerCta;
+    int grid = (int)(want < sms ? want : sms);
+    if (grid < 1) grid = 1;
+    int64_t R = (n + grid - 1) / grid;
+    const size_t per_cta = (size_t)(R + (R + 2 * H) + (R + 2 * H + 6) + (R + 6));
+    const size_t smem = per_cta * sizeof(double);
+    plan->threads = kPcgThreads;
+    plan->halo = H;
+    plan->grid = grid;
+    plan->rows = R;
+    plan->smem_state = (mode != kChain) && (smem + static_smem <= (size_t)optin);
+    plan->smem_bytes = plan->smem_state ? smem : 0;
+    const size_t slice = (size_t)(R + (R + 2 * H) + (R + 2 * H + 6) + (R + 6) + 2 * (R + 2 * H));
+    plan->scratch_doubles = plan->smem_state ? 0 : slice * (size_t)grid;
+    // co-residency check for the cooperative launch
+    int per_sm = 0;
+    cudaError_t e;
+    if (plan->smem_state) {
+        if (mode == kIdentity)
+            e = cudaFuncSetAttribute(pcg_kernel<true, kIdentity>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        else
+            e = cudaFuncSetAttribute(pcg_kernel<true, kBand1>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return fail(AIRGA_E_CUDA, "pcg: cannot reserve shared memory");
+        if (mode == kIdentity)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<true, kIdentity>,
+                                                              kPcgThreads, smem);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<true, kBand1>,
+                                                              kPcgThreads, smem);
+    } else {
+        if (mode == kIdentity)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<false, kIdentity>,
+                                                              kPcgThreads, 0);
+        else if (mode == kBand1)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<false, kBand1>,
+                                                              kPcgThreads, 0);
+        else
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<false, kChain>,
+                                                              kPcgThreads, 0);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pcg occupancy");
+    if (per_sm < 1 || grid > per_sm * sms)
+        return fail(AIRGA_E_INVALID_ARG, "pcg: grid cannot be co-resident");
+    return AIRGA_OK;
+}
+
+cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
+    const int mode = mode_of(args.nf, args.psym != nullptr);
+    if (plan.smem_state) {
+        if (mode == kIdentity) return launch_mode<true, kIdentity>(plan, args, s);
+        return launch_mode<true, kBand1>(plan, args, s);
+    }
+    if (mode == kIdentity) return launch_mode<false, kIdentity>(plan, args, s);
+    if (mode == kBand1) return launch_mode<false, kBand1>(plan, args, s);
+    return launch_mode<false, kChain>(plan, args, s);
+}
+
+}  // namespace airga

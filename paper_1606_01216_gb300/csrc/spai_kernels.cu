@@ -1,0 +1,308 @@
+// SPAI and SPAI-update factors on a band pattern, one column per thread.
+//
+// Column j of the factor solves the small least-squares problem of Eq. (3.1)
+// (SPAI: b_j = e_j) or of the update objective of Sec. 3.2 (b_j = A_old e_j):
+//     m_j = argmin || b_j - A m ||_2   over m supported on J_j = {j-W..j+W}.
+// Only the rows I_j = {j-W-3 .. j+W+3} of A(:, J_j) can be nonzero, so the
+// problem is the (2W+7) x (2W+1) block  Ahat(r, c) = A(j-W-3+r, j-W+c),
+// which is itself banded: column c is nonzero only in local rows c..c+6.
+//
+// QR mode: Householder triangularisation of Ahat exploiting that band — the
+// reflector of column c acts on local rows c..c+6 only (rows below c+6 of
+// every later column are still zero when column c is reached), so each
+// reflector has 7 entries however tall the block.  The whole block, the
+// right-hand side and R live in registers (all loops unrolled with
+// compile-time indices); one thread owns one column, so every FP64 lane of
+// a warp does useful work (the FP64 pipe is GB300's binding resource here).
+//
+// Columns of J_j outside [0, n) have no unknown: they are given the unit
+// vector on their own (out-of-range, otherwise all-zero) local row, which
+// decouples them (their solution is exactly 0 and is not stored) and keeps
+// the block full rank without changing the other columns' solution.
+//
+// MR mode: the paper's minimal-residual iteration (Algorithms 2 and 4) on
+// the same block, with the direction restricted to the pattern.
+#include <utility>
+
+#include "airga_internal.cuh"
+
+namespace airga {
+namespace {
+
+constexpr int kThreadsSpai = 128;
+
+// Gather Ahat (banded: a[r][c] for r in c..c+6) for column j; columns outside
+// [0, n) become unit columns on local row c+3.
+template <int W>
+__device__ __forceinline__ void gather_block(int64_t n, int64_t j, const double *__restrict__ A,
+                                             double (&a)[2 * W + 7][2 * W + 1]) {
+    constexpr int NC = 2 * W + 1;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int r = 0; r < c; ++r) a[r][c] = 0.0;     // above the band: fills in during QR
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int64_t k = j - W + c;                  // global column
+        const bool col_ok = (k >= 0 && k < n);
+#pragma unroll
+        for (int t = 0; t < 7; ++t) {
+            const int r = c + t;                       // local row
+            const int64_t g = j - W - 3 + r;           // global row
+            double v = 0.0;
+            if (col_ok && g >= 0 && g < n) v = __ldg(A + (int64_t)(c - r + 6) * n + g);
+            if (!col_ok && t == 3) v = 1.0;            // decoupled unit column
+            a[r][c] = v;
+        }
+    }
+}
+
+// Right-hand side: e_j (build) or A_old(I_j, j) (update).  b has 2W+7 rows.
+template <int W>
+__device__ __forceinline__ void gather_rhs(int64_t n, int64_t j, const double *__restrict__ Aold,
+                                           double (&b)[2 * W + 7]) {
+    constexpr int NR = 2 * W + 7;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) b[r] = 0.0;
+    if (!Aold) {
+        b[W + 3] = 1.0;
+        return;
+    }
+#pragma unroll
+    for (int r = W; r <= W + 6; ++r) {
+        const int64_t g = j - W - 3 + r;               // row of A_old(:, j)
+        if (g >= 0 && g < n) b[r] = __ldg(Aold + (int64_t)(W + 6 - r) * n + g);
+    }
+}
+
+// Store column j of the factor: F(j-W+c, j) = m[c]; diagonals |d| > W and
+// entries whose column is outside the matrix are written as 0 by the thread
+// that owns that row, so the whole band is defined.
+template <int W>
+__device__ __forceinline__ void store_column(int64_t n, int64_t j, const double (&m)[2 * W + 1],
+                                             double *__restrict__ F) {
+    constexpr int NC = 2 * W + 1;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int64_t i = j - W + c;                   // row of F
+        if (i >= 0 && i < n) F[(int64_t)(W - c + 3) * n + i] = m[c];
+    }
+#pragma unroll
+    for (int d = -3; d <= 3; ++d) {
+        const int64_t c = j + d;
+        const bool outside = (c < 0 || c >= n);
+        if (d < -W || d > W || outside) F[(int64_t)(d + 3) * n + j] = 0.0;
+    }
+}
+
+// One Householder step on column C of the banded block (local rows C..C+6):
+// v = x + sign(x_0) ||x|| e_0, applied to the later columns and to b;
+// R_CC stored in a[C][C], 1/R_CC in rinv[C].  Written as a template on C so
+// every array index is a compile-time constant and the block stays in
+// registers.
+template <int W, int C>
+__device__ __forceinline__ void qr_step(double (&a)[2 * W + 7][2 * W + 1], double (&b)[2 * W + 7],
+                                        double (&rinv)[2 * W + 1], double &rmax, double &rmin) {
+    constexpr int NC = 2 * W + 1;
+    double sigma = 0.0;
+#pragma unroll
+    for (int t = 0; t < 7; ++t) sigma = fma(a[C + t][C], a[C + t][C], sigma);
+    const double x0 = a[C][C];
+    const double rs = sigma > 0.0 ? rsqrt(sigma) : 0.0;
+    const double nrm = sigma * rs;                     // ||x||
+    const double alpha = x0 >= 0.0 ? -nrm : nrm;       // R_CC
+    const double v0 = x0 - alpha;                      // x0 + sign(x0) ||x||
+    // H = I - tau v v^T, v = (v0, a[C+1..C+6][C]), tau = 2 / v^T v = 1 / (||x|| |v0|)
+    const double tau = sigma > 0.0 ? 1.0 / (nrm * fabs(v0)) : 0.0;
+#pragma unroll
+    for (int cc = C + 1; cc < NC; ++cc) {
+        double s = v0 * a[C][cc];
+#pragma unroll
+        for (int t = 1; t < 7; ++t) s = fma(a[C + t][C], a[C + t][cc], s);
+        s *= tau;
+        a[C][cc] = fma(-s, v0, a[C][cc]);
+#pragma unroll
+        for (int t = 1; t < 7; ++t) a[C + t][cc] = fma(-s, a[C + t][C], a[C + t][cc]);
+    }
+    {
+        double s = v0 * b[C];
+#pragma unroll
+        for (int t = 1; t < 7; ++t) s = fma(a[C + t][C], b[C + t], s);
+        s *= tau;
+        b[C] = fma(-s, v0, b[C]);
+#pragma unroll
+        for (int t = 1; t < 7; ++t) b[C + t] = fma(-s, a[C + t][C], b[C + t]);
+    }
+    a[C][C] = alpha;
+    rinv[C] = x0 >= 0.0 ? -rs : rs;                    // 1 / R_CC
+    rmax = fmax(rmax, nrm);
+    rmin = fmin(rmin, nrm);
+}
+
+template <int W, int... Cs>
+__device__ __forceinline__ void qr_all(std::integer_sequence<int, Cs...>,
+                                       double (&a)[2 * W + 7][2 * W + 1], double (&b)[2 * W + 7],
+                                       double (&rinv)[2 * W + 1], double &rmax, double &rmin) {
+    (qr_step<W, Cs>(a, b, rinv, rmax, rmin), ...);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreadsSpai)
+spai_qr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
+               double *__restrict__ F, double *__restrict__ colres, int32_t *rank_flag) {
+    constexpr int NC = 2 * W + 1;
+    constexpr int NR = NC + 6;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+
+    double a[NR][NC];
+    double b[NR];
+    gather_block<W>(n, j, A, a);
+    gather_rhs<W>(n, j, Aold, b);
+
+    double rinv[NC];
+    double rmax = 0.0, rmin = 1e300;
+    qr_all<W>(std::make_integer_sequence<int, NC>{}, a, b, rinv, rmax, rmin);
+    double m[NC];
+    const bool rank_ok = rmin > 0.0 && rmin >= 1e-14 * rmax;
+#pragma unroll
+    for (int ci = 0; ci < NC; ++ci) {
+        const int c = NC - 1 - ci;
+        double s = b[c];
+#pragma unroll
+        for (int cc = c + 1; cc < NC; ++cc) s = fma(-a[c][cc], m[cc], s);
+        m[c] = rank_ok ? s * rinv[c] : 0.0;
+    }
+    if (!rank_ok) atomicOr(rank_flag, 1);
+    if (colres) {
+        double rr = 0.0;
+#pragma unroll
+        for (int r = NC; r < NR; ++r) rr = fma(b[r], b[r], rr);
+        colres[j] = sqrt(rr);
+    }
+    store_column<W>(n, j, m, F);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreadsSpai)
+spai_mr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
+               const double *__restrict__ alpha0p, double tol, int kmax,
+               double *__restrict__ F, int32_t *__restrict__ steps,
+               double *__restrict__ colres) {
+    constexpr int NC = 2 * W + 1;
+    constexpr int NR = NC + 6;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+
+    double a[NR][NC];
+    double b[NR];
+    gather_block<W>(n, j, A, a);
+    gather_rhs<W>(n, j, Aold, b);
+    bool in[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int64_t k = j - W + c;
+        in[c] = (k >= 0 && k < n);
+        if (!in[c]) a[c + 3][c] = 0.0;                 // no unknown here: drop the unit column
+    }
+    // m = alpha0 e_j (local column W); r = b - Ahat m
+    const double alpha0 = *alpha0p;
+    double m[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) m[c] = 0.0;
+    m[W] = alpha0;
+    double r[NR];
+    double bb = 0.0;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        bb = fma(b[q], b[q], bb);
+        double am = (q >= W && q <= W + 6) ? a[q][W] * alpha0 : 0.0;
+        r[q] = b[q] - am;
+    }
+    const double thr = tol * sqrt(bb);
+    double rn2 = 0.0;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) rn2 = fma(r[q], r[q], rn2);
+    double rn = sqrt(rn2);
+    int k = 0;
+    while (rn > thr && k < kmax) {
+        // d = r restricted to the pattern: column c's unknown sits on local row c+3
+        double d[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c) d[c] = in[c] ? r[c + 3] : 0.0;
+        double w[NR];
+#pragma unroll
+        for (int q = 0; q < NR; ++q) w[q] = 0.0;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+#pragma unroll
+            for (int t = 0; t < 7; ++t) w[c + t] = fma(a[c + t][c], d[c], w[c + t]);
+        double ww = 0.0, rw = 0.0;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            ww = fma(w[q], w[q], ww);
+            rw = fma(r[q], w[q], rw);
+        }
+        if (ww == 0.0) break;                          // r vanishes on the pattern
+        const double al = rw / ww;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) m[c] = fma(al, d[c], m[c]);
+        rn2 = 0.0;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+            r[q] = fma(-al, w[q], r[q]);
+            rn2 = fma(r[q], r[q], rn2);
+        }
+        rn = sqrt(rn2);
+        ++k;
+    }
+    steps[j] = k;
+    if (colres) colres[j] = rn;
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+        if (!in[c]) m[c] = 0.0;
+    store_column<W>(n, j, m, F);
+}
+
+template <int W>
+cudaError_t qr_w(int64_t n, const double *A, const double *Aold, double *F, double *colres,
+                 int32_t *flag, cudaStream_t s) {
+    int64_t blocks = (n + kThreadsSpai - 1) / kThreadsSpai;
+    spai_qr_kernel<W><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag);
+    return cudaGetLastError();
+}
+
+template <int W>
+cudaError_t mr_w(int64_t n, const double *A, const double *Aold, const double *alpha0,
+                 double tol, int kmax, double *F, int32_t *steps, double *colres,
+                 cudaStream_t s) {
+    int64_t blocks = (n + kThreadsSpai - 1) / kThreadsSpai;
+    spai_mr_kernel<W><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, alpha0, tol, kmax,
+                                                                 F, steps, colres);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_spai_qr(int64_t n, int hbw, const double *A, const double *A_old, double *F,
+                           double *colres, int32_t *rank_flag, cudaStream_t s) {
+    switch (hbw) {
+        case 0: return qr_w<0>(n, A, A_old, F, colres, rank_flag, s);
+        case 1: return qr_w<1>(n, A, A_old, F, colres, rank_flag, s);
+        case 2: return qr_w<2>(n, A, A_old, F, colres, rank_flag, s);
+        default: return qr_w<3>(n, A, A_old, F, colres, rank_flag, s);
+    }
+}
+
+cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_old,
+                           const double *alpha0, double tol, int kmax, double *F,
+                           int32_t *steps, double *colres, cudaStream_t s) {
+    switch (hbw) {
+        case 0: return mr_w<0>(n, A, A_old, alpha0, tol, kmax, F, steps, colres, s);
+        case 1: return mr_w<1>(n, A, A_old, alpha0, tol, kmax, F, steps, colres, s);
+        case 2: return mr_w<2>(n, A, A_old, alpha0, tol, kmax, F, steps, colres, s);
+        default: return mr_w<3>(n, A, A_old, alpha0, tol, kmax, F, steps, colres, s);
+    }
+}
+
+}  // namespace airga

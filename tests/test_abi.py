@@ -1,0 +1,86 @@
+"""C-ABI library: builds, loads without a GPU and exports every declared
+symbol; host-side argument checks run without touching the device."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "airga.h")
+
+
+@pytest.fixture(scope="module")
+def G():
+    from paper_1606_01216_gb300 import build
+    build.build()
+    from paper_1606_01216_gb300 import airga
+    airga.lib()
+    return airga
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(airga_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declarations_are_exported(G):
+    decl = declared_functions()
+    assert len(decl) >= 20
+    L = G.lib()
+    for name in decl:
+        assert hasattr(L, name), name
+    assert sorted(G.EXPORTS) == decl
+
+
+def test_no_torch_or_cuda_types_in_header():
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    for bad in ("torch", "at::", "cudaStream_t", "#include <cuda"):
+        assert bad not in text
+
+
+def test_host_only_calls(G):
+    assert G.lib().airga_version() == 100
+    o = G.options()
+    assert o.tol == 1e-10 and o.maxit == 20000 and o.pattern_hbw == 3 and o.symmetrize == 1
+    assert o.mr_tol == 0.01 and o.mr_kmax == 50 and o.spai_mode == G.SPAI_QR
+    assert G.status_string(G.E_NOT_BANDED).startswith("matrix has entries")
+    assert G.status_string(1234) == "unknown status"
+
+
+def test_argument_checks_need_no_gpu(G):
+    L = G.lib()
+    out = C.c_void_p()
+    # n < 1 and NULL arrays are rejected before any CUDA call
+    assert L.airga_mat_from_csr(0, 0, None, None, None, None, C.byref(out)) == G.E_INVALID_ARG
+    assert "n must be" in G.last_error()
+    assert L.airga_mat_from_csr(5, 3, None, None, None, None, C.byref(out)) == G.E_INVALID_ARG
+    assert L.airga_assemble_shifted(None, None, 0.1, 1e-4, 1.0, None, C.byref(out)) == G.E_INVALID_ARG
+    assert L.airga_spai_build(None, None, None, C.byref(out)) == G.E_INVALID_ARG
+    assert L.airga_spai_update(None, None, None, None, None, C.byref(out)) == G.E_INVALID_ARG
+    assert L.airga_pcg_solve(None, None, None, 1, None, None, None, None, None, None, None) \
+        == G.E_INVALID_ARG
+    assert L.airga_precond_length(None) == 0 and L.airga_mat_rows(None) == 0
+    assert L.airga_debug_set_fault(99) == G.E_INVALID_ARG
+    assert L.airga_debug_set_fault(G.FAULT_NONE) == G.OK
+    assert L.airga_precond_from_bands(10, 0, None, None, C.byref(out)) == G.E_INVALID_ARG
+    L.airga_mat_free(None)
+    L.airga_precond_free(None)
+
+
+def test_options_layout_matches_header(G):
+    # offsets follow C's natural alignment of the struct in airga.h
+    O = G.Options
+    assert O.tol.offset == 0 and O.maxit.offset == 8 and O.mr_tol.offset == 16
+    assert O.barrier_timeout_ms.offset == 40 and C.sizeof(O) == 48
+
+
+def test_product_path_does_not_import_oracle():
+    pkg = os.path.join(ROOT, "paper_1606_01216_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert "import oracle" not in text and "from oracle" not in text, f
+                assert "airga_oracle" not in text and "liboracle" not in text, f

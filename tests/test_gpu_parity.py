@@ -1,0 +1,426 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (from the stated targets and the arithmetic):
+  band import            bit-exact (a copy)
+  assemble_shifted       |a_gpu - a_ora| <= 4 eps (|c_m m| + |c_k k|) per entry
+  SpMV / apply           |y_gpu - y_ora| <= 8 eps sum_k |a_ik x_k| per row
+  SPAI / update columns  ||m_gpu - m_ora|| / ||m_ora|| <= 1e-10 per column
+  PCG                    ||x_gpu - x_ora|| / ||x_ora|| <= 1e-8, true FP64 residual <= 2 tol
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1606_01216_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = np.finfo(float).eps
+AL, BE = W.ALPHA, W.BETA
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_01216_gb300 import build
+    build.build()
+    from paper_1606_01216_gb300 import airga
+    airga.lib()
+    return airga
+
+
+def band_at(band, rows, cols):
+    n = band.size // 7
+    return band.reshape(7, n)[cols - rows + 3, rows]
+
+
+def csr_rows(A):
+    return np.repeat(np.arange(A.n), np.diff(A.rowptr))
+
+
+def factor_dense_cols(band, n):
+    """Column-wise view of a band-7 factor: returns (rows, cols, vals)."""
+    B = band.reshape(7, n)
+    out_r, out_c, out_v = [], [], []
+    for d in range(-3, 4):
+        i = np.arange(max(0, -d), min(n, n - d))
+        out_r.append(i); out_c.append(i + d); out_v.append(B[d + 3, i])
+    return np.concatenate(out_r), np.concatenate(out_c), np.concatenate(out_v)
+
+
+def column_errors(band_gpu, F_ora: O.CSR):
+    """max_j ||f_gpu(:,j) - f_ora(:,j)|| / ||f_ora(:,j)|| on the band."""
+    n = F_ora.n
+    r, c, vg = factor_dense_cols(band_gpu, n)
+    Fd = {}
+    rr = csr_rows(F_ora)
+    ref = np.zeros_like(vg)
+    key = r.astype(np.int64) * n + c
+    okey = rr.astype(np.int64) * n + F_ora.col
+    order = np.argsort(okey)
+    pos = np.searchsorted(okey[order], key)
+    pos = np.clip(pos, 0, len(okey) - 1)
+    hit = okey[order][pos] == key
+    ref[hit] = F_ora.val[order][pos[hit]]
+    # every oracle entry must land on the band
+    assert np.all(np.abs(rr - F_ora.col) <= 3)
+    num = np.sqrt(np.bincount(c, weights=(vg - ref) ** 2, minlength=n))
+    den = np.sqrt(np.bincount(c, weights=ref ** 2, minlength=n))
+    return num / np.where(den > 0, den, 1.0)
+
+
+def setup_beam(G, n_e, scaling="unit"):
+    beam = W.beam(n_e, scaling)
+    M, K = G.beam_mats(beam)
+    return beam, M, K
+
+
+# ---------------------------------------------------------------------------
+# matrices and assembly
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_e", [1, 2, 500, 1237])
+def test_csr_import_bit_exact(G, n_e):
+    beam, M, K = setup_beam(G, n_e)
+    for H, vals in ((M, beam.m_val), (K, beam.k_val)):
+        band = H.band().cpu().numpy()
+        rows = np.repeat(np.arange(beam.n), np.diff(beam.rowptr))
+        assert np.array_equal(band_at(band, rows, beam.col.astype(np.int64)), vals)
+        # entries outside the matrix are held as 0
+        B = band.reshape(7, beam.n)
+        for d in range(-3, 4):
+            bad = [i for i in range(beam.n) if not (0 <= i + d < beam.n)]
+            assert np.all(B[d + 3, bad] == 0)
+
+
+def test_csr_import_rejects(G):
+    n = 6
+    rp = torch.tensor([0, 1, 2, 3, 4, 5, 6], dtype=torch.int64, device="cuda")
+    ci = torch.tensor([0, 1, 2, 3, 4, 0], dtype=torch.int32, device="cuda")   # (5, 0): |d| = 5
+    v = torch.ones(6, dtype=torch.float64, device="cuda")
+    with pytest.raises(G.AirgaError) as e:
+        G.mat_from_csr(n, rp, ci, v)
+    assert e.value.code == G.E_NOT_BANDED
+    ci2 = torch.tensor([0, 1, 2, 3, 4, 9], dtype=torch.int32, device="cuda")
+    with pytest.raises(G.AirgaError) as e:
+        G.mat_from_csr(n, rp, ci2, v)
+    assert e.value.code == G.E_INVALID_ARG
+
+
+def test_csr_import_sums_duplicates(G):
+    rp = torch.tensor([0, 3, 4], dtype=torch.int64, device="cuda")
+    ci = torch.tensor([0, 0, 1, 1], dtype=torch.int32, device="cuda")
+    v = torch.tensor([1.0, 2.0, 5.0, 7.0], dtype=torch.float64, device="cuda")
+    B = G.mat_from_csr(2, rp, ci, v).band().cpu().numpy().reshape(7, 2)
+    assert B[3, 0] == 3.0 and B[4, 0] == 5.0 and B[3, 1] == 7.0
+
+
+@pytest.mark.parametrize("s", [0.0, 0.1, 1.0, 37.5, 1e4])
+@pytest.mark.parametrize("scaling", ["unit", "literal"])
+def test_assemble_shifted(G, s, scaling):
+    beam, M, K = setup_beam(G, 1237, scaling)
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    band = A.band().cpu().numpy()
+    rows = np.repeat(np.arange(beam.n), np.diff(beam.rowptr))
+    got = band_at(band, rows, beam.col.astype(np.int64))
+    ref = O.shifted(beam.m_val, beam.k_val, AL, BE, s)
+    scale = np.abs((s * s + AL * s) * beam.m_val) + np.abs((1 + BE * s) * beam.k_val)
+    assert np.all(np.abs(got - ref) <= 4 * EPS * scale)
+
+
+@pytest.mark.parametrize("n_e", [1, 500, 1237])
+def test_spmv(G, n_e):
+    beam, M, K = setup_beam(G, n_e)
+    A = G.assemble_shifted(M, K, AL, BE, 2.5)
+    Ao = O.shifted_csr(beam, AL, BE, 2.5)
+    X = np.asfortranarray(np.random.default_rng(n_e).standard_normal((beam.n, 3)))
+    Xd = torch.from_numpy(X.T.copy()).cuda().t()          # column-major n x 3
+    Yh = G.spmv(A, Xd).cpu().numpy()
+    absA = O.CSR(Ao.n, Ao.rowptr, Ao.col, np.abs(Ao.val))
+    for c in range(3):
+        ref = O.spmv(Ao, X[:, c])
+        bound = 8 * EPS * O.spmv(absA, np.abs(X[:, c]))
+        assert np.all(np.abs(Yh[:, c] - ref) <= bound + 1e-300)
+
+
+# ---------------------------------------------------------------------------
+# SPAI (Eq. 3.1) and SPAI update (Sec. 3.2), QR mode
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_e", [500, 1237])
+@pytest.mark.parametrize("s", [0.1, 1.0, 100.0, 1e4])
+def test_spai_build_qr(G, n_e, s):
+    beam, M, K = setup_beam(G, n_e)
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    P = G.spai_build(A)
+    Ao = O.shifted_csr(beam, AL, BE, s)
+    Po, colres_o = O.spai(Ao, want_colres=True)
+    err = column_errors(G.precond_factor(P, 0).cpu().numpy(), Po)
+    assert err.max() <= 1e-10, err.max()
+    steps, colres, st = G.precond_status(P)
+    assert st == G.OK and int(steps.abs().max()) == 0
+    assert np.allclose(colres.cpu().numpy(), colres_o, rtol=1e-8, atol=1e-14)
+
+
+@pytest.mark.parametrize("hbw", [0, 1, 2])
+def test_spai_narrow_patterns(G, hbw):
+    beam, M, K = setup_beam(G, 600)
+    A = G.assemble_shifted(M, K, AL, BE, 3.0)
+    P = G.spai_build(A, G.options(pattern_hbw=hbw))
+    Ao = O.shifted_csr(beam, AL, BE, 3.0)
+    rp, ci = W.band_pattern(beam.n, hbw)
+    Po = O.spai(Ao, pattern=O.CSR(beam.n, rp, ci, np.ones(ci.size)))
+    band = G.precond_factor(P, 0).cpu().numpy()
+    assert column_errors(band, Po).max() <= 1e-10
+    B = band.reshape(7, beam.n)
+    for d in range(-3, 4):
+        if abs(d) > hbw:
+            assert np.all(B[d + 3] == 0)
+
+
+def test_spai_full_pattern_is_inverse(G):
+    beam, M, K = setup_beam(G, 2)      # n = 4: the band covers the matrix
+    A = G.assemble_shifted(M, K, AL, BE, 0.7)
+    band = G.precond_factor(G.spai_build(A), 0).cpu().numpy()
+    n = 4
+    r, c, v = factor_dense_cols(band, n)
+    P = np.zeros((n, n)); P[r, c] = v
+    Ainv = np.linalg.inv(O.shifted_csr(beam, AL, BE, 0.7).dense())
+    assert np.allclose(P, Ainv, rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("pair", [(0.1, 0.518), (1.0, 5.18), (100.0, 518.0)])
+def test_spai_update_qr(G, pair):
+    s0, s1 = pair
+    beam, M, K = setup_beam(G, 1237)
+    A0 = G.assemble_shifted(M, K, AL, BE, s0)
+    A1 = G.assemble_shifted(M, K, AL, BE, s1)
+    P0 = G.spai_build(A0)
+    P1 = G.spai_update(P0, A0, A1)
+    assert len(P1) == 2 and len(P0) == 1
+    Ao0, Ao1 = O.shifted_csr(beam, AL, BE, s0), O.shifted_csr(beam, AL, BE, s1)
+    Qo = O.spai(Ao1, A_old=Ao0)
+    assert column_errors(G.precond_factor(P1, 1).cpu().numpy(), Qo).max() <= 1e-10
+    # factor 0 is shared with P0
+    assert torch.equal(G.precond_factor(P1, 0), G.precond_factor(P0, 0))
+    del P0   # the chain keeps its factors alive
+    assert torch.isfinite(G.precond_factor(P1, 0)).all()
+
+
+def test_update_same_matrix_is_identity(G):
+    beam, M, K = setup_beam(G, 300)
+    A = G.assemble_shifted(M, K, AL, BE, 4.0)
+    Q = G.precond_factor(G.spai_update(G.spai_build(A), A, A), 1).cpu().numpy().reshape(7, -1)
+    assert np.allclose(Q[3], 1.0, atol=1e-12)
+    assert np.abs(np.delete(Q, 3, axis=0)).max() <= 1e-12
+
+
+# ---------------------------------------------------------------------------
+# preconditioner apply
+# ---------------------------------------------------------------------------
+
+def test_precond_apply_single_and_chain(G):
+    beam, M, K = setup_beam(G, 700)
+    shifts = (1.0, 1.6, 2.5)
+    As = [G.assemble_shifted(M, K, AL, BE, s) for s in shifts]
+    P = G.spai_build(As[0])
+    P2 = G.spai_update(P, As[0], As[1])
+    P3 = G.spai_update(P2, As[1], As[2])
+    Aos = [O.shifted_csr(beam, AL, BE, s) for s in shifts]
+    facs = [O.spai(Aos[0]), O.spai(Aos[1], A_old=Aos[0]), O.spai(Aos[2], A_old=Aos[1])]
+    r = np.random.default_rng(3).standard_normal(beam.n)
+    rd = torch.from_numpy(r).cuda()
+    for handle, k in ((P, 1), (P2, 2), (P3, 3)):
+        Cd = np.eye(beam.n)
+        for f in facs[:k]:
+            Cd = f.dense() @ Cd
+        for sym in (True, False):
+            z = G.precond_apply(handle, rd, symmetrize=sym).cpu().numpy()
+            ref = 0.5 * (Cd + Cd.T) @ r if sym else Cd @ r
+            assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
+
+
+# ---------------------------------------------------------------------------
+# PCG
+# ---------------------------------------------------------------------------
+
+def run_pcg(G, A, P, F, **kw):
+    Fd = torch.from_numpy(np.ascontiguousarray(F.T)).cuda().t() if F.ndim == 2 else \
+        torch.from_numpy(F).cuda()
+    res = G.pcg_solve(A, P, Fd, G.options(**kw), want_hist=True)
+    torch.cuda.synchronize()
+    return res
+
+
+@pytest.mark.parametrize("n_e,s", [(500, 1.0), (500, 10.0), (500, 100.0), (500, 1000.0),
+                                   (1237, 0.1), (1237, 13.9), (1237, 1e4)])
+def test_pcg_matches_oracle(G, n_e, s):
+    beam, M, K = setup_beam(G, n_e)
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    P = G.spai_build(A)
+    F = W.loads(beam.n)[:, 0]
+    res = run_pcg(G, A, P, F)
+    Ao = O.shifted_csr(beam, AL, BE, s)
+    x_o, it_o, st_o, hist_o = O.pcg(Ao, F, [O.spai(Ao)], tol=1e-10, maxit=20000)
+    x = res["X"].cpu().numpy()
+    it = int(res["iters"][0])
+    assert int(res["status"][0]) == G.OK and st_o == O.OK
+    assert np.linalg.norm(x - x_o) <= 1e-8 * np.linalg.norm(x_o)
+    xd = O.chol_solve(Ao, F)[:, 0]
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+    assert abs(it - it_o) <= max(1, it_o // 50)
+    assert float(res["true_relres"][0]) <= 2e-10
+    true = np.linalg.norm(F - O.spmv(Ao, x)) / np.linalg.norm(F)
+    assert abs(true - float(res["true_relres"][0])) <= 1e-3 * true + 1e-16
+    h = res["res_hist"][0, : it + 1].cpu().numpy()
+    k = min(5, it, it_o)
+    assert np.allclose(h[:k + 1], hist_o[:k + 1], rtol=1e-8)
+    assert h[it] <= 1e-10 and h[0] == pytest.approx(1.0)
+
+
+def test_pcg_multi_rhs_and_identity(G):
+    beam, M, K = setup_beam(G, 800)
+    s = 2.68
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    P = G.spai_build(A)
+    F = W.loads(beam.n, 3, seed=11)
+    Ao = O.shifted_csr(beam, AL, BE, s)
+    Xd = O.chol_solve(Ao, F)
+    for handle in (P, None):
+        res = run_pcg(G, A, handle, F)
+        X = res["X"].cpu().numpy()
+        assert X.shape == (beam.n, 3)
+        for c in range(3):
+            assert int(res["status"][c]) == G.OK
+            assert np.linalg.norm(X[:, c] - Xd[:, c]) <= 1e-8 * np.linalg.norm(Xd[:, c])
+            facs = [O.spai(Ao)] if handle is not None else []
+            _, it_o, _, _ = O.pcg(Ao, F[:, c], facs, tol=1e-10, maxit=20000)
+            assert abs(int(res["iters"][c]) - it_o) <= max(1, it_o // 50)
+
+
+@pytest.mark.parametrize("chain", [2, 3])
+def test_pcg_update_chain(G, chain):
+    beam, M, K = setup_beam(G, 1237)
+    shifts = W.log_shifts(-1, 4, 8)[2:2 + chain]
+    As = [G.assemble_shifted(M, K, AL, BE, s) for s in shifts]
+    P = G.spai_build(As[0])
+    for a0, a1 in zip(As, As[1:]):
+        P = G.spai_update(P, a0, a1)
+    assert len(P) == chain
+    Aos = [O.shifted_csr(beam, AL, BE, s) for s in shifts]
+    facs = [O.spai(Aos[0])] + [O.spai(b, A_old=a) for a, b in zip(Aos, Aos[1:])]
+    F = W.loads(beam.n)[:, 0]
+    res = run_pcg(G, As[-1], P, F)
+    x_o, it_o, st_o, _ = O.pcg(Aos[-1], F, facs, tol=1e-10, maxit=20000)
+    x = res["X"].cpu().numpy()
+    assert int(res["status"][0]) == G.OK and st_o == O.OK
+    assert np.linalg.norm(x - x_o) <= 1e-8 * np.linalg.norm(x_o)
+    assert abs(int(res["iters"][0]) - it_o) <= max(1, it_o // 50)
+
+
+def test_pcg_edge_cases(G):
+    beam, M, K = setup_beam(G, 1)           # n = 2
+    A = G.assemble_shifted(M, K, AL, BE, 1.0)
+    F = W.loads(beam.n)[:, 0]
+    res = run_pcg(G, A, G.spai_build(A), F)
+    xd = np.linalg.solve(O.shifted_csr(beam, AL, BE, 1.0).dense(), F)
+    assert int(res["status"][0]) == G.OK
+    assert np.allclose(res["X"].cpu().numpy(), xd, rtol=1e-12)
+
+    beam, M, K = setup_beam(G, 400)
+    A = G.assemble_shifted(M, K, AL, BE, 0.5)
+    P = G.spai_build(A)
+    Ao = O.shifted_csr(beam, AL, BE, 0.5)
+    # zero right-hand side
+    res = run_pcg(G, A, P, np.zeros(beam.n))
+    assert int(res["iters"][0]) == 0 and int(res["status"][0]) == G.OK
+    assert not res["X"].any() and float(res["true_relres"][0]) == 0.0
+    # iteration cap: X is the oracle's 3rd iterate
+    F = W.loads(beam.n)[:, 0]
+    res = run_pcg(G, A, P, F, maxit=3)
+    x3, it3, st3, _ = O.pcg(Ao, F, [O.spai(Ao)], tol=1e-10, maxit=3)
+    assert int(res["status"][0]) == G.E_MAXIT and st3 == O.EMAXIT and int(res["iters"][0]) == 3
+    assert np.linalg.norm(res["X"].cpu().numpy() - x3) <= 1e-11 * np.linalg.norm(x3)
+    # warm start from the direct solution converges at k = 0
+    xd = O.chol_solve(Ao, F)[:, 0]
+    Xw = torch.from_numpy(xd.copy()).cuda()
+    out = G.pcg_solve(A, P, torch.from_numpy(F).cuda(), G.options(warm_start=1), X=Xw)
+    torch.cuda.synchronize()
+    assert int(out["iters"][0]) == 0 and int(out["status"][0]) == G.OK
+
+
+def test_pcg_deterministic(G):
+    beam, M, K = setup_beam(G, 3000)
+    A = G.assemble_shifted(M, K, AL, BE, 0.3)
+    P = G.spai_build(A)
+    F = W.loads(beam.n, 2, seed=5)
+    r1 = run_pcg(G, A, P, F)
+    r2 = run_pcg(G, A, P, F)
+    assert torch.equal(r1["X"], r2["X"]) and torch.equal(r1["iters"], r2["iters"])
+
+
+def test_barrier_timeout_reports_status(G):
+    """A CTA that never arrives (host-injected) makes every bounded barrier
+    wait expire; the solve returns AIRGA_E_TIMEOUT and the context stays
+    usable."""
+    beam, M, K = setup_beam(G, 5000)
+    A = G.assemble_shifted(M, K, AL, BE, 1.0)
+    P = G.spai_build(A)
+    F = W.loads(beam.n)[:, 0]
+    G.debug_set_fault(G.FAULT_SKIP_ARRIVAL)
+    res = run_pcg(G, A, P, F, barrier_timeout_ms=100)
+    assert int(res["status"][0]) == G.E_TIMEOUT
+    res = run_pcg(G, A, P, F)
+    assert int(res["status"][0]) == G.OK
+
+
+# ---------------------------------------------------------------------------
+# MR mode (Algorithms 2 and 4)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [0.5, 13.9, 373.0])
+def test_spai_mr_build_and_update(G, s):
+    beam, M, K = setup_beam(G, 700)
+    A0 = G.assemble_shifted(M, K, AL, BE, s / 5.18)
+    A1 = G.assemble_shifted(M, K, AL, BE, s)
+    opts = G.options(spai_mode=G.SPAI_MR, mr_tol=0.01, mr_kmax=50)
+    P = G.spai_build(A1, opts)
+    Ao0, Ao1 = O.shifted_csr(beam, AL, BE, s / 5.18), O.shifted_csr(beam, AL, BE, s)
+    Po, steps_o, res_o, a0 = O.spai_mr(Ao1, tol=0.01, kmax=50)
+    steps, colres, _ = G.precond_status(P)
+    steps = steps.cpu().numpy()
+    same = steps == steps_o
+    assert same.mean() >= 0.99
+    err = column_errors(G.precond_factor(P, 0).cpu().numpy(), Po)
+    assert err[same].max() <= 1e-10
+    Pu = G.spai_update(G.spai_build(A0), A0, A1, opts)
+    Qo, steps_uo, _, _ = O.spai_mr(Ao1, tol=0.01, kmax=50, A_old=Ao0)
+    steps_u = G.precond_status(Pu)[0].cpu().numpy()
+    same = steps_u == steps_uo
+    assert same.mean() >= 0.99
+    assert column_errors(G.precond_factor(Pu, 1).cpu().numpy(), Qo)[same].max() <= 1e-10
+
+
+# ---------------------------------------------------------------------------
+# full size: n = 1e6 beam (500,000 elements), the measured configuration
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [0.1, 1e4])
+def test_full_size_beam(G, s):
+    beam, M, K = setup_beam(G, 500_000)
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    P = G.spai_build(A)
+    Ao = O.shifted_csr(beam, AL, BE, s)
+    # every SPAI column against the oracle's exact LS
+    Po = O.spai(Ao)
+    assert column_errors(G.precond_factor(P, 0).cpu().numpy(), Po).max() <= 1e-10
+    F = W.loads(beam.n)[:, 0]
+    res = run_pcg(G, A, P, F)
+    x = res["X"].cpu().numpy()
+    xd = O.chol_solve(Ao, F)[:, 0]
+    assert int(res["status"][0]) == G.OK
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+    true = np.linalg.norm(F - O.spmv(Ao, x)) / np.linalg.norm(F)
+    assert true <= 2e-10
