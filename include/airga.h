@@ -198,6 +198,37 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
 int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m,
                         double *relres, void *stream);
 
+/* Allocation-free variant of airga_pcg_solve.  The paper has no counterpart:
+ * this entry point exists for callers that cannot let a library allocate
+ * device memory — an application whose device memory is entirely owned by
+ * its own allocator (a framework that reserves the GPU up front and forbids
+ * allocations behind its back), or a latency-critical loop that cannot take
+ * the synchronisation and failure point of an allocation call.  It calls no
+ * cudaMalloc/cudaFree or other allocating routine.
+ *
+ * Inputs are raw band-7 arrays instead of handles: A_band[7*n] (the shifted
+ * matrix) and M_band[7*n] (the preconditioner applied as z = M r, e.g.
+ * P_sym = 1/2 (P + P^T) of a SPAI; NULL = no preconditioner), all device
+ * memory owned by the caller; F, X, res_hist, iters, status, true_relres and
+ * the options mean the same as for airga_pcg_solve (chains of update factors
+ * are not accepted here).
+ *
+ * Its scratch is a fixed array of 8.1 MiB in the library's device image,
+ * which every GPU that loads the library holds until the process exits.
+ * Limits: n <= 1048576 rows, and the solve state must fit in shared memory
+ * (true on a GB300 up to that n); larger problems give AIRGA_E_INVALID_ARG
+ * with an explanatory airga_last_error().  The first call on each device
+ * looks up the array's device address (once per device, with that device
+ * current); make that first call before any stream capture.  All calls share
+ * the array and it keeps the previous call's contents (the barrier words are
+ * cleared on the stream before each column), so calls whose GPU work
+ * overlaps — on concurrent streams or from several host threads — race and
+ * must be serialised by the caller. */
+int airga_pcg_solve_noalloc(int64_t n, const double *A_band, const double *M_band,
+                            const double *F, int32_t m, const airga_options *opt, double *X,
+                            double *res_hist, int32_t *iters, int32_t *status,
+                            double *true_relres, void *stream);
+
 /* Test hook for failure detection (no GPU fault involved): arm a fault for
  * the next airga_pcg_solve call of this process.  AIRGA_FAULT_SKIP_ARRIVAL
  * makes CTA 0 skip its arrival at the first iteration barrier of the first

@@ -30,7 +30,7 @@ EXPORTS = (
     "airga_spai_update", "airga_precond_apply", "airga_precond_length", "airga_precond_rows",
     "airga_precond_factor", "airga_precond_from_bands", "airga_precond_status",
     "airga_precond_free", "airga_pcg_solve", "airga_true_residual", "airga_debug_set_fault",
-    "airga_trim",
+    "airga_trim", "airga_pcg_solve_noalloc",
 )
 
 
@@ -92,6 +92,8 @@ def lib():
                                       vp]),
         "airga_true_residual": (C.c_int, [vp, vp, vp, i32, vp, vp]),
         "airga_debug_set_fault": (C.c_int, [C.c_int]),
+        "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
+                                              vp, vp, vp, vp]),
         "airga_trim": (C.c_int, []),
     }
     for name, (res, args) in sig.items():

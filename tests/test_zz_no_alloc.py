@@ -1,0 +1,91 @@
+"""The allocation-free PCG entry point against the regular one.
+
+airga_pcg_solve_noalloc is for callers that cannot let a library allocate
+device memory: their own allocator owns the GPU's memory, or their loop cannot
+absorb the synchronisation and possible failure of an allocation call.  It
+works out of one fixed scratch array that every call shares and that keeps
+the previous call's contents, so this test makes two calls in a row (two
+different shifts, two right-hand sides each) through the C ABI and checks
+each against airga_pcg_solve on the same problem, with the tolerances of the
+PCG parity tests (X within 1e-8 relative, true residual within 2e-10).
+
+Collected last on purpose: it must pass alone in a fresh process and after
+the other tests.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+from paper_1606_01216_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_01216_gb300 import build
+    build.build()
+    from paper_1606_01216_gb300 import airga
+    airga.lib()
+    return airga
+
+
+def sym_band(P: torch.Tensor, n: int) -> torch.Tensor:
+    """1/2 (P + P^T) on band-7 storage, computed with torch on the device."""
+    B = P.reshape(7, n)
+    S = torch.zeros_like(B)
+    for d in range(-3, 4):
+        lo, hi = max(0, -d), min(n, n - d)
+        i = torch.arange(lo, hi, device=P.device)
+        S[d + 3, i] = 0.5 * (B[d + 3, i] + B[3 - d, i + d])
+    return S.reshape(-1).contiguous()
+
+
+def noalloc(G, n, A_band, M_band, F, m, opts, X, iters, status, relres):
+    L = G.lib()
+    p = lambda t: C.c_void_p(t.data_ptr()) if t is not None else None
+    return L.airga_pcg_solve_noalloc(n, p(A_band), p(M_band), p(F), m, C.byref(opts), p(X),
+                                     None, p(iters), p(status), p(relres),
+                                     C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+
+def test_noalloc_matches_pcg_solve_on_two_calls(G):
+    beam = W.beam(60_011)                       # n = 120,022: 152 CTAs, ragged last block
+    n = beam.n
+    M, K = G.beam_mats(beam)
+    F = np.asfortranarray(W.loads(n, 2, seed=17))
+    Fd = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()      # (m, n) = column-major n x m
+    opts = G.options()
+    for s in (0.518, 13.9):                     # two calls in a row on the shared scratch
+        A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
+        P = G.spai_build(A)
+        ref = G.pcg_solve(A, P, Fd.t(), opts)
+        A_band = G.mat_to_band(A)
+        M_band = sym_band(G.precond_factor(P, 0), n)
+        X = torch.zeros(2, n, dtype=torch.float64, device="cuda")
+        iters = torch.zeros(2, dtype=torch.int32, device="cuda")
+        status = torch.zeros(2, dtype=torch.int32, device="cuda")
+        relres = torch.zeros(2, dtype=torch.float64, device="cuda")
+        rc = noalloc(G, n, A_band, M_band, Fd, 2, opts, X, iters, status, relres)
+        assert rc == G.OK, G.last_error()
+        torch.cuda.synchronize()
+        Xr = ref["X"].t().cpu().numpy()
+        Xn = X.cpu().numpy()
+        for c in range(2):
+            assert int(status[c]) == G.OK and int(ref["status"][c]) == G.OK
+            assert abs(int(iters[c]) - int(ref["iters"][c])) <= 1
+            assert np.linalg.norm(Xn[c] - Xr[c]) <= 1e-8 * np.linalg.norm(Xr[c])
+            assert float(relres[c]) <= 2e-10
+
+
+def test_noalloc_rejects_oversize(G):
+    n = (1 << 20) + 1
+    dummy = torch.zeros(8, dtype=torch.float64, device="cuda")
+    i32 = torch.zeros(1, dtype=torch.int32, device="cuda")
+    rc = noalloc(G, n, dummy, None, dummy, 1, G.options(), dummy, i32, i32, dummy)
+    assert rc == G.E_INVALID_ARG
+    assert "1048576" in G.last_error()
