@@ -50,6 +50,9 @@ int make_band(int64_t n, cudaStream_t s, BandPtr *out);
 struct airga_mat_s {
     int64_t n = 0;
     airga::BandPtr band;
+    // device int32: nonzero when every row pair (2k, 2k+1) but the last has the
+    // Hermite-beam zeros (even rows: offsets -3, +1; odd rows: +3, -1)
+    std::shared_ptr<void> pairz;
 };
 
 struct airga_precond_s {
@@ -70,7 +73,11 @@ namespace airga {
 cudaError_t launch_csr_to_band(int64_t n, const int64_t *rowptr, const int32_t *col,
                                const double *val, double *band, int32_t *flag, cudaStream_t s);
 cudaError_t launch_assemble(int64_t n, const double *M, const double *K, double alpha,
-                            double beta, double sh, double *A, cudaStream_t s);
+                            double beta, double sh, double *A, cudaStream_t s,
+                            const int32_t *fm = nullptr, const int32_t *fk = nullptr,
+                            int32_t *fa = nullptr);
+// beam zero-structure flag of a band (flag must be preset to nonzero)
+cudaError_t launch_detect_pairz(int64_t n, const double *band, int32_t *flag, cudaStream_t s);
 cudaError_t launch_spmv(int64_t n, const double *band, const double *X, double *Y, int32_t m,
                         cudaStream_t s);
 cudaError_t launch_band_apply(int64_t n, const double *band, const double *x, double *y,
@@ -109,6 +116,7 @@ cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_
 constexpr int kMaxChain = 16;
 
 struct PcgPlan {
+    int kind = 0;          // 0 generic (shared-memory state), 1 generic (global state), 2 node-pair
     int grid = 0;          // CTAs (all co-resident)
     int threads = 0;
     int64_t rows = 0;      // rows per CTA (R)
@@ -142,12 +150,20 @@ struct PcgArgs {
     unsigned int *bar;             // barrier counter (zeroed before launch)
     int *abort_flag;               // set by a CTA whose barrier wait timed out
     int fault_skip_arrival;        // test injection: CTA 0 skips its first iteration barrier
+    const int32_t *pairz;          // device flag: A has the beam zero structure (may be null)
 };
 
 // process-wide test fault consumed by the next pcg_solve (airga_debug_set_fault)
 int take_fault();
 
-int pcg_plan(int64_t n, int nf, bool psym_path, int device, PcgPlan *plan);
+// aligned16: A, the preconditioner band, b and x are 16-byte aligned (needed
+// by the node-pair kernel together with an even n)
+int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgPlan *plan);
 cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
+// node-pair kernel (pcg_pair.cu)
+size_t pcg_pair_smem(int64_t R);
+int pcg_pair_threads();
+int pcg_pair_occupancy(int mode, size_t smem, int *per_sm);
+cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
 
 }  // namespace airga

@@ -117,6 +117,17 @@ static int make_buf(size_t bytes, cudaStream_t s, std::shared_ptr<void> *out) {
 
 static cudaStream_t S(void *stream) { return (cudaStream_t)stream; }
 
+// device flag of the beam zero structure, detected from the band on the stream
+static int detect_flag(airga_mat_s *m, cudaStream_t s) {
+    int st = make_buf(sizeof(int32_t), s, &m->pairz);
+    if (st) return st;
+    AIRGA_CUDA(cudaMemsetAsync(m->pairz.get(), 1, sizeof(int32_t), s));
+    AIRGA_CUDA(launch_detect_pairz(m->n, m->band->d, (int32_t *)m->pairz.get(), s));
+    return AIRGA_OK;
+}
+
+static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+
 static std::atomic<int> g_fault{AIRGA_FAULT_NONE};
 
 int take_fault() { return g_fault.exchange(AIRGA_FAULT_NONE); }
@@ -242,6 +253,11 @@ int airga_mat_from_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int3
     auto *m = new airga_mat_s;
     m->n = n;
     m->band = b;
+    st = detect_flag(m, s);
+    if (st) {
+        delete m;
+        return st;
+    }
     *out = m;
     return AIRGA_OK;
 }
@@ -259,6 +275,11 @@ int airga_mat_from_band(int64_t n, const double *band, void *stream, airga_mat *
     auto *m = new airga_mat_s;
     m->n = n;
     m->band = b;
+    st = detect_flag(m, s);
+    if (st) {
+        delete m;
+        return st;
+    }
     *out = m;
     return AIRGA_OK;
 }
@@ -293,10 +314,17 @@ int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, 
     BandPtr b;
     st = make_band(M->n, cs, &b);
     if (st) return st;
-    AIRGA_CUDA(launch_assemble(M->n, M->band->d, K->band->d, alpha, beta, s, b->d, cs));
+    std::shared_ptr<void> flag;
+    st = make_buf(sizeof(int32_t), cs, &flag);
+    if (st) return st;
+    AIRGA_CUDA(launch_assemble(M->n, M->band->d, K->band->d, alpha, beta, s, b->d, cs,
+                               (const int32_t *)(M->pairz ? M->pairz.get() : nullptr),
+                               (const int32_t *)(K->pairz ? K->pairz.get() : nullptr),
+                               (int32_t *)flag.get()));
     auto *m = new airga_mat_s;
     m->n = M->n;
     m->band = b;
+    m->pairz = flag;
     *A_out = m;
     return AIRGA_OK;
 }
@@ -502,8 +530,11 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
     int dev = 0;
     AIRGA_CUDA(cudaGetDevice(&dev));
     const int64_t n = A->n;
+    const double *mband = nf == 1 ? (o.symmetrize && P->psym ? P->psym->d : P->factors[0]->d)
+                                  : nullptr;
+    bool al = aligned16(A->band->d) && aligned16(F) && aligned16(X) && (!mband || aligned16(mband));
     PcgPlan plan;
-    st = pcg_plan(n, nf, nf == 1 && o.symmetrize, dev, &plan);
+    st = pcg_plan(n, nf, nf == 1 && o.symmetrize, al, dev, &plan);
     if (st) return st;
     cudaStream_t s = S(stream);
 
@@ -530,6 +561,7 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
     a.warm = o.warm_start ? 1 : 0;
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
     a.fault_skip_arrival = take_fault() == AIRGA_FAULT_SKIP_ARRIVAL ? 1 : 0;
+    a.pairz = A->pairz ? (const int32_t *)A->pairz.get() : nullptr;
     a.pbuf = base;
     a.state = base + n_pbuf;
     a.partials = a.state + plan.scratch_doubles;

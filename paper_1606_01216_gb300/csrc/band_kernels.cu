@@ -69,7 +69,11 @@ __global__ void csr_to_band_kernel(int64_t n, const int64_t *__restrict__ rowptr
 // ---------------------------------------------------------------------------
 __global__ void assemble_kernel(int64_t total, const double *__restrict__ M,
                                 const double *__restrict__ K, double cm, double ck,
-                                double *__restrict__ A) {
+                                double *__restrict__ A, const int32_t *fm, const int32_t *fk,
+                                int32_t *fa) {
+    // a zero of both M and K stays an exact zero of A: the structure flag of
+    // A is the AND of the two input flags
+    if (fa && blockIdx.x == 0 && threadIdx.x == 0) *fa = (fm && fk && *fm && *fk) ? 1 : 0;
     int64_t pairs = total >> 1;
     const double2 *M2 = reinterpret_cast<const double2 *>(M);
     const double2 *K2 = reinterpret_cast<const double2 *>(K);
@@ -84,6 +88,22 @@ __global__ void assemble_kernel(int64_t total, const double *__restrict__ M,
     }
     if ((total & 1) && blockIdx.x == 0 && threadIdx.x == 0)
         A[total - 1] = fma(cm, M[total - 1], ck * K[total - 1]);
+}
+
+// Beam zero structure: every row pair (2k, 2k+1) except the last has exact
+// zeros at offsets -3, +1 (even row) and +3, -1 (odd row).  `flag` arrives
+// nonzero; any violation clears it (all writers store the same 0).
+__global__ void detect_pairz_kernel(int64_t n, const double *__restrict__ band, int32_t *flag) {
+    if (n < 2 || (n & 1)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) *flag = 0;
+        return;
+    }
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n - 2;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const bool bad = (i & 1) ? (band[6 * n + i] != 0.0 || band[2 * n + i] != 0.0)
+                                 : (band[0 * n + i] != 0.0 || band[4 * n + i] != 0.0);
+        if (bad) *flag = 0;
+    }
 }
 
 // one row of y = A x for the band-7 stencil (x read through a bounds check)
@@ -267,11 +287,18 @@ cudaError_t launch_csr_to_band(int64_t n, const int64_t *rowptr, const int32_t *
 }
 
 cudaError_t launch_assemble(int64_t n, const double *M, const double *K, double alpha,
-                            double beta, double sh, double *A, cudaStream_t s) {
+                            double beta, double sh, double *A, cudaStream_t s,
+                            const int32_t *fm, const int32_t *fk, int32_t *fa) {
     double cm = sh * sh + alpha * sh;
     double ck = 1.0 + beta * sh;
     int64_t total = (int64_t)kBand * n;
-    assemble_kernel<<<grid_for(total / 2 + 1), kThreads, 0, s>>>(total, M, K, cm, ck, A);
+    assemble_kernel<<<grid_for(total / 2 + 1), kThreads, 0, s>>>(total, M, K, cm, ck, A, fm, fk,
+                                                                   fa);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_detect_pairz(int64_t n, const double *band, int32_t *flag, cudaStream_t s) {
+    detect_pairz_kernel<<<grid_for(n), kThreads, 0, s>>>(n, band, flag);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,136 @@
+// Device helpers shared by the persistent PCG kernels: bounded grid barrier,
+// deterministic block and grid reductions.
+#pragma once
+
+#include "airga_internal.cuh"
+
+namespace airga {
+namespace pcgdev {
+namespace {
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Bounded grid barrier.  Returns false (in every thread) if this CTA gave up.
+// `arrive` is false only under the test fault injection (a CTA that never
+// arrives, so every wait runs into its bound).
+__device__ bool grid_barrier(unsigned *bar, int *abort_flag, unsigned target,
+                             long long timeout_ns, int *s_flag, bool arrive = true) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (arrive) atomicAdd(bar, 1u);
+        int ok = 1;
+        unsigned long long t0 = global_ns();
+        unsigned spins = 0;
+        while (ld_acquire(bar) < target) {
+            if ((++spins & 63u) == 0) {
+                if (*(volatile int *)abort_flag) { ok = 0; break; }
+                if ((long long)(global_ns() - t0) > timeout_ns) {
+                    atomicExch(abort_flag, 1);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-sum NV values; thread 0 writes them to partials[slot][v][cta].
+template <int NV>
+__device__ void block_partials(double (&v)[NV], double *red, double *partials, int slot,
+                               int grid) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+    if (l == 0)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) red[q * 32 + w] = v[q];
+    __syncthreads();
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = l < nw ? red[q * 32 + l] : 0.0;
+            t = warp_sum(t);
+            if (l == 0) partials[(slot * 4 + q) * grid + blockIdx.x] = t;
+        }
+    }
+}
+
+// After a barrier: every CTA sums the G partials of `slot` in the same order;
+// the NV totals go through the shared slots `out_sm` to every thread.
+template <int NV>
+__device__ void grid_totals(const double *partials, int slot, int grid, double *out_sm,
+                            double (&out)[NV]) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (w == 0) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double t = 0.0;
+            for (int g = l; g < grid; g += 32) t += __ldcg(partials + (slot * 4 + q) * grid + g);
+            t = warp_sum(t);
+            if (l == 0) out_sm[q] = t;
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = out_sm[q];
+    __syncthreads();
+}
+
+// Block-sum NV values with a shared-memory tree; thread 0 writes them to
+// partials[slot][v][cta].  `red` holds NV * blockDim.x doubles.  On GB300 a
+// warp-wide FP64 add occupies the FP64 pipe for ~64 cycles, so the tree
+// halves the number of participating warps at each level instead of running
+// a 5-level shuffle tree in every warp (about 20 warp-wide adds per value
+// instead of 85 for 512 threads).  blockDim.x must be a multiple of 128.
+template <int NV>
+__device__ void block_partials_tree(double (&v)[NV], double *red, double *partials, int slot,
+                                    int grid) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[q * nt + tid] = v[q];
+    __syncthreads();
+    const int quarter = nt >> 2;
+    if (tid < quarter) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            double *r = red + q * nt;
+            r[tid] = (r[tid] + r[tid + quarter]) + (r[tid + 2 * quarter] + r[tid + 3 * quarter]);
+        }
+    }
+    __syncthreads();
+    if (tid < 32) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            const double *r = red + q * nt;
+            double t = 0.0;
+            for (int k = tid; k < quarter; k += 32) t += r[k];
+            t = warp_sum(t);
+            if (tid == 0) partials[(slot * 4 + q) * grid + blockIdx.x] = t;
+        }
+    }
+}
+
+}  // namespace
+}  // namespace pcgdev
+}  // namespace airga

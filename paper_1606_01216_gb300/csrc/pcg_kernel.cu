@@ -26,103 +26,17 @@
 // * The barrier is a monotone arrival counter with a bounded wait (global
 //   timer); a CTA that gives up sets an abort flag that ends the others'
 //   waits, and the column's status becomes AIRGA_E_TIMEOUT.
-#include "airga_internal.cuh"
+#include "pcg_common.cuh"
 
 namespace airga {
 namespace {
+
+using namespace pcgdev;
 
 constexpr int kPcgThreads = 512;
 constexpr int kMinRowsPerCta = 128;
 
 enum Mode { kIdentity = 0, kBand1 = 1, kChain = 2 };
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-// Bounded grid barrier.  Returns false (in every thread) if this CTA gave up.
-// `arrive` is false only under the test fault injection (a CTA that never
-// arrives, so every wait runs into its bound).
-__device__ bool grid_barrier(unsigned *bar, int *abort_flag, unsigned target,
-                             long long timeout_ns, int *s_flag, bool arrive = true) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (arrive) atomicAdd(bar, 1u);
-        int ok = 1;
-        unsigned long long t0 = global_ns();
-        unsigned spins = 0;
-        while (ld_acquire(bar) < target) {
-            if ((++spins & 63u) == 0) {
-                if (*(volatile int *)abort_flag) { ok = 0; break; }
-                if ((long long)(global_ns() - t0) > timeout_ns) {
-                    atomicExch(abort_flag, 1);
-                    ok = 0;
-                    break;
-                }
-            }
-        }
-        __threadfence();
-        *s_flag = ok;
-    }
-    __syncthreads();
-    return *s_flag != 0;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
-// Block-sum NV values; thread 0 writes them to partials[slot][v][cta].
-template <int NV>
-__device__ void block_partials(double (&v)[NV], double *red, double *partials, int slot,
-                               int grid) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) v[q] = warp_sum(v[q]);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (l == 0)
-#pragma unroll
-        for (int q = 0; q < NV; ++q) red[q * 32 + w] = v[q];
-    __syncthreads();
-    if (w == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double t = l < nw ? red[q * 32 + l] : 0.0;
-            t = warp_sum(t);
-            if (l == 0) partials[(slot * 4 + q) * grid + blockIdx.x] = t;
-        }
-    }
-}
-
-// After a barrier: every CTA sums the G partials of `slot` in the same order.
-template <int NV>
-__device__ void grid_totals(const double *partials, int slot, int grid, double *red,
-                            double (&out)[NV]) {
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (w == 0) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double t = 0.0;
-            for (int g = l; g < grid; g += 32) t += __ldcg(partials + (slot * 4 + q) * grid + g);
-            t = warp_sum(t);
-            if (l == 0) red[128 + q] = t;
-        }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int q = 0; q < NV; ++q) out[q] = red[128 + q];
-    __syncthreads();
-}
 
 // One row of (band) x from a window buffer holding rows [wbase, ...).
 __device__ __forceinline__ double stencil(const double *__restrict__ band, int64_t n, int64_t i,
@@ -265,7 +179,7 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
         goto finish;
     }
     double tot0[3];
-    grid_totals<3>(a.partials, bar_no & 1, G, red, tot0);
+    grid_totals<3>(a.partials, bar_no & 1, G, red + 128, tot0);
     ++bar_no;
     {
         double rz = tot0[0];
@@ -309,7 +223,7 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
                 goto finish;
             }
             double pqt[1];
-            grid_totals<1>(a.partials, bar_no & 1, G, red, pqt);
+            grid_totals<1>(a.partials, bar_no & 1, G, red + 128, pqt);
             ++bar_no;
             const double pq = pqt[0];
             if (!(pq > 0.0) || !isfinite(pq)) {
@@ -351,7 +265,7 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
                 goto finish;
             }
             double t2v[2];
-            grid_totals<2>(a.partials, bar_no & 1, G, red, t2v);
+            grid_totals<2>(a.partials, bar_no & 1, G, red + 128, t2v);
             ++bar_no;
             iters = k;
             rn = sqrt(t2v[1]);
@@ -397,11 +311,36 @@ int mode_of(int nf, bool psym_path) {
 
 }  // namespace
 
-int pcg_plan(int64_t n, int nf, bool psym_path, int device, PcgPlan *plan) {
+int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgPlan *plan) {
     const int mode = mode_of(nf, psym_path);
     int sms = 0, optin = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    // node-pair kernel: even n, aligned operands, state in shared memory
+    if (mode != kChain && aligned16 && n % 2 == 0) {
+        int64_t want_p = (n + kMinRowsPerCta - 1) / kMinRowsPerCta;
+        int grid_p = (int)(want_p < sms ? want_p : sms);
+        if (grid_p < 1) grid_p = 1;
+        int64_t Rp = (n + grid_p - 1) / grid_p;
+        Rp += Rp & 1;
+        const size_t smem_p = pcg_pair_smem(Rp);
+        if (smem_p + 256 <= (size_t)optin) {
+            int per_sm = 0;
+            int st = pcg_pair_occupancy(mode == kIdentity ? 0 : 1, smem_p, &per_sm);
+            if (st) return st;
+            if (per_sm >= 1 && grid_p <= per_sm * sms) {
+                plan->kind = 2;
+                plan->threads = pcg_pair_threads();
+                plan->halo = 8;
+                plan->grid = grid_p;
+                plan->rows = Rp;
+                plan->smem_state = true;
+                plan->smem_bytes = smem_p;
+                plan->scratch_doubles = 0;
+                return AIRGA_OK;
+            }
+        }
+    }
     const int H = mode == kIdentity ? 3 : (mode == kBand1 ? 6 : 3 + 3 * nf);
     const size_t static_smem = 160 * sizeof(double) + 64;
     // grid: one CTA per SM at most (the state fills shared memory), fewer for
@@ -417,6 +356,7 @@ int pcg_plan(int64_t n, int nf, bool psym_path, int device, PcgPlan *plan) {
     plan->grid = grid;
     plan->rows = R;
     plan->smem_state = (mode != kChain) && (smem + static_smem <= (size_t)optin);
+    plan->kind = plan->smem_state ? 0 : 1;
     plan->smem_bytes = plan->smem_state ? smem : 0;
     const size_t slice = (size_t)(R + (R + 2 * H) + (R + 2 * H + 6) + (R + 6) + 2 * (R + 2 * H));
     plan->scratch_doubles = plan->smem_state ? 0 : slice * (size_t)grid;
@@ -455,6 +395,7 @@ int pcg_plan(int64_t n, int nf, bool psym_path, int device, PcgPlan *plan) {
 }
 
 cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
+    if (plan.kind == 2) return launch_pcg_pair(plan, args, s);
     const int mode = mode_of(args.nf, args.psym != nullptr);
     if (plan.smem_state) {
         if (mode == kIdentity) return launch_mode<true, kIdentity>(plan, args, s);

@@ -1,0 +1,353 @@
+// Persistent PCG, node-pair form (shared-memory state, n even).
+//
+// Same recurrence, ownership, halo and barrier scheme as pcg_kernel.cu (see
+// the comment there); what changes is how a CTA walks its rows:
+//
+// * Each thread owns row PAIRS (i, i+1), i even — for the beam these are the
+//   two DOFs (w, theta) of one node.  Band loads are double2 (both rows of a
+//   diagonal in one 16-byte load) and the seven window values a pair needs
+//   on each side come from five double2 shared-memory loads.
+// * Structure-aware A stencil: for the Hermite-cubic beam the band-7 rows
+//   have two exact zeros each — the structural +-3 corner and the w_k/theta_k
+//   coupling that cancels between neighbouring elements (even rows: offsets
+//   -3 and +1; odd rows: +3 and -1; every row but the free-end pair).  When
+//   the matrix carries that flag (checked on the device when the matrix is
+//   made) the A stencil issues 5 FP64 FMAs per row instead of 7; FP64 issue
+//   is the binding resource on GB300 (2 FMA/clk/SM).
+// * Reductions use the shared-memory tree of pcg_common.cuh.
+//
+// Windows (global rows, all bases even so double2 accesses stay aligned):
+//   x  [lo, hi)              own rows
+//   r  [lo-8, hi+8)          z on own +-4 needs r on own +-7
+//   p  [lo-12, hi+12)        q on r's halo needs p on own +-11
+//   zq [lo-4, hi+4)          z (then q on own rows)
+// Out-of-matrix window slots are zero.  Boundary rows of p (first/last 12)
+// go to `pbuf` before barrier 1; the outer p halo is read back after it.
+#include "pcg_common.cuh"
+
+namespace airga {
+namespace {
+
+using namespace pcgdev;
+
+constexpr int kThreads = 512;
+constexpr int HR = 8, HP = 12, HZ = 4;
+
+__device__ __forceinline__ void load_band_pair(const double *__restrict__ band, int64_t n,
+                                               int64_t i, double2 (&a)[kBand]) {
+#pragma unroll
+    for (int d = 0; d < kBand; ++d)
+        a[d] = __ldg(reinterpret_cast<const double2 *>(band + (int64_t)d * n + i));
+}
+
+// v[k] = window row i-4+k, k = 0..9 (five aligned double2 loads)
+__device__ __forceinline__ void load_win(const double *w, int64_t wbase, int64_t i,
+                                         double (&v)[10]) {
+    const double2 *w2 = reinterpret_cast<const double2 *>(w + (i - 4 - wbase));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double2 t = w2[k];
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+
+// (y_i, y_{i+1}) = band-7 rows i, i+1 applied to the window values v.
+__device__ __forceinline__ double2 pair_full(const double2 (&a)[kBand], const double (&v)[10]) {
+    double y0 = a[0].x * v[1], y1 = a[0].y * v[2];
+#pragma unroll
+    for (int d = 1; d < kBand; ++d) {
+        y0 = fma(a[d].x, v[1 + d], y0);
+        y1 = fma(a[d].y, v[2 + d], y1);
+    }
+    return make_double2(y0, y1);
+}
+
+// Same with the beam's exact zeros skipped: even row drops d = 0 (-3) and
+// d = 4 (+1); odd row drops d = 6 (+3) and d = 2 (-1).  The free-end pair
+// (i = n-2) keeps its +-1 couplings.
+__device__ __forceinline__ double2 pair_beam(const double2 (&a)[kBand], const double (&v)[10],
+                                             bool last) {
+    double y0 = a[1].x * v[2];
+    y0 = fma(a[2].x, v[3], y0);
+    y0 = fma(a[3].x, v[4], y0);
+    y0 = fma(a[5].x, v[6], y0);
+    y0 = fma(a[6].x, v[7], y0);
+    double y1 = a[0].y * v[2];
+    y1 = fma(a[1].y, v[3], y1);
+    y1 = fma(a[3].y, v[5], y1);
+    y1 = fma(a[4].y, v[6], y1);
+    y1 = fma(a[5].y, v[7], y1);
+    if (last) {
+        y0 = fma(a[4].x, v[5], y0);
+        y1 = fma(a[2].y, v[4], y1);
+    }
+    return make_double2(y0, y1);
+}
+
+template <int MODE>   // 0: identity, 1: one symmetric band
+__global__ void __launch_bounds__(kThreads, 1)
+pcg_pair_kernel(PcgArgs a, int64_t R) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ double tot[8];
+    __shared__ int s_flag;
+
+    const int G = gridDim.x;
+    const int64_t n = a.n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * R < n ? (int64_t)blockIdx.x * R : n;
+    const int64_t hi = lo + R < n ? lo + R : n;
+
+    double *xs = smem;
+    double *rs = xs + R;
+    double *ps = rs + (R + 2 * HR);
+    double *zq = ps + (R + 2 * HP);
+    double *red = zq + (R + 2 * HZ);
+    const int64_t xbase = lo, rbase = lo - HR, pbase = lo - HP, zbase = lo - HZ;
+    const int64_t rlo = lo - HR > 0 ? lo - HR : 0, rhi = hi + HR < n ? hi + HR : n;
+    const int64_t zlo = lo - HZ > 0 ? lo - HZ : 0, zhi = hi + HZ < n ? hi + HZ : n;
+    const int64_t bw = HP < (hi - lo) ? HP : (hi - lo);
+    const bool beam = a.pairz != nullptr && *a.pairz != 0;
+    const double *Pb = MODE == 1 ? (a.psym ? a.psym : a.fac[0]) : nullptr;
+
+    auto stencil_A = [&](int64_t i, const double *w, int64_t wbase) {
+        double2 ab[kBand];
+        load_band_pair(a.A, n, i, ab);
+        double v[10];
+        load_win(w, wbase, i, v);
+        return beam ? pair_beam(ab, v, i == n - 2) : pair_full(ab, v);
+    };
+
+    // zero every window (out-of-matrix slots must read as 0)
+    {
+        const int64_t total = 4 * R + 2 * (HR + HP + HZ);
+        for (int64_t k = tid; k < total; k += nt) smem[k] = 0.0;
+    }
+    __syncthreads();
+
+    unsigned bar_no = 0;
+    const long long tmo = a.timeout_ns;
+    int status = AIRGA_E_MAXIT;
+    int iters = 0;
+
+    // ---- x_0, r_0 = b - A x_0 on own +- HR, z_0 = M r_0 on own +- HZ ----
+    for (int64_t i = lo + tid; i < hi; i += nt) xs[i - xbase] = a.warm ? a.x[i] : 0.0;
+    for (int64_t i = rlo + tid; i < rhi; i += nt) {
+        double v = a.b[i];
+        if (a.warm) {
+            double ax = 0.0;
+#pragma unroll
+            for (int d = 0; d < kBand; ++d) {
+                const int64_t c = i + d - kHalf;
+                if (c >= 0 && c < n) ax = fma(__ldg(a.A + (int64_t)d * n + i), a.x[c], ax);
+            }
+            v -= ax;
+        }
+        rs[i - rbase] = v;
+    }
+    __syncthreads();
+    auto apply_M = [&]() {
+        for (int64_t i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
+            double2 z;
+            if (MODE == 1) {
+                double2 pb[kBand];
+                load_band_pair(Pb, n, i, pb);
+                double v[10];
+                load_win(rs, rbase, i, v);
+                z = pair_full(pb, v);
+            } else {
+                z = *reinterpret_cast<const double2 *>(rs + (i - rbase));
+            }
+            *reinterpret_cast<double2 *>(zq + (i - zbase)) = z;
+        }
+    };
+    apply_M();
+    __syncthreads();
+    {
+        double v[3] = {0.0, 0.0, 0.0};
+        for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+            const double2 r = *reinterpret_cast<const double2 *>(rs + (i - rbase));
+            const double2 z = *reinterpret_cast<const double2 *>(zq + (i - zbase));
+            const double2 b = *reinterpret_cast<const double2 *>(a.b + i);
+            v[0] = fma(r.x, z.x, fma(r.y, z.y, v[0]));
+            v[1] = fma(r.x, r.x, fma(r.y, r.y, v[1]));
+            v[2] = fma(b.x, b.x, fma(b.y, b.y, v[2]));
+        }
+        block_partials_tree<3>(v, red, a.partials, bar_no & 1, G);
+    }
+    if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+        status = AIRGA_E_TIMEOUT;
+        goto finish;
+    }
+    double t0[3];
+    grid_totals<3>(a.partials, bar_no & 1, G, tot, t0);
+    ++bar_no;
+    {
+        double rz = t0[0];
+        const double nb = sqrt(t0[2]);
+        double rn = sqrt(t0[1]);
+        if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[0] = nb > 0.0 ? rn / nb : 0.0;
+        if (nb == 0.0) {
+            for (int64_t i = lo + tid; i < hi; i += nt) xs[i - xbase] = 0.0;
+            status = AIRGA_OK;
+            goto finish;
+        }
+        if (rn <= a.tol * nb) { status = AIRGA_OK; goto finish; }
+        if (!isfinite(rz) || rz == 0.0) { status = AIRGA_E_BREAKDOWN; goto finish; }
+
+        double beta = 0.0;
+        for (int k = 1; k <= a.maxit; ++k) {
+            // ---- phase 1: p = z + beta p on own +- 4, boundary rows out, q = A p ----
+            for (int64_t i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
+                double2 *pp = reinterpret_cast<double2 *>(ps + (i - pbase));
+                const double2 z = *reinterpret_cast<const double2 *>(zq + (i - zbase));
+                if (k == 1) {
+                    *pp = z;
+                } else {
+                    double2 p = *pp;
+                    p.x = fma(beta, p.x, z.x);
+                    p.y = fma(beta, p.y, z.y);
+                    *pp = p;
+                }
+            }
+            __syncthreads();
+            for (int64_t t = tid; t < 2 * bw; t += nt) {
+                const int64_t i = t < bw ? lo + t : hi - bw + (t - bw);
+                a.pbuf[i] = ps[i - pbase];
+            }
+            double vq[1] = {0.0};
+            for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                const double2 q = stencil_A(i, ps, pbase);
+                *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
+                const double2 p = *reinterpret_cast<const double2 *>(ps + (i - pbase));
+                vq[0] = fma(p.x, q.x, fma(p.y, q.y, vq[0]));
+            }
+            block_partials_tree<1>(vq, red, a.partials, bar_no & 1, G);
+            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+                status = AIRGA_E_TIMEOUT;
+                iters = k - 1;
+                goto finish;
+            }
+            double pqt[1];
+            grid_totals<1>(a.partials, bar_no & 1, G, tot, pqt);
+            ++bar_no;
+            const double pq = pqt[0];
+            if (!(pq > 0.0) || !isfinite(pq)) {
+                status = AIRGA_E_BREAKDOWN;
+                iters = k - 1;
+                goto finish;
+            }
+            const double alpha = rz / pq;
+
+            // ---- phase 2: outer p halo in, x and r updates, r halo, z = M r ----
+            for (int64_t t = tid; t < 2 * (HP - HZ); t += nt) {
+                const int64_t i = t < HP - HZ ? lo - HP + t : hi + HZ + (t - (HP - HZ));
+                if (i >= 0 && i < n) ps[i - pbase] = __ldcg(a.pbuf + i);
+            }
+            for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                double2 *xp = reinterpret_cast<double2 *>(xs + (i - xbase));
+                double2 *rp = reinterpret_cast<double2 *>(rs + (i - rbase));
+                const double2 p = *reinterpret_cast<const double2 *>(ps + (i - pbase));
+                const double2 q = *reinterpret_cast<const double2 *>(zq + (i - zbase));
+                double2 x = *xp, r = *rp;
+                x.x = fma(alpha, p.x, x.x);
+                x.y = fma(alpha, p.y, x.y);
+                r.x = fma(-alpha, q.x, r.x);
+                r.y = fma(-alpha, q.y, r.y);
+                *xp = x;
+                *rp = r;
+            }
+            __syncthreads();
+            for (int64_t t = tid; t < HR; t += nt) {          // HR/2 pairs on each side
+                const int64_t i = t < HR / 2 ? lo - HR + 2 * t : hi + 2 * (t - HR / 2);
+                if (i < 0 || i >= n) continue;
+                const double2 q = stencil_A(i, ps, pbase);
+                double2 *rp = reinterpret_cast<double2 *>(rs + (i - rbase));
+                double2 r = *rp;
+                r.x = fma(-alpha, q.x, r.x);
+                r.y = fma(-alpha, q.y, r.y);
+                *rp = r;
+            }
+            __syncthreads();
+            apply_M();
+            __syncthreads();
+            double v2[2] = {0.0, 0.0};
+            for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                const double2 r = *reinterpret_cast<const double2 *>(rs + (i - rbase));
+                const double2 z = *reinterpret_cast<const double2 *>(zq + (i - zbase));
+                v2[0] = fma(r.x, z.x, fma(r.y, z.y, v2[0]));
+                v2[1] = fma(r.x, r.x, fma(r.y, r.y, v2[1]));
+            }
+            block_partials_tree<2>(v2, red, a.partials, bar_no & 1, G);
+            const bool arrive = !(a.fault_skip_arrival && k == 1 && blockIdx.x == 0);
+            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
+                              arrive)) {
+                status = AIRGA_E_TIMEOUT;
+                iters = k;
+                goto finish;
+            }
+            double t2v[2];
+            grid_totals<2>(a.partials, bar_no & 1, G, tot, t2v);
+            ++bar_no;
+            iters = k;
+            rn = sqrt(t2v[1]);
+            if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[k] = rn / nb;
+            if (rn <= a.tol * nb) { status = AIRGA_OK; break; }
+            const double rz_new = t2v[0];
+            if (!isfinite(rz_new) || rz_new == 0.0) { status = AIRGA_E_BREAKDOWN; break; }
+            beta = rz_new / rz;
+            rz = rz_new;
+        }
+    }
+finish:
+    __syncthreads();
+    for (int64_t i = lo + tid; i < hi; i += nt) a.x[i] = xs[i - xbase];
+    if (blockIdx.x == 0 && tid == 0) {
+        *a.iters = iters;
+        *a.status = status;
+    }
+}
+
+template <int MODE>
+cudaError_t launch_pair_mode(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
+    auto kern = pcg_pair_kernel<MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)plan.smem_bytes);
+    if (e != cudaSuccess) return e;
+    PcgArgs a = args;
+    int64_t R = plan.rows;
+    void *kargs[] = {(void *)&a, (void *)&R};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(plan.grid), dim3(plan.threads),
+                                       kargs, plan.smem_bytes, s);
+}
+
+}  // namespace
+
+size_t pcg_pair_smem(int64_t R) {
+    return (size_t)(4 * R + 2 * (HR + HP + HZ) + 3 * kThreads) * sizeof(double);
+}
+
+int pcg_pair_threads() { return kThreads; }
+
+int pcg_pair_occupancy(int mode, size_t smem, int *per_sm) {
+    cudaError_t e;
+    if (mode == 0) {
+        e = cudaFuncSetAttribute(pcg_pair_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<0>, kThreads, smem);
+    } else {
+        e = cudaFuncSetAttribute(pcg_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<1>, kThreads, smem);
+    }
+    return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg pair occupancy");
+}
+
+cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
+    if (args.nf == 0) return launch_pair_mode<0>(plan, args, s);
+    return launch_pair_mode<1>(plan, args, s);
+}
+
+}  // namespace airga

@@ -85,8 +85,10 @@ extern "C" int airga_pcg_solve_noalloc(int64_t n, const double *A_band, const do
     int dev = 0;
     AIRGA_CUDA(cudaGetDevice(&dev));
     const int nf = M_band ? 1 : 0;
+    const bool al = ((uintptr_t)A_band & 15u) == 0 && ((uintptr_t)F & 15u) == 0 &&
+                    ((uintptr_t)X & 15u) == 0 && ((uintptr_t)M_band & 15u) == 0;
     PcgPlan plan;
-    st = pcg_plan(n, nf, nf == 1, dev, &plan);
+    st = pcg_plan(n, nf, nf == 1, al, dev, &plan);
     if (st) return st;
     if (!plan.smem_state || plan.scratch_doubles != 0)
         return fail(AIRGA_E_INVALID_ARG,

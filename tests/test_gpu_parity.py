@@ -424,3 +424,62 @@ def test_full_size_beam(G, s):
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
     true = np.linalg.norm(F - O.spmv(Ao, x)) / np.linalg.norm(F)
     assert true <= 2e-10
+
+
+# ---------------------------------------------------------------------------
+# kernel-variant coverage: odd n (generic kernel) and an even-n matrix whose
+# beam zero structure is broken (node-pair kernel, full stencil)
+# ---------------------------------------------------------------------------
+
+def random_spd_band(n, seed):
+    """Symmetric, strictly diagonally dominant band-7 matrix (CSR, full band)."""
+    rng = np.random.default_rng(seed)
+    rp, ci = W.band_pattern(n)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    A = np.zeros((7, n))
+    for d in range(1, 4):
+        v = rng.uniform(-1.0, 1.0, n - d)
+        A[3 + d, : n - d] = v           # (i, i+d)
+        A[3 - d, d:] = v                # (i+d, i)
+    A[3] = np.abs(A).sum(axis=0) + rng.uniform(0.5, 2.0, n)
+    vals = A[ci.astype(np.int64) - rows + 3, rows]
+    return O.CSR(n, rp, ci, vals)
+
+
+@pytest.mark.parametrize("n", [2001, 777])
+def test_pcg_generic_odd_n(G, n):
+    Ao = random_spd_band(n, n)
+    A = G.mat_from_csr(n, torch.from_numpy(Ao.rowptr).cuda(), torch.from_numpy(Ao.col).cuda(),
+                       torch.from_numpy(Ao.val).cuda())
+    P = G.spai_build(A)
+    Po = O.spai(Ao)
+    assert column_errors(G.precond_factor(P, 0).cpu().numpy(), Po).max() <= 1e-10
+    F = np.random.default_rng(1).standard_normal(n)
+    res = run_pcg(G, A, P, F)
+    x_o, it_o, st_o, _ = O.pcg(Ao, F, [Po], tol=1e-10, maxit=5000)
+    x = res["X"].cpu().numpy()
+    assert int(res["status"][0]) == G.OK and st_o == O.OK
+    assert np.linalg.norm(x - x_o) <= 1e-8 * np.linalg.norm(x_o)
+    assert abs(int(res["iters"][0]) - it_o) <= 1
+
+
+def test_pcg_even_n_without_beam_structure(G):
+    beam = W.beam(2000)
+    k_val = beam.k_val.copy()
+    rows = np.repeat(np.arange(beam.n), np.diff(beam.rowptr))
+    # break one cancelled w/theta coupling symmetrically (rows 100 and 101)
+    for (r, c) in ((100, 101), (101, 100)):
+        k = np.nonzero((rows == r) & (beam.col == c))[0][0]
+        k_val[k] = 0.25
+    beam.k_val = k_val
+    M, K = G.beam_mats(beam)
+    A = G.assemble_shifted(M, K, AL, BE, 3.0)
+    P = G.spai_build(A)
+    Ao = O.shifted_csr(beam, AL, BE, 3.0)
+    F = W.loads(beam.n)[:, 0]
+    res = run_pcg(G, A, P, F)
+    x_o, it_o, st_o, _ = O.pcg(Ao, F, [O.spai(Ao)], tol=1e-10, maxit=5000)
+    x = res["X"].cpu().numpy()
+    assert int(res["status"][0]) == G.OK and st_o == O.OK
+    assert np.linalg.norm(x - x_o) <= 1e-8 * np.linalg.norm(x_o)
+    assert abs(int(res["iters"][0]) - it_o) <= 1
