@@ -27,8 +27,9 @@ __device__ bool grid_barrier(unsigned *bar, int *abort_flag, unsigned target,
                              long long timeout_ns, int *s_flag, bool arrive = true) {
     __syncthreads();
     if (threadIdx.x == 0) {
-        __threadfence();
-        if (arrive) atomicAdd(bar, 1u);
+        // release-reduction: orders this CTA's writes (gathered by the CTA
+        // barrier above) before the arrival, without a separate fence
+        if (arrive) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
         int ok = 1;
         unsigned long long t0 = global_ns();
         unsigned spins = 0;
@@ -42,7 +43,6 @@ __device__ bool grid_barrier(unsigned *bar, int *abort_flag, unsigned target,
                 }
             }
         }
-        __threadfence();
         *s_flag = ok;
     }
     __syncthreads();

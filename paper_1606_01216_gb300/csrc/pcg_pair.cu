@@ -19,10 +19,15 @@
 // Windows (global rows, all bases even so double2 accesses stay aligned):
 //   x  [lo, hi)              own rows
 //   r  [lo-8, hi+8)          z on own +-4 needs r on own +-7
-//   p  [lo-12, hi+12)        q on r's halo needs p on own +-11
+//   p  [lo-4, hi+4)          q on own rows (and p itself on own +-4)
 //   zq [lo-4, hi+4)          z (then q on own rows)
 // Out-of-matrix window slots are zero.  Boundary rows of p (first/last 12)
-// go to `pbuf` before barrier 1; the outer p halo is read back after it.
+// go to `pbuf` before barrier 1.  The r halo (4 pairs per side) is updated by
+// the last 8 threads from p read straight out of `pbuf` and from A's halo
+// rows cached in shared memory at launch; that work overlaps the interior
+// z = M r pairs, and only the 8 boundary z pairs wait for it.  Convergence is
+// tested as r.r <= (tol ||b||)^2, keeping square roots off the per-iteration
+// critical path.
 #include "pcg_common.cuh"
 
 namespace airga {
@@ -32,6 +37,7 @@ using namespace pcgdev;
 
 constexpr int kThreads = 512;
 constexpr int HR = 8, HP = 12, HZ = 4;
+constexpr int kHaloPairs = HR;   // 4 pairs of r halo on each side
 
 __device__ __forceinline__ void load_band_pair(const double *__restrict__ band, int64_t n,
                                                int64_t i, double2 (&a)[kBand]) {
@@ -101,27 +107,36 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
     double *xs = smem;
     double *rs = xs + R;
     double *ps = rs + (R + 2 * HR);
-    double *zq = ps + (R + 2 * HP);
-    double *red = zq + (R + 2 * HZ);
-    const int64_t xbase = lo, rbase = lo - HR, pbase = lo - HP, zbase = lo - HZ;
+    double *zq = ps + (R + 2 * HZ);
+    double2 *ah = reinterpret_cast<double2 *>(zq + (R + 2 * HZ));   // A rows of the r halo
+    double *red = reinterpret_cast<double *>(ah + kHaloPairs * kBand);
+    const int64_t xbase = lo, rbase = lo - HR, pbase = lo - HZ, zbase = lo - HZ;
     const int64_t rlo = lo - HR > 0 ? lo - HR : 0, rhi = hi + HR < n ? hi + HR : n;
     const int64_t zlo = lo - HZ > 0 ? lo - HZ : 0, zhi = hi + HZ < n ? hi + HZ : n;
+    // z / p pairs split into boundary (left, right) and interior ranges
+    const int64_t left_end = lo + HZ < hi ? lo + HZ : hi;
+    const int64_t right_start = hi - HZ > left_end ? hi - HZ : left_end;
     const int64_t bw = HP < (hi - lo) ? HP : (hi - lo);
     const bool beam = a.pairz != nullptr && *a.pairz != 0;
     const double *Pb = MODE == 1 ? (a.psym ? a.psym : a.fac[0]) : nullptr;
+    // r-halo pairs are recomputed by the last kHaloPairs threads (they own
+    // one pair fewer than the first threads when R/2 is not a multiple of nt)
+    const int hslot = nt - 1 - tid;                  // 0..7 for the halo threads
+    const bool halo_thread = hslot < kHaloPairs;
+    const int64_t hpair = hslot < kHaloPairs / 2 ? lo - HR + 2 * hslot
+                                                 : hi + 2 * (hslot - kHaloPairs / 2);
+    const bool hvalid = halo_thread && hpair >= 0 && hpair < n;
 
-    auto stencil_A = [&](int64_t i, const double *w, int64_t wbase) {
-        double2 ab[kBand];
-        load_band_pair(a.A, n, i, ab);
-        double v[10];
-        load_win(w, wbase, i, v);
-        return beam ? pair_beam(ab, v, i == n - 2) : pair_full(ab, v);
-    };
-
-    // zero every window (out-of-matrix slots must read as 0)
+    // zero every window (out-of-matrix slots must read as 0), cache A's halo rows
     {
-        const int64_t total = 4 * R + 2 * (HR + HP + HZ);
+        const int64_t total = 4 * R + 2 * (HR + 2 * HZ);
         for (int64_t k = tid; k < total; k += nt) smem[k] = 0.0;
+        if (hvalid) {
+            double2 t[kBand];
+            load_band_pair(a.A, n, hpair, t);
+#pragma unroll
+            for (int d = 0; d < kBand; ++d) ah[hslot * kBand + d] = t[d];
+        }
     }
     __syncthreads();
 
@@ -146,8 +161,10 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
         rs[i - rbase] = v;
     }
     __syncthreads();
-    auto apply_M = [&]() {
-        for (int64_t i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
+    // z = M r for the pairs [from, to) (stride 2 nt starting at this thread's
+    // slot); r.z and r.r of own pairs accumulate into v2
+    auto apply_M = [&](int64_t from, int64_t to, double (&v2)[2]) {
+        for (int64_t i = from + 2 * tid; i < to; i += 2 * nt) {
             double2 z;
             if (MODE == 1) {
                 double2 pb[kBand];
@@ -159,18 +176,19 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
                 z = *reinterpret_cast<const double2 *>(rs + (i - rbase));
             }
             *reinterpret_cast<double2 *>(zq + (i - zbase)) = z;
+            if (i >= lo && i < hi) {
+                const double2 r = *reinterpret_cast<const double2 *>(rs + (i - rbase));
+                v2[0] = fma(r.x, z.x, fma(r.y, z.y, v2[0]));
+                v2[1] = fma(r.x, r.x, fma(r.y, r.y, v2[1]));
+            }
         }
     };
-    apply_M();
-    __syncthreads();
     {
-        double v[3] = {0.0, 0.0, 0.0};
+        double v2[2] = {0.0, 0.0};
+        apply_M(zlo, zhi, v2);
+        double v[3] = {v2[0], v2[1], 0.0};
         for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
-            const double2 r = *reinterpret_cast<const double2 *>(rs + (i - rbase));
-            const double2 z = *reinterpret_cast<const double2 *>(zq + (i - zbase));
             const double2 b = *reinterpret_cast<const double2 *>(a.b + i);
-            v[0] = fma(r.x, z.x, fma(r.y, z.y, v[0]));
-            v[1] = fma(r.x, r.x, fma(r.y, r.y, v[1]));
             v[2] = fma(b.x, b.x, fma(b.y, b.y, v[2]));
         }
         block_partials_tree<3>(v, red, a.partials, bar_no & 1, G);
@@ -184,20 +202,21 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
     ++bar_no;
     {
         double rz = t0[0];
-        const double nb = sqrt(t0[2]);
-        double rn = sqrt(t0[1]);
-        if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[0] = nb > 0.0 ? rn / nb : 0.0;
+        const double bb = t0[2];
+        const double nb = sqrt(bb);
+        const double thr2 = (a.tol * nb) * (a.tol * nb);     // stop when r.r <= (tol ||b||)^2
+        if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[0] = nb > 0.0 ? sqrt(t0[1]) / nb : 0.0;
         if (nb == 0.0) {
             for (int64_t i = lo + tid; i < hi; i += nt) xs[i - xbase] = 0.0;
             status = AIRGA_OK;
             goto finish;
         }
-        if (rn <= a.tol * nb) { status = AIRGA_OK; goto finish; }
+        if (t0[1] <= thr2) { status = AIRGA_OK; goto finish; }
         if (!isfinite(rz) || rz == 0.0) { status = AIRGA_E_BREAKDOWN; goto finish; }
 
         double beta = 0.0;
         for (int k = 1; k <= a.maxit; ++k) {
-            // ---- phase 1: p = z + beta p on own +- 4, boundary rows out, q = A p ----
+            // ---- phase 1: p = z + beta p on own +- 4; boundary rows out; q = A p ----
             for (int64_t i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
                 double2 *pp = reinterpret_cast<double2 *>(ps + (i - pbase));
                 const double2 z = *reinterpret_cast<const double2 *>(zq + (i - zbase));
@@ -217,10 +236,13 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
             }
             double vq[1] = {0.0};
             for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
-                const double2 q = stencil_A(i, ps, pbase);
+                double2 ab[kBand];
+                load_band_pair(a.A, n, i, ab);
+                double v[10];
+                load_win(ps, pbase, i, v);
+                const double2 q = beam ? pair_beam(ab, v, i == n - 2) : pair_full(ab, v);
                 *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
-                const double2 p = *reinterpret_cast<const double2 *>(ps + (i - pbase));
-                vq[0] = fma(p.x, q.x, fma(p.y, q.y, vq[0]));
+                vq[0] = fma(v[4], q.x, fma(v[5], q.y, vq[0]));
             }
             block_partials_tree<1>(vq, red, a.partials, bar_no & 1, G);
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
@@ -239,10 +261,18 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
             }
             const double alpha = rz / pq;
 
-            // ---- phase 2: outer p halo in, x and r updates, r halo, z = M r ----
-            for (int64_t t = tid; t < 2 * (HP - HZ); t += nt) {
-                const int64_t i = t < HP - HZ ? lo - HP + t : hi + HZ + (t - (HP - HZ));
-                if (i >= 0 && i < n) ps[i - pbase] = __ldcg(a.pbuf + i);
+            // ---- phase 2: x, r updates; r halo (overlapped with interior z); z = M r ----
+            double pv[10];
+            if (hvalid) {
+                // p around this halo pair: the outer rows come from their owners
+#pragma unroll
+                for (int q = 0; q < 10; ++q) {
+                    const int64_t row = hpair - 4 + q;
+                    double v = 0.0;
+                    if (row >= 0 && row < n)
+                        v = (row >= lo - HZ && row < hi + HZ) ? ps[row - pbase] : __ldcg(a.pbuf + row);
+                    pv[q] = v;
+                }
             }
             for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
                 double2 *xp = reinterpret_cast<double2 *>(xs + (i - xbase));
@@ -258,26 +288,22 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
                 *rp = r;
             }
             __syncthreads();
-            for (int64_t t = tid; t < HR; t += nt) {          // HR/2 pairs on each side
-                const int64_t i = t < HR / 2 ? lo - HR + 2 * t : hi + 2 * (t - HR / 2);
-                if (i < 0 || i >= n) continue;
-                const double2 q = stencil_A(i, ps, pbase);
-                double2 *rp = reinterpret_cast<double2 *>(rs + (i - rbase));
+            double v2[2] = {0.0, 0.0};
+            if (hvalid) {
+                double2 t[kBand];
+#pragma unroll
+                for (int d = 0; d < kBand; ++d) t[d] = ah[hslot * kBand + d];
+                const double2 q = beam ? pair_beam(t, pv, hpair == n - 2) : pair_full(t, pv);
+                double2 *rp = reinterpret_cast<double2 *>(rs + (hpair - rbase));
                 double2 r = *rp;
                 r.x = fma(-alpha, q.x, r.x);
                 r.y = fma(-alpha, q.y, r.y);
                 *rp = r;
             }
+            apply_M(left_end, right_start, v2);           // interior: own rows of r only
             __syncthreads();
-            apply_M();
-            __syncthreads();
-            double v2[2] = {0.0, 0.0};
-            for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
-                const double2 r = *reinterpret_cast<const double2 *>(rs + (i - rbase));
-                const double2 z = *reinterpret_cast<const double2 *>(zq + (i - zbase));
-                v2[0] = fma(r.x, z.x, fma(r.y, z.y, v2[0]));
-                v2[1] = fma(r.x, r.x, fma(r.y, r.y, v2[1]));
-            }
+            apply_M(zlo, left_end, v2);                   // boundary pairs need the r halo
+            apply_M(right_start, zhi, v2);
             block_partials_tree<2>(v2, red, a.partials, bar_no & 1, G);
             const bool arrive = !(a.fault_skip_arrival && k == 1 && blockIdx.x == 0);
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
@@ -290,9 +316,8 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
             grid_totals<2>(a.partials, bar_no & 1, G, tot, t2v);
             ++bar_no;
             iters = k;
-            rn = sqrt(t2v[1]);
-            if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[k] = rn / nb;
-            if (rn <= a.tol * nb) { status = AIRGA_OK; break; }
+            if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[k] = sqrt(t2v[1]) / nb;
+            if (t2v[1] <= thr2) { status = AIRGA_OK; break; }
             const double rz_new = t2v[0];
             if (!isfinite(rz_new) || rz_new == 0.0) { status = AIRGA_E_BREAKDOWN; break; }
             beta = rz_new / rz;
@@ -324,7 +349,8 @@ cudaError_t launch_pair_mode(const PcgPlan &plan, const PcgArgs &args, cudaStrea
 }  // namespace
 
 size_t pcg_pair_smem(int64_t R) {
-    return (size_t)(4 * R + 2 * (HR + HP + HZ) + 3 * kThreads) * sizeof(double);
+    return (size_t)(4 * R + 2 * (HR + 2 * HZ) + 2 * kHaloPairs * kBand + 3 * kThreads) *
+           sizeof(double);
 }
 
 int pcg_pair_threads() { return kThreads; }
