@@ -81,15 +81,23 @@ __device__ void block_partials(double (&v)[NV], double *red, double *partials, i
 template <int NV>
 __device__ void grid_totals(const double *partials, int slot, int grid, double *out_sm,
                             double (&out)[NV]) {
+    // warp q sums value q: the NV sums run side by side.  Every lane issues
+    // all of its loads before the first add, so the partials (written by
+    // other SMs, read from L2) cost one round trip instead of one per add.
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (w == 0) {
+    if (w < NV) {
+        const double *src = partials + (slot * 4 + w) * grid;
+        constexpr int kPerLane = 8;                 // up to 256 CTAs in one sweep
+        double v[kPerLane];
 #pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            double t = 0.0;
-            for (int g = l; g < grid; g += 32) t += __ldcg(partials + (slot * 4 + q) * grid + g);
-            t = warp_sum(t);
-            if (l == 0) out_sm[q] = t;
+        for (int j = 0; j < kPerLane; ++j) {
+            const int g = l + 32 * j;
+            v[j] = g < grid ? __ldcg(src + g) : 0.0;
         }
+        double t = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7]));
+        for (int g = l + 32 * kPerLane; g < grid; g += 32) t += __ldcg(src + g);
+        t = warp_sum(t);
+        if (l == 0) out_sm[w] = t;
     }
     __syncthreads();
 #pragma unroll
@@ -119,15 +127,19 @@ __device__ void block_partials_tree(double (&v)[NV], double *red, double *partia
         }
     }
     __syncthreads();
-    if (tid < 32) {
-#pragma unroll
-        for (int q = 0; q < NV; ++q) {
-            const double *r = red + q * nt;
-            double t = 0.0;
-            for (int k = tid; k < quarter; k += 32) t += r[k];
-            t = warp_sum(t);
-            if (tid == 0) partials[(slot * 4 + q) * grid + blockIdx.x] = t;
+    const int w = tid >> 5, l = tid & 31;
+    if (w < NV) {                      // warp q finishes value q
+        const double *r = red + w * nt;
+        double t;
+        if (quarter == 128) {          // 512 threads: four values per lane, loaded together
+            const double a0 = r[l], a1 = r[l + 32], a2 = r[l + 64], a3 = r[l + 96];
+            t = (a0 + a1) + (a2 + a3);
+        } else {
+            t = 0.0;
+            for (int k = l; k < quarter; k += 32) t += r[k];
         }
+        t = warp_sum(t);
+        if (l == 0) partials[(slot * 4 + w) * grid + blockIdx.x] = t;
     }
 }
 

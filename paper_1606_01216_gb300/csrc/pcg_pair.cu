@@ -23,11 +23,12 @@
 //   zq [lo-4, hi+4)          z (then q on own rows)
 // Out-of-matrix window slots are zero.  Boundary rows of p (first/last 12)
 // go to `pbuf` before barrier 1.  The r halo (4 pairs per side) is updated by
-// the last 8 threads from p read straight out of `pbuf` and from A's halo
-// rows cached in shared memory at launch; that work overlaps the interior
-// z = M r pairs, and only the 8 boundary z pairs wait for it.  Convergence is
-// tested as r.r <= (tol ||b||)^2, keeping square roots off the per-iteration
-// critical path.
+// the last 8 threads from p read straight out of `pbuf` (loads issued first)
+// and from A's halo rows cached in shared memory at launch; it depends on no
+// own-row update, so it runs during the x/r sweep and a single CTA barrier
+// precedes z = M r.  Convergence is tested as r.r <= (tol ||b||)^2, keeping
+// square roots off the per-iteration critical path; the residual history is
+// stored as r.r and converted once at exit.
 #include "pcg_common.cuh"
 
 namespace airga {
@@ -97,12 +98,14 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
     extern __shared__ __align__(16) double smem[];
     __shared__ double tot[8];
     __shared__ int s_flag;
+    __shared__ double s_nb;
 
     const int G = gridDim.x;
     const int64_t n = a.n;
     const int tid = threadIdx.x, nt = blockDim.x;
     const int64_t lo = (int64_t)blockIdx.x * R < n ? (int64_t)blockIdx.x * R : n;
     const int64_t hi = lo + R < n ? lo + R : n;
+    if (tid == 0) s_nb = 0.0;
 
     double *xs = smem;
     double *rs = xs + R;
@@ -113,9 +116,6 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
     const int64_t xbase = lo, rbase = lo - HR, pbase = lo - HZ, zbase = lo - HZ;
     const int64_t rlo = lo - HR > 0 ? lo - HR : 0, rhi = hi + HR < n ? hi + HR : n;
     const int64_t zlo = lo - HZ > 0 ? lo - HZ : 0, zhi = hi + HZ < n ? hi + HZ : n;
-    // z / p pairs split into boundary (left, right) and interior ranges
-    const int64_t left_end = lo + HZ < hi ? lo + HZ : hi;
-    const int64_t right_start = hi - HZ > left_end ? hi - HZ : left_end;
     const int64_t bw = HP < (hi - lo) ? HP : (hi - lo);
     const bool beam = a.pairz != nullptr && *a.pairz != 0;
     const double *Pb = MODE == 1 ? (a.psym ? a.psym : a.fac[0]) : nullptr;
@@ -205,7 +205,8 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
         const double bb = t0[2];
         const double nb = sqrt(bb);
         const double thr2 = (a.tol * nb) * (a.tol * nb);     // stop when r.r <= (tol ||b||)^2
-        if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[0] = nb > 0.0 ? sqrt(t0[1]) / nb : 0.0;
+        if (tid == 0) s_nb = nb;
+        if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[0] = t0[1];
         if (nb == 0.0) {
             for (int64_t i = lo + tid; i < hi; i += nt) xs[i - xbase] = 0.0;
             status = AIRGA_OK;
@@ -261,7 +262,7 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
             }
             const double alpha = rz / pq;
 
-            // ---- phase 2: x, r updates; r halo (overlapped with interior z); z = M r ----
+            // ---- phase 2: x, r updates; r halo (beside the x/r sweep); z = M r ----
             double pv[10];
             if (hvalid) {
                 // p around this halo pair: the outer rows come from their owners
@@ -287,9 +288,8 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
                 *xp = x;
                 *rp = r;
             }
-            __syncthreads();
-            double v2[2] = {0.0, 0.0};
             if (hvalid) {
+                // the r halo needs no own-row update: it runs beside the x/r sweep
                 double2 t[kBand];
 #pragma unroll
                 for (int d = 0; d < kBand; ++d) t[d] = ah[hslot * kBand + d];
@@ -300,10 +300,9 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
                 r.y = fma(-alpha, q.y, r.y);
                 *rp = r;
             }
-            apply_M(left_end, right_start, v2);           // interior: own rows of r only
             __syncthreads();
-            apply_M(zlo, left_end, v2);                   // boundary pairs need the r halo
-            apply_M(right_start, zhi, v2);
+            double v2[2] = {0.0, 0.0};
+            apply_M(zlo, zhi, v2);
             block_partials_tree<2>(v2, red, a.partials, bar_no & 1, G);
             const bool arrive = !(a.fault_skip_arrival && k == 1 && blockIdx.x == 0);
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
@@ -316,7 +315,7 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
             grid_totals<2>(a.partials, bar_no & 1, G, tot, t2v);
             ++bar_no;
             iters = k;
-            if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[k] = sqrt(t2v[1]) / nb;
+            if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[k] = t2v[1];
             if (t2v[1] <= thr2) { status = AIRGA_OK; break; }
             const double rz_new = t2v[0];
             if (!isfinite(rz_new) || rz_new == 0.0) { status = AIRGA_E_BREAKDOWN; break; }
@@ -327,9 +326,14 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
 finish:
     __syncthreads();
     for (int64_t i = lo + tid; i < hi; i += nt) a.x[i] = xs[i - xbase];
-    if (blockIdx.x == 0 && tid == 0) {
-        *a.iters = iters;
-        *a.status = status;
+    if (blockIdx.x == 0) {
+        if (a.hist && s_nb > 0.0)       // r.r -> ||r_k|| / ||b||
+            for (int k = tid; k <= iters; k += nt) a.hist[k] = sqrt(a.hist[k]) / s_nb;
+        if (tid == 0) {
+            if (a.hist && !(s_nb > 0.0)) a.hist[0] = 0.0;
+            *a.iters = iters;
+            *a.status = status;
+        }
     }
 }
 
