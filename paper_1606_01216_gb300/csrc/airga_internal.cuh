@@ -53,6 +53,9 @@ struct airga_mat_s {
     // device int32: nonzero when every row pair (2k, 2k+1) but the last has the
     // Hermite-beam zeros (even rows: offsets -3, +1; odd rows: +3, -1)
     std::shared_ptr<void> pairz;
+    // packed copy of the beam's nonzero entries for the PCG row-pair stencil
+    // (5 doubles per row, made on the first solve with this matrix)
+    std::shared_ptr<void> packed;
 };
 
 struct airga_precond_s {
@@ -76,6 +79,10 @@ cudaError_t launch_assemble(int64_t n, const double *M, const double *K, double 
                             double beta, double sh, double *A, cudaStream_t s,
                             const int32_t *fm = nullptr, const int32_t *fk = nullptr,
                             int32_t *fa = nullptr);
+// packed[k n + i], packed[k n + i + 1] (i even, k = 0..4): entries of rows
+// i and i+1 at offsets (-2,-1,0,+2,+3) and (-3,-2,0,+1,+2) — the nonzeros of
+// the beam row pair (n even)
+cudaError_t launch_pack_pairs(int64_t n, const double *band, double *packed, cudaStream_t s);
 // beam zero-structure flag of a band (flag must be preset to nonzero)
 cudaError_t launch_detect_pairz(int64_t n, const double *band, int32_t *flag, cudaStream_t s);
 cudaError_t launch_spmv(int64_t n, const double *band, const double *X, double *Y, int32_t m,
@@ -151,6 +158,7 @@ struct PcgArgs {
     int *abort_flag;               // set by a CTA whose barrier wait timed out
     int fault_skip_arrival;        // test injection: CTA 0 skips its first iteration barrier
     const int32_t *pairz;          // device flag: A has the beam zero structure (may be null)
+    const double *Apk;             // packed beam entries of A (launch_pack_pairs) or null
 };
 
 // process-wide test fault consumed by the next pcg_solve (airga_debug_set_fault)

@@ -562,6 +562,22 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
     a.fault_skip_arrival = take_fault() == AIRGA_FAULT_SKIP_ARRIVAL ? 1 : 0;
     a.pairz = A->pairz ? (const int32_t *)A->pairz.get() : nullptr;
+    if (plan.kind == 2 && A->pairz) {
+        // packed beam entries for the row-pair stencil, made once per matrix
+        if (!A->packed) {
+            st = make_buf(sizeof(double) * 5 * (size_t)n, s, &A->packed);
+            if (st) {
+                dev_free(ws, s);
+                return st;
+            }
+            cudaError_t pe = launch_pack_pairs(n, A->band->d, (double *)A->packed.get(), s);
+            if (pe != cudaSuccess) {
+                dev_free(ws, s);
+                return cuda_fail(pe, "pack pairs");
+            }
+        }
+        a.Apk = (const double *)A->packed.get();
+    }
     a.pbuf = base;
     a.state = base + n_pbuf;
     a.partials = a.state + plan.scratch_doubles;

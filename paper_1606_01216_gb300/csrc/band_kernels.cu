@@ -106,6 +106,23 @@ __global__ void detect_pairz_kernel(int64_t n, const double *__restrict__ band, 
     }
 }
 
+// Packed nonzeros of the beam row pairs: for pair (i, i+1), slot k holds the
+// even row's offset dE[k] and the odd row's offset dO[k].
+__global__ void pack_pairs_kernel(int64_t n, const double *__restrict__ band,
+                                  double *__restrict__ packed) {
+    const int dE[5] = {-2, -1, 0, 2, 3};
+    const int dO[5] = {-3, -2, 0, 1, 2};
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; 2 * j < n;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = 2 * j;
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            packed[k * n + i] = band[(dE[k] + kHalf) * n + i];
+            packed[k * n + i + 1] = band[(dO[k] + kHalf) * n + i + 1];
+        }
+    }
+}
+
 // one row of y = A x for the band-7 stencil (x read through a bounds check)
 __device__ __forceinline__ double band_row(const double *__restrict__ band, int64_t n, int64_t i,
                                            const double *__restrict__ x) {
@@ -294,6 +311,11 @@ cudaError_t launch_assemble(int64_t n, const double *M, const double *K, double 
     int64_t total = (int64_t)kBand * n;
     assemble_kernel<<<grid_for(total / 2 + 1), kThreads, 0, s>>>(total, M, K, cm, ck, A, fm, fk,
                                                                    fa);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_pairs(int64_t n, const double *band, double *packed, cudaStream_t s) {
+    pack_pairs_kernel<<<grid_for(n / 2 + 1), kThreads, 0, s>>>(n, band, packed);
     return cudaGetLastError();
 }
 

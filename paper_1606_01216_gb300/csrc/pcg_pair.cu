@@ -92,6 +92,40 @@ __device__ __forceinline__ double2 pair_beam(const double2 (&a)[kBand], const do
     return make_double2(y0, y1);
 }
 
+// Warm L2 with the 16-byte rows of `count` band arrays of stride n at pair i
+// (no registers held; issued before a barrier so the first loads of the next
+// phase find their lines in L2 instead of DRAM).
+__device__ __forceinline__ void prefetch_pair(const double *band, int64_t n, int64_t i, int count) {
+    for (int k = 0; k < count; ++k)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(band + (int64_t)k * n + i));
+}
+
+// Beam row pair from the packed nonzeros (5 double2 loads = 80 B instead of
+// the band's 112 B): even row offsets (-2,-1,0,+2,+3), odd row
+// (-3,-2,0,+1,+2); the free-end pair adds its +-1 couplings from the band.
+__device__ __forceinline__ double2 pair_packed(const double *__restrict__ pk,
+                                               const double *__restrict__ band, int64_t n,
+                                               int64_t i, const double (&v)[10]) {
+    double2 c[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) c[k] = __ldg(reinterpret_cast<const double2 *>(pk + k * n + i));
+    double y0 = c[0].x * v[2];
+    y0 = fma(c[1].x, v[3], y0);
+    y0 = fma(c[2].x, v[4], y0);
+    y0 = fma(c[3].x, v[6], y0);
+    y0 = fma(c[4].x, v[7], y0);
+    double y1 = c[0].y * v[2];
+    y1 = fma(c[1].y, v[3], y1);
+    y1 = fma(c[2].y, v[5], y1);
+    y1 = fma(c[3].y, v[6], y1);
+    y1 = fma(c[4].y, v[7], y1);
+    if (i == n - 2) {
+        y0 = fma(__ldg(band + 4 * n + i), v[5], y0);
+        y1 = fma(__ldg(band + 2 * n + i + 1), v[4], y1);
+    }
+    return make_double2(y0, y1);
+}
+
 template <int MODE>   // 0: identity, 1: one symmetric band
 __global__ void __launch_bounds__(kThreads, 1)
 pcg_pair_kernel(PcgArgs a, int64_t R) {
@@ -118,6 +152,7 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
     const int64_t zlo = lo - HZ > 0 ? lo - HZ : 0, zhi = hi + HZ < n ? hi + HZ : n;
     const int64_t bw = HP < (hi - lo) ? HP : (hi - lo);
     const bool beam = a.pairz != nullptr && *a.pairz != 0;
+    const bool packed = beam && a.Apk != nullptr;
     const double *Pb = MODE == 1 ? (a.psym ? a.psym : a.fac[0]) : nullptr;
     // r-halo pairs are recomputed by the last kHaloPairs threads (they own
     // one pair fewer than the first threads when R/2 is not a multiple of nt)
@@ -236,15 +271,26 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
                 a.pbuf[i] = ps[i - pbase];
             }
             double vq[1] = {0.0};
-            for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
-                double2 ab[kBand];
-                load_band_pair(a.A, n, i, ab);
-                double v[10];
-                load_win(ps, pbase, i, v);
-                const double2 q = beam ? pair_beam(ab, v, i == n - 2) : pair_full(ab, v);
-                *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
-                vq[0] = fma(v[4], q.x, fma(v[5], q.y, vq[0]));
+            if (packed) {
+                for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                    double v[10];
+                    load_win(ps, pbase, i, v);
+                    const double2 q = pair_packed(a.Apk, a.A, n, i, v);
+                    *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
+                    vq[0] = fma(v[4], q.x, fma(v[5], q.y, vq[0]));
+                }
+            } else {
+                for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                    double2 ab[kBand];
+                    load_band_pair(a.A, n, i, ab);
+                    double v[10];
+                    load_win(ps, pbase, i, v);
+                    const double2 q = beam ? pair_beam(ab, v, i == n - 2) : pair_full(ab, v);
+                    *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
+                    vq[0] = fma(v[4], q.x, fma(v[5], q.y, vq[0]));
+                }
             }
+            if (MODE == 1 && zlo + 2 * tid < zhi) prefetch_pair(Pb, n, zlo + 2 * tid, kBand);
             block_partials_tree<1>(vq, red, a.partials, bar_no & 1, G);
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
                 status = AIRGA_E_TIMEOUT;
@@ -303,6 +349,10 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
             __syncthreads();
             double v2[2] = {0.0, 0.0};
             apply_M(zlo, zhi, v2);
+            if (lo + 2 * tid < hi) {
+                if (packed) prefetch_pair(a.Apk, n, lo + 2 * tid, 5);
+                else prefetch_pair(a.A, n, lo + 2 * tid, kBand);
+            }
             block_partials_tree<2>(v2, red, a.partials, bar_no & 1, G);
             const bool arrive = !(a.fault_skip_arrival && k == 1 && blockIdx.x == 0);
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
