@@ -105,6 +105,35 @@ __device__ void grid_totals(const double *partials, int slot, int grid, double *
     __syncthreads();
 }
 
+// Warp 0 alone sums the NV partials of `slot` (all lanes' loads issued
+// together, fixed order, identical in every CTA) into tot[0..NV); call from
+// warp 0 only, then derive the scalars there and broadcast them through
+// shared memory.  Keeping the scalar FP64 work (divisions, tests) in one
+// warp matters on GB300, where each warp-wide FP64 instruction occupies the
+// FP64 pipe of its SM sub-partition for ~64 cycles.
+template <int NV>
+__device__ __forceinline__ void warp0_totals(const double *partials, int slot, int grid,
+                                             double (&tot)[NV]) {
+    const int l = threadIdx.x & 31;
+    constexpr int kPerLane = 8;                     // up to 256 CTAs in one sweep
+    double v[NV][kPerLane];
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+#pragma unroll
+        for (int j = 0; j < kPerLane; ++j) {
+            const int g = l + 32 * j;
+            v[q][j] = g < grid ? __ldcg(partials + (slot * 4 + q) * grid + g) : 0.0;
+        }
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+        double t = ((v[q][0] + v[q][1]) + (v[q][2] + v[q][3])) +
+                   ((v[q][4] + v[q][5]) + (v[q][6] + v[q][7]));
+        for (int g = l + 32 * kPerLane; g < grid; g += 32)
+            t += __ldcg(partials + (slot * 4 + q) * grid + g);
+        tot[q] = warp_sum(t);
+    }
+}
+
 // Block-sum NV values with a shared-memory tree; thread 0 writes them to
 // partials[slot][v][cta].  `red` holds NV * blockDim.x doubles.  On GB300 a
 // warp-wide FP64 add occupies the FP64 pipe for ~64 cycles, so the tree

@@ -40,15 +40,15 @@ constexpr int kThreads = 512;
 constexpr int HR = 8, HP = 12, HZ = 4;
 constexpr int kHaloPairs = HR;   // 4 pairs of r halo on each side
 
-__device__ __forceinline__ void load_band_pair(const double *__restrict__ band, int64_t n,
-                                               int64_t i, double2 (&a)[kBand]) {
+__device__ __forceinline__ void load_band_pair(const double *__restrict__ band, int n,
+                                               int i, double2 (&a)[kBand]) {
 #pragma unroll
     for (int d = 0; d < kBand; ++d)
-        a[d] = __ldg(reinterpret_cast<const double2 *>(band + (int64_t)d * n + i));
+        a[d] = __ldg(reinterpret_cast<const double2 *>(band + (long long)d * n + i));
 }
 
 // v[k] = window row i-4+k, k = 0..9 (five aligned double2 loads)
-__device__ __forceinline__ void load_win(const double *w, int64_t wbase, int64_t i,
+__device__ __forceinline__ void load_win(const double *w, int wbase, int i,
                                          double (&v)[10]) {
     const double2 *w2 = reinterpret_cast<const double2 *>(w + (i - 4 - wbase));
 #pragma unroll
@@ -95,20 +95,23 @@ __device__ __forceinline__ double2 pair_beam(const double2 (&a)[kBand], const do
 // Warm L2 with the 16-byte rows of `count` band arrays of stride n at pair i
 // (no registers held; issued before a barrier so the first loads of the next
 // phase find their lines in L2 instead of DRAM).
-__device__ __forceinline__ void prefetch_pair(const double *band, int64_t n, int64_t i, int count) {
+__device__ __forceinline__ void prefetch_pair(const double *band, int n, int i, int count) {
     for (int k = 0; k < count; ++k)
-        asm volatile("prefetch.global.L2 [%0];" ::"l"(band + (int64_t)k * n + i));
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(band + (long long)k * n + i));
 }
 
 // Beam row pair from the packed nonzeros (5 double2 loads = 80 B instead of
 // the band's 112 B): even row offsets (-2,-1,0,+2,+3), odd row
 // (-3,-2,0,+1,+2); the free-end pair adds its +-1 couplings from the band.
-__device__ __forceinline__ double2 pair_packed(const double *__restrict__ pk,
-                                               const double *__restrict__ band, int64_t n,
-                                               int64_t i, const double (&v)[10]) {
-    double2 c[5];
+__device__ __forceinline__ void load_packed(const double *__restrict__ pk, int n, int i,
+                                            double2 (&c)[5]) {
 #pragma unroll
-    for (int k = 0; k < 5; ++k) c[k] = __ldg(reinterpret_cast<const double2 *>(pk + k * n + i));
+    for (int k = 0; k < 5; ++k) c[k] = __ldg(reinterpret_cast<const double2 *>(pk + (long long)k * n + i));
+}
+
+__device__ __forceinline__ double2 pair_packed_c(const double2 (&c)[5],
+                                                 const double *__restrict__ band, int n,
+                                                 int i, const double (&v)[10]) {
     double y0 = c[0].x * v[2];
     y0 = fma(c[1].x, v[3], y0);
     y0 = fma(c[2].x, v[4], y0);
@@ -120,25 +123,26 @@ __device__ __forceinline__ double2 pair_packed(const double *__restrict__ pk,
     y1 = fma(c[3].y, v[6], y1);
     y1 = fma(c[4].y, v[7], y1);
     if (i == n - 2) {
-        y0 = fma(__ldg(band + 4 * n + i), v[5], y0);
-        y1 = fma(__ldg(band + 2 * n + i + 1), v[4], y1);
+        y0 = fma(__ldg(band + 4LL * n + i), v[5], y0);
+        y1 = fma(__ldg(band + 2LL * n + i + 1), v[4], y1);
     }
     return make_double2(y0, y1);
 }
 
 template <int MODE>   // 0: identity, 1: one symmetric band
 __global__ void __launch_bounds__(kThreads, 1)
-pcg_pair_kernel(PcgArgs a, int64_t R) {
+pcg_pair_kernel(PcgArgs a, int R) {
     extern __shared__ __align__(16) double smem[];
     __shared__ double tot[8];
     __shared__ int s_flag;
+    __shared__ int s_dec;
     __shared__ double s_nb;
 
     const int G = gridDim.x;
-    const int64_t n = a.n;
+    const int n = (int)a.n;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int64_t lo = (int64_t)blockIdx.x * R < n ? (int64_t)blockIdx.x * R : n;
-    const int64_t hi = lo + R < n ? lo + R : n;
+    const int lo = (int)blockIdx.x * R < n ? (int)blockIdx.x * R : n;
+    const int hi = lo + R < n ? lo + R : n;
     if (tid == 0) s_nb = 0.0;
 
     double *xs = smem;
@@ -147,10 +151,10 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
     double *zq = ps + (R + 2 * HZ);
     double2 *ah = reinterpret_cast<double2 *>(zq + (R + 2 * HZ));   // A rows of the r halo
     double *red = reinterpret_cast<double *>(ah + kHaloPairs * kBand);
-    const int64_t xbase = lo, rbase = lo - HR, pbase = lo - HZ, zbase = lo - HZ;
-    const int64_t rlo = lo - HR > 0 ? lo - HR : 0, rhi = hi + HR < n ? hi + HR : n;
-    const int64_t zlo = lo - HZ > 0 ? lo - HZ : 0, zhi = hi + HZ < n ? hi + HZ : n;
-    const int64_t bw = HP < (hi - lo) ? HP : (hi - lo);
+    const int xbase = lo, rbase = lo - HR, pbase = lo - HZ, zbase = lo - HZ;
+    const int rlo = lo - HR > 0 ? lo - HR : 0, rhi = hi + HR < n ? hi + HR : n;
+    const int zlo = lo - HZ > 0 ? lo - HZ : 0, zhi = hi + HZ < n ? hi + HZ : n;
+    const int bw = HP < (hi - lo) ? HP : (hi - lo);
     const bool beam = a.pairz != nullptr && *a.pairz != 0;
     const bool packed = beam && a.Apk != nullptr;
     const double *Pb = MODE == 1 ? (a.psym ? a.psym : a.fac[0]) : nullptr;
@@ -158,14 +162,14 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
     // one pair fewer than the first threads when R/2 is not a multiple of nt)
     const int hslot = nt - 1 - tid;                  // 0..7 for the halo threads
     const bool halo_thread = hslot < kHaloPairs;
-    const int64_t hpair = hslot < kHaloPairs / 2 ? lo - HR + 2 * hslot
+    const int hpair = hslot < kHaloPairs / 2 ? lo - HR + 2 * hslot
                                                  : hi + 2 * (hslot - kHaloPairs / 2);
     const bool hvalid = halo_thread && hpair >= 0 && hpair < n;
 
     // zero every window (out-of-matrix slots must read as 0), cache A's halo rows
     {
-        const int64_t total = 4 * R + 2 * (HR + 2 * HZ);
-        for (int64_t k = tid; k < total; k += nt) smem[k] = 0.0;
+        const int total = 4 * R + 2 * (HR + 2 * HZ);
+        for (int k = tid; k < total; k += nt) smem[k] = 0.0;
         if (hvalid) {
             double2 t[kBand];
             load_band_pair(a.A, n, hpair, t);
@@ -181,15 +185,15 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
     int iters = 0;
 
     // ---- x_0, r_0 = b - A x_0 on own +- HR, z_0 = M r_0 on own +- HZ ----
-    for (int64_t i = lo + tid; i < hi; i += nt) xs[i - xbase] = a.warm ? a.x[i] : 0.0;
-    for (int64_t i = rlo + tid; i < rhi; i += nt) {
+    for (int i = lo + tid; i < hi; i += nt) xs[i - xbase] = a.warm ? a.x[i] : 0.0;
+    for (int i = rlo + tid; i < rhi; i += nt) {
         double v = a.b[i];
         if (a.warm) {
             double ax = 0.0;
 #pragma unroll
             for (int d = 0; d < kBand; ++d) {
-                const int64_t c = i + d - kHalf;
-                if (c >= 0 && c < n) ax = fma(__ldg(a.A + (int64_t)d * n + i), a.x[c], ax);
+                const int c = i + d - kHalf;
+                if (c >= 0 && c < n) ax = fma(__ldg(a.A + (long long)d * n + i), a.x[c], ax);
             }
             v -= ax;
         }
@@ -198,8 +202,8 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
     __syncthreads();
     // z = M r for the pairs [from, to) (stride 2 nt starting at this thread's
     // slot); r.z and r.r of own pairs accumulate into v2
-    auto apply_M = [&](int64_t from, int64_t to, double (&v2)[2]) {
-        for (int64_t i = from + 2 * tid; i < to; i += 2 * nt) {
+    auto apply_M = [&](int from, int to, double (&v2)[2]) {
+        for (int i = from + 2 * tid; i < to; i += 2 * nt) {
             double2 z;
             if (MODE == 1) {
                 double2 pb[kBand];
@@ -222,7 +226,7 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
         double v2[2] = {0.0, 0.0};
         apply_M(zlo, zhi, v2);
         double v[3] = {v2[0], v2[1], 0.0};
-        for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+        for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
             const double2 b = *reinterpret_cast<const double2 *>(a.b + i);
             v[2] = fma(b.x, b.x, fma(b.y, b.y, v[2]));
         }
@@ -243,7 +247,7 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
         if (tid == 0) s_nb = nb;
         if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[0] = t0[1];
         if (nb == 0.0) {
-            for (int64_t i = lo + tid; i < hi; i += nt) xs[i - xbase] = 0.0;
+            for (int i = lo + tid; i < hi; i += nt) xs[i - xbase] = 0.0;
             status = AIRGA_OK;
             goto finish;
         }
@@ -253,7 +257,7 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
         double beta = 0.0;
         for (int k = 1; k <= a.maxit; ++k) {
             // ---- phase 1: p = z + beta p on own +- 4; boundary rows out; q = A p ----
-            for (int64_t i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
+            for (int i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
                 double2 *pp = reinterpret_cast<double2 *>(ps + (i - pbase));
                 const double2 z = *reinterpret_cast<const double2 *>(zq + (i - zbase));
                 if (k == 1) {
@@ -266,21 +270,23 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
                 }
             }
             __syncthreads();
-            for (int64_t t = tid; t < 2 * bw; t += nt) {
-                const int64_t i = t < bw ? lo + t : hi - bw + (t - bw);
+            for (int t = tid; t < 2 * bw; t += nt) {
+                const int i = t < bw ? lo + t : hi - bw + (t - bw);
                 a.pbuf[i] = ps[i - pbase];
             }
             double vq[1] = {0.0};
             if (packed) {
-                for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                    double2 c[5];
+                    load_packed(a.Apk, n, i, c);
                     double v[10];
                     load_win(ps, pbase, i, v);
-                    const double2 q = pair_packed(a.Apk, a.A, n, i, v);
+                    const double2 q = pair_packed_c(c, a.A, n, i, v);
                     *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
                     vq[0] = fma(v[4], q.x, fma(v[5], q.y, vq[0]));
                 }
             } else {
-                for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
                     double2 ab[kBand];
                     load_band_pair(a.A, n, i, ab);
                     double v[10];
@@ -297,16 +303,25 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
                 iters = k - 1;
                 goto finish;
             }
-            double pqt[1];
-            grid_totals<1>(a.partials, bar_no & 1, G, tot, pqt);
+            // warp 0: (p, q) total, breakdown test and alpha; one CTA barrier
+            if (tid < 32) {
+                double pqt[1];
+                warp0_totals<1>(a.partials, bar_no & 1, G, pqt);
+                if (tid == 0) {
+                    const double pq = pqt[0];
+                    const bool bad = !(pq > 0.0) || !isfinite(pq);
+                    s_dec = bad ? 1 : 0;
+                    tot[0] = bad ? 0.0 : rz / pq;
+                }
+            }
+            __syncthreads();
             ++bar_no;
-            const double pq = pqt[0];
-            if (!(pq > 0.0) || !isfinite(pq)) {
+            if (s_dec) {
                 status = AIRGA_E_BREAKDOWN;
                 iters = k - 1;
                 goto finish;
             }
-            const double alpha = rz / pq;
+            const double alpha = tot[0];
 
             // ---- phase 2: x, r updates; r halo (beside the x/r sweep); z = M r ----
             double pv[10];
@@ -314,14 +329,14 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
                 // p around this halo pair: the outer rows come from their owners
 #pragma unroll
                 for (int q = 0; q < 10; ++q) {
-                    const int64_t row = hpair - 4 + q;
+                    const int row = hpair - 4 + q;
                     double v = 0.0;
                     if (row >= 0 && row < n)
                         v = (row >= lo - HZ && row < hi + HZ) ? ps[row - pbase] : __ldcg(a.pbuf + row);
                     pv[q] = v;
                 }
             }
-            for (int64_t i = lo + 2 * tid; i < hi; i += 2 * nt) {
+            for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
                 double2 *xp = reinterpret_cast<double2 *>(xs + (i - xbase));
                 double2 *rp = reinterpret_cast<double2 *>(rs + (i - rbase));
                 const double2 p = *reinterpret_cast<const double2 *>(ps + (i - pbase));
@@ -361,21 +376,36 @@ pcg_pair_kernel(PcgArgs a, int64_t R) {
                 iters = k;
                 goto finish;
             }
-            double t2v[2];
-            grid_totals<2>(a.partials, bar_no & 1, G, tot, t2v);
+            // warp 0: (r, z) and (r, r) totals, stopping tests and beta
+            if (tid < 32) {
+                double t2v[2];
+                warp0_totals<2>(a.partials, bar_no & 1, G, t2v);
+                if (tid == 0) {
+                    if (blockIdx.x == 0 && a.hist) a.hist[k] = t2v[1];
+                    const double rz_new = t2v[0];
+                    int dec = 0;
+                    if (t2v[1] <= thr2) dec = 1;                               // converged
+                    else if (!isfinite(rz_new) || rz_new == 0.0) dec = 2;      // breakdown
+                    s_dec = dec;
+                    tot[1] = dec ? 0.0 : rz_new / rz;                          // beta
+                    tot[2] = rz_new;
+                }
+            }
+            __syncthreads();
             ++bar_no;
             iters = k;
-            if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[k] = t2v[1];
-            if (t2v[1] <= thr2) { status = AIRGA_OK; break; }
-            const double rz_new = t2v[0];
-            if (!isfinite(rz_new) || rz_new == 0.0) { status = AIRGA_E_BREAKDOWN; break; }
-            beta = rz_new / rz;
-            rz = rz_new;
+            {
+                const int dec = s_dec;
+                if (dec == 1) { status = AIRGA_OK; break; }
+                if (dec == 2) { status = AIRGA_E_BREAKDOWN; break; }
+            }
+            beta = tot[1];
+            rz = tot[2];
         }
     }
 finish:
     __syncthreads();
-    for (int64_t i = lo + tid; i < hi; i += nt) a.x[i] = xs[i - xbase];
+    for (int i = lo + tid; i < hi; i += nt) a.x[i] = xs[i - xbase];
     if (blockIdx.x == 0) {
         if (a.hist && s_nb > 0.0)       // r.r -> ||r_k|| / ||b||
             for (int k = tid; k <= iters; k += nt) a.hist[k] = sqrt(a.hist[k]) / s_nb;
@@ -394,7 +424,7 @@ cudaError_t launch_pair_mode(const PcgPlan &plan, const PcgArgs &args, cudaStrea
                                          (int)plan.smem_bytes);
     if (e != cudaSuccess) return e;
     PcgArgs a = args;
-    int64_t R = plan.rows;
+    int R = (int)plan.rows;
     void *kargs[] = {(void *)&a, (void *)&R};
     return cudaLaunchCooperativeKernel((const void *)kern, dim3(plan.grid), dim3(plan.threads),
                                        kargs, plan.smem_bytes, s);
