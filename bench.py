@@ -204,6 +204,10 @@ def gpu_arm(args, world, rank, local):
 
     # per-shift split of one step (untimed diagnostics)
     detail = None if args.profile else split_timings(G, torch, M, K, F, opts, stream)
+    forms = None
+    if not args.profile and not args.no_forms:
+        del M, K
+        forms = {"precision": precision_form(G, torch, stream)}
 
     # end to end through the public API with host buffers
     e2e = e2e_arm(G, torch, beam, opts, args) if rank == 0 and not args.profile else None
@@ -219,7 +223,7 @@ def gpu_arm(args, world, rank, local):
                           "hbm_frac": round(achieved_gbs / pk["hbm_gbs"], 4),
                           "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz"
                                          % pk["sm_max_mhz"]},
-                detail=detail, e2e=e2e, dist=dist)
+                detail=detail, e2e=e2e, dist=dist, forms=forms)
 
 
 def split_timings(G, torch, M, K, F, opts, stream):
@@ -289,6 +293,78 @@ def split_timings(G, torch, M, K, F, opts, stream):
     return dict(rebuild=rows, update_arm=upd, mr_arm=mr,
                 rebuild_precond_plus_cg_ms=round(reb_ms, 3),
                 update_precond_plus_cg_ms=round(upd_ms, 3))
+
+
+def precision_form(G, torch, stream):
+    """Precision workload: 1,000,000 elements (n = 2e6), m = 8 right-hand sides
+    (tip force + 7 seeded N(0,1) loads, seed 4), 16 shifts log-spaced in
+    [1e-1, 1e4]; SPAI (QR) per shift.  The same matrices and preconditioners
+    are solved by the plain FP64 PCG and by the FP32-inner / FP64-refinement
+    solve; each reports solves/s (shift x RHS systems at FP64 relative residual
+    <= 1e-10 per second of solve time) and the largest FP64 true residual.  The
+    relative difference between the two solutions bounds their error against
+    each other (the oracle comparison lives in the parity tests)."""
+    beam = W.beam(1_000_000)
+    n = beam.n
+    M, K = G.beam_mats(beam)
+    F = np.asfortranarray(W.loads(n, 8, seed=4))
+    Fd = torch.from_numpy(np.ascontiguousarray(F.T)).cuda().t()
+    shifts = W.log_shifts(-1, 4, 16)
+    o64 = G.options(tol=TOL, maxit=20000)
+    omx = G.options(tol=TOL, maxit=20000)
+    t64 = tmx = tsp = 0.0
+    ok64 = okmx = 0
+    worst64 = worstmx = 0.0
+    maxdiff = 0.0
+    inner_tot = outer_tot = it64_tot = 0
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record(stream)
+        return e
+
+    for rep in range(2):            # first pass warms up, second is measured
+        for s in shifts:
+            A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
+            e0 = ev()
+            P = G.spai_build(A)
+            e1 = ev()
+            r64 = G.pcg_solve(A, P, Fd, o64)
+            e2 = ev()
+            rmx = G.pcg_solve_mixed(A, P, Fd, omx)
+            e3 = ev()
+            torch.cuda.synchronize()
+            if rep == 0:
+                continue
+            tsp += e0.elapsed_time(e1)
+            t64 += e1.elapsed_time(e2)
+            tmx += e2.elapsed_time(e3)
+            rr64 = r64["true_relres"].cpu().numpy()
+            rrmx = rmx["true_relres"].cpu().numpy()
+            ok64 += int(((r64["status"] == G.OK).cpu().numpy() & (rr64 <= 2 * TOL)).sum())
+            okmx += int(((rmx["status"] == G.OK).cpu().numpy() & (rrmx <= TOL)).sum())
+            worst64 = max(worst64, float(rr64.max()))
+            worstmx = max(worstmx, float(rrmx.max()))
+            d = (rmx["X"] - r64["X"]).norm(dim=0) / r64["X"].norm(dim=0)
+            maxdiff = max(maxdiff, float(d.max()))
+            inner_tot += int(rmx["inner_iters"].sum())
+            outer_tot += int(rmx["outer_iters"].sum())
+            it64_tot += int(r64["iters"].sum())
+    nsol = len(shifts) * 8
+    return {"workload": "beam n_e=1e6 (n=2e6), m=8 (tip + 7 N(0,1), seed 4), 16 shifts "
+                        "logspace(-1,4), SPAI (QR) per shift",
+            "systems": nsol,
+            "fp64_pcg": {"solves_per_s": round(ok64 / (t64 * 1e-3), 3), "converged": ok64,
+                         "ms": round(t64, 3), "cg_iterations": it64_tot,
+                         "max_true_relres": worst64},
+            "fp32_inner_fp64_refinement": {"solves_per_s": round(okmx / (tmx * 1e-3), 3),
+                                           "converged": okmx, "ms": round(tmx, 3),
+                                           "inner_iterations": inner_tot,
+                                           "refinement_steps": outer_tot,
+                                           "max_true_relres": worstmx},
+            "speedup": round(t64 / tmx, 3) if tmx > 0 else None,
+            "spai_ms_total": round(tsp, 3),
+            "max_rel_diff_mixed_vs_fp64": maxdiff}
 
 
 def e2e_arm(G, torch, beam, opts, args):
@@ -428,6 +504,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the growth-form measurements (precision, batching)")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no per-phase split, e2e or CPU legs): for ncu")
     args = ap.parse_args()
@@ -454,7 +532,7 @@ def main():
                        "parallelism": "replicas" if world > 1 else "single"},
             "converged": r["ok"], "iters": r["iters"], "true_relres": r["relres"],
             "roofline": r["roofline"], "gpu_launches": r["launches"], "clocks": r["clocks"],
-            "e2e": r["e2e"], "detail": r["detail"],
+            "e2e": r["e2e"], "detail": r["detail"], "forms": r["forms"],
         }
         if world == 1 and not args.no_cpu_baseline and not args.profile:
             line["cpu_baseline"] = cpu_baseline()

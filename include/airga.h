@@ -77,6 +77,8 @@ typedef struct {
     int32_t pattern_hbw;        /* SPAI pattern: band |i - j| <= pattern_hbw, 0..3 (default 3) */
     int32_t warm_start;         /* CG: nonzero = use X's content on entry as x_0 (default 0: x_0 = 0) */
     int32_t barrier_timeout_ms; /* bound on any single grid-barrier wait (default 2000) */
+    double inner_tol;           /* mixed precision: FP32 inner solve to ||r_in|| <= inner_tol ||r|| (default 1e-5) */
+    int32_t max_outer;          /* mixed precision: FP64 refinement steps per column (default 12) */
 } airga_options;
 
 void airga_options_default(airga_options *opt);
@@ -192,6 +194,29 @@ void airga_precond_free(airga_precond P);
 int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
                     const airga_options *opt, double *X, double *res_hist, int32_t *iters,
                     int32_t *status, double *true_relres, void *stream);
+
+/* Mixed-precision solve of A X = F (FP32 inner CG inside FP64 iterative
+ * refinement): for each column, starting from x = 0,
+ *   r = f - A x            in FP64 (true residual; stop when ||r|| <= tol ||f||)
+ *   solve A d = r          by preconditioned CG in FP32 — FP32 copies of A
+ *                          and of the single-factor preconditioner P_sym (or
+ *                          of P itself when opt->symmetrize is 0), FP32
+ *                          vectors, FP64 reduction totals — until
+ *                          ||r - A d|| <= opt->inner_tol ||r|| or opt->maxit
+ *   x = x + d              in FP64,
+ * at most opt->max_outer times.  The SPAI (built in FP64) is only rounded to
+ * FP32 for the inner applications.  Outputs (device): X[n*m];
+ * outer_iters[m] and inner_iters[m] (int32: refinement steps taken and
+ * total FP32 CG iterations); status[m] (AIRGA_OK when the FP64 residual
+ * reached tol, AIRGA_E_MAXIT when max_outer steps did not, AIRGA_E_BREAKDOWN
+ * or AIRGA_E_TIMEOUT from an inner solve); true_relres[m] as for
+ * airga_pcg_solve.  P must be NULL (no preconditioner) or a single factor.
+ * Uses a per-call workspace from the library pool (about 3 n doubles plus
+ * FP32 copies of A and P). */
+int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double *F, int32_t m,
+                          const airga_options *opt, double *X, int32_t *outer_iters,
+                          int32_t *inner_iters, int32_t *status, double *true_relres,
+                          void *stream);
 
 /* relres[c] = ||F(:,c) - A X(:,c)||_2 / ||F(:,c)||_2 (0 when F(:,c) = 0),
  * the FP64 acceptance residual of a solve. */

@@ -30,7 +30,7 @@ EXPORTS = (
     "airga_spai_update", "airga_precond_apply", "airga_precond_length", "airga_precond_rows",
     "airga_precond_factor", "airga_precond_from_bands", "airga_precond_status",
     "airga_precond_free", "airga_pcg_solve", "airga_true_residual", "airga_debug_set_fault",
-    "airga_trim", "airga_pcg_solve_noalloc",
+    "airga_trim", "airga_pcg_solve_noalloc", "airga_pcg_solve_mixed",
 )
 
 
@@ -45,6 +45,8 @@ class Options(C.Structure):
         ("pattern_hbw", C.c_int32),
         ("warm_start", C.c_int32),
         ("barrier_timeout_ms", C.c_int32),
+        ("inner_tol", C.c_double),
+        ("max_outer", C.c_int32),
     ]
 
 
@@ -91,6 +93,8 @@ def lib():
         "airga_pcg_solve": (C.c_int, [vp, vp, vp, i32, C.POINTER(Options), vp, vp, vp, vp, vp,
                                       vp]),
         "airga_true_residual": (C.c_int, [vp, vp, vp, i32, vp, vp]),
+        "airga_pcg_solve_mixed": (C.c_int, [vp, vp, vp, i32, C.POINTER(Options), vp, vp, vp, vp,
+                                            vp, vp]),
         "airga_debug_set_fault": (C.c_int, [C.c_int]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
@@ -325,6 +329,29 @@ def pcg_solve(A: Mat, P: Precond | None, F: torch.Tensor, opts: Options | None =
     if want_hist:
         out["res_hist"] = hist
     return out
+
+
+def pcg_solve_mixed(A: Mat, P: Precond | None, F: torch.Tensor, opts: Options | None = None,
+                    stream=None):
+    """FP32-inner / FP64-refinement solve of A X = F (F an n-vector or a
+    column-major n x m block).  Returns X, outer_iters, inner_iters, status,
+    true_relres (device tensors)."""
+    Fc = _colmajor(F) if F.dim() == 2 and F.t().is_contiguous() else \
+        (F.reshape(1, -1) if F.dim() == 1 else F.t().contiguous())
+    m = Fc.shape[0]
+    o = opts if opts is not None else options()
+    Xc = torch.zeros_like(Fc)
+    outer = torch.zeros(m, dtype=torch.int32, device="cuda")
+    inner = torch.zeros(m, dtype=torch.int32, device="cuda")
+    status = torch.zeros(m, dtype=torch.int32, device="cuda")
+    relres = torch.zeros(m, dtype=torch.float64, device="cuda")
+    _check(lib().airga_pcg_solve_mixed(A.h, P.h if P is not None else None,
+                                       _ptr(Fc, torch.float64), m, C.byref(o),
+                                       _ptr(Xc, torch.float64), _ptr(outer), _ptr(inner),
+                                       _ptr(status), _ptr(relres), _stream(stream)),
+           "pcg_solve_mixed")
+    return dict(X=Xc.reshape(-1) if F.dim() == 1 else Xc.t(), outer_iters=outer,
+                inner_iters=inner, status=status, true_relres=relres)
 
 
 def true_residual(A: Mat, X: torch.Tensor, F: torch.Tensor, stream=None) -> torch.Tensor:

@@ -32,6 +32,11 @@ int cuda_fail(cudaError_t e, const char *what);
 // device memory: one stream-ordered pool per device, owned by the library
 // ---------------------------------------------------------------------------
 int dev_alloc(void **p, size_t bytes, cudaStream_t s);
+int check_options(const airga_options *o);
+// shared_ptr<void> owning a pool allocation (freed on `s`, on its device)
+int make_buf(size_t bytes, cudaStream_t s, std::shared_ptr<void> *out);
+int check_mat(airga_mat A, const char *name);
+bool aligned16(const void *p);
 void dev_free(void *p, cudaStream_t s);
 
 // A band-7 array of 7*n doubles, freed on its creation stream.

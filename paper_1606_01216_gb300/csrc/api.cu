@@ -99,7 +99,7 @@ int make_band(int64_t n, cudaStream_t s, BandPtr *out) {
 }
 
 // shared_ptr<void> owning a pool allocation
-static int make_buf(size_t bytes, cudaStream_t s, std::shared_ptr<void> *out) {
+int make_buf(size_t bytes, cudaStream_t s, std::shared_ptr<void> *out) {
     void *p = nullptr;
     int st = dev_alloc(&p, bytes, s);
     if (st) return st;
@@ -126,13 +126,13 @@ static int detect_flag(airga_mat_s *m, cudaStream_t s) {
     return AIRGA_OK;
 }
 
-static bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
+bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 static std::atomic<int> g_fault{AIRGA_FAULT_NONE};
 
 int take_fault() { return g_fault.exchange(AIRGA_FAULT_NONE); }
 
-static int check_options(const airga_options *o) {
+int check_options(const airga_options *o) {
     if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return fail(AIRGA_E_INVALID_ARG, "tol must be finite and >= 0");
     if (o->maxit < 0) return fail(AIRGA_E_INVALID_ARG, "maxit must be >= 0");
     if (o->spai_mode != AIRGA_SPAI_QR && o->spai_mode != AIRGA_SPAI_MR)
@@ -142,10 +142,13 @@ static int check_options(const airga_options *o) {
     if (o->pattern_hbw < 0 || o->pattern_hbw > 3)
         return fail(AIRGA_E_INVALID_ARG, "pattern_hbw must be in 0..3");
     if (o->barrier_timeout_ms <= 0) return fail(AIRGA_E_INVALID_ARG, "barrier_timeout_ms must be > 0");
+    if (!(o->inner_tol > 0.0) || !(o->inner_tol < 1.0))
+        return fail(AIRGA_E_INVALID_ARG, "inner_tol must be in (0, 1)");
+    if (o->max_outer < 1) return fail(AIRGA_E_INVALID_ARG, "max_outer must be >= 1");
     return AIRGA_OK;
 }
 
-static int check_mat(airga_mat A, const char *name) {
+int check_mat(airga_mat A, const char *name) {
     if (!A || !A->band || A->n < 1) return fail(AIRGA_E_INVALID_ARG, std::string(name) + " is not a valid matrix");
     return AIRGA_OK;
 }
@@ -202,6 +205,8 @@ void airga_options_default(airga_options *o) {
     o->pattern_hbw = 3;
     o->warm_start = 0;
     o->barrier_timeout_ms = 2000;
+    o->inner_tol = 1e-5;
+    o->max_outer = 12;
 }
 
 const char *airga_status_string(int s) {

@@ -1,0 +1,626 @@
+// Mixed precision: FP32 inner preconditioned CG inside FP64 iterative
+// refinement (airga_pcg_solve_mixed).
+//
+// Per right-hand side f, with x = 0:
+//   k = 0, 1, ...:  r = f - A x            FP64 (resid_* kernels, true residual)
+//                   stop if ||r|| <= tol ||f||
+//                   A d = r by FP32 PCG   (pcg32_pair_kernel: FP32 bands of A
+//                                          and P_sym, FP32 vectors)
+//                   x = x + d             FP64 (fused into the inner kernel's exit)
+// Every kernel reads a per-column state block in device memory; once the
+// column has converged (or failed) the remaining enqueued kernels return at
+// once, so the whole refinement is enqueued without host synchronisation.
+//
+// Why on GB300: an FP64 FMA issues at 2/clk/SM, an FP32 FMA at 128/clk/SM.
+// The inner iterations — the bulk of the work — leave the FP64 pipe for the
+// FP32 one and halve the band and vector bytes (FP32 copies of A and P_sym
+// stay resident in L2 up to n of about 2.3e6); FP64 is kept where accuracy
+// is decided: the outer residual, the refinement update, the SPAI QR, and
+// the reduction totals of the inner CG (per-thread FP32 partials are summed
+// in FP64).
+//
+// The inner kernel is the row-pair persistent PCG of pcg_pair.cu with float
+// data: same ownership, halo and barrier scheme, r halo recomputed beside
+// the x/r sweep, warp-0 scalar updates.
+#include "pcg_common.cuh"
+
+namespace airga {
+namespace {
+
+using namespace pcgdev;
+
+constexpr int kThreads = 512;
+constexpr int HR = 8, HP = 12, HZ = 4, kHaloPairs = 8;
+
+struct MixState {
+    double nf2;      // ||f||^2
+    double rr;       // ||r||^2 of the latest FP64 residual
+    int done;        // 1: converged or failed; later kernels return at once
+    int outer;       // refinement steps taken
+    int inner;       // FP32 CG iterations, all steps
+    int status;
+};
+
+// ---------------------------------------------------------------------------
+// FP64 -> FP32 copies
+// ---------------------------------------------------------------------------
+__global__ void to_f32_kernel(int64_t total, const double *__restrict__ src,
+                              float *__restrict__ dst) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = (float)src[i];
+}
+
+__global__ void state_init_kernel(MixState *st) {
+    st->nf2 = 0.0;
+    st->rr = 0.0;
+    st->done = 0;
+    st->outer = 0;
+    st->inner = 0;
+    st->status = AIRGA_E_MAXIT;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 residual r = f - A x, r32 = (float) r, per-block ||r||^2
+// ---------------------------------------------------------------------------
+__global__ void resid_partial_kernel(int64_t n, const double *__restrict__ A,
+                                     const double *__restrict__ x,
+                                     const double *__restrict__ f, float *__restrict__ r32,
+                                     double *__restrict__ partial, const MixState *st) {
+    if (st->done) return;
+    __shared__ double sh[32];
+    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = blockIdx.x * per, hi = lo + per < n ? lo + per : n;
+    double rr = 0.0;
+    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        double ax = 0.0;
+#pragma unroll
+        for (int d = 0; d < kBand; ++d) {
+            const int64_t c = i + d - kHalf;
+            if (c >= 0 && c < n) ax = fma(A[(int64_t)d * n + i], x[c], ax);
+        }
+        const double r = f[i] - ax;
+        r32[i] = (float)r;
+        rr = fma(r, r, rr);
+    }
+    rr = warp_sum_d(rr);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = rr;
+    __syncthreads();
+    if (w == 0) {
+        double t = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
+        t = warp_sum_d(t);
+        if (l == 0) partial[blockIdx.x] = t;
+    }
+}
+
+// Sum the partials; decide convergence of the column.  `k` is the number of
+// refinement steps done so far; after the last allowed step an unconverged
+// column is closed with AIRGA_E_MAXIT.
+__global__ void resid_final_kernel(int nblk, const double *__restrict__ partial, MixState *st,
+                                   double tol, int k, int max_outer, double *relres) {
+    if (st->done) return;
+    __shared__ double sh[32];
+    double t = 0.0;
+    for (int b = threadIdx.x; b < nblk; b += blockDim.x) t += partial[b];
+    t = warp_sum_d(t);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double rr = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) rr += sh[q];
+        if (k == 0) st->nf2 = rr;                      // x = 0: r = f
+        st->rr = rr;
+        const double nf2 = st->nf2;
+        const bool conv = rr <= tol * tol * nf2;
+        *relres = nf2 > 0.0 ? sqrt(rr / nf2) : 0.0;
+        if (conv) {
+            st->done = 1;
+            st->status = AIRGA_OK;
+            st->outer = k;
+        } else if (k >= max_outer) {
+            st->done = 1;
+            st->status = AIRGA_E_MAXIT;
+            st->outer = k;
+        }
+    }
+}
+
+__global__ void state_out_kernel(const MixState *st, int32_t *outer, int32_t *inner,
+                                 int32_t *status) {
+    *outer = st->outer;
+    *inner = st->inner;
+    *status = st->status;
+}
+
+// ---------------------------------------------------------------------------
+// FP32 row-pair PCG (inner solve of A d = r32, d_0 = 0)
+// ---------------------------------------------------------------------------
+struct Args32 {
+    int n;
+    const float *A;       // FP32 band-7 of A
+    const float *Apk;     // FP32 packed beam nonzeros of A, or null
+    const int32_t *pairz; // beam structure flag of A (device), or null
+    const float *M;       // FP32 band-7 preconditioner (or null = identity)
+    const float *b;       // r32
+    double *x64;          // refinement iterate: x64 += d at exit
+    float *pbuf;
+    double *partials;
+    unsigned *bar;
+    int *abort_flag;
+    double tol;           // inner relative tolerance
+    int maxit;
+    long long timeout_ns;
+    MixState *st;
+};
+
+__device__ __forceinline__ void load_band_pair_f(const float *__restrict__ band, int n, int i,
+                                                 float2 (&a)[kBand]) {
+#pragma unroll
+    for (int d = 0; d < kBand; ++d)
+        a[d] = __ldg(reinterpret_cast<const float2 *>(band + (long long)d * n + i));
+}
+
+__device__ __forceinline__ void load_win_f(const float *w, int wbase, int i, float (&v)[10]) {
+    const float2 *w2 = reinterpret_cast<const float2 *>(w + (i - 4 - wbase));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const float2 t = w2[k];
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ float2 pair_full_f(const float2 (&a)[kBand], const float (&v)[10]) {
+    float y0 = a[0].x * v[1], y1 = a[0].y * v[2];
+#pragma unroll
+    for (int d = 1; d < kBand; ++d) {
+        y0 = fmaf(a[d].x, v[1 + d], y0);
+        y1 = fmaf(a[d].y, v[2 + d], y1);
+    }
+    return make_float2(y0, y1);
+}
+
+// packed beam pair (see pack_pairs in band_kernels.cu), free-end couplings from the band
+__device__ __forceinline__ float2 pair_packed_f(const float *__restrict__ pk,
+                                                const float *__restrict__ band, int n, int i,
+                                                const float (&v)[10]) {
+    float2 c[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) c[k] = __ldg(reinterpret_cast<const float2 *>(pk + (long long)k * n + i));
+    float y0 = c[0].x * v[2];
+    y0 = fmaf(c[1].x, v[3], y0);
+    y0 = fmaf(c[2].x, v[4], y0);
+    y0 = fmaf(c[3].x, v[6], y0);
+    y0 = fmaf(c[4].x, v[7], y0);
+    float y1 = c[0].y * v[2];
+    y1 = fmaf(c[1].y, v[3], y1);
+    y1 = fmaf(c[2].y, v[5], y1);
+    y1 = fmaf(c[3].y, v[6], y1);
+    y1 = fmaf(c[4].y, v[7], y1);
+    if (i == n - 2) {
+        y0 = fmaf(__ldg(band + 4LL * n + i), v[5], y0);
+        y1 = fmaf(__ldg(band + 2LL * n + i + 1), v[4], y1);
+    }
+    return make_float2(y0, y1);
+}
+
+template <int MODE>   // 0: identity, 1: one band preconditioner
+__global__ void __launch_bounds__(kThreads, 1)
+pcg32_pair_kernel(Args32 a, int R) {
+    extern __shared__ __align__(16) double smem64[];
+    __shared__ double tot[8];
+    __shared__ int s_flag;
+    __shared__ int s_dec;
+
+    if (a.st->done) return;                 // converged or failed column: nothing to do
+
+    const int G = gridDim.x;
+    const int n = a.n;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    const int lo = blockIdx.x * R < n ? blockIdx.x * R : n;
+    const int hi = lo + R < n ? lo + R : n;
+
+    double *red = smem64;                                        // 3 * nt doubles
+    float *xs = reinterpret_cast<float *>(red + 3 * nt);
+    float *rs = xs + R;
+    float *ps = rs + (R + 2 * HR);
+    float *zq = ps + (R + 2 * HZ);
+    float2 *ah = reinterpret_cast<float2 *>(zq + (R + 2 * HZ));  // A rows of the r halo
+    const int xbase = lo, rbase = lo - HR, pbase = lo - HZ, zbase = lo - HZ;
+    const int rlo = lo - HR > 0 ? lo - HR : 0, rhi = hi + HR < n ? hi + HR : n;
+    const int zlo = lo - HZ > 0 ? lo - HZ : 0, zhi = hi + HZ < n ? hi + HZ : n;
+    const int bw = HP < (hi - lo) ? HP : (hi - lo);
+    const bool packed = a.Apk != nullptr && a.pairz != nullptr && *a.pairz != 0;
+    const int hslot = nt - 1 - tid;
+    const bool halo_thread = hslot < kHaloPairs;
+    const int hpair = hslot < kHaloPairs / 2 ? lo - HR + 2 * hslot : hi + 2 * (hslot - kHaloPairs / 2);
+    const bool hvalid = halo_thread && hpair >= 0 && hpair < n;
+
+    {
+        const int total = 4 * R + 2 * (HR + 2 * HZ);
+        for (int k = tid; k < total; k += nt) xs[k] = 0.0f;
+        if (hvalid) {
+            float2 t[kBand];
+            load_band_pair_f(a.A, n, hpair, t);
+#pragma unroll
+            for (int d = 0; d < kBand; ++d) ah[hslot * kBand + d] = t[d];
+        }
+    }
+    __syncthreads();
+
+    unsigned bar_no = 0;
+    const long long tmo = a.timeout_ns;
+    int status = AIRGA_E_MAXIT;
+    int iters = 0;
+
+    // r_0 = b (d_0 = 0) on own +- HR
+    for (int i = rlo + tid; i < rhi; i += nt) rs[i - rbase] = a.b[i];
+    __syncthreads();
+    auto apply_M = [&](int from, int to, float (&v2)[2]) {
+        for (int i = from + 2 * tid; i < to; i += 2 * nt) {
+            float2 z;
+            if (MODE == 1) {
+                float2 pb[kBand];
+                load_band_pair_f(a.M, n, i, pb);
+                float v[10];
+                load_win_f(rs, rbase, i, v);
+                z = pair_full_f(pb, v);
+            } else {
+                z = *reinterpret_cast<const float2 *>(rs + (i - rbase));
+            }
+            *reinterpret_cast<float2 *>(zq + (i - zbase)) = z;
+            if (i >= lo && i < hi) {
+                const float2 r = *reinterpret_cast<const float2 *>(rs + (i - rbase));
+                v2[0] = fmaf(r.x, z.x, fmaf(r.y, z.y, v2[0]));
+                v2[1] = fmaf(r.x, r.x, fmaf(r.y, r.y, v2[1]));
+            }
+        }
+    };
+    {
+        float v2[2] = {0.0f, 0.0f};
+        apply_M(zlo, zhi, v2);
+        double v[2] = {(double)v2[0], (double)v2[1]};
+        block_partials_tree<2>(v, red, a.partials, bar_no & 1, G);
+    }
+    if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+        status = AIRGA_E_TIMEOUT;
+        goto finish;
+    }
+    if (tid < 32) {
+        double t0[2];
+        warp0_totals<2>(a.partials, bar_no & 1, G, t0);
+        if (tid == 0) {
+            tot[0] = t0[0];                                  // (r, z)
+            tot[1] = t0[1];                                  // (r, r) = ||b||^2
+            s_dec = t0[1] == 0.0 ? 1 : ((!isfinite(t0[0]) || t0[0] == 0.0) ? 2 : 0);
+        }
+    }
+    __syncthreads();
+    ++bar_no;
+    {
+        double rz = tot[0];
+        const double thr2 = a.tol * a.tol * tot[1];
+        if (s_dec == 1) { status = AIRGA_OK; goto finish; }
+        if (s_dec == 2) { status = AIRGA_E_BREAKDOWN; goto finish; }
+        float beta = 0.0f;
+        for (int k = 1; k <= a.maxit; ++k) {
+            for (int i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
+                float2 *pp = reinterpret_cast<float2 *>(ps + (i - pbase));
+                const float2 z = *reinterpret_cast<const float2 *>(zq + (i - zbase));
+                if (k == 1) {
+                    *pp = z;
+                } else {
+                    float2 p = *pp;
+                    p.x = fmaf(beta, p.x, z.x);
+                    p.y = fmaf(beta, p.y, z.y);
+                    *pp = p;
+                }
+            }
+            __syncthreads();
+            for (int t = tid; t < 2 * bw; t += nt) {
+                const int i = t < bw ? lo + t : hi - bw + (t - bw);
+                a.pbuf[i] = ps[i - pbase];
+            }
+            float vq = 0.0f;
+            for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                float v[10];
+                load_win_f(ps, pbase, i, v);
+                float2 q;
+                if (packed) {
+                    q = pair_packed_f(a.Apk, a.A, n, i, v);
+                } else {
+                    float2 ab[kBand];
+                    load_band_pair_f(a.A, n, i, ab);
+                    q = pair_full_f(ab, v);
+                }
+                *reinterpret_cast<float2 *>(zq + (i - zbase)) = q;
+                vq = fmaf(v[4], q.x, fmaf(v[5], q.y, vq));
+            }
+            {
+                double vv[1] = {(double)vq};
+                block_partials_tree<1>(vv, red, a.partials, bar_no & 1, G);
+            }
+            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+                status = AIRGA_E_TIMEOUT;
+                iters = k - 1;
+                goto finish;
+            }
+            if (tid < 32) {
+                double pqt[1];
+                warp0_totals<1>(a.partials, bar_no & 1, G, pqt);
+                if (tid == 0) {
+                    const double pq = pqt[0];
+                    const bool bad = !(pq > 0.0) || !isfinite(pq);
+                    s_dec = bad ? 1 : 0;
+                    tot[2] = bad ? 0.0 : rz / pq;
+                }
+            }
+            __syncthreads();
+            ++bar_no;
+            if (s_dec) {
+                status = AIRGA_E_BREAKDOWN;
+                iters = k - 1;
+                goto finish;
+            }
+            const float alpha = (float)tot[2];
+
+            float pv[10];
+            if (hvalid) {
+#pragma unroll
+                for (int q = 0; q < 10; ++q) {
+                    const int row = hpair - 4 + q;
+                    float v = 0.0f;
+                    if (row >= 0 && row < n)
+                        v = (row >= lo - HZ && row < hi + HZ) ? ps[row - pbase] : __ldcg(a.pbuf + row);
+                    pv[q] = v;
+                }
+            }
+            for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                float2 *xp = reinterpret_cast<float2 *>(xs + (i - xbase));
+                float2 *rp = reinterpret_cast<float2 *>(rs + (i - rbase));
+                const float2 p = *reinterpret_cast<const float2 *>(ps + (i - pbase));
+                const float2 q = *reinterpret_cast<const float2 *>(zq + (i - zbase));
+                float2 x = *xp, r = *rp;
+                x.x = fmaf(alpha, p.x, x.x);
+                x.y = fmaf(alpha, p.y, x.y);
+                r.x = fmaf(-alpha, q.x, r.x);
+                r.y = fmaf(-alpha, q.y, r.y);
+                *xp = x;
+                *rp = r;
+            }
+            if (hvalid) {
+                float2 t[kBand];
+#pragma unroll
+                for (int d = 0; d < kBand; ++d) t[d] = ah[hslot * kBand + d];
+                const float2 q = pair_full_f(t, pv);
+                float2 *rp = reinterpret_cast<float2 *>(rs + (hpair - rbase));
+                float2 r = *rp;
+                r.x = fmaf(-alpha, q.x, r.x);
+                r.y = fmaf(-alpha, q.y, r.y);
+                *rp = r;
+            }
+            __syncthreads();
+            float v2[2] = {0.0f, 0.0f};
+            apply_M(zlo, zhi, v2);
+            {
+                double vv[2] = {(double)v2[0], (double)v2[1]};
+                block_partials_tree<2>(vv, red, a.partials, bar_no & 1, G);
+            }
+            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+                status = AIRGA_E_TIMEOUT;
+                iters = k;
+                goto finish;
+            }
+            if (tid < 32) {
+                double t2v[2];
+                warp0_totals<2>(a.partials, bar_no & 1, G, t2v);
+                if (tid == 0) {
+                    const double rz_new = t2v[0];
+                    int dec = 0;
+                    if (t2v[1] <= thr2) dec = 1;
+                    else if (!isfinite(rz_new) || rz_new == 0.0) dec = 2;
+                    s_dec = dec;
+                    tot[3] = dec ? 0.0 : rz_new / rz;
+                    tot[4] = rz_new;
+                }
+            }
+            __syncthreads();
+            ++bar_no;
+            iters = k;
+            {
+                const int dec = s_dec;
+                if (dec == 1) { status = AIRGA_OK; break; }
+                if (dec == 2) { status = AIRGA_E_BREAKDOWN; break; }
+            }
+            beta = (float)tot[3];
+            rz = tot[4];
+        }
+    }
+finish:
+    __syncthreads();
+    // refinement update x += d in FP64 (own rows)
+    for (int i = lo + tid; i < hi; i += nt) a.x64[i] += (double)xs[i - xbase];
+    if (blockIdx.x == 0 && tid == 0) {
+        a.st->inner += iters;
+        // an inner solve that stopped on its cap still improved x; breakdown
+        // and timeout end the column
+        if (status == AIRGA_E_BREAKDOWN || status == AIRGA_E_TIMEOUT) {
+            a.st->status = status;
+            a.st->done = 1;
+        }
+    }
+}
+
+size_t pcg32_smem(int64_t R) {
+    return (size_t)3 * kThreads * sizeof(double) +
+           (size_t)(4 * R + 2 * (HR + 2 * HZ) + 2 * kHaloPairs * kBand) * sizeof(float);
+}
+
+template <int MODE>
+cudaError_t launch32(int grid, int64_t R, size_t smem, const Args32 &args, cudaStream_t s) {
+    auto kern = pcg32_pair_kernel<MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    Args32 a = args;
+    int r = (int)R;
+    void *kargs[] = {(void *)&a, (void *)&r};
+    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid), dim3(kThreads), kargs, smem, s);
+}
+
+template <int MODE>
+int occupancy32(size_t smem, int *per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(pcg32_pair_kernel<MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg32_pair_kernel<MODE>, kThreads,
+                                                          smem);
+    return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg32 occupancy");
+}
+
+int grid_for(int64_t work) {
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int64_t want = (work + 255) / 256, cap = (int64_t)sms * 8;
+    if (want < 1) want = 1;
+    return (int)(want < cap ? want : cap);
+}
+
+}  // namespace
+}  // namespace airga
+
+using namespace airga;
+
+extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double *F, int32_t m,
+                                     const airga_options *opt, double *X, int32_t *outer_iters,
+                                     int32_t *inner_iters, int32_t *status, double *true_relres,
+                                     void *stream) {
+    int st = check_mat(A, "A");
+    if (st) return st;
+    if (m < 0) return fail(AIRGA_E_INVALID_ARG, "m must be >= 0");
+    if (m == 0) return AIRGA_OK;
+    if (!F || !X || !outer_iters || !inner_iters || !status || !true_relres)
+        return fail(AIRGA_E_INVALID_ARG, "F, X, outer_iters, inner_iters, status, true_relres are required");
+    if (P && (P->n != A->n || P->factors.size() != 1))
+        return fail(AIRGA_E_INVALID_ARG, "mixed solve takes no preconditioner or a single-factor one");
+    airga_options o;
+    airga_options_default(&o);
+    if (opt) o = *opt;
+    st = check_options(&o);
+    if (st) return st;
+    const int64_t n = A->n;
+    if (n % 2 != 0 || n > (int64_t)INT32_MAX / 8)
+        return fail(AIRGA_E_INVALID_ARG, "mixed solve needs an even n below 2^28");
+    int dev = 0, sms = 0, optin = 0;
+    AIRGA_CUDA(cudaGetDevice(&dev));
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int mode = P ? 1 : 0;
+    int64_t want = (n + 127) / 128;
+    int grid = (int)(want < sms ? want : sms);
+    if (grid < 1) grid = 1;
+    int64_t R = (n + grid - 1) / grid;
+    R += R & 1;
+    const size_t smem = pcg32_smem(R);
+    if (smem + 256 > (size_t)optin)
+        return fail(AIRGA_E_INVALID_ARG, "mixed solve: the FP32 state does not fit in shared memory");
+    int per_sm = 0;
+    st = mode ? occupancy32<1>(smem, &per_sm) : occupancy32<0>(smem, &per_sm);
+    if (st) return st;
+    if (per_sm < 1 || grid > per_sm * sms) return fail(AIRGA_E_INVALID_ARG, "mixed solve: grid not co-resident");
+
+    cudaStream_t s = (cudaStream_t)stream;
+    const int rblk = (int)((n + 4095) / 4096 < 1216 ? (n + 4095) / 4096 : 1216);
+    // workspace: FP32 A band (7n), FP32 packed (5n), FP32 M band (7n), r32 (n),
+    // pbuf32 (n) as floats; partials, residual partials, states, control
+    const size_t nf = (size_t)n;
+    const size_t floats = 7 * nf + 5 * nf + (mode ? 7 * nf : 0) + nf + nf;
+    const size_t doubles = (size_t)8 * grid + (size_t)rblk + 4;
+    const size_t bytes = floats * sizeof(float) + 256 + doubles * sizeof(double) +
+                         (size_t)m * sizeof(MixState) + 256;
+    void *ws = nullptr;
+    st = dev_alloc(&ws, bytes, s);
+    if (st) return st;
+    char *base = (char *)ws;
+    float *A32 = (float *)base;
+    float *Apk32 = A32 + 7 * nf;
+    float *M32 = Apk32 + 5 * nf;
+    float *r32 = M32 + (mode ? 7 * nf : 0);
+    float *pbuf = r32 + nf;
+    double *dbase = (double *)(((uintptr_t)(pbuf + nf) + 255) & ~(uintptr_t)255);
+    double *partials = dbase;
+    double *rpart = partials + 8 * grid;
+    unsigned *ctl = (unsigned *)(rpart + rblk);
+    MixState *states = (MixState *)(((uintptr_t)(ctl + 8) + 15) & ~(uintptr_t)15);
+
+    cudaError_t e = cudaSuccess;
+    const int gconv = grid_for(7 * n);
+    to_f32_kernel<<<gconv, 256, 0, s>>>(7 * n, A->band->d, A32);
+    if (A->pairz) {
+        if (!A->packed) {
+            st = make_buf(sizeof(double) * 5 * nf, s, &A->packed);
+            if (!st) {
+                cudaError_t pe = launch_pack_pairs(n, A->band->d, (double *)A->packed.get(), s);
+                if (pe != cudaSuccess) st = cuda_fail(pe, "pack pairs");
+            }
+            if (st) {
+                dev_free(ws, s);
+                return st;
+            }
+        }
+        to_f32_kernel<<<gconv, 256, 0, s>>>(5 * n, (const double *)A->packed.get(), Apk32);
+    }
+    if (mode) {
+        const double *mb = (o.symmetrize && P->psym) ? P->psym->d : P->factors[0]->d;
+        to_f32_kernel<<<gconv, 256, 0, s>>>(7 * n, mb, M32);
+    }
+    e = cudaGetLastError();
+    Args32 a{};
+    a.n = (int)n;
+    a.A = A32;
+    a.Apk = A->pairz ? Apk32 : nullptr;
+    a.pairz = A->pairz ? (const int32_t *)A->pairz.get() : nullptr;
+    a.M = mode ? M32 : nullptr;
+    a.b = r32;
+    a.pbuf = pbuf;
+    a.partials = partials;
+    a.bar = ctl;
+    a.abort_flag = (int *)(ctl + 1);
+    a.tol = o.inner_tol;
+    a.maxit = o.maxit;
+    a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
+    for (int32_t c = 0; c < m && e == cudaSuccess; ++c) {
+        const double *f = F + (size_t)c * nf;
+        double *x = X + (size_t)c * nf;
+        MixState *stc = states + c;
+        e = cudaMemsetAsync(x, 0, sizeof(double) * nf, s);
+        if (e != cudaSuccess) break;
+        state_init_kernel<<<1, 1, 0, s>>>(stc);
+        a.x64 = x;
+        a.st = stc;
+        for (int k = 0; k <= o.max_outer && e == cudaSuccess; ++k) {
+            resid_partial_kernel<<<rblk, 256, 0, s>>>(n, A->band->d, x, f, r32, rpart, stc);
+            resid_final_kernel<<<1, 256, 0, s>>>(rblk, rpart, stc, o.tol, k, o.max_outer,
+                                                 true_relres + c);
+            e = cudaGetLastError();
+            if (e != cudaSuccess || k == o.max_outer) break;
+            e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
+            if (e == cudaSuccess) e = mode ? launch32<1>(grid, R, smem, a, s) : launch32<0>(grid, R, smem, a, s);
+        }
+        if (e == cudaSuccess) {
+            state_out_kernel<<<1, 1, 0, s>>>(stc, outer_iters + c, inner_iters + c, status + c);
+            e = cudaGetLastError();
+        }
+    }
+    dev_free(ws, s);
+    if (e != cudaSuccess) return cuda_fail(e, "mixed solve launch");
+    return AIRGA_OK;
+}

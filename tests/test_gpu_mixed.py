@@ -1,0 +1,95 @@
+"""FP32-inner / FP64-refinement solve (airga_pcg_solve_mixed) against the
+FP64 oracle.  The refinement stops on the FP64 true residual, so the same
+targets as the plain FP64 PCG apply: X within 1e-8 relative of the oracle's
+direct solution, ||f - A x|| / ||f|| <= tol = 1e-10."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1606_01216_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+AL, BE = W.ALPHA, W.BETA
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_01216_gb300 import build
+    build.build()
+    from paper_1606_01216_gb300 import airga
+    airga.lib()
+    return airga
+
+
+def solve(G, beam, s, F, precond=True, **kw):
+    M, K = G.beam_mats(beam)
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    P = G.spai_build(A) if precond else None
+    Fd = torch.from_numpy(np.ascontiguousarray(np.atleast_2d(F.T))).cuda()
+    res = G.pcg_solve_mixed(A, P, Fd.t() if F.ndim == 2 else Fd.reshape(-1), G.options(**kw))
+    torch.cuda.synchronize()
+    return res
+
+
+@pytest.mark.parametrize("s", [0.1, 1.0, 13.9, 100.0, 1e4])
+def test_mixed_matches_fp64_oracle(G, s):
+    beam = W.beam(1237)
+    F = W.loads(beam.n)[:, 0]
+    res = solve(G, beam, s, F)
+    Ao = O.shifted_csr(beam, AL, BE, s)
+    xd = O.chol_solve(Ao, F)[:, 0]
+    x = res["X"].cpu().numpy()
+    assert int(res["status"][0]) == G.OK
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+    true = np.linalg.norm(F - O.spmv(Ao, x)) / np.linalg.norm(F)
+    assert true <= 1e-10 and float(res["true_relres"][0]) <= 1e-10
+    # both residuals are evaluated in FP64 with different summation orders;
+    # near 1e-13 they agree only up to that evaluation noise
+    assert abs(true - float(res["true_relres"][0])) <= 1e-3 * true + 1e-11
+    assert int(res["outer_iters"][0]) >= 1 and int(res["inner_iters"][0]) >= int(res["outer_iters"][0])
+
+
+def test_mixed_multi_rhs_and_identity(G):
+    beam = W.beam(2000)
+    F = W.loads(beam.n, 3, seed=9)
+    Ao = O.shifted_csr(beam, AL, BE, 50.0)
+    Xd = O.chol_solve(Ao, F)
+    for pre in (True, False):
+        res = solve(G, beam, 50.0, F, precond=pre)
+        X = res["X"].cpu().numpy()
+        for c in range(3):
+            assert int(res["status"][c]) == G.OK
+            assert np.linalg.norm(X[:, c] - Xd[:, c]) <= 1e-8 * np.linalg.norm(Xd[:, c])
+
+
+def test_mixed_outer_cap(G):
+    beam = W.beam(1500)
+    F = W.loads(beam.n)[:, 0]
+    res = solve(G, beam, 0.1, F, max_outer=1, inner_tol=1e-2)
+    assert int(res["status"][0]) == G.E_MAXIT and int(res["outer_iters"][0]) == 1
+    assert 1e-10 < float(res["true_relres"][0]) < 1.0
+
+
+def test_mixed_zero_rhs(G):
+    beam = W.beam(300)
+    res = solve(G, beam, 1.0, np.zeros(beam.n))
+    assert int(res["status"][0]) == G.OK and int(res["outer_iters"][0]) == 0
+    assert not res["X"].any()
+
+
+@pytest.mark.parametrize("s", [0.1, 1e4])
+def test_mixed_full_size_two_million(G, s):
+    """The precision workload's size: 1,000,000 elements (n = 2e6)."""
+    beam = W.beam(1_000_000)
+    F = W.loads(beam.n, 2, seed=4)
+    res = solve(G, beam, s, F)
+    Ao = O.shifted_csr(beam, AL, BE, s)
+    Xd = O.chol_solve(Ao, F)
+    X = res["X"].cpu().numpy()
+    for c in range(2):
+        assert int(res["status"][c]) == G.OK
+        assert np.linalg.norm(X[:, c] - Xd[:, c]) <= 1e-8 * np.linalg.norm(Xd[:, c])
+        assert float(res["true_relres"][c]) <= 1e-10
