@@ -63,6 +63,7 @@ extern "C" {
 
 typedef struct airga_mat_s *airga_mat;
 typedef struct airga_precond_s *airga_precond;
+typedef struct airga_batch_s *airga_batch;
 
 /* Options shared by the SPAI and CG calls.  Fill with airga_options_default
  * and change fields; passing NULL where an options pointer is taken means
@@ -194,6 +195,40 @@ void airga_precond_free(airga_precond P);
 int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
                     const airga_options *opt, double *X, double *res_hist, int32_t *iters,
                     int32_t *status, double *true_relres, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* batched solves                                                          */
+/* ---------------------------------------------------------------------- */
+
+/* Plan nsys independent single-RHS solves A[s] x_s = f_s (each the PCG of
+ * airga_pcg_solve, e.g. the shifts x right-hand sides of several beams; the
+ * RHS reuse of Algorithms 3/5) for ONE persistent launch.  Each system s gets
+ * a group of CTAs, sized so that its rows per CTA stay near rows_per_cta
+ * (0 = 4096) and fit shared memory; systems are placed largest cost first on
+ * the CTAs that become free first.  cost[s] (host, may be NULL = rows) is
+ * the caller's work estimate, e.g. rows x CG iterations of an earlier run —
+ * the hook an autotuner uses.  Requirements: every n even, F[s] and X[s]
+ * (device, n-vectors) 16-byte aligned, either every P[s] a single factor of
+ * matching size or P NULL / every P[s] NULL.  Results of each solve go to the
+ * caller's device arrays iters[s], status[s] and relres[s] (true residual).
+ * The handles A[s], P[s] and all buffers must outlive the plan.  Uploads the
+ * plan and SYNCHRONISES `stream`. */
+int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
+                       const double *const *F, double *const *X, const double *cost,
+                       int32_t rows_per_cta, const airga_options *opt, int32_t *iters,
+                       int32_t *status, double *relres, void *stream, airga_batch *out);
+
+/* Run the planned solves: one memset and one cooperative launch on `stream`,
+ * no allocation (the call may be captured in a CUDA graph and replayed; each
+ * replay solves again from x_0 = 0 unless opt->warm_start was set). */
+int airga_batch_solve(airga_batch b, void *stream);
+
+/* Plan facts: CTAs, requested and largest rows per CTA, estimated makespan
+ * (cost units per CTA).  Any pointer may be NULL. */
+int airga_batch_info(airga_batch b, int32_t *grid, int32_t *rows_target, int32_t *rows_max,
+                     double *makespan);
+
+void airga_batch_free(airga_batch b);
 
 /* Mixed-precision solve of A X = F (FP32 inner CG inside FP64 iterative
  * refinement): for each column, starting from x = 0,

@@ -30,7 +30,8 @@ EXPORTS = (
     "airga_spai_update", "airga_precond_apply", "airga_precond_length", "airga_precond_rows",
     "airga_precond_factor", "airga_precond_from_bands", "airga_precond_status",
     "airga_precond_free", "airga_pcg_solve", "airga_true_residual", "airga_debug_set_fault",
-    "airga_trim", "airga_pcg_solve_noalloc", "airga_pcg_solve_mixed",
+    "airga_trim", "airga_pcg_solve_noalloc", "airga_pcg_solve_mixed", "airga_batch_create",
+    "airga_batch_solve", "airga_batch_info", "airga_batch_free",
 )
 
 
@@ -95,6 +96,13 @@ def lib():
         "airga_true_residual": (C.c_int, [vp, vp, vp, i32, vp, vp]),
         "airga_pcg_solve_mixed": (C.c_int, [vp, vp, vp, i32, C.POINTER(Options), vp, vp, vp, vp,
                                             vp, vp]),
+        "airga_batch_create": (C.c_int, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
+                                         C.POINTER(vp), C.POINTER(C.c_double), i32,
+                                         C.POINTER(Options), vp, vp, vp, vp, C.POINTER(vp)]),
+        "airga_batch_solve": (C.c_int, [vp, vp]),
+        "airga_batch_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
+                                       C.POINTER(C.c_double)]),
+        "airga_batch_free": (None, [vp]),
         "airga_debug_set_fault": (C.c_int, [C.c_int]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
@@ -352,6 +360,48 @@ def pcg_solve_mixed(A: Mat, P: Precond | None, F: torch.Tensor, opts: Options | 
            "pcg_solve_mixed")
     return dict(X=Xc.reshape(-1) if F.dim() == 1 else Xc.t(), outer_iters=outer,
                 inner_iters=inner, status=status, true_relres=relres)
+
+
+class Batch:
+    """A planned set of independent single-RHS solves run by one launch
+    (airga_batch_*).  systems: list of (A, P or None, f, x) with f, x device
+    n-vectors (x receives the solution)."""
+
+    def __init__(self, systems, opts: Options | None = None, cost=None, rows_per_cta: int = 0,
+                 stream=None):
+        k = len(systems)
+        self.systems = systems           # keep handles and buffers alive
+        self.iters = torch.zeros(k, dtype=torch.int32, device="cuda")
+        self.status = torch.zeros(k, dtype=torch.int32, device="cuda")
+        self.relres = torch.zeros(k, dtype=torch.float64, device="cuda")
+        Ah = (C.c_void_p * k)(*[s[0].h.value for s in systems])
+        any_p = any(s[1] is not None for s in systems)
+        Ph = (C.c_void_p * k)(*[(s[1].h.value if s[1] is not None else None) for s in systems])
+        Fp = (C.c_void_p * k)(*[s[2].data_ptr() for s in systems])
+        Xp = (C.c_void_p * k)(*[s[3].data_ptr() for s in systems])
+        cst = (C.c_double * k)(*cost) if cost is not None else None
+        o = opts if opts is not None else options()
+        self.opts = o
+        out = C.c_void_p()
+        _check(lib().airga_batch_create(k, Ah, Ph if any_p else None, Fp, Xp, cst,
+                                        int(rows_per_cta), C.byref(o), _ptr(self.iters),
+                                        _ptr(self.status), _ptr(self.relres), _stream(stream),
+                                        C.byref(out)), "batch_create")
+        self.h = out
+
+    def solve(self, stream=None):
+        _check(lib().airga_batch_solve(self.h, _stream(stream)), "batch_solve")
+
+    def info(self):
+        g, rt, rm, ms = C.c_int32(), C.c_int32(), C.c_int32(), C.c_double()
+        _check(lib().airga_batch_info(self.h, C.byref(g), C.byref(rt), C.byref(rm), C.byref(ms)),
+               "batch_info")
+        return dict(grid=g.value, rows_target=rt.value, rows_max=rm.value, makespan=ms.value)
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.airga_batch_free(self.h)
+            self.h = C.c_void_p(None)
 
 
 def true_residual(A: Mat, X: torch.Tensor, F: torch.Tensor, stream=None) -> torch.Tensor:

@@ -164,6 +164,7 @@ struct PcgArgs {
     int fault_skip_arrival;        // test injection: CTA 0 skips its first iteration barrier
     const int32_t *pairz;          // device flag: A has the beam zero structure (may be null)
     const double *Apk;             // packed beam entries of A (launch_pack_pairs) or null
+    double *relres;                // node-pair kernel: true residual written here (or null)
 };
 
 // process-wide test fault consumed by the next pcg_solve (airga_debug_set_fault)
@@ -178,5 +179,11 @@ size_t pcg_pair_smem(int64_t R);
 int pcg_pair_threads();
 int pcg_pair_occupancy(int mode, size_t smem, int *per_sm);
 cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
+// batched node-pair kernel: systems `sys`, assignments asg (int4: system,
+// group size, rank, rows per CTA) per CTA from off[c] to off[c+1]
+int pcg_pair_batch_prepare(int mode, size_t smem);
+int pcg_pair_batch_occupancy(int mode, size_t smem, int *per_sm);
+cudaError_t launch_pcg_pair_batch(int mode, int grid, size_t smem, const PcgArgs *sys,
+                                  const int4 *asg, const int *off, cudaStream_t s);
 
 }  // namespace airga

@@ -288,7 +288,7 @@ pcg32_pair_kernel(Args32 a, int R) {
         float v2[2] = {0.0f, 0.0f};
         apply_M(zlo, zhi, v2);
         double v[2] = {(double)v2[0], (double)v2[1]};
-        block_partials_tree<2>(v, red, a.partials, bar_no & 1, G);
+        block_partials_tree<2>(v, red, a.partials, bar_no & 1, G, blockIdx.x);
     }
     if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
         status = AIRGA_E_TIMEOUT;
@@ -346,7 +346,7 @@ pcg32_pair_kernel(Args32 a, int R) {
             }
             {
                 double vv[1] = {(double)vq};
-                block_partials_tree<1>(vv, red, a.partials, bar_no & 1, G);
+                block_partials_tree<1>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
             }
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
                 status = AIRGA_E_TIMEOUT;
@@ -412,7 +412,7 @@ pcg32_pair_kernel(Args32 a, int R) {
             apply_M(zlo, zhi, v2);
             {
                 double vv[2] = {(double)v2[0], (double)v2[1]};
-                block_partials_tree<2>(vv, red, a.partials, bar_no & 1, G);
+                block_partials_tree<2>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
             }
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
                 status = AIRGA_E_TIMEOUT;

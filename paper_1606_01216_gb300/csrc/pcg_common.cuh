@@ -142,7 +142,7 @@ __device__ __forceinline__ void warp0_totals(const double *partials, int slot, i
 // instead of 85 for 512 threads).  blockDim.x must be a multiple of 128.
 template <int NV>
 __device__ void block_partials_tree(double (&v)[NV], double *red, double *partials, int slot,
-                                    int grid) {
+                                    int grid, int rank) {
     const int tid = threadIdx.x, nt = blockDim.x;
 #pragma unroll
     for (int q = 0; q < NV; ++q) red[q * nt + tid] = v[q];
@@ -168,7 +168,7 @@ __device__ void block_partials_tree(double (&v)[NV], double *red, double *partia
             for (int k = l; k < quarter; k += 32) t += r[k];
         }
         t = warp_sum(t);
-        if (l == 0) partials[(slot * 4 + w) * grid + blockIdx.x] = t;
+        if (l == 0) partials[(slot * 4 + w) * grid + rank] = t;
     }
 }
 

@@ -129,19 +129,28 @@ __device__ __forceinline__ double2 pair_packed_c(const double2 (&c)[5],
     return make_double2(y0, y1);
 }
 
-template <int MODE>   // 0: identity, 1: one symmetric band
-__global__ void __launch_bounds__(kThreads, 1)
-pcg_pair_kernel(PcgArgs a, int R) {
-    extern __shared__ __align__(16) double smem[];
-    __shared__ double tot[8];
-    __shared__ int s_flag;
-    __shared__ int s_dec;
-    __shared__ double s_nb;
+// Block-wide scalars of one solve.
+struct PairShared {
+    double tot[8];
+    int s_flag;
+    int s_dec;
+    double s_nb;
+};
 
-    const int G = gridDim.x;
+// The whole solve of one system by one CTA of a group of G CTAs, this CTA
+// being `rank` (rows [rank R, rank R + R)).  The group's barriers, partials
+// and p boundary buffer come from `a`; the single-system kernel runs it with
+// the whole grid as the group, the batched kernel once per assignment.
+template <int MODE>   // 0: identity, 1: one symmetric band
+__device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem,
+                          PairShared &sh) {
+    double *tot = sh.tot;
+    int &s_flag = sh.s_flag;
+    int &s_dec = sh.s_dec;
+    double &s_nb = sh.s_nb;
     const int n = (int)a.n;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lo = (int)blockIdx.x * R < n ? (int)blockIdx.x * R : n;
+    const int lo = rank * R < n ? rank * R : n;
     const int hi = lo + R < n ? lo + R : n;
     if (tid == 0) s_nb = 0.0;
 
@@ -230,7 +239,7 @@ pcg_pair_kernel(PcgArgs a, int R) {
             const double2 b = *reinterpret_cast<const double2 *>(a.b + i);
             v[2] = fma(b.x, b.x, fma(b.y, b.y, v[2]));
         }
-        block_partials_tree<3>(v, red, a.partials, bar_no & 1, G);
+        block_partials_tree<3>(v, red, a.partials, bar_no & 1, G, rank);
     }
     if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
         status = AIRGA_E_TIMEOUT;
@@ -245,7 +254,7 @@ pcg_pair_kernel(PcgArgs a, int R) {
         const double nb = sqrt(bb);
         const double thr2 = (a.tol * nb) * (a.tol * nb);     // stop when r.r <= (tol ||b||)^2
         if (tid == 0) s_nb = nb;
-        if (blockIdx.x == 0 && tid == 0 && a.hist) a.hist[0] = t0[1];
+        if (rank == 0 && tid == 0 && a.hist) a.hist[0] = t0[1];
         if (nb == 0.0) {
             for (int i = lo + tid; i < hi; i += nt) xs[i - xbase] = 0.0;
             status = AIRGA_OK;
@@ -297,7 +306,7 @@ pcg_pair_kernel(PcgArgs a, int R) {
                 }
             }
             if (MODE == 1 && zlo + 2 * tid < zhi) prefetch_pair(Pb, n, zlo + 2 * tid, kBand);
-            block_partials_tree<1>(vq, red, a.partials, bar_no & 1, G);
+            block_partials_tree<1>(vq, red, a.partials, bar_no & 1, G, rank);
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
                 status = AIRGA_E_TIMEOUT;
                 iters = k - 1;
@@ -368,8 +377,8 @@ pcg_pair_kernel(PcgArgs a, int R) {
                 if (packed) prefetch_pair(a.Apk, n, lo + 2 * tid, 5);
                 else prefetch_pair(a.A, n, lo + 2 * tid, kBand);
             }
-            block_partials_tree<2>(v2, red, a.partials, bar_no & 1, G);
-            const bool arrive = !(a.fault_skip_arrival && k == 1 && blockIdx.x == 0);
+            block_partials_tree<2>(v2, red, a.partials, bar_no & 1, G, rank);
+            const bool arrive = !(a.fault_skip_arrival && k == 1 && rank == 0);
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
                               arrive)) {
                 status = AIRGA_E_TIMEOUT;
@@ -381,7 +390,7 @@ pcg_pair_kernel(PcgArgs a, int R) {
                 double t2v[2];
                 warp0_totals<2>(a.partials, bar_no & 1, G, t2v);
                 if (tid == 0) {
-                    if (blockIdx.x == 0 && a.hist) a.hist[k] = t2v[1];
+                    if (rank == 0 && a.hist) a.hist[k] = t2v[1];
                     const double rz_new = t2v[0];
                     int dec = 0;
                     if (t2v[1] <= thr2) dec = 1;                               // converged
@@ -406,7 +415,7 @@ pcg_pair_kernel(PcgArgs a, int R) {
 finish:
     __syncthreads();
     for (int i = lo + tid; i < hi; i += nt) a.x[i] = xs[i - xbase];
-    if (blockIdx.x == 0) {
+    if (rank == 0) {
         if (a.hist && s_nb > 0.0)       // r.r -> ||r_k|| / ||b||
             for (int k = tid; k <= iters; k += nt) a.hist[k] = sqrt(a.hist[k]) / s_nb;
         if (tid == 0) {
@@ -414,6 +423,60 @@ finish:
             *a.iters = iters;
             *a.status = status;
         }
+    }
+    if (a.relres && status != AIRGA_E_TIMEOUT) {
+        // true residual ||b - A x|| / ||b|| of the final x, in FP64: the group
+        // exchanges x through global memory (one barrier), each CTA sums its rows
+        if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) return;
+        ++bar_no;
+        double v[2] = {0.0, 0.0};
+        for (int i = lo + tid; i < hi; i += nt) {
+            double ax = 0.0;
+#pragma unroll
+            for (int d = 0; d < kBand; ++d) {
+                const int c = i + d - kHalf;
+                if (c >= 0 && c < n) ax = fma(__ldg(a.A + (long long)d * n + i), __ldcg(a.x + c), ax);
+            }
+            const double bi = a.b[i], r = bi - ax;
+            v[0] = fma(r, r, v[0]);
+            v[1] = fma(bi, bi, v[1]);
+        }
+        block_partials_tree<2>(v, red, a.partials, bar_no & 1, G, rank);
+        if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) return;
+        if (rank == 0 && tid < 32) {
+            double t[2];
+            warp0_totals<2>(a.partials, bar_no & 1, G, t);
+            if (tid == 0) *a.relres = t[1] > 0.0 ? sqrt(t[0]) / sqrt(t[1]) : 0.0;
+        }
+    }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+pcg_pair_kernel(PcgArgs a, int R) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ PairShared sh;
+    pair_body<MODE>(a, R, gridDim.x, blockIdx.x, smem, sh);
+}
+
+// Batched form: CTA c runs the assignments asg[off[c] .. off[c+1]) in order;
+// each names a system (its PcgArgs in `sys`, with group-private barrier,
+// partials and p buffer), the group size, this CTA's rank and the rows per
+// CTA.  Assignments are appended in one global order of systems, so a CTA
+// waiting at a group barrier only waits for CTAs that are at the same or an
+// earlier system in that order: the schedule cannot deadlock.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads, 1)
+pcg_pair_batch_kernel(const PcgArgs *__restrict__ sys, const int4 *__restrict__ asg,
+                      const int *__restrict__ off) {
+    extern __shared__ __align__(16) double smem[];
+    __shared__ PairShared sh;
+    const int b = off[blockIdx.x], e = off[blockIdx.x + 1];
+    for (int k = b; k < e; ++k) {
+        const int4 w = asg[k];                       // (system, group size, rank, rows per CTA)
+        const PcgArgs a = sys[w.x];
+        if ((MODE == 1) == (a.nf == 1)) pair_body<MODE>(a, w.w, w.y, w.z, smem, sh);
+        __syncthreads();
     }
 }
 
@@ -453,6 +516,29 @@ int pcg_pair_occupancy(int mode, size_t smem, int *per_sm) {
             e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<1>, kThreads, smem);
     }
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg pair occupancy");
+}
+
+int pcg_pair_batch_prepare(int mode, size_t smem) {
+    cudaError_t e = mode ? cudaFuncSetAttribute(pcg_pair_batch_kernel<1>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                         : cudaFuncSetAttribute(pcg_pair_batch_kernel<0>,
+                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "batch smem");
+}
+
+int pcg_pair_batch_occupancy(int mode, size_t smem, int *per_sm) {
+    cudaError_t e = mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_batch_kernel<1>,
+                                                                         kThreads, smem)
+                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_batch_kernel<0>,
+                                                                         kThreads, smem);
+    return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "batch occupancy");
+}
+
+cudaError_t launch_pcg_pair_batch(int mode, int grid, size_t smem, const PcgArgs *sys,
+                                  const int4 *asg, const int *off, cudaStream_t s) {
+    void *kargs[] = {(void *)&sys, (void *)&asg, (void *)&off};
+    const void *kern = mode ? (const void *)pcg_pair_batch_kernel<1> : (const void *)pcg_pair_batch_kernel<0>;
+    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreads), kargs, smem, s);
 }
 
 cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
