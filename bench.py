@@ -207,7 +207,8 @@ def gpu_arm(args, world, rank, local):
     forms = None
     if not args.profile and not args.no_forms:
         del M, K
-        forms = {"precision": precision_form(G, torch, stream)}
+        forms = {"precision": precision_form(G, torch, stream),
+                 "batching": batching_form(G, torch, stream)}
 
     # end to end through the public API with host buffers
     e2e = e2e_arm(G, torch, beam, opts, args) if rank == 0 and not args.profile else None
@@ -365,6 +366,85 @@ def precision_form(G, torch, stream):
             "speedup": round(t64 / tmx, 3) if tmx > 0 else None,
             "spai_ms_total": round(tsp, 3),
             "max_rel_diff_mixed_vs_fp64": maxdiff}
+
+
+def batching_form(G, torch, stream):
+    """Batching workload: 32 beams, element counts log-uniform in
+    [5e3, 5e5] (seed 20261203), 4..16 shifts log-spaced in [1e-1, 1e4] each,
+    m in {1, 4} right-hand sides (tip + N(0,1) loads); SPAI (QR) per
+    (beam, shift).  All systems are solved (a) one pcg_solve call per
+    (beam, shift) in sequence and (b) in ONE persistent batched launch,
+    schedule chosen by the autotuner, captured in a CUDA graph and replayed.
+    Both report solves/s (systems at FP64 relative residual <= 1e-10)."""
+    from paper_1606_01216_gb300 import autotune
+    spec = W.batched_beams()
+    opts = G.options(tol=TOL, maxit=20000)
+    keep, systems, per_shift = [], [], []
+    for cfg in spec:
+        beam = W.beam(cfg["n_e"])
+        M, K = G.beam_mats(beam)
+        F = W.loads(beam.n, cfg["m"], seed=cfg["seed"])
+        Fd = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()          # (m, n)
+        keep.append((M, K, Fd))
+        for s in cfg["shifts"]:
+            A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
+            P = G.spai_build(A)
+            Xd = torch.zeros_like(Fd)
+            per_shift.append((A, P, Fd, Xd))
+            for c in range(cfg["m"]):
+                systems.append((A, P, Fd[c], Xd[c]))
+    torch.cuda.synchronize()
+    nsys = len(systems)
+    rows = int(sum(s[0].n for s in systems))
+
+    def seq_pass():
+        outs = []
+        for (A, P, Fd, Xd) in per_shift:
+            outs.append(G.pcg_solve(A, P, Fd.t(), opts))
+        return outs
+
+    seq_pass()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    outs = seq_pass()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1)
+    seq_ok = int(sum(int(((o["status"] == G.OK) & (o["true_relres"] <= 2 * TOL)).sum())
+                     for o in outs))
+
+    batch, report = autotune.tune(systems, opts=opts, stream=stream)
+    graph = torch.cuda.CUDAGraph()
+    gs = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    with torch.cuda.stream(gs):
+        with torch.cuda.graph(graph, stream=gs):
+            batch.solve(stream=gs)
+    graph.replay()
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    bat_ms = min(times)
+    bat_ok = int(((batch.status == G.OK) & (batch.relres <= 2 * TOL)).sum())
+    return {"workload": "32 beams n_e log-uniform [5e3, 5e5] (seed 20261203), 4..16 shifts "
+                        "logspace(-1,4) each, m in {1,4}; SPAI (QR) per (beam, shift)",
+            "systems": nsys, "rows_total": rows,
+            "sequential_pcg": {"solves_per_s": round(seq_ok / (seq_ms * 1e-3), 2),
+                               "converged": seq_ok, "ms": round(seq_ms, 3),
+                               "launches": len(per_shift)},
+            "batched_graph": {"solves_per_s": round(bat_ok / (bat_ms * 1e-3), 2),
+                              "converged": bat_ok, "ms": round(bat_ms, 3), "launches": 1,
+                              "autotune": report},
+            "speedup": round(seq_ms / bat_ms, 3)}
 
 
 def e2e_arm(G, torch, beam, opts, args):
