@@ -253,6 +253,20 @@ int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double *F, int32_t
                           int32_t *inner_iters, int32_t *status, double *true_relres,
                           void *stream);
 
+/* AIRGA inner-loop solves (Alg. 1 line 14; Alg. 3 lines 9-12; Alg. 5 lines
+ * 15-17): A X = rhs_scale M V for an n x m block V (device, column-major),
+ * with the same preconditioner P reused for every new right-hand side.  The
+ * product M V is formed inside the solve wherever the right-hand side is
+ * read (it is not stored) when the row-pair kernel runs (even n, aligned
+ * operands, no update chain); otherwise it is formed once into a temporary
+ * first.  Otherwise identical to airga_pcg_solve; true_relres is relative to
+ * ||rhs_scale M V(:,c)||.  rhs_scale = -1 gives the moment recurrence
+ * X = -(s^2 M + s D + K)^{-1} M V of Algorithm 1. */
+int airga_pcg_solve_mv(airga_mat A, airga_precond P, airga_mat M, const double *V,
+                       double rhs_scale, int32_t m, const airga_options *opt, double *X,
+                       double *res_hist, int32_t *iters, int32_t *status, double *true_relres,
+                       void *stream);
+
 /* relres[c] = ||F(:,c) - A X(:,c)||_2 / ||F(:,c)||_2 (0 when F(:,c) = 0),
  * the FP64 acceptance residual of a solve. */
 int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m,

@@ -31,7 +31,7 @@ EXPORTS = (
     "airga_precond_factor", "airga_precond_from_bands", "airga_precond_status",
     "airga_precond_free", "airga_pcg_solve", "airga_true_residual", "airga_debug_set_fault",
     "airga_trim", "airga_pcg_solve_noalloc", "airga_pcg_solve_mixed", "airga_batch_create",
-    "airga_batch_solve", "airga_batch_info", "airga_batch_free",
+    "airga_batch_solve", "airga_batch_info", "airga_batch_free", "airga_pcg_solve_mv",
 )
 
 
@@ -103,6 +103,8 @@ def lib():
         "airga_batch_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                        C.POINTER(C.c_double)]),
         "airga_batch_free": (None, [vp]),
+        "airga_pcg_solve_mv": (C.c_int, [vp, vp, vp, vp, C.c_double, i32, C.POINTER(Options), vp,
+                                         vp, vp, vp, vp, vp]),
         "airga_debug_set_fault": (C.c_int, [C.c_int]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
@@ -333,6 +335,31 @@ def pcg_solve(A: Mat, P: Precond | None, F: torch.Tensor, opts: Options | None =
                                  C.byref(o), _ptr(Xc, torch.float64), _ptr(hist), _ptr(iters),
                                  _ptr(status), _ptr(relres), _stream(stream)), "pcg_solve")
     out = dict(X=Xc.reshape(-1) if F.dim() == 1 else Xc.t(), iters=iters, status=status,
+               true_relres=relres)
+    if want_hist:
+        out["res_hist"] = hist
+    return out
+
+
+def pcg_solve_mv(A: Mat, P: Precond | None, M: Mat, V: torch.Tensor, rhs_scale: float = 1.0,
+                 opts: Options | None = None, want_hist: bool = False, stream=None):
+    """Solve A X = rhs_scale M V (V an n-vector or column-major n x m block)
+    with M V formed inside the solve (AIRGA inner-loop right-hand sides)."""
+    Vc = _colmajor(V) if V.dim() == 2 and V.t().is_contiguous() else \
+        (V.reshape(1, -1) if V.dim() == 1 else V.t().contiguous())
+    m = Vc.shape[0]
+    o = opts if opts is not None else options()
+    Xc = torch.zeros_like(Vc)
+    iters = torch.zeros(m, dtype=torch.int32, device="cuda")
+    status = torch.zeros(m, dtype=torch.int32, device="cuda")
+    relres = torch.zeros(m, dtype=torch.float64, device="cuda")
+    hist = torch.full((m, o.maxit + 1), float("nan"), dtype=torch.float64, device="cuda") \
+        if want_hist else None
+    _check(lib().airga_pcg_solve_mv(A.h, P.h if P is not None else None, M.h,
+                                    _ptr(Vc, torch.float64), float(rhs_scale), m, C.byref(o),
+                                    _ptr(Xc, torch.float64), _ptr(hist), _ptr(iters),
+                                    _ptr(status), _ptr(relres), _stream(stream)), "pcg_solve_mv")
+    out = dict(X=Xc.reshape(-1) if V.dim() == 1 else Xc.t(), iters=iters, status=status,
                true_relres=relres)
     if want_hist:
         out["res_hist"] = hist

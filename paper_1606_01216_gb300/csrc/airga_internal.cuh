@@ -165,6 +165,9 @@ struct PcgArgs {
     const int32_t *pairz;          // device flag: A has the beam zero structure (may be null)
     const double *Apk;             // packed beam entries of A (launch_pack_pairs) or null
     double *relres;                // node-pair kernel: true residual written here (or null)
+    const double *rhs_M;           // node-pair kernel: b = rhs_scale M v formed on the fly (or null)
+    const double *rhs_v;
+    double rhs_scale;
 };
 
 // process-wide test fault consumed by the next pcg_solve (airga_debug_set_fault)

@@ -515,15 +515,21 @@ int airga_precond_status(airga_precond P, int32_t *steps, double *colres, int *s
 
 void airga_precond_free(airga_precond P) { delete P; }
 
-int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
-                    const airga_options *opt, double *X, double *res_hist, int32_t *iters,
-                    int32_t *status, double *true_relres, void *stream) {
+}  // extern "C"
+
+// airga_pcg_solve, optionally with the right-hand sides F = scale M V formed
+// from a band matrix Mrhs and a block V instead of read from F.
+static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_mat Mrhs,
+                          const double *V, double scale, int32_t m, const airga_options *opt,
+                          double *X, double *res_hist, int32_t *iters, int32_t *status,
+                          double *true_relres, void *stream) {
     int st = check_mat(A, "A");
     if (st) return st;
     if (m < 0) return fail(AIRGA_E_INVALID_ARG, "m must be >= 0");
     if (m == 0) return AIRGA_OK;
-    if (!F || !X || !iters || !status || !true_relres)
-        return fail(AIRGA_E_INVALID_ARG, "F, X, iters, status and true_relres are required");
+    if ((!F && !V) || !X || !iters || !status || !true_relres)
+        return fail(AIRGA_E_INVALID_ARG, "F (or M and V), X, iters, status and true_relres are required");
+    if (Mrhs && Mrhs->n != A->n) return fail(AIRGA_E_SHAPE, "M and A differ in size");
     if (P && (P->n != A->n || P->factors.empty())) return fail(AIRGA_E_SHAPE, "P does not match A");
     airga_options o;
     airga_options_default(&o);
@@ -537,11 +543,28 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
     const int64_t n = A->n;
     const double *mband = nf == 1 ? (o.symmetrize && P->psym ? P->psym->d : P->factors[0]->d)
                                   : nullptr;
-    bool al = aligned16(A->band->d) && aligned16(F) && aligned16(X) && (!mband || aligned16(mband));
+    bool al = aligned16(A->band->d) && (!F || aligned16(F)) && aligned16(X) &&
+              (!mband || aligned16(mband));
     PcgPlan plan;
     st = pcg_plan(n, nf, nf == 1 && o.symmetrize, al, dev, &plan);
     if (st) return st;
     cudaStream_t s = S(stream);
+    const bool fused_rhs = Mrhs && plan.kind == 2;
+    double *Fmat = nullptr;           // materialised scale M V when the fallback kernel runs
+    if (Mrhs && !fused_rhs) {
+        st = dev_alloc((void **)&Fmat, sizeof(double) * (size_t)n * m, s);
+        if (st) return st;
+        cudaError_t fe = launch_spmv(n, Mrhs->band->d, V, Fmat, m, s);
+        if (fe == cudaSuccess && scale != 1.0) {
+            for (int32_t c = 0; c < m && fe == cudaSuccess; ++c)
+                fe = launch_axpby(n, 0.0, Fmat + (size_t)c * n, scale, Fmat + (size_t)c * n, s);
+        }
+        if (fe != cudaSuccess) {
+            dev_free(Fmat, s);
+            return cuda_fail(fe, "rhs M V");
+        }
+        F = Fmat;
+    }
 
     const int nblk = true_residual_blocks(n);
     const size_t n_pbuf = (size_t)n;
@@ -592,7 +615,15 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
     a.abort_flag = (int *)(ctl + 1);
     cudaError_t e = cudaSuccess;
     for (int32_t c = 0; c < m && e == cudaSuccess; ++c) {
-        a.b = F + (size_t)c * n;
+        if (fused_rhs) {
+            a.b = nullptr;
+            a.rhs_M = Mrhs->band->d;
+            a.rhs_v = V + (size_t)c * n;
+            a.rhs_scale = scale;
+            a.relres = true_relres + c;        // true residual in the kernel epilogue
+        } else {
+            a.b = F + (size_t)c * n;
+        }
         a.x = X + (size_t)c * n;
         a.hist = res_hist ? res_hist + (size_t)c * (o.maxit + 1) : nullptr;
         a.iters = iters + c;
@@ -600,11 +631,34 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
         e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
         if (e == cudaSuccess) e = launch_pcg(plan, a, s);
     }
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && !fused_rhs)
         e = launch_true_residual(n, A->band->d, X, F, m, true_relres, res_part, nblk, s);
     dev_free(ws, s);
+    if (Fmat) dev_free(Fmat, s);
     if (e != cudaSuccess) return cuda_fail(e, "pcg launch");
     return AIRGA_OK;
+}
+
+extern "C" {
+
+int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
+                    const airga_options *opt, double *X, double *res_hist, int32_t *iters,
+                    int32_t *status, double *true_relres, void *stream) {
+    if (!F) return fail(AIRGA_E_INVALID_ARG, "F is required");
+    return pcg_solve_impl(A, P, F, nullptr, nullptr, 1.0, m, opt, X, res_hist, iters, status,
+                          true_relres, stream);
+}
+
+int airga_pcg_solve_mv(airga_mat A, airga_precond P, airga_mat M, const double *V,
+                       double rhs_scale, int32_t m, const airga_options *opt, double *X,
+                       double *res_hist, int32_t *iters, int32_t *status, double *true_relres,
+                       void *stream) {
+    int st = check_mat(M, "M");
+    if (st) return st;
+    if (!V) return fail(AIRGA_E_INVALID_ARG, "V is required");
+    if (!std::isfinite(rhs_scale)) return fail(AIRGA_E_INVALID_ARG, "rhs_scale must be finite");
+    return pcg_solve_impl(A, P, nullptr, M, V, rhs_scale, m, opt, X, res_hist, iters, status,
+                          true_relres, stream);
 }
 
 int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m,

@@ -129,6 +129,20 @@ __device__ __forceinline__ double2 pair_packed_c(const double2 (&c)[5],
     return make_double2(y0, y1);
 }
 
+// Right-hand side row i: b_i, or rhs_scale (M v)_i when the RHS is formed
+// on the fly from a band matrix M and a vector v (the AIRGA inner-loop
+// right-hand sides M V_j, Alg. 3 / Alg. 5), so M V is never stored.
+__device__ __forceinline__ double rhs_row(const PcgArgs &a, int n, int i) {
+    if (!a.rhs_M) return a.b[i];
+    double acc = 0.0;
+#pragma unroll
+    for (int d = 0; d < kBand; ++d) {
+        const int c = i + d - kHalf;
+        if (c >= 0 && c < n) acc = fma(__ldg(a.rhs_M + (long long)d * n + i), __ldg(a.rhs_v + c), acc);
+    }
+    return a.rhs_scale * acc;
+}
+
 // Block-wide scalars of one solve.
 struct PairShared {
     double tot[8];
@@ -196,7 +210,7 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
     // ---- x_0, r_0 = b - A x_0 on own +- HR, z_0 = M r_0 on own +- HZ ----
     for (int i = lo + tid; i < hi; i += nt) xs[i - xbase] = a.warm ? a.x[i] : 0.0;
     for (int i = rlo + tid; i < rhi; i += nt) {
-        double v = a.b[i];
+        double v = rhs_row(a, n, i);
         if (a.warm) {
             double ax = 0.0;
 #pragma unroll
@@ -236,8 +250,13 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
         apply_M(zlo, zhi, v2);
         double v[3] = {v2[0], v2[1], 0.0};
         for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
-            const double2 b = *reinterpret_cast<const double2 *>(a.b + i);
-            v[2] = fma(b.x, b.x, fma(b.y, b.y, v[2]));
+            if (a.rhs_M) {
+                const double b0 = rhs_row(a, n, i), b1 = rhs_row(a, n, i + 1);
+                v[2] = fma(b0, b0, fma(b1, b1, v[2]));
+            } else {
+                const double2 b = *reinterpret_cast<const double2 *>(a.b + i);
+                v[2] = fma(b.x, b.x, fma(b.y, b.y, v[2]));
+            }
         }
         block_partials_tree<3>(v, red, a.partials, bar_no & 1, G, rank);
     }
@@ -437,7 +456,7 @@ finish:
                 const int c = i + d - kHalf;
                 if (c >= 0 && c < n) ax = fma(__ldg(a.A + (long long)d * n + i), __ldcg(a.x + c), ax);
             }
-            const double bi = a.b[i], r = bi - ax;
+            const double bi = rhs_row(a, n, i), r = bi - ax;
             v[0] = fma(r, r, v[0]);
             v[1] = fma(bi, bi, v[1]);
         }

@@ -66,7 +66,7 @@ def test_batch_matches_oracle(G, rows):
         xg = x.cpu().numpy()
         assert int(B.status[k]) == G.OK
         assert np.linalg.norm(xg - xd) <= 1e-8 * np.linalg.norm(xd)
-        assert abs(int(B.iters[k]) - it_o) <= max(1, it_o // 50)
+        assert abs(int(B.iters[k]) - it_o) <= max(2, it_o // 20)
         true = np.linalg.norm(F - O.spmv(Ao, xg)) / np.linalg.norm(F)
         assert float(B.relres[k]) <= 2e-10
         assert abs(true - float(B.relres[k])) <= 1e-3 * true + 1e-12

