@@ -37,6 +37,10 @@ TOL = 1e-10
 FP64_FMA_PER_CLK_SM = 2          # GB300 FP64 pipe
 PCG_FLOP_PER_ROW_ITER = 40       # 20 FMA: A (7) + P_sym (7) + 3 dots + 3 axpys
 PCG_BYTES_PER_ROW_ITER = 160     # A 56 + P_sym 56 + x, r, p read+write 48
+# DRAM bytes per row and iteration of pcg_pair_kernel from one ncu capture of
+# the s = 0.1 launch on this workload (dram read + write / (229 x 1e6)); the
+# bands stay in L2, see profiles/pcg_pair_kernel_beam_n1e6_s0.1.md
+PCG_DRAM_BYTES_PER_ROW_ITER = 8.54
 
 
 def peaks():
@@ -217,8 +221,12 @@ def gpu_arm(args, world, rank, local):
                 launches=launches_per_step * args.steps, n=n,
                 roofline={"bound": "alu", "achieved": round(achieved_tf, 4),
                           "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                          "frac": round(achieved_tf / fp64_peak, 4), "traffic": None,
-                          "kernel": "pcg_kernel (persistent PCG, FP64)",
+                          "frac": round(achieved_tf / fp64_peak, 4),
+                          "traffic": round(sum(pcg_it) * n * PCG_DRAM_BYTES_PER_ROW_ITER /
+                                           len(pcg_it)),
+                          "traffic_note": "ncu DRAM bytes per launch, 8.54 B/row/iter x the "
+                                          "mean row-iterations of a launch",
+                          "kernel": "pcg_pair_kernel (persistent row-pair PCG, FP64)",
                           "hbm_achieved_gbs": round(achieved_gbs, 1),
                           "hbm_peak_gbs": pk["hbm_gbs"],
                           "hbm_frac": round(achieved_gbs / pk["hbm_gbs"], 4),
@@ -435,6 +443,10 @@ def batching_form(G, torch, stream):
         times.append(e0.elapsed_time(e1))
     bat_ms = min(times)
     bat_ok = int(((batch.status == G.OK) & (batch.relres <= 2 * TOL)).sum())
+    # FP64 work of the batch in the model count (20 FMA per row and iteration)
+    row_iters = float(sum(s[0].n * int(it) for s, it in zip(systems, batch.iters.cpu().tolist())))
+    pk = peaks()
+    fp64_peak = 152 * FP64_FMA_PER_CLK_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
     return {"workload": "32 beams n_e log-uniform [5e3, 5e5] (seed 20261203), 4..16 shifts "
                         "logspace(-1,4) each, m in {1,4}; SPAI (QR) per (beam, shift)",
             "systems": nsys, "rows_total": rows,
@@ -443,6 +455,11 @@ def batching_form(G, torch, stream):
                                "launches": len(per_shift)},
             "batched_graph": {"solves_per_s": round(bat_ok / (bat_ms * 1e-3), 2),
                               "converged": bat_ok, "ms": round(bat_ms, 3), "launches": 1,
+                              "row_iterations": row_iters,
+                              "tflops_model": round(row_iters * PCG_FLOP_PER_ROW_ITER /
+                                                    (bat_ms * 1e-3) / 1e12, 4),
+                              "frac_fp64_peak": round(row_iters * PCG_FLOP_PER_ROW_ITER /
+                                                      (bat_ms * 1e-3) / 1e12 / fp64_peak, 4),
                               "autotune": report},
             "speedup": round(seq_ms / bat_ms, 3)}
 
