@@ -188,3 +188,45 @@ def cantilever_beta_l(k: int) -> float:
         else:
             hi = mid
     return 0.5 * (lo + hi)
+
+
+# ---------------------------------------------------------------------------
+# inputs of the learned SPAI-column predictor (network shapes, seeded draws)
+# ---------------------------------------------------------------------------
+
+MLP_IN, MLP_HID, MLP_OUT = 16, 64, 16
+MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_OUT * MLP_HID + MLP_OUT
+
+
+def mlp_random_params(seed: int, bias_scale: float = 0.5) -> np.ndarray:
+    """FP32 parameter vector W1|b1|W2|b2|W3|b3 (W[out][in]) with Glorot-uniform
+    weights and uniform biases, for parity tests."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for o, i in ((MLP_HID, MLP_IN), (MLP_HID, MLP_HID), (MLP_OUT, MLP_HID)):
+        lim = math.sqrt(6.0 / (o + i))
+        parts.append(rng.uniform(-lim, lim, o * i))
+        parts.append(rng.uniform(-bias_scale, bias_scale, o))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def mlp_random_samples(seed: int, count: int):
+    """Feature rows X[count, 16] (FP32, U(-1, 1)), targets T[count, 8] (FP32,
+    U(-2, 2)) and 7-bit output masks (uint8; every fourth row all ones)."""
+    rng = np.random.default_rng(seed)
+    X = rng.uniform(-1.0, 1.0, (count, MLP_IN)).astype(np.float32)
+    T = rng.uniform(-2.0, 2.0, (count, 8)).astype(np.float32)
+    mask = rng.integers(0, 128, count).astype(np.uint8)
+    mask[::4] = 127
+    return X, T, mask
+
+
+def mlp_training_columns(n: int, n_interior: int, seed: int, edge: int = 16) -> np.ndarray:
+    """Columns of an n-row beam matrix that enter the training set: the
+    `edge` columns at each end (clamped and free) and n_interior columns
+    drawn uniformly from the rest, sorted (int64)."""
+    rng = np.random.default_rng(seed)
+    e = min(edge, n // 2)
+    inner = np.arange(e, n - e)
+    pick = rng.choice(inner, size=min(n_interior, inner.size), replace=False) if inner.size else inner
+    return np.unique(np.concatenate([np.arange(e), np.arange(n - e, n), pick])).astype(np.int64)
