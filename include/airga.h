@@ -170,8 +170,10 @@ int airga_precond_from_bands(int64_t n, int32_t nfactors, const double *const *b
 /* Per-column results of the SPAI call that produced the newest factor:
  * steps[n] (int32, MR steps; 0 in QR mode) and colres[n] (double,
  * ||b_j - A m_j||_2 of the column least-squares problem); either may be
- * NULL.  *status_out (host) is AIRGA_OK or AIRGA_E_RANK and SYNCHRONISES
- * `stream` when status_out is not NULL. */
+ * NULL.  *status_out (host) is AIRGA_OK, AIRGA_E_RANK, or — for a handle
+ * made by airga_mlp_spai — AIRGA_E_INVALID_ARG (A has a non-positive or
+ * non-finite diagonal entry) or AIRGA_E_TIMEOUT (a bounded tensor-core wait
+ * gave up); it SYNCHRONISES `stream` when status_out is not NULL. */
 int airga_precond_status(airga_precond P, int32_t *steps, double *colres, int *status_out,
                          void *stream);
 
@@ -302,6 +304,114 @@ int airga_pcg_solve_noalloc(int64_t n, const double *A_band, const double *M_ban
                             const double *F, int32_t m, const airga_options *opt, double *X,
                             double *res_hist, int32_t *iters, int32_t *status,
                             double *true_relres, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* learned SPAI-column predictor                                           */
+/* ---------------------------------------------------------------------- */
+
+/* A small perceptron that predicts the seven entries of SPAI column j
+ * (Sec. 3.1, Eq. 3.1, pattern J_j = {j-3..j+3}) of a shifted matrix
+ * A = s^2 M + s D + K (Eq. 1.1) from local features, trained on columns of
+ * SPAIs built by airga_spai_build.  It stands in for the SPAI update of
+ * Sec. 3.2 (a new preconditioner for a new shift at far lower cost than a
+ * build); a caller that needs a guarantee solves with it under an iteration
+ * cap and falls back to airga_spai_build.
+ *
+ * Network: y = W3 relu(W2 relu(W1 x + b1) + b2) + b3, relu(z) = max(z, 0),
+ * 16 -> 64 -> 64 -> 16
+ * (outputs 7..15 unused).  FP32 master parameters, BF16 copies of the
+ * weights and BF16 activations as tensor-core operands, FP32 accumulation,
+ * FP32 biases and activation functions.  Parameter vector (FP32,
+ * AIRGA_MLP_NPARAM values): W1[64][16] | b1[64] | W2[64][64] | b2[64] |
+ * W3[16][64] | b3[16], W[out][in] row-major.
+ *
+ * Features of column j of an n-row A (FP32 rows of 16):
+ *   log10(s)/4, alpha, beta, log10(A_jj)/8,
+ *   A(j+d, j) / sqrt(A(j+d, j+d) A_jj) for d = -3,-2,-1,1,2,3 (0 outside),
+ *   min(j, 8)/8, min(n-1-j, 8)/8, j mod 2, 0, 0, 0.
+ * Targets (FP32 rows of 8): t_o = P(j+d, j) sqrt(A(j+d, j+d) A_jj) for
+ * d = o - 3, o = 0..6, t_7 = 0; mask byte: bit o set when 0 <= j+d < n.
+ * Loss: L = 1/(2B) sum over the B samples of a minibatch and the masked
+ * outputs of (y_o - t_o)^2.  Training: Adam (Kingma and Ba 2015) with bias
+ * correction, optional half-cosine learning-rate decay. */
+#define AIRGA_MLP_IN 16
+#define AIRGA_MLP_HIDDEN 64
+#define AIRGA_MLP_OUT 16
+#define AIRGA_MLP_NPARAM 6288
+
+typedef struct airga_mlp_s *airga_mlp;
+
+typedef struct {
+    float lr;                   /* Adam step size (default 2e-3) */
+    float beta1, beta2, eps;    /* Adam moments (defaults 0.9, 0.999, 1e-8) */
+    int32_t batch;              /* samples per step (default 4096) */
+    int32_t cosine_steps;       /* > 0: lr_t = lr (1 + cos(pi min(t, c) / c)) / 2 at Adam step t (default 0 = constant) */
+    uint64_t seed;              /* minibatch draw: sample k of step t is SplitMix64 output number
+                                   t * 2^32 + k of the sequence started at seed, modulo count */
+} airga_mlp_train_options;
+
+void airga_mlp_train_options_default(airga_mlp_train_options *opt);
+
+/* New network with Glorot-uniform weights drawn from SplitMix64(seed) on the
+ * host and zero biases; Adam state zero.  SYNCHRONISES `stream`.  The handle
+ * owns about 0.1 MB plus a gradient scratch of 25 KB per SM. */
+int airga_mlp_create(uint64_t seed, void *stream, airga_mlp *out);
+
+/* Copy AIRGA_MLP_NPARAM FP32 parameters in from device memory and reset the
+ * Adam state and the step counter. */
+int airga_mlp_set_params(airga_mlp net, const float *params, void *stream);
+
+/* Copy the AIRGA_MLP_NPARAM FP32 master parameters out to device memory. */
+int airga_mlp_get_params(airga_mlp net, float *params, void *stream);
+
+/* Adam steps taken so far and an error status (AIRGA_OK, AIRGA_E_INVALID_ARG
+ * for an out-of-range sample index, AIRGA_E_TIMEOUT for a tensor-core wait
+ * that gave up).  SYNCHRONISES `stream`. */
+int airga_mlp_status(airga_mlp net, int64_t *steps_done, int *status_out, void *stream);
+
+/* Training pairs from a shifted matrix A (shift s > 0, damping alpha, beta)
+ * and, optionally, its SPAI P (a single-factor handle, e.g. from
+ * airga_spai_build): for the columns cols[0..count) (device int64; NULL =
+ * columns 0..count-1, count <= n) write X[count][16] and, when P is given,
+ * T[count][8] and mask[count].  X and T are 16-byte aligned device arrays.
+ * *flag (device int32, caller-zeroed) gets bit 8 for a column index outside
+ * [0, n) (that row is skipped) and bit 2 for a non-positive diagonal. */
+int airga_mlp_features(airga_mat A, airga_precond P, double s, double alpha, double beta,
+                       const int64_t *cols, int64_t count, float *X, float *T, uint8_t *mask,
+                       int32_t *flag, void *stream);
+
+/* Y[count][16] = network outputs for the feature rows X[count][16]
+ * (tensor-core inference kernel; X, Y 16-byte aligned). */
+int airga_mlp_forward(airga_mlp net, const float *X, int64_t count, float *Y, void *stream);
+
+/* Mean gradient dL/dparams (grad: AIRGA_MLP_NPARAM floats, device) and loss
+ * (*loss, device double, may be NULL) over the minibatch idx[0..batch)
+ * (device int32 row indices into X, T, mask; count <= 2^31 - 1) at the
+ * current parameters; nothing is updated. */
+int airga_mlp_grad(airga_mlp net, const float *X, const float *T, const uint8_t *mask,
+                   int64_t count, const int32_t *idx, int32_t batch, float *grad, double *loss,
+                   void *stream);
+
+/* `steps` Adam steps on the training set (X, T, mask; count rows), each one
+ * forward/backward launch and one update launch, enqueued without host
+ * synchronisation (graph-capturable; the step counter lives on the device).
+ * idx: NULL = draw minibatches on the device (opt->seed), else device int32
+ * [steps * batch] explicit indices.  loss_hist (device, may be NULL) gets
+ * the loss of each step's minibatch before its update. */
+int airga_mlp_train(airga_mlp net, const float *X, const float *T, const uint8_t *mask,
+                    int64_t count, int32_t steps, const airga_mlp_train_options *opt,
+                    const int32_t *idx, float *loss_hist, void *stream);
+
+/* Learned SPAI for A = s^2 M + s D + K: the network's outputs for every
+ * column, unscaled, as a band-7 factor P (entries outside the matrix 0),
+ * plus P_sym = 1/2 (P + P^T), in a new single-factor handle usable wherever
+ * a built SPAI is (airga_pcg_solve, airga_batch_create, ...).  Per-column
+ * SPAI data (steps, colres) are not produced.  Errors found on the device
+ * are reported by airga_precond_status. */
+int airga_mlp_spai(airga_mlp net, airga_mat A, double s, double alpha, double beta, void *stream,
+                   airga_precond *P_out);
+
+void airga_mlp_free(airga_mlp net);
 
 /* Test hook for failure detection (no GPU fault involved): arm a fault for
  * the next airga_pcg_solve call of this process.  AIRGA_FAULT_SKIP_ARRIVAL

@@ -16,8 +16,8 @@ What it computes (all written from the definitions, no blocking or fusion):
     mask      bit o set when 0 <= j+d < n.
   The symmetric diagonal scaling makes the targets O(1) at every shift and is
   undone exactly by `decode`.
-* A three-layer perceptron y = W3 tanh(W2 tanh(W1 x + b1) + b2) + b3
-  (16 -> 64 -> 64 -> 16; outputs 7..15 unused) and the loss
+* A three-layer perceptron y = W3 relu(W2 relu(W1 x + b1) + b2) + b3,
+  relu(z) = max(z, 0) (16 -> 64 -> 64 -> 16; outputs 7..15 unused), and the loss
   L = 1/(2B) sum_samples sum_{o in mask} (y_o - t_o)^2 with its gradient by
   the chain rule (back-propagation).
 * The Adam update of Kingma and Ba (ICLR 2015, Algorithm 1) with bias
@@ -30,7 +30,7 @@ rounding the tensor-core kernels apply — every GEMM operand (inputs, weights,
 hidden activations, output errors, hidden deltas) rounded to bfloat16 with
 round-to-nearest-even, products accumulated exactly (FP64 here, FP32 on the
 GPU), biases and activations in full precision — so GPU results can be
-compared tightly.
+compared tightly.  relu'(0) is taken as 0.
 
 Parameter vector layout (FP32 on the GPU, 6288 values):
   W1[64][16] | b1[64] | W2[64][64] | b2[64] | W3[16][64] | b3[16]
@@ -148,13 +148,13 @@ def forward(params, X, emulate_bf16=True):
     Xq = r(X)
     W1, W2, W3 = r(p["W1"]), r(p["W2"]), r(p["W3"])
     z1 = Xq @ W1.T + p["b1"]
-    h1 = np.tanh(z1)
+    h1 = np.maximum(z1, 0.0)
     H1 = r(h1)
     z2 = H1 @ W2.T + p["b2"]
-    h2 = np.tanh(z2)
+    h2 = np.maximum(z2, 0.0)
     H2 = r(h2)
     y = H2 @ W3.T + p["b3"]
-    return y, dict(Xq=Xq, W1=W1, W2=W2, W3=W3, h1=h1, H1=H1, h2=h2, H2=H2)
+    return y, dict(Xq=Xq, W1=W1, W2=W2, W3=W3, z1=z1, H1=H1, z2=z2, H2=H2)
 
 
 def mask_matrix(mask, cols=N_OUT):
@@ -176,9 +176,9 @@ def loss_grad(params, X, T, mask, emulate_bf16=True):
     e = (y - Tm) * mask_matrix(mask)
     loss = 0.5 * float((e * e).sum()) / B
     E = r(e)
-    dz2 = (E @ c["W3"]) * (1.0 - c["h2"] ** 2)
+    dz2 = (E @ c["W3"]) * (c["z2"] > 0.0)          # relu'(z) = 1 for z > 0, else 0
     Dz2 = r(dz2)
-    dz1 = (Dz2 @ c["W2"]) * (1.0 - c["h1"] ** 2)
+    dz1 = (Dz2 @ c["W2"]) * (c["z1"] > 0.0)
     Dz1 = r(dz1)
     g = dict(W3=E.T @ c["H2"], b3=E.sum(0), W2=Dz2.T @ c["H1"], b2=Dz2.sum(0),
              W1=Dz1.T @ c["Xq"], b1=Dz1.sum(0))

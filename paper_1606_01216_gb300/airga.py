@@ -32,7 +32,12 @@ EXPORTS = (
     "airga_precond_free", "airga_pcg_solve", "airga_true_residual", "airga_debug_set_fault",
     "airga_trim", "airga_pcg_solve_noalloc", "airga_pcg_solve_mixed", "airga_batch_create",
     "airga_batch_solve", "airga_batch_info", "airga_batch_free", "airga_pcg_solve_mv",
+    "airga_mlp_train_options_default", "airga_mlp_create", "airga_mlp_set_params",
+    "airga_mlp_get_params", "airga_mlp_status", "airga_mlp_features", "airga_mlp_forward",
+    "airga_mlp_grad", "airga_mlp_train", "airga_mlp_spai", "airga_mlp_free",
 )
+
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
 
 
 class Options(C.Structure):
@@ -48,6 +53,18 @@ class Options(C.Structure):
         ("barrier_timeout_ms", C.c_int32),
         ("inner_tol", C.c_double),
         ("max_outer", C.c_int32),
+    ]
+
+
+class MlpTrainOptions(C.Structure):
+    _fields_ = [
+        ("lr", C.c_float),
+        ("beta1", C.c_float),
+        ("beta2", C.c_float),
+        ("eps", C.c_float),
+        ("batch", C.c_int32),
+        ("cosine_steps", C.c_int32),
+        ("seed", C.c_uint64),
     ]
 
 
@@ -109,6 +126,20 @@ def lib():
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
         "airga_trim": (C.c_int, []),
+        "airga_mlp_train_options_default": (None, [C.POINTER(MlpTrainOptions)]),
+        "airga_mlp_create": (C.c_int, [C.c_uint64, vp, C.POINTER(vp)]),
+        "airga_mlp_set_params": (C.c_int, [vp, vp, vp]),
+        "airga_mlp_get_params": (C.c_int, [vp, vp, vp]),
+        "airga_mlp_status": (C.c_int, [vp, C.POINTER(i64), C.POINTER(C.c_int), vp]),
+        "airga_mlp_features": (C.c_int, [vp, vp, C.c_double, C.c_double, C.c_double, vp, i64,
+                                         vp, vp, vp, vp, vp]),
+        "airga_mlp_forward": (C.c_int, [vp, vp, i64, vp, vp]),
+        "airga_mlp_grad": (C.c_int, [vp, vp, vp, vp, i64, vp, i32, vp, vp, vp]),
+        "airga_mlp_train": (C.c_int, [vp, vp, vp, vp, i64, i32, C.POINTER(MlpTrainOptions), vp,
+                                      vp, vp]),
+        "airga_mlp_spai": (C.c_int, [vp, vp, C.c_double, C.c_double, C.c_double, vp,
+                                     C.POINTER(vp)]),
+        "airga_mlp_free": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -309,6 +340,14 @@ def precond_status(P: Precond, stream=None):
     return steps, colres, st.value
 
 
+def precond_status_code(P: Precond, stream=None) -> int:
+    """Status of the newest factor alone (synchronises the stream)."""
+    st = C.c_int(0)
+    _check(lib().airga_precond_status(P.h, None, None, C.byref(st), _stream(stream)),
+           "precond_status")
+    return st.value
+
+
 def pcg_solve(A: Mat, P: Precond | None, F: torch.Tensor, opts: Options | None = None,
               X: torch.Tensor | None = None, want_hist: bool = False, stream=None):
     """Solve A X = F (F: n or n x m column-major, i.e. a contiguous (m, n)
@@ -466,3 +505,95 @@ def beam_mats(beam, stream=None):
     M = mat_from_csr(beam.n, rp, ci, mv, stream)
     K = mat_from_csr(beam.n, rp, ci, kv, stream)
     return M, K
+
+
+# ---------------------------------------------------------------------------
+# learned SPAI-column predictor
+# ---------------------------------------------------------------------------
+
+def mlp_train_options(**kw) -> MlpTrainOptions:
+    o = MlpTrainOptions()
+    lib().airga_mlp_train_options_default(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+class Mlp:
+    """Owning wrapper of an airga_mlp handle (the learned SPAI-column
+    predictor: parameters, Adam state and step counter on the device)."""
+
+    def __init__(self, seed: int = 0, stream=None):
+        out = C.c_void_p()
+        _check(lib().airga_mlp_create(C.c_uint64(int(seed)), _stream(stream), C.byref(out)),
+               "mlp_create")
+        self.h = out
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value and _lib is not None:
+            _lib.airga_mlp_free(self.h)
+            self.h = C.c_void_p(None)
+
+    def set_params(self, params: torch.Tensor, stream=None):
+        _check(lib().airga_mlp_set_params(self.h, _ptr(params, torch.float32), _stream(stream)),
+               "mlp_set_params")
+
+    def params(self, stream=None) -> torch.Tensor:
+        out = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
+        _check(lib().airga_mlp_get_params(self.h, _ptr(out), _stream(stream)), "mlp_get_params")
+        return out
+
+    def status(self, stream=None):
+        """(Adam steps done, status code); synchronises the stream."""
+        steps, st = C.c_int64(), C.c_int()
+        _check(lib().airga_mlp_status(self.h, C.byref(steps), C.byref(st), _stream(stream)),
+               "mlp_status")
+        return steps.value, st.value
+
+    def forward(self, X: torch.Tensor, stream=None) -> torch.Tensor:
+        Y = torch.empty(X.shape[0], MLP_OUT, dtype=torch.float32, device="cuda")
+        _check(lib().airga_mlp_forward(self.h, _ptr(X, torch.float32), X.shape[0], _ptr(Y),
+                                       _stream(stream)), "mlp_forward")
+        return Y
+
+    def grad(self, X, T, mask, idx, stream=None):
+        """(mean gradient float32[NPARAM], loss float64[1]) over rows idx."""
+        g = torch.empty(MLP_NPARAM, dtype=torch.float32, device="cuda")
+        loss = torch.empty(1, dtype=torch.float64, device="cuda")
+        _check(lib().airga_mlp_grad(self.h, _ptr(X, torch.float32), _ptr(T, torch.float32),
+                                    _ptr(mask, torch.uint8), X.shape[0], _ptr(idx, torch.int32),
+                                    idx.numel(), _ptr(g), _ptr(loss), _stream(stream)),
+               "mlp_grad")
+        return g, loss
+
+    def train(self, X, T, mask, steps: int, opts: MlpTrainOptions | None = None, idx=None,
+              loss_hist: torch.Tensor | None = None, stream=None):
+        o = opts if opts is not None else mlp_train_options()
+        _check(lib().airga_mlp_train(self.h, _ptr(X, torch.float32), _ptr(T, torch.float32),
+                                     _ptr(mask, torch.uint8), X.shape[0], int(steps), C.byref(o),
+                                     _ptr(idx, torch.int32), _ptr(loss_hist, torch.float32),
+                                     _stream(stream)), "mlp_train")
+        return loss_hist
+
+    def spai(self, A: Mat, s: float, alpha: float, beta: float, stream=None) -> Precond:
+        out = C.c_void_p()
+        _check(lib().airga_mlp_spai(self.h, A.h, float(s), float(alpha), float(beta),
+                                    _stream(stream), C.byref(out)), "mlp_spai")
+        return Precond(out.value, A.n)
+
+
+def mlp_features(A: Mat, P: Precond | None, s: float, alpha: float, beta: float,
+                 cols: torch.Tensor | None = None, stream=None):
+    """(X[count,16] float32, T[count,8] float32 or None, mask[count] uint8 or
+    None, flag int32[1]) for the columns `cols` (device int64) or all columns."""
+    count = cols.numel() if cols is not None else A.n
+    X = torch.empty(count, MLP_IN, dtype=torch.float32, device="cuda")
+    T = torch.empty(count, 8, dtype=torch.float32, device="cuda") if P is not None else None
+    mask = torch.empty(count, dtype=torch.uint8, device="cuda") if P is not None else None
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    _check(lib().airga_mlp_features(A.h, P.h if P is not None else None, float(s), float(alpha),
+                                    float(beta), _ptr(cols, torch.int64), count, _ptr(X), _ptr(T),
+                                    _ptr(mask), _ptr(flag), _stream(stream)), "mlp_features")
+    return X, T, mask, flag

@@ -508,7 +508,12 @@ int airga_precond_status(airga_precond P, int32_t *steps, double *colres, int *s
             AIRGA_CUDA(cudaMemcpyAsync(&f, P->rank_flag.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, s));
             AIRGA_CUDA(cudaStreamSynchronize(s));
         }
-        *status_out = f ? AIRGA_E_RANK : AIRGA_OK;
+        // status word bits: 1 rank-deficient column block (SPAI), 2 non-positive
+        // diagonal of A (learned SPAI), 4 tensor-core wait timeout (learned SPAI)
+        *status_out = f == 0 ? AIRGA_OK
+                             : (f & 4) ? AIRGA_E_TIMEOUT
+                             : (f & 2) ? AIRGA_E_INVALID_ARG
+                                       : AIRGA_E_RANK;
     }
     return AIRGA_OK;
 }

@@ -86,3 +86,27 @@ def test_product_path_does_not_import_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "airga_oracle" not in text and "liboracle" not in text, f
+
+
+def test_mlp_options_layout_and_defaults(G):
+    O = G.MlpTrainOptions
+    assert O.lr.offset == 0 and O.beta1.offset == 4 and O.beta2.offset == 8 and O.eps.offset == 12
+    assert O.batch.offset == 16 and O.cosine_steps.offset == 20 and O.seed.offset == 24
+    assert C.sizeof(O) == 32
+    o = G.mlp_train_options()
+    assert o.batch == 4096 and o.cosine_steps == 0 and abs(o.lr - 2e-3) < 1e-9
+    assert abs(o.beta1 - 0.9) < 1e-7 and abs(o.beta2 - 0.999) < 1e-7 and o.eps > 0
+
+
+def test_mlp_argument_checks_need_no_gpu(G):
+    L = G.lib()
+    out = C.c_void_p()
+    assert L.airga_mlp_spai(None, None, 1.0, 0.1, 1e-4, None, C.byref(out)) == G.E_INVALID_ARG
+    assert L.airga_mlp_grad(None, None, None, None, 10, None, 4, None, None, None) == G.E_INVALID_ARG
+    assert L.airga_mlp_train(None, None, None, None, 10, 1, None, None, None, None) == G.E_INVALID_ARG
+    assert L.airga_mlp_forward(None, None, 1, None, None) == G.E_INVALID_ARG
+    assert L.airga_mlp_features(None, None, 1.0, 0.1, 1e-4, None, 1, None, None, None, None,
+                                None) == G.E_INVALID_ARG
+    assert L.airga_mlp_set_params(None, None, None) == G.E_INVALID_ARG
+    assert L.airga_mlp_spai(None, None, 1.0, 0.1, 1e-4, None, None) == G.E_INVALID_ARG
+    L.airga_mlp_free(None)

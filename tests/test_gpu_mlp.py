@@ -1,0 +1,302 @@
+"""Learned SPAI-column predictor on the GPU vs the CPU oracle (oracle/mlp.py).
+
+Tolerances (from the arithmetic):
+  features           |x_gpu - x_ora| <= 6e-7 (1 + |x_ora|): the GPU computes them in FP32
+                     (a product of three correctly rounded factors: <= 4 FP32 ulps), the
+                     oracle in FP64 rounded once to FP32
+  targets            |t_gpu - t_ora| <= 2e-7 (1 + |t_ora|): FP64 on both sides, one
+                     rounding to FP32, on entries of A and P that agree to 1e-10
+  masks, corners     bit-exact
+  forward            vs the BF16-emulating oracle: every output within 2e-3, 99 % within
+                     1e-4.  Both sides round the same operands to BF16; they differ by
+                     FP32 accumulation (~1e-6 relative), which now and then moves a hidden
+                     activation across a BF16 rounding boundary (one BF16 ulp, 2^-8
+                     relative, of one activation: <= 1.2e-3 on an output for these weights)
+  gradient           vs the emulating oracle: per parameter block ||g_gpu - g_ora|| <= 2e-3
+                     ||g_ora||; vs the exact FP64 gradient (pinned by finite differences)
+                     no further than the emulating oracle is, plus that 2e-3 — BF16 operand
+                     rounding (2^-9 relative per operand, and a flipped relu' where it moves
+                     a pre-activation across 0) is the whole difference
+  Adam step          step 1 moves every parameter by lr g / (|g| + eps): equal to the
+                     oracle's within 1e-6 relative wherever |g| is not tiny
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import mlp as om
+from paper_1606_01216_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+AL, BE = W.ALPHA, W.BETA
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_01216_gb300 import build
+    build.build()
+    from paper_1606_01216_gb300 import airga
+    airga.lib()
+    return airga
+
+
+def _band(csr):
+    n = csr.n
+    b = np.zeros((7, n))
+    rows = np.repeat(np.arange(n), np.diff(csr.rowptr))
+    b[csr.col - rows + 3, rows] = csr.val
+    return b
+
+
+def _net(G, params):
+    net = G.Mlp(seed=1)
+    net.set_params(torch.from_numpy(params).cuda())
+    return net
+
+
+def _blocks(g):
+    return om.unpack(g)
+
+
+def test_forward_parity(G):
+    p = W.mlp_random_params(101)
+    for count in (1, 128, 300, 1000):          # one row, one tile, ragged tail, several tiles
+        X, _, _ = W.mlp_random_samples(102 + count, count)
+        net = _net(G, p)
+        Y = net.forward(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+        Yo, _ = om.forward(p, X.astype(np.float64), emulate_bf16=True)
+        err = np.abs(Y - Yo)
+        assert err.max() <= 2e-3, err.max()
+        assert np.quantile(err, 0.99) <= 1e-4
+        Yx, _ = om.forward(p, X.astype(np.float64), emulate_bf16=False)
+        assert np.all(np.abs(Y - Yx) <= 3e-2 * (1 + np.abs(Yx)))
+
+
+def test_gradient_parity(G):
+    p = W.mlp_random_params(111)
+    X, T, mask = W.mlp_random_samples(112, 1000)
+    rng = np.random.default_rng(113)
+    for B in (1, 300, 2500):                   # single sample, ragged tail, many tiles per CTA
+        idx = rng.integers(0, 1000, B).astype(np.int32)
+        net = _net(G, p)
+        g, loss = net.grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(),
+                           torch.from_numpy(mask).cuda(), torch.from_numpy(idx).cuda())
+        g = g.cpu().numpy().astype(np.float64)
+        Lo, go = om.loss_grad(p, X[idx], T[idx], mask[idx], emulate_bf16=True)
+        Lx, gx = om.loss_grad(p, X[idx], T[idx], mask[idx], emulate_bf16=False)
+        assert float(loss.item()) == pytest.approx(Lo, rel=1e-5)
+        gb, gob, gxb = _blocks(g), _blocks(go), _blocks(gx)
+        for k in gob:
+            if k in ("W3", "b3"):   # rows 7..15 have zero gradient exactly
+                assert not gb[k][7:].any()
+            ref = np.linalg.norm(gob[k])
+            assert np.linalg.norm(gb[k] - gob[k]) <= 2e-3 * ref + 1e-12, (B, k)
+            # no further from the exact gradient than the BF16 rounding model itself
+            gap = np.linalg.norm(gob[k] - gxb[k])
+            assert np.linalg.norm(gb[k] - gxb[k]) <= gap + 2e-3 * ref + 1e-12, (B, k)
+            assert gap <= 0.1 * np.linalg.norm(gxb[k]) + 1e-12, (B, k)
+
+
+def test_adam_step_parity(G):
+    p = W.mlp_random_params(121)
+    X, T, mask = W.mlp_random_samples(122, 700)
+    B = 512
+    idx = np.random.default_rng(123).integers(0, 700, B).astype(np.int32)
+    net = _net(G, p)
+    lr = 1e-3
+    opts = G.mlp_train_options(lr=lr, batch=B)
+    hist = torch.zeros(1, dtype=torch.float32, device="cuda")
+    net.train(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), torch.from_numpy(mask).cuda(),
+              1, opts, idx=torch.from_numpy(idx).cuda(), loss_hist=hist)
+    p1 = net.params().cpu().numpy().astype(np.float64)
+    L, go = om.loss_grad(p, X[idx], T[idx], mask[idx], emulate_bf16=True)
+    po, _, _ = om.adam(p.astype(np.float64), np.zeros(om.NPARAM), np.zeros(om.NPARAM), go, 1, lr)
+    assert float(hist.item()) == pytest.approx(L, rel=1e-5)
+    big = np.abs(go) > 1e-2 * np.sqrt(np.mean(go ** 2))
+    assert big.sum() > 0.5 * om.NPARAM
+    assert np.all(np.abs(p1[big] - po[big]) <= 1e-6 * np.abs(po[big]) + 2e-3 * lr)
+    assert np.all(np.abs(p1 - po) <= 2.0 * lr + 1e-6 * np.abs(po))
+    steps, st = net.status()
+    assert steps == 1 and st == G.OK
+
+
+def test_features_targets_parity(G, ora):
+    n_e = 700
+    beam = W.beam(n_e)
+    M, K = G.beam_mats(beam)
+    for s in (0.3, 7.0, 2e3):
+        A = G.assemble_shifted(M, K, AL, BE, s)
+        P = G.spai_build(A)
+        Ao = ora.shifted_csr(beam, AL, BE, s)
+        bA, bP = _band(Ao), _band(ora.spai(Ao))
+        cols = W.mlp_training_columns(beam.n, 200, seed=7)
+        X, T, mask, flag = G.mlp_features(A, P, s, AL, BE, torch.from_numpy(cols).cuda())
+        Xo = om.features(bA, s, AL, BE, cols)
+        To, mo = om.targets(bA, bP, cols)
+        assert int(flag.item()) == 0
+        assert np.all(np.abs(X.cpu().numpy() - Xo) <= 6e-7 * (1 + np.abs(Xo)))
+        assert np.all(np.abs(T.cpu().numpy() - To) <= 2e-7 * (1 + np.abs(To)))
+        assert np.array_equal(mask.cpu().numpy(), mo)
+        Xa, Ta, ma, _ = G.mlp_features(A, None, s, AL, BE)          # all columns, no targets
+        assert Ta is None and ma is None
+        Xao = om.features(bA, s, AL, BE)
+        assert np.all(np.abs(Xa.cpu().numpy() - Xao) <= 6e-7 * (1 + np.abs(Xao)))
+
+
+def test_learned_spai_parity(G, ora):
+    p = W.mlp_random_params(131, bias_scale=0.2)
+    net = _net(G, p)
+    for n_e in (1, 2, 700):                     # n = 2, 4 (every column touches a corner), 1400
+        beam = W.beam(n_e)
+        M, K = G.beam_mats(beam)
+        s = 5.0
+        A = G.assemble_shifted(M, K, AL, BE, s)
+        P = net.spai(A, s, AL, BE)
+        Pg = G.precond_factor(P, 0).cpu().numpy().reshape(7, beam.n)
+        bA = _band(ora.shifted_csr(beam, AL, BE, s))
+        Po = om.learned_spai(p, bA, s, AL, BE, emulate_bf16=True)
+        n = beam.n
+        # network units: P(i, j) sqrt(A_ii A_jj)
+        scale = np.zeros((7, n))
+        for d in range(-3, 4):
+            i = np.arange(n)
+            ok = (i + d >= 0) & (i + d < n)
+            scale[d + 3, ok] = np.sqrt(bA[3, i[ok]] * bA[3, i[ok] + d])
+        err = np.abs(Pg - Po) * scale
+        assert err.max() <= 1e-2 and np.quantile(err[scale > 0], 0.99) <= 1e-4
+        assert np.array_equal(Pg[scale == 0], np.zeros(int((scale == 0).sum())))
+        assert G.precond_status_code(P) == G.OK
+        Psym = 0.5 * (Pg + _transpose_band(Pg))
+        z = G.precond_apply(P, torch.ones(n, dtype=torch.float64, device="cuda")).cpu().numpy()
+        assert np.allclose(z, _band_matvec(Psym, np.ones(n)), rtol=1e-12, atol=1e-300)
+
+
+def _transpose_band(b):
+    n = b.shape[1]
+    t = np.zeros_like(b)
+    for d in range(-3, 4):
+        i = np.arange(max(0, -d), min(n, n - d))
+        t[-d + 3, i + d] = b[d + 3, i]
+    return t
+
+
+def _band_matvec(b, x):
+    n = b.shape[1]
+    y = np.zeros(n)
+    for d in range(-3, 4):
+        i = np.arange(max(0, -d), min(n, n - d))
+        y[i] += b[d + 3, i] * x[i + d]
+    return y
+
+
+def test_rejects_and_flags(G):
+    p = W.mlp_random_params(141)
+    net = _net(G, p)
+    X, T, mask = W.mlp_random_samples(142, 100)
+    Xd, Td, md = (torch.from_numpy(a).cuda() for a in (X, T, mask))
+    bad = torch.tensor([0, 5, 100, -1], dtype=torch.int32, device="cuda")   # two out of range
+    net.grad(Xd, Td, md, bad)
+    torch.cuda.synchronize()
+    steps, st = net.status()
+    assert st == G.E_INVALID_ARG
+    beam = W.beam(10)
+    M, K = G.beam_mats(beam)
+    A = G.assemble_shifted(M, K, AL, BE, 1.0)
+    with pytest.raises(G.AirgaError):
+        net.spai(A, 0.0, AL, BE)
+    with pytest.raises(G.AirgaError):
+        G.mlp_features(A, None, -1.0, AL, BE)
+    buf = torch.zeros(10 * 16 + 1, dtype=torch.float32, device="cuda")
+    with pytest.raises(G.AirgaError):
+        net.forward(buf[1:].view(10, 16))                       # 4-byte offset: not 16-byte aligned
+
+
+def _dataset(G, n_es, shifts, n_interior, seed):
+    Xs, Ts, Ms = [], [], []
+    for k, n_e in enumerate(n_es):
+        beam = W.beam(n_e)
+        M, K = G.beam_mats(beam)
+        cols = torch.from_numpy(W.mlp_training_columns(beam.n, n_interior, seed + k)).cuda()
+        for s in shifts:
+            A = G.assemble_shifted(M, K, AL, BE, float(s))
+            P = G.spai_build(A)
+            X, T, m, flag = G.mlp_features(A, P, float(s), AL, BE, cols)
+            Xs.append(X)
+            Ts.append(T)
+            Ms.append(m)
+    return torch.cat(Xs), torch.cat(Ts), torch.cat(Ms)
+
+
+def test_training_gain_and_fallback(G):
+    """Train on SPAI columns of small beams at 64 shifts, then precondition a
+    larger beam at unseen shifts: the trained network's SPAI gives CG
+    iteration counts close to the exact SPAI's (fallback to the exact SPAI
+    above 1.5x), far below the untrained network's and no preconditioner."""
+    X, T, m = _dataset(G, (500, 1500), W.log_shifts(-1, 4, 64), 96, seed=11)
+    net = G.Mlp(seed=3)
+    untrained = G.Mlp(seed=3)
+    steps = 20000
+    hist = torch.zeros(steps, dtype=torch.float32, device="cuda")
+    net.train(X, T, m, steps, G.mlp_train_options(lr=2e-3, batch=4096, cosine_steps=steps),
+              loss_hist=hist)
+    h = hist.cpu().numpy()
+    assert np.all(np.isfinite(h))
+    assert h[-500:].mean() < 0.01 * h[:10].mean()
+    assert net.status() == (steps, G.OK)
+
+    beam = W.beam(20000)
+    M, K = G.beam_mats(beam)
+    f = torch.from_numpy(W.loads(beam.n, 1)[:, 0].copy()).cuda()
+    o = G.options(tol=1e-10, maxit=20000)
+    rows = []
+    for s in W.midpoint_shifts(-1, 4, 8):
+        A = G.assemble_shifted(M, K, AL, BE, float(s))
+        ex = G.pcg_solve(A, G.spai_build(A), f, o)
+        k_ex = int(ex["iters"].item())
+        cap = int(math.ceil(1.5 * k_ex))
+        le = G.pcg_solve(A, net.spai(A, float(s), AL, BE), f, G.options(tol=1e-10, maxit=cap))
+        k_le, st_le = int(le["iters"].item()), int(le["status"].item())
+        un = G.pcg_solve(A, untrained.spai(A, float(s), AL, BE), f, G.options(tol=1e-10, maxit=20000))
+        none = G.pcg_solve(A, None, f, G.options(tol=1e-10, maxit=20000))
+        rows.append((s, k_ex, k_le, st_le, int(un["iters"].item()), int(un["status"].item()),
+                     int(none["iters"].item())))
+        if st_le == G.OK:
+            assert float(le["true_relres"].item()) <= 2e-10
+    print("\n s, exact, learned, status, untrained, status, none:", rows)
+    accepted = [r for r in rows if r[3] == G.OK]
+    assert len(accepted) >= 6                                  # fallback needed on at most 2 shifts
+    assert all(r[2] <= math.ceil(1.5 * r[1]) for r in accepted)
+    assert sum(r[2] for r in accepted) < 0.5 * sum(min(r[4] if r[5] == G.OK else 20000, r[6]) for r in accepted)
+
+
+def test_training_deterministic(G):
+    X, T, m = _dataset(G, (300,), W.log_shifts(-1, 4, 8), 64, seed=21)
+    outs = []
+    for _ in range(2):
+        net = G.Mlp(seed=9)
+        net.train(X, T, m, 50, G.mlp_train_options(batch=1000, seed=77))
+        outs.append(net.params().cpu().numpy())
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_training_graph_replay(G):
+    X, T, m = _dataset(G, (300,), W.log_shifts(-1, 4, 8), 64, seed=31)
+    ref = G.Mlp(seed=5)
+    ref.train(X, T, m, 20, G.mlp_train_options(batch=512, seed=3))
+    net = G.Mlp(seed=5)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            net.train(X, T, m, 10, G.mlp_train_options(batch=512, seed=3), stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert net.status()[0] == 20
+    assert np.array_equal(net.params().cpu().numpy(), ref.params().cpu().numpy())
