@@ -43,6 +43,7 @@
 #include <vector>
 
 #include "airga_internal.cuh"
+#include "ieee_conv.cuh"
 #include "tc_common.cuh"
 
 namespace airga {
@@ -67,6 +68,9 @@ constexpr long long kWaitNs = 2000000000ll;   // bound on any tensor-core comple
 constexpr int kFlagIndex = 8, kFlagDiag = 2, kFlagTimeout = 4;
 
 using tc::kmaj_off;
+using ieee::f64_to_f32;
+using ieee::f32_to_f64;
+using ieee::half_of;
 
 __device__ __forceinline__ uint32_t pack2(float a, float b) {
     __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
@@ -86,22 +90,25 @@ __device__ __forceinline__ long long gtime() {
     return t;
 }
 
-// Bounded wait for an MMA commit; the outcome is made uniform across the CTA.
-// On a timeout `code` is OR-ed into *err.
+// Bounded wait for an MMA commit.  Thread 0 alone polls the mbarrier (the
+// others wait at the CTA barrier and take no issue slots); the outcome is
+// made uniform across the CTA.  On a timeout `code` is OR-ed into *err.
 __device__ __forceinline__ bool wait_mma(uint64_t *mbar, uint32_t &phase, int *err, int code) {
-    const uint32_t addr = tc::smem_u32(mbar);
-    uint32_t done = 0;
-    const long long t0 = gtime();
-    while (true) {
-        asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-                     "selp.u32 %0, 1, 0, p;\n}"
-                     : "=r"(done)
-                     : "r"(addr), "r"(phase));
-        if (done || gtime() - t0 > kWaitNs) break;
+    uint32_t done = 1;
+    if (threadIdx.x == 0) {
+        const uint32_t addr = tc::smem_u32(mbar);
+        const long long t0 = gtime();
+        while (true) {
+            asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                         "selp.u32 %0, 1, 0, p;\n}"
+                         : "=r"(done)
+                         : "r"(addr), "r"(phase));
+            if (done || gtime() - t0 > kWaitNs) break;
+        }
     }
     phase ^= 1u;
-    tc::fence_after();
     const int ok = __syncthreads_and((int)done);
+    tc::fence_after();
     if (!ok && threadIdx.x == 0 && err) atomicOr(err, code);
     return ok != 0;
 }
@@ -146,19 +153,20 @@ struct RawRow {
     float x[16];     // MODE 0: the feature row
 };
 
-// band values of column j of A (j < n)
+// band values of column j of A (zeros when j is outside [0, n))
 __device__ __forceinline__ void fetch_band_row(const double *__restrict__ A, int64_t n, int64_t j,
                                                RawRow &w) {
+    const bool in = j >= 0 && j < n;
 #pragma unroll
     for (int o = 0; o < 7; ++o) {
         const int64_t i = j + o - 3;
-        w.dg[o] = (j < n && i >= 0 && i < n) ? band_at(A, n, i, 0) : 0.0;
+        w.dg[o] = (in && i >= 0 && i < n) ? band_at(A, n, i, 0) : 0.0;
     }
     const int ds[6] = {-3, -2, -1, 1, 2, 3};
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         const int64_t i = j + ds[c];
-        w.od[c] = (j < n && i >= 0 && i < n) ? band_at(A, n, i, -ds[c]) : 0.0;
+        w.od[c] = (in && i >= 0 && i < n) ? band_at(A, n, i, -ds[c]) : 0.0;
     }
 }
 
@@ -169,29 +177,32 @@ __device__ __forceinline__ void fetch_band_row(const double *__restrict__ A, int
 __device__ __forceinline__ bool row_features(const RawRow &w, int64_t n, int64_t j, const FeatConst &fc,
                                              float (&f)[16], float (&r)[7]) {
     bool ok = true;
+    float dg[7];
 #pragma unroll
     for (int o = 0; o < 7; ++o) {
         const int64_t i = j + o - 3;
         r[o] = 0.0f;
+        dg[o] = f64_to_f32(w.dg[o]);
         if (i >= 0 && i < n) {
-            const float d = (float)w.dg[o];
-            ok = ok && d > 0.0f && d < INFINITY;
-            r[o] = __frsqrt_rn(d);
+            ok = ok && dg[o] > 0.0f && dg[o] < INFINITY;
+            r[o] = rsqrtf(dg[o]);   // hardware reciprocal square root (<= 2 ulp)
         }
     }
     f[0] = fc.f0;
     f[1] = fc.f1;
     f[2] = fc.f2;
-    f[3] = log10f((float)w.dg[3]) * 0.125f;
+    f[3] = log10f(dg[3]) * 0.125f;
     const int ds[6] = {-3, -2, -1, 1, 2, 3};
 #pragma unroll
     for (int c = 0; c < 6; ++c) {
         const int64_t i = j + ds[c];
-        f[4 + c] = (i >= 0 && i < n) ? ((float)w.od[c] * r[ds[c] + 3]) * r[3] : 0.0f;
+        f[4 + c] = (i >= 0 && i < n) ? (f64_to_f32(w.od[c]) * r[ds[c] + 3]) * r[3] : 0.0f;
     }
-    f[10] = (float)(j < kDistCap ? j : (int64_t)kDistCap) * (1.0f / kDistCap);
-    f[11] = (float)(n - 1 - j < kDistCap ? n - 1 - j : (int64_t)kDistCap) * (1.0f / kDistCap);
-    f[12] = (float)(j & 1);
+    const int d0 = j < kDistCap ? (int)j : kDistCap;
+    const int d1 = n - 1 - j < kDistCap ? (int)(n - 1 - j) : kDistCap;
+    f[10] = __int2float_rn(d0) * (1.0f / kDistCap);
+    f[11] = __int2float_rn(d1) * (1.0f / kDistCap);
+    f[12] = (j & 1) ? 1.0f : 0.0f;
     f[13] = f[14] = f[15] = 0.0f;
     return ok;
 }
@@ -292,13 +303,23 @@ struct InferArgs {
     float *Y;                // MODE 0: [count][16]
     const double *A;         // MODE 1: band of A
     double *P;               // MODE 1: band of the predicted P (written)
+    double *Psym;            // MODE 1: band of 1/2 (P + P^T) (written)
     FeatConst fc;
     int *flag;               // MODE 1: status bits of the new preconditioner
 };
 
-constexpr int kInferThreads = 256;   // two column groups; two CTAs per SM
-constexpr int kInferSmem = kImgFwd + 4096 + 16384 + 16384 + 1024;   // image | X | H1 | H2 | align slack
-constexpr uint32_t kInferCols = 128;
+// One warp group per CTA, several CTAs per SM: a tile's steps (features,
+// three MMAs, two ReLU epilogues, output) form a dependent chain, and the
+// chains of the CTAs sharing an SM overlap.  One 64-column tensor-memory
+// accumulator serves all three layers and one shared-memory buffer both
+// hidden layers (each is consumed before the next MMA overwrites it).
+constexpr int kInferThreads = 128;
+constexpr int kInferPerSm = 4;
+constexpr int kInferSmem = kImgFwd + 4096 + 16384 + 4096 + 1024;   // image | X | H | P exchange | slack
+constexpr uint32_t kInferCols = 64;
+// MODE 1 tiles: 128 consecutive columns, of which the middle kOwn are owned;
+// 3 halo columns on each side supply the transposed entries of P_sym.
+constexpr int kHalo = 3, kOwn = kTile - 2 * kHalo;
 
 template <int MODE>
 __device__ __forceinline__ void fetch_row(const InferArgs &a, int64_t row, RawRow &w) {
@@ -323,18 +344,22 @@ __device__ __forceinline__ void fetch_row(const InferArgs &a, int64_t row, RawRo
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(InferArgs a) {
-    constexpr int QW = kInferThreads / 128, CW = kHid / QW;   // column groups, columns per group
+__device__ __forceinline__ int64_t tile_row(int64_t tile, int r) {
+    return MODE == 0 ? tile * kTile + r : tile * kOwn - kHalo + r;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kInferThreads, kInferPerSm) mlp_infer_kernel(InferArgs a) {
     extern __shared__ uint8_t smraw[];
     uint8_t *sm = (uint8_t *)(((uintptr_t)smraw + 1023) & ~(uintptr_t)1023);
     uint8_t *sW1 = sm + kImgW1, *sW2 = sm + kImgW2, *sW3 = sm + kImgW3, *sX = sm + kImgFwd,
-            *sH1 = sX + 4096, *sH2 = sH1 + 16384;
+            *sH = sX + 4096;
+    float(*sP)[8] = reinterpret_cast<float(*)[8]>(sH + 16384);   // MODE 1: P(j+d, j), d = o - 3
     __shared__ float sb[kHid + kHid + kOut];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_holder;
-    const int tid = threadIdx.x, warp = tid >> 5, lane_id = tid & 31;
-    const int rg = warp & 3, q = warp >> 2;
-    const int r = rg * 32 + lane_id;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int r = tid;   // sample row = tensor-memory lane
 
     stage_image<kImgFwd, kInferThreads>(a.wimg, sm);
     for (int e = tid; e < kHid; e += blockDim.x) {
@@ -348,26 +373,26 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(InferArgs a
     __syncthreads();
     tc::fence_after();
     const uint32_t tmem = tmem_holder;
-    const uint32_t lane = tmem + ((uint32_t)(rg * 32) << 16);
-    const uint32_t Z1 = 0, Z2 = 64, Yc = 0;
+    const uint32_t lane = tmem + ((uint32_t)(warp * 32) << 16);
     uint32_t phase = 0;
     bool bad = false;
 
-    const int64_t ntiles = (a.count + kTile - 1) / kTile;
+    const int64_t n = a.count;
+    const int64_t ntiles = MODE == 0 ? (n + kTile - 1) / kTile : (n + kOwn - 1) / kOwn;
     RawRow nxt;
     int64_t tile = blockIdx.x;
-    if (q == 0 && tile < ntiles) fetch_row<MODE>(a, tile * kTile + r, nxt);
+    if (tile < ntiles) fetch_row<MODE>(a, tile_row<MODE>(tile, r), nxt);
     for (; tile < ntiles; tile += gridDim.x) {
-        const int64_t row = tile * kTile + r;
-        const bool valid = row < a.count;
+        const int64_t row = tile_row<MODE>(tile, r);
+        const bool valid = row >= 0 && row < n;
         float rs[7];
-        if (q == 0) {
+        {
             float f[16];
             if (MODE == 0) {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) f[k] = nxt.x[k];
             } else if (valid) {
-                if (!row_features(nxt, a.count, row, a.fc, f, rs)) bad = true;
+                if (!row_features(nxt, n, row, a.fc, f, rs)) bad = true;
             } else {
 #pragma unroll
                 for (int k = 0; k < 16; ++k) f[k] = 0.0f;
@@ -377,74 +402,78 @@ __global__ void __launch_bounds__(kInferThreads, 2) mlp_infer_kernel(InferArgs a
         }
         sync_for_mma();
         if (tid == 0) {
-            tc::gemm(tmem + Z1, sX, sW1, kIn, kHid, false);
+            tc::gemm(tmem, sX, sW1, kIn, kHid, false);
             tc::commit(&mbar);
         }
         // fetch the next tile's inputs while this one runs
-        if (q == 0 && tile + gridDim.x < ntiles) fetch_row<MODE>(a, (tile + gridDim.x) * kTile + r, nxt);
+        if (tile + gridDim.x < ntiles) fetch_row<MODE>(a, tile_row<MODE>(tile + gridDim.x, r), nxt);
         if (!wait_mma(&mbar, phase, a.flag, kFlagTimeout)) break;
 #pragma unroll
-        for (int c0 = q * CW; c0 < q * CW + CW; c0 += 16) {
+        for (int c0 = 0; c0 < kHid; c0 += 16) {
             float z[16];
-            tc::tmem_ld16(lane + Z1 + c0, z);
+            tc::tmem_ld16(lane + c0, z);
 #pragma unroll
             for (int k = 0; k < 16; ++k) z[k] = fmaxf(z[k] + sb[c0 + k], 0.0f);
-            st8(sH1, r, c0, kHid, z);
-            st8(sH1, r, c0 + 8, kHid, z + 8);
+            st8(sH, r, c0, kHid, z);
+            st8(sH, r, c0 + 8, kHid, z + 8);
         }
         sync_for_mma();
         if (tid == 0) {
-            tc::gemm(tmem + Z2, sH1, sW2, kHid, kHid, false);
+            tc::gemm(tmem, sH, sW2, kHid, kHid, false);
             tc::commit(&mbar);
         }
         if (!wait_mma(&mbar, phase, a.flag, kFlagTimeout)) break;
 #pragma unroll
-        for (int c0 = q * CW; c0 < q * CW + CW; c0 += 16) {
+        for (int c0 = 0; c0 < kHid; c0 += 16) {
             float z[16];
-            tc::tmem_ld16(lane + Z2 + c0, z);
+            tc::tmem_ld16(lane + c0, z);
 #pragma unroll
             for (int k = 0; k < 16; ++k) z[k] = fmaxf(z[k] + sb[kHid + c0 + k], 0.0f);
-            st8(sH2, r, c0, kHid, z);
-            st8(sH2, r, c0 + 8, kHid, z + 8);
+            st8(sH, r, c0, kHid, z);
+            st8(sH, r, c0 + 8, kHid, z + 8);
         }
         sync_for_mma();
         if (tid == 0) {
-            tc::gemm(tmem + Yc, sH2, sW3, kHid, kOut, false);
+            tc::gemm(tmem, sH, sW3, kHid, kOut, false);
             tc::commit(&mbar);
         }
         if (!wait_mma(&mbar, phase, a.flag, kFlagTimeout)) break;
         float y[16];
-        tc::tmem_ld16(lane + Yc, y);
-        if (valid) {
-            if (MODE == 0) {
-                static_assert(QW == 2, "two output halves");
-                float h[8];   // outputs 8q..8q+7 (register indices stay compile-time)
+        tc::tmem_ld16(lane, y);
 #pragma unroll
-                for (int k = 0; k < 8; ++k) h[k] = (q == 0 ? y[k] : y[8 + k]) + sb[2 * kHid + 8 * q + k];
-                float4 *yr = reinterpret_cast<float4 *>(a.Y + row * kOut + 8 * q);
-                yr[0] = make_float4(h[0], h[1], h[2], h[3]);
-                yr[1] = make_float4(h[4], h[5], h[6], h[7]);
-            } else if (q == 0) {
-                const int64_t n = a.count, j = row;
+        for (int o = 0; o < 16; ++o) y[o] += sb[2 * kHid + o];
+        if (MODE == 0) {
+            if (valid) {
+                float4 *yr = reinterpret_cast<float4 *>(a.Y + row * kOut);
 #pragma unroll
-                for (int o = 0; o < kUsed; ++o) {
-                    const int d = o - 3;
-                    const int64_t i = j + d;
-                    if (i >= 0 && i < n)   // P(i, j) = P(i, i - d)
-                        a.P[(int64_t)(3 - d) * n + i] = (double)(((y[o] + sb[2 * kHid + o]) * rs[o]) * rs[3]);
+                for (int v = 0; v < 4; ++v) yr[v] = make_float4(y[4 * v], y[4 * v + 1], y[4 * v + 2], y[4 * v + 3]);
+            }
+        } else {
+            // P(j+d, j) = y_o / sqrt(A(j+d, j+d) A_jj), exchanged through shared memory
+#pragma unroll
+            for (int o = 0; o < kUsed; ++o) sP[r][o] = valid ? (y[o] * rs[o]) * rs[3] : 0.0f;
+            __syncthreads();
+            const bool owned = r >= kHalo && r < kTile - kHalo && valid;
+            if (owned) {
+                const int64_t i = row;   // this thread writes row i of P and of P_sym
+#pragma unroll
+                for (int dp = -3; dp <= 3; ++dp) {
+                    const int64_t c = i + dp;
+                    double p = 0.0, ps = 0.0;
+                    if (c >= 0 && c < n) {
+                        const float pic = sP[r + dp][3 - dp];   // P(i, c): column c, offset -dp
+                        const float pci = sP[r][3 + dp];        // P(c, i): column i, offset +dp
+                        p = f32_to_f64(pic);
+                        ps = half_of(p + f32_to_f64(pci));
+                    }
+                    a.P[(int64_t)(dp + 3) * n + i] = p;
+                    a.Psym[(int64_t)(dp + 3) * n + i] = ps;
                 }
             }
         }
-        tc::fence_before();   // tensor-memory reads done before the next tile's MMA
-    }
-    if (MODE == 1 && blockIdx.x == 0 && tid == 0) {
-        // band slots (d, i) whose column i + d lies outside the matrix hold 0
-        const int64_t n = a.count;
-        for (int d = -3; d <= 3; ++d) {
-            const int64_t lo = d < 0 ? 0 : (n - d > 0 ? n - d : 0);
-            const int64_t hi = d < 0 ? (n < -d ? n : (int64_t)-d) : (d > 0 ? n : 0);
-            for (int64_t i = lo; i < hi; ++i) a.P[(int64_t)(d + 3) * n + i] = 0.0;
-        }
+        tc::fence_before();   // tensor-memory reads (and the P exchange) done before the next tile
+        __syncthreads();
+        tc::fence_after();
     }
     if (MODE == 1 && bad) atomicOr(a.flag, kFlagDiag);
     tc::fence_before();
@@ -547,7 +576,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) mlp_train_kernel(TrainArgs a
     const uint32_t tmem = tmem_holder;
     const uint32_t lane = tmem + ((uint32_t)(rg * 32) << 16);
     uint32_t phase = 0;
-    double lsum = 0.0;
+    float lsum = 0.0f;   // this thread's squared errors (a few tiles at most per launch)
     bool alive = true;
 
     const int64_t ntiles = ((int64_t)a.B + kTile - 1) / kTile;
@@ -639,7 +668,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) mlp_train_kernel(TrainArgs a
                 e[k] = (o < kUsed && ((mk >> o) & 1u)) ? (yo + sb[2 * kHid + o]) - tg[k] : 0.0f;
                 l += e[k] * e[k];
             }
-            lsum += (double)l;
+            lsum += l;
             st4(sDY, r, 4 * q, kOut, e);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
@@ -727,7 +756,7 @@ __global__ void __launch_bounds__(kTrainThreads, 1) mlp_train_kernel(TrainArgs a
         for (int k = tid; k < kNParam; k += NT) gp[k] = 0.0f;
     }
     // loss partial (fixed-order reduction)
-    double l = lsum;
+    double l = (double)lsum;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) l += __shfl_down_sync(0xffffffffu, l, o);
     if (lane_id == 0) sred[warp] = l;
@@ -885,8 +914,8 @@ int launch_infer(int mode, const InferArgs &a, cudaStream_t s) {
     int sms = 0;
     st = sm_count(&sms);
     if (st) return st;
-    const int64_t ntiles = (a.count + kTile - 1) / kTile;
-    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)2 * sms);
+    const int64_t ntiles = mode == 0 ? (a.count + kTile - 1) / kTile : (a.count + kOwn - 1) / kOwn;
+    const int grid = (int)std::min<int64_t>(ntiles, (int64_t)kInferPerSm * sms);
     if (grid < 1) return AIRGA_OK;
     if (mode == 0) mlp_infer_kernel<0><<<grid, kInferThreads, kInferSmem, s>>>(a);
     else mlp_infer_kernel<1><<<grid, kInferThreads, kInferSmem, s>>>(a);
@@ -1159,13 +1188,10 @@ int airga_mlp_spai(airga_mlp net, airga_mat A, double s, double alpha, double be
         a.count = A->n;
         a.A = A->band->d;
         a.P = F->d;
+        a.Psym = P->psym->d;
         a.fc = FeatConst{(float)(std::log10(s) / 4.0), (float)alpha, (float)beta};
         a.flag = (int *)P->rank_flag.get();
         st = launch_infer(1, a, cs);
-    }
-    if (!st) {
-        cudaError_t e = launch_symmetrize(A->n, F->d, P->psym->d, cs);
-        if (e != cudaSuccess) st = cuda_fail(e, "symmetrize");
     }
     if (st) {
         delete P;
