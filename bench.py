@@ -211,8 +211,9 @@ def gpu_arm(args, world, rank, local):
     forms = None
     if not args.profile and not args.no_forms:
         del M, K
-        forms = {"precision": precision_form(G, torch, stream),
-                 "batching": batching_form(G, torch, stream)}
+        makers = {"precision": precision_form, "batching": batching_form,
+                  "learned": learned_form}
+        forms = {k: makers[k](G, torch, stream) for k in args.forms.split(",") if k}
 
     # end to end through the public API with host buffers
     e2e = e2e_arm(G, torch, beam, opts, args) if rank == 0 and not args.profile else None
@@ -464,6 +465,154 @@ def batching_form(G, torch, stream):
             "speedup": round(seq_ms / bat_ms, 3)}
 
 
+MLP_FLOP_PER_SAMPLE_FWD = 2 * (16 * 64 + 64 * 64 + 64 * 16)   # 12288 (MACs x 2)
+
+
+def learned_form(G, torch, stream):
+    """Learned-preconditioner workload: a 16-64-64-16 BF16 tensor-core MLP
+    trained on the GPU on exact SPAI columns (training set: the 32 end
+    columns and 96 random interior columns of beams of 1e4, 3e4 and 1e5
+    elements at 64 shifts log-spaced in [1e-1, 1e4]; 30,000 Adam steps of
+    4096 samples), then evaluated on the n = 1e6 beam at 16 unseen shifts
+    (geometric midpoints of a 17-point logspace over [1e-1, 1e4]) against
+    the exact SPAI (rebuilt per shift) and the updated SPAI (Q P_prev from
+    the previous shift's exact SPAI, Sec. 3.2).  A learned preconditioner's
+    CG run is capped at 1.5x the exact SPAI's iterations at that shift; past
+    the cap the shift falls back to the exact SPAI (both runs counted).
+    solves/s = converged solves / (preconditioner + CG device time)."""
+    import math
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    # training set from SPAIs the method builds
+    t0 = time.time()
+    Xs, Ts, Ms = [], [], []
+    for k, n_e in enumerate((10_000, 30_000, 100_000)):
+        beam = W.beam(n_e)
+        M, K = G.beam_mats(beam)
+        cols = torch.from_numpy(W.mlp_training_columns(beam.n, 96, seed=100 + k)).cuda()
+        for s in W.log_shifts(-1, 4, 64):
+            A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
+            P = G.spai_build(A)
+            X, T, m, _ = G.mlp_features(A, P, float(s), W.ALPHA, W.BETA, cols)
+            Xs.append(X)
+            Ts.append(T)
+            Ms.append(m)
+    X, T, m = torch.cat(Xs), torch.cat(Ts), torch.cat(Ms)
+    torch.cuda.synchronize()
+    data_s = time.time() - t0
+
+    steps, batch = 30_000, 4096
+    net = G.Mlp(seed=3)
+    hist = torch.zeros(steps, dtype=torch.float32, device="cuda")
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    net.train(X, T, m, steps, G.mlp_train_options(lr=2e-3, batch=batch, cosine_steps=steps),
+              loss_hist=hist, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    h = hist.cpu().numpy()
+    done, st = net.status()
+
+    # evaluation on the n = 1e6 beam
+    beam = W.beam(N_E)
+    n = beam.n
+    M, K = G.beam_mats(beam)
+    f = torch.from_numpy(W.loads(n, 1)[:, 0].copy()).cuda()
+    opts = G.options(tol=TOL, maxit=20000)
+    shifts = W.midpoint_shifts(-1, 4, 16)
+    rows = []
+    tot = {"exact": [0.0, 0], "updated": [0.0, 0], "learned": [0.0, 0]}
+    build_ms = {"exact": [], "learned": []}
+    prev = None
+    fallbacks = 0
+    for rep in range(2):            # first pass warms up, second is measured
+        prev = None
+        for s in shifts:
+            A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
+            a0, a1, a2 = ev(), ev(), ev()
+            a0.record(stream)
+            Pex = G.spai_build(A)
+            a1.record(stream)
+            rex = G.pcg_solve(A, Pex, f, opts)
+            a2.record(stream)
+            torch.cuda.synchronize()
+            it_ex = int(rex["iters"].item())
+            ok_ex = int(rex["status"].item()) == G.OK and float(rex["true_relres"].item()) <= 2 * TOL
+            # learned, capped at 1.5x the exact SPAI's iterations
+            cap = int(math.ceil(1.5 * it_ex))
+            b0, b1, b2 = ev(), ev(), ev()
+            b0.record(stream)
+            Pl = net.spai(A, float(s), W.ALPHA, W.BETA)
+            b1.record(stream)
+            rl = G.pcg_solve(A, Pl, f, G.options(tol=TOL, maxit=cap))
+            b2.record(stream)
+            torch.cuda.synchronize()
+            it_l = int(rl["iters"].item())
+            ok_l = int(rl["status"].item()) == G.OK and float(rl["true_relres"].item()) <= 2 * TOL
+            l_ms = b0.elapsed_time(b2)
+            if not ok_l:            # fallback: exact SPAI and a fresh solve
+                c0, c1 = ev(), ev()
+                c0.record(stream)
+                Pfb = G.spai_build(A)
+                rfb = G.pcg_solve(A, Pfb, f, opts)
+                c1.record(stream)
+                torch.cuda.synchronize()
+                l_ms += c0.elapsed_time(c1)
+                ok_l = int(rfb["status"].item()) == G.OK
+            # updated SPAI from the previous shift (chain Q P_prev)
+            it_u, ok_u, u_ms = None, False, None
+            if prev is not None:
+                d0, d1 = ev(), ev()
+                d0.record(stream)
+                Pu = G.spai_update(prev[1], prev[0], A)
+                ru = G.pcg_solve(A, Pu, f, opts)
+                d1.record(stream)
+                torch.cuda.synchronize()
+                it_u = int(ru["iters"].item())
+                ok_u = int(ru["status"].item()) == G.OK and float(ru["true_relres"].item()) <= 2 * TOL
+                u_ms = d0.elapsed_time(d1)
+            prev = (A, Pex)
+            if rep == 0:
+                continue
+            ex_ms = a0.elapsed_time(a2)
+            tot["exact"][0] += ex_ms
+            tot["exact"][1] += int(ok_ex)
+            tot["learned"][0] += l_ms
+            tot["learned"][1] += int(ok_l)
+            if u_ms is not None:
+                tot["updated"][0] += u_ms
+                tot["updated"][1] += int(ok_u)
+            fallbacks += int(it_l >= cap and int(rl["status"].item()) != G.OK)
+            build_ms["exact"].append(a0.elapsed_time(a1))
+            build_ms["learned"].append(b0.elapsed_time(b1))
+            rows.append([round(float(s), 4), it_ex, it_u, it_l if int(rl["status"].item()) == G.OK else None])
+    sps = {k: (round(v[1] / (v[0] * 1e-3), 2) if v[0] > 0 else None) for k, v in tot.items()}
+    lb = statistics.median(build_ms["learned"])
+    return {"workload": "train: 32 end + 96 interior columns of beams n_e in {1e4, 3e4, 1e5} at "
+                        "64 shifts logspace(-1,4); evaluate: beam n_e=5e5 (n=1e6), tip force, "
+                        "16 unseen shifts (midpoints of a 17-point logspace(-1,4))",
+            "training": {"samples": int(X.shape[0]), "steps": steps, "batch": batch,
+                         "device_ms": round(train_ms, 2), "dataset_s": round(data_s, 2),
+                         "us_per_step": round(1e3 * train_ms / steps, 2),
+                         "samples_per_s": round(steps * batch / (train_ms * 1e-3), 1),
+                         "tflops_model": round(3 * MLP_FLOP_PER_SAMPLE_FWD * steps * batch /
+                                               (train_ms * 1e-3) / 1e12, 3),
+                         "loss_first": float(h[:10].mean()), "loss_last": float(h[-500:].mean()),
+                         "status": st, "adam_steps": done},
+            "per_shift": {"columns": ["s", "cg_iters_exact", "cg_iters_updated",
+                                      "cg_iters_learned (None = fell back)"], "rows": rows},
+            "solves_per_s": {"exact_spai": sps["exact"], "updated_spai": sps["updated"],
+                             "learned_spai": sps["learned"]},
+            "device_ms": {k: round(v[0], 3) for k, v in tot.items()},
+            "updated_shifts": len(shifts) - 1,
+            "learned_fallbacks": fallbacks,
+            "build_ms_median": {"exact_spai_qr": round(statistics.median(build_ms["exact"]), 4),
+                                "learned_spai": round(lb, 4)},
+            "learned_build_tflops_model": round(n * 1.06 * MLP_FLOP_PER_SAMPLE_FWD / (lb * 1e-3) / 1e12, 4),
+            "speedup_learned_vs_exact": round(tot["exact"][0] / tot["learned"][0], 3)}
+
+
 def e2e_arm(G, torch, beam, opts, args):
     """Same step through the public API with host inputs: CSR of M and K and
     F copied from pinned host memory, X of every shift copied back."""
@@ -601,6 +750,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--forms", default="precision,batching,learned",
+                    help="comma-separated growth forms to run after the timed steps")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the growth-form measurements (precision, batching)")
     ap.add_argument("--profile", action="store_true",
