@@ -212,7 +212,7 @@ def gpu_arm(args, world, rank, local):
     if not args.profile and not args.no_forms:
         del M, K
         makers = {"precision": precision_form, "batching": batching_form,
-                  "learned": learned_form}
+                  "learned": learned_form, "inner_loop": inner_loop_form}
         forms = {k: makers[k](G, torch, stream) for k in args.forms.split(",") if k}
 
     # end to end through the public API with host buffers
@@ -613,6 +613,62 @@ def learned_form(G, torch, stream):
             "speedup_learned_vs_exact": round(tot["exact"][0] / tot["learned"][0], 3)}
 
 
+def inner_loop_form(G, torch, stream):
+    """AIRGA inner-loop workload (Alg. 3 lines 9-12, Alg. 5 lines 15-17): on
+    the n = 1e6 beam at 4 shifts log-spaced in [1e-1, 1e4] the exact SPAI is
+    built once per shift and reused for q = 8 successive solves,
+    V_1 = A^{-1} F (tip force) and V_{j+1} = -A^{-1} M V_j (the moment
+    recurrence of Algorithm 1).  fused: pcg_solve_mv forms M V_j inside the
+    PCG kernel; unfused: an SpMV writes M V_j, then pcg_solve (the sign of the
+    right-hand side is dropped, which changes no cost).  The basis is not
+    orthonormalised (AIRGA does; a solve's cost does not depend on the scale
+    of its right-hand side).  solves/s = converged solves / device time of the
+    solves (preconditioner builds excluded, they are shared)."""
+    beam = W.beam(N_E)
+    n = beam.n
+    M, K = G.beam_mats(beam)
+    f = torch.from_numpy(W.loads(n, 1)[:, 0].copy()).cuda()
+    opts = G.options(tol=TOL, maxit=20000)
+    shifts = W.log_shifts(-1, 4, 4)
+    q = 8
+    res = {}
+    for arm in ("fused", "unfused"):
+        for rep in range(2):
+            ms, ok, its, worst = 0.0, 0, [], 0.0
+            for s in shifts:
+                A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
+                P = G.spai_build(A)
+                y = torch.empty(n, dtype=torch.float64, device="cuda")
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                outs = [G.pcg_solve(A, P, f, opts)]
+                v = outs[0]["X"]
+                for _ in range(q - 1):
+                    if arm == "fused":
+                        r = G.pcg_solve_mv(A, P, M, v, -1.0, opts)
+                    else:
+                        G.spmv(M, v, y)
+                        r = G.pcg_solve(A, P, y, opts)
+                    outs.append(r)
+                    v = r["X"]
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms += e0.elapsed_time(e1)
+                for r in outs:
+                    st = int(r["status"].item())
+                    rr = float(r["true_relres"].item())
+                    ok += int(st == G.OK and rr <= 2 * TOL)
+                    worst = max(worst, rr)
+                    its.append(int(r["iters"].item()))
+            res[arm] = {"solves_per_s": round(ok / (ms * 1e-3), 2), "converged": ok,
+                        "ms": round(ms, 3), "cg_iterations": its, "max_true_relres": worst}
+    return {"workload": "beam n_e=5e5 (n=1e6), 4 shifts logspace(-1,4), 8 recurrence solves "
+                        "per shift with the shift's SPAI reused",
+            "solves": len(shifts) * q, **res,
+            "speedup_fused": round(res["unfused"]["ms"] / res["fused"]["ms"], 3)}
+
+
 def e2e_arm(G, torch, beam, opts, args):
     """Same step through the public API with host inputs: CSR of M and K and
     F copied from pinned host memory, X of every shift copied back."""
@@ -750,7 +806,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="precision,batching,learned",
+    ap.add_argument("--forms", default="precision,batching,learned,inner_loop",
                     help="comma-separated growth forms to run after the timed steps")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the growth-form measurements (precision, batching)")
