@@ -466,6 +466,7 @@ def batching_form(G, torch, stream):
 
 
 MLP_FLOP_PER_SAMPLE_FWD = 2 * (16 * 64 + 64 * 64 + 64 * 16)   # 12288 (MACs x 2)
+LEARNED_TRAIN_STEPS = 30_000     # --learned-train-steps (shorter only for profiling runs)
 
 
 def learned_form(G, torch, stream):
@@ -501,7 +502,7 @@ def learned_form(G, torch, stream):
     torch.cuda.synchronize()
     data_s = time.time() - t0
 
-    steps, batch = 30_000, 4096
+    steps, batch = LEARNED_TRAIN_STEPS, 4096
     net = G.Mlp(seed=3)
     hist = torch.zeros(steps, dtype=torch.float32, device="cuda")
     e0, e1 = ev(), ev()
@@ -800,6 +801,7 @@ def reference_arm(args, world, rank):
 
 
 def main():
+    global LEARNED_TRAIN_STEPS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
@@ -808,11 +810,14 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--forms", default="precision,batching,learned,inner_loop",
                     help="comma-separated growth forms to run after the timed steps")
+    ap.add_argument("--learned-train-steps", type=int, default=LEARNED_TRAIN_STEPS,
+                    help="Adam steps of the learned form (default 30000; fewer only to profile)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the growth-form measurements (precision, batching)")
     ap.add_argument("--profile", action="store_true",
                     help="timed steps only (no per-phase split, e2e or CPU legs): for ncu")
     args = ap.parse_args()
+    LEARNED_TRAIN_STEPS = max(1, args.learned_train_steps)
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     world, rank, local = dist_env()
