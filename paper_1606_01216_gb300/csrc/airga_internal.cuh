@@ -115,8 +115,11 @@ int mr_alpha_blocks(int64_t n);
 // update (b_j = A_old e_j).  Output band-7 factor F (entries outside the
 // pattern 0).  colres: ||b_j - A m_j|| per column.  rank_flag set on a
 // rank-deficient column block.
+// zA, zAold: device beam zero-structure flags of A and A_old (may be null);
+// when set, interior columns skip the structural zeros of their blocks.
 cudaError_t launch_spai_qr(int64_t n, int hbw, const double *A, const double *A_old, double *F,
-                           double *colres, int32_t *rank_flag, cudaStream_t s);
+                           double *colres, int32_t *rank_flag, const int32_t *zA,
+                           const int32_t *zAold, cudaStream_t s);
 // MR mode (Algorithms 2 / 4); alpha0 read from device memory.
 cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_old,
                            const double *alpha0, double tol, int kmax, double *F,

@@ -171,7 +171,9 @@ static int spai_factor(airga_mat A, airga_mat A_old, const airga_options &o, cud
     if (o.spai_mode == AIRGA_SPAI_QR) {
         AIRGA_CUDA(cudaMemsetAsync(out->col_steps.get(), 0, sizeof(int32_t) * (size_t)n, s));
         AIRGA_CUDA(launch_spai_qr(n, o.pattern_hbw, A->band->d, Aold, (*F)->d,
-                                  (double *)out->col_res.get(), (int32_t *)out->rank_flag.get(), s));
+                                  (double *)out->col_res.get(), (int32_t *)out->rank_flag.get(),
+                                  (const int32_t *)A->pairz.get(),
+                                  A_old ? (const int32_t *)A_old->pairz.get() : nullptr, s));
         return AIRGA_OK;
     }
     const int nblk = mr_alpha_blocks(n);

@@ -25,6 +25,7 @@
 #include <utility>
 
 #include "airga_internal.cuh"
+#include "fp64_lean.cuh"
 
 namespace airga {
 namespace {
@@ -95,76 +96,201 @@ __device__ __forceinline__ void store_column(int64_t n, int64_t j, const double 
     }
 }
 
+// Compile-time fill-in plan of the banded Householder sweep.  For every step
+// C it records which local rows of each block column and of the right-hand
+// side can be nonzero before the step (bit r of a[C][c] / b[C]).  Row C of
+// the reflector is always nonzero; a later column (or b) is transformed only
+// if its support meets the reflector's, and then fills in on the reflector's
+// support.  Every product with a structural zero is dropped from the unrolled
+// code.
+//   PAR = -1  general band: only the band shape and, for the build, the sparse
+//             right-hand side e_j are used.
+//   PAR = 0/1 beam band of a column j of that parity: additionally the
+//             Hermite-beam zeros (every row pair but the last: even rows have
+//             A(i, i-3) = A(i, i+1) = 0, odd rows A(i, i+3) = A(i, i-1) = 0).
+//   RHS = 0   b = e_j (SPAI build); 1: b = a general band column (update);
+//         2   b = a beam band column (update from a beam matrix, PAR >= 0).
+struct QrPlan {
+    unsigned short a[8][7];
+    unsigned short b[8];
+};
+
+__host__ __device__ constexpr bool beam_zero(int W, int par, int r, int c) {
+    // local entry (r, c) is A(g, k), g = j - W - 3 + r, k = g + (c - r + 3)
+    const int g = par + W + 3 + r;   // parity of g
+    const int d = c - r + 3;
+    return (g & 1) == 0 ? (d == -3 || d == 1) : (d == 3 || d == -1);
+}
+
+__host__ __device__ constexpr QrPlan make_plan(int W, int PAR, int RHS) {
+    QrPlan P{};
+    const int NC = 2 * W + 1;
+    unsigned a[7] = {0, 0, 0, 0, 0, 0, 0};
+    unsigned b = 0;
+    for (int c = 0; c < NC; ++c)
+        for (int r = c; r < c + 7; ++r)
+            if (PAR < 0 || !beam_zero(W, PAR, r, c)) a[c] |= 1u << r;
+    if (RHS == 0) {
+        b = 1u << (W + 3);
+    } else {
+        for (int r = W; r <= W + 6; ++r)   // b_r = A_old(g, j): local column W of the block
+            if (RHS == 1 || !beam_zero(W, PAR, r, W)) b |= 1u << r;
+    }
+    for (int C = 0; C < NC; ++C) {
+        for (int c = 0; c < NC; ++c) P.a[C][c] = (unsigned short)a[c];
+        P.b[C] = (unsigned short)b;
+        const unsigned v = (a[C] & (0x7Fu << C)) | (1u << C);
+        for (int c = C + 1; c < NC; ++c)
+            if (v & a[c]) a[c] |= v;
+        if (v & b) b |= v;
+    }
+    for (int c = 0; c < NC; ++c) P.a[NC][c] = (unsigned short)a[c];
+    P.b[NC] = (unsigned short)b;
+    return P;
+}
+
+// Gather the block entries the plan says can be nonzero (the others are 0);
+// columns outside [0, n) become unit columns on local row c+3 (general plan
+// only).
+template <int W, int PAR>
+__device__ __forceinline__ void gather_block_p(int64_t n, int64_t j, const double *__restrict__ A,
+                                               double (&a)[2 * W + 7][2 * W + 1]) {
+    constexpr int NC = 2 * W + 1;
+    constexpr QrPlan P = make_plan(W, PAR, 0);
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+#pragma unroll
+        for (int r = 0; r < c; ++r) a[r][c] = 0.0;     // above the band: fills in during QR
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int64_t k = j - W + c;                  // global column
+        const bool col_ok = (k >= 0 && k < n);
+#pragma unroll
+        for (int t = 0; t < 7; ++t) {
+            const int r = c + t;                       // local row
+            const int64_t g = j - W - 3 + r;           // global row
+            double v = 0.0;
+            if ((P.a[0][c] >> r) & 1u) {
+                if (col_ok && g >= 0 && g < n) v = __ldg(A + (int64_t)(c - r + 6) * n + g);
+                if (!col_ok && t == 3) v = 1.0;        // decoupled unit column
+            }
+            a[r][c] = v;
+        }
+    }
+}
+
 // One Householder step on column C of the banded block (local rows C..C+6):
 // v = x + sign(x_0) ||x|| e_0, applied to the later columns and to b;
-// R_CC stored in a[C][C], 1/R_CC in rinv[C].  Written as a template on C so
-// every array index is a compile-time constant and the block stays in
-// registers.
-template <int W, int C>
+// R_CC stored in a[C][C], 1/R_CC in rinv[C].  Every array index is a
+// compile-time constant after unrolling, so the block stays in registers and
+// the plan's zero tests fold away.
+//
+// The scalar part costs few FP64-pipe instructions: 1/sqrt and the
+// reciprocal come from lean::rsqrt / lean::rcp (FP32 hardware seed, two FP64
+// Newton steps), signs and absolute values are integer bit operations, and
+// the rank test tracks the largest and smallest ||x|| by their bit patterns
+// (non-negative doubles order like their bits).
+template <int W, int PAR, int RHS, int C>
 __device__ __forceinline__ void qr_step(double (&a)[2 * W + 7][2 * W + 1], double (&b)[2 * W + 7],
-                                        double (&rinv)[2 * W + 1], double &rmax, double &rmin) {
+                                        double (&rinv)[2 * W + 1], unsigned long long &rmax,
+                                        unsigned long long &rmin) {
     constexpr int NC = 2 * W + 1;
+    constexpr QrPlan P = make_plan(W, PAR, RHS);
+    constexpr unsigned V = (P.a[C][C] & (0x7Fu << C)) | (1u << C);   // reflector support
     double sigma = 0.0;
 #pragma unroll
-    for (int t = 0; t < 7; ++t) sigma = fma(a[C + t][C], a[C + t][C], sigma);
+    for (int t = 0; t < 7; ++t)
+        if ((P.a[C][C] >> (C + t)) & 1u) sigma = fma(a[C + t][C], a[C + t][C], sigma);
     const double x0 = a[C][C];
-    const double rs = sigma > 0.0 ? rsqrt(sigma) : 0.0;
+    const double rs = lean::rsqrt(sigma);              // 0 when sigma == 0
     const double nrm = sigma * rs;                     // ||x||
-    const double alpha = x0 >= 0.0 ? -nrm : nrm;       // R_CC
+    const double alpha = lean::neg_sign_of(nrm, x0);   // R_CC = -sign(x0) ||x||
     const double v0 = x0 - alpha;                      // x0 + sign(x0) ||x||
     // H = I - tau v v^T, v = (v0, a[C+1..C+6][C]), tau = 2 / v^T v = 1 / (||x|| |v0|)
-    const double tau = sigma > 0.0 ? 1.0 / (nrm * fabs(v0)) : 0.0;
+    const double tau = lean::rcp(nrm * lean::abs_of(v0));   // 0 when sigma == 0
 #pragma unroll
     for (int cc = C + 1; cc < NC; ++cc) {
-        double s = v0 * a[C][cc];
+        const unsigned col = P.a[C][cc];
+        if ((V & col) == 0u) continue;                 // disjoint supports: column unchanged
+        double s = ((col >> C) & 1u) ? v0 * a[C][cc] : 0.0;
 #pragma unroll
-        for (int t = 1; t < 7; ++t) s = fma(a[C + t][C], a[C + t][cc], s);
+        for (int t = 1; t < 7; ++t)
+            if (((V & col) >> (C + t)) & 1u) s = fma(a[C + t][C], a[C + t][cc], s);
         s *= tau;
-        a[C][cc] = fma(-s, v0, a[C][cc]);
+        a[C][cc] = ((col >> C) & 1u) ? fma(-s, v0, a[C][cc]) : -s * v0;
 #pragma unroll
-        for (int t = 1; t < 7; ++t) a[C + t][cc] = fma(-s, a[C + t][C], a[C + t][cc]);
+        for (int t = 1; t < 7; ++t) {
+            if (!((V >> (C + t)) & 1u)) continue;
+            a[C + t][cc] = ((col >> (C + t)) & 1u) ? fma(-s, a[C + t][C], a[C + t][cc])
+                                                   : -s * a[C + t][C];
+        }
     }
     {
-        double s = v0 * b[C];
+        const unsigned bm = P.b[C];
+        if ((V & bm) != 0u) {
+            double s = ((bm >> C) & 1u) ? v0 * b[C] : 0.0;
 #pragma unroll
-        for (int t = 1; t < 7; ++t) s = fma(a[C + t][C], b[C + t], s);
-        s *= tau;
-        b[C] = fma(-s, v0, b[C]);
+            for (int t = 1; t < 7; ++t)
+                if (((V & bm) >> (C + t)) & 1u) s = fma(a[C + t][C], b[C + t], s);
+            s *= tau;
+            b[C] = ((bm >> C) & 1u) ? fma(-s, v0, b[C]) : -s * v0;
 #pragma unroll
-        for (int t = 1; t < 7; ++t) b[C + t] = fma(-s, a[C + t][C], b[C + t]);
+            for (int t = 1; t < 7; ++t) {
+                if (!((V >> (C + t)) & 1u)) continue;
+                b[C + t] = ((bm >> (C + t)) & 1u) ? fma(-s, a[C + t][C], b[C + t]) : -s * a[C + t][C];
+            }
+        }
     }
     a[C][C] = alpha;
-    rinv[C] = x0 >= 0.0 ? -rs : rs;                    // 1 / R_CC
-    rmax = fmax(rmax, nrm);
-    rmin = fmin(rmin, nrm);
+    rinv[C] = lean::neg_sign_of(rs, x0);               // 1 / R_CC
+    const unsigned long long nb = lean::bits_of(nrm);
+    rmax = nb > rmax ? nb : rmax;
+    rmin = nb < rmin ? nb : rmin;
 }
 
-template <int W, int... Cs>
+template <int W, int PAR, int RHS, int... Cs>
 __device__ __forceinline__ void qr_all(std::integer_sequence<int, Cs...>,
                                        double (&a)[2 * W + 7][2 * W + 1], double (&b)[2 * W + 7],
-                                       double (&rinv)[2 * W + 1], double &rmax, double &rmin) {
-    (qr_step<W, Cs>(a, b, rinv, rmax, rmin), ...);
+                                       double (&rinv)[2 * W + 1], unsigned long long &rmax,
+                                       unsigned long long &rmin) {
+    (qr_step<W, PAR, RHS, Cs>(a, b, rinv, rmax, rmin), ...);
 }
 
-template <int W>
-__global__ void __launch_bounds__(kThreadsSpai)
-spai_qr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
-               double *__restrict__ F, double *__restrict__ colres, int32_t *rank_flag) {
+// Right-hand side entries the plan says can be nonzero (RHS 1/2: A_old(I_j, j))
+template <int W, int PAR, int RHS>
+__device__ __forceinline__ void gather_rhs_p(int64_t n, int64_t j, const double *__restrict__ Aold,
+                                             double (&b)[2 * W + 7]) {
+    constexpr int NR = 2 * W + 7;
+    constexpr QrPlan P = make_plan(W, PAR, RHS);
+#pragma unroll
+    for (int r = 0; r < NR; ++r) b[r] = 0.0;
+    if constexpr (RHS == 0) {
+        b[W + 3] = 1.0;
+    } else {
+#pragma unroll
+        for (int r = W; r <= W + 6; ++r) {
+            const int64_t g = j - W - 3 + r;           // row of A_old(:, j)
+            if (((P.b[0] >> r) & 1u) && g >= 0 && g < n) b[r] = __ldg(Aold + (int64_t)(W + 6 - r) * n + g);
+        }
+    }
+}
+
+// Solve column j's least-squares problem with the plan (PAR, RHS) and store it.
+template <int W, int PAR, int RHS>
+__device__ __forceinline__ void qr_column(int64_t n, int64_t j, const double *__restrict__ A,
+                                          const double *__restrict__ Aold, double *__restrict__ F,
+                                          double *__restrict__ colres, int32_t *rank_flag) {
     constexpr int NC = 2 * W + 1;
     constexpr int NR = NC + 6;
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n) return;
-
     double a[NR][NC];
     double b[NR];
-    gather_block<W>(n, j, A, a);
-    gather_rhs<W>(n, j, Aold, b);
-
+    gather_block_p<W, PAR>(n, j, A, a);
+    gather_rhs_p<W, PAR, RHS>(n, j, Aold, b);
     double rinv[NC];
-    double rmax = 0.0, rmin = 1e300;
-    qr_all<W>(std::make_integer_sequence<int, NC>{}, a, b, rinv, rmax, rmin);
+    unsigned long long rmax = 0ull, rmin = ~0ull;      // bit patterns of ||x|| >= 0
+    qr_all<W, PAR, RHS>(std::make_integer_sequence<int, NC>{}, a, b, rinv, rmax, rmin);
     double m[NC];
-    const bool rank_ok = rmin > 0.0 && rmin >= 1e-14 * rmax;
+    const bool rank_ok = rmin != 0ull && lean::from_bits(rmin) >= 1e-14 * lean::from_bits(rmax);
 #pragma unroll
     for (int ci = 0; ci < NC; ++ci) {
         const int c = NC - 1 - ci;
@@ -178,9 +304,37 @@ spai_qr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
         double rr = 0.0;
 #pragma unroll
         for (int r = NC; r < NR; ++r) rr = fma(b[r], b[r], rr);
-        colres[j] = sqrt(rr);
+        colres[j] = rr * lean::rsqrt(rr);              // ||b_j - A m_j||
     }
     store_column<W>(n, j, m, F);
+}
+
+// One column per thread.  For the full band pattern (W = 3) the warps take
+// columns of one parity each (warp w: j = 2 (32 (w / 2) + lane) + w mod 2),
+// so that on a beam matrix (device flags zA, zAold) the interior columns run
+// the beam plan without divergence; all other columns run the general plan.
+template <int W, int UPD>
+__global__ void __launch_bounds__(kThreadsSpai)
+spai_qr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
+               double *__restrict__ F, double *__restrict__ colres, int32_t *rank_flag,
+               const int32_t *__restrict__ zA, const int32_t *__restrict__ zAold) {
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t j = gt;
+    if (W == 3) {
+        const int64_t w = gt >> 5;
+        j = 2 * ((w >> 1) * 32 + (gt & 31)) + (w & 1);
+    }
+    if (j >= n) return;
+    if (W == 3) {
+        const bool beam = zA && *zA != 0 && (!UPD || (zAold && *zAold != 0)) && (n % 2 == 0) &&
+                          j >= 3 && j <= n - 9;
+        if (beam) {
+            if (j & 1) qr_column<W, 1, UPD ? 2 : 0>(n, j, A, Aold, F, colres, rank_flag);
+            else qr_column<W, 0, UPD ? 2 : 0>(n, j, A, Aold, F, colres, rank_flag);
+            return;
+        }
+    }
+    qr_column<W, -1, UPD ? 1 : 0>(n, j, A, Aold, F, colres, rank_flag);
 }
 
 template <int W>
@@ -266,9 +420,14 @@ spai_mr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
 
 template <int W>
 cudaError_t qr_w(int64_t n, const double *A, const double *Aold, double *F, double *colres,
-                 int32_t *flag, cudaStream_t s) {
-    int64_t blocks = (n + kThreadsSpai - 1) / kThreadsSpai;
-    spai_qr_kernel<W><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag);
+                 int32_t *flag, const int32_t *zA, const int32_t *zAold, cudaStream_t s) {
+    // W == 3 maps warps to columns of one parity: 64 columns per warp pair
+    const int64_t threads = W == 3 ? 64 * ((n + 63) / 64) : n;
+    const int64_t blocks = (threads + kThreadsSpai - 1) / kThreadsSpai;
+    if (Aold)
+        spai_qr_kernel<W, 1><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, zA, zAold);
+    else
+        spai_qr_kernel<W, 0><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, zA, zAold);
     return cudaGetLastError();
 }
 
@@ -285,12 +444,13 @@ cudaError_t mr_w(int64_t n, const double *A, const double *Aold, const double *a
 }  // namespace
 
 cudaError_t launch_spai_qr(int64_t n, int hbw, const double *A, const double *A_old, double *F,
-                           double *colres, int32_t *rank_flag, cudaStream_t s) {
+                           double *colres, int32_t *rank_flag, const int32_t *zA,
+                           const int32_t *zAold, cudaStream_t s) {
     switch (hbw) {
-        case 0: return qr_w<0>(n, A, A_old, F, colres, rank_flag, s);
-        case 1: return qr_w<1>(n, A, A_old, F, colres, rank_flag, s);
-        case 2: return qr_w<2>(n, A, A_old, F, colres, rank_flag, s);
-        default: return qr_w<3>(n, A, A_old, F, colres, rank_flag, s);
+        case 0: return qr_w<0>(n, A, A_old, F, colres, rank_flag, zA, zAold, s);
+        case 1: return qr_w<1>(n, A, A_old, F, colres, rank_flag, zA, zAold, s);
+        case 2: return qr_w<2>(n, A, A_old, F, colres, rank_flag, zA, zAold, s);
+        default: return qr_w<3>(n, A, A_old, F, colres, rank_flag, zA, zAold, s);
     }
 }
 

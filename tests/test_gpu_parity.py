@@ -211,6 +211,59 @@ def test_spai_update_qr(G, pair):
     assert torch.isfinite(G.precond_factor(P1, 0)).all()
 
 
+def _broken_beam(n_e, rows=(100, 101)):
+    """Beam whose w/theta coupling of one node is not cancelled: no beam zero
+    structure, so the SPAI kernels take their general plan."""
+    beam = W.beam(n_e)
+    k_val = beam.k_val.copy()
+    rr = np.repeat(np.arange(beam.n), np.diff(beam.rowptr))
+    for (r, c) in (rows, rows[::-1]):
+        k = np.nonzero((rr == r) & (beam.col == c))[0][0]
+        k_val[k] = 0.25
+    beam.k_val = k_val
+    return beam
+
+
+@pytest.mark.parametrize("s", [0.1, 30.0])
+def test_spai_general_plan_build_and_update(G, s):
+    # build and update on a matrix without the beam zero structure, and an
+    # update whose A_old has it while A_next does not (and vice versa)
+    beam_b = _broken_beam(900)
+    beam_g = W.beam(900)
+    Mb, Kb = G.beam_mats(beam_b)
+    Mg, Kg = G.beam_mats(beam_g)
+    Ab = G.assemble_shifted(Mb, Kb, AL, BE, s)
+    Ag = G.assemble_shifted(Mg, Kg, AL, BE, 1.7 * s)
+    Aob = O.shifted_csr(beam_b, AL, BE, s)
+    Aog = O.shifted_csr(beam_g, AL, BE, 1.7 * s)
+    Pb = G.spai_build(Ab)
+    assert column_errors(G.precond_factor(Pb, 0).cpu().numpy(), O.spai(Aob)).max() <= 1e-10
+    for (A_prev, A_next, Ao_prev, Ao_next) in ((Ab, Ag, Aob, Aog), (Ag, Ab, Aog, Aob)):
+        P = G.spai_update(G.spai_build(A_prev), A_prev, A_next)
+        Qo = O.spai(Ao_next, A_old=Ao_prev)
+        assert column_errors(G.precond_factor(P, 1).cpu().numpy(), Qo).max() <= 1e-10
+
+
+def test_spai_odd_n_random_band(G):
+    # odd n: the beam plan is never taken; random diagonally dominant band
+    rng = np.random.default_rng(17)
+    n = 501
+    D = np.zeros((n, n))
+    for d in range(-3, 4):
+        i = np.arange(max(0, -d), min(n, n - d))
+        D[i, i + d] = rng.uniform(-1, 1, i.size)
+    D = D + D.T + np.diag(10.0 + rng.uniform(0, 1, n))
+    band = np.zeros((7, n))
+    for d in range(-3, 4):
+        i = np.arange(max(0, -d), min(n, n - d))
+        band[d + 3, i] = D[i, i + d]
+    A = G.mat_from_band(torch.from_numpy(band.ravel()).cuda())
+    rp, ci = W.band_pattern(n, 3)
+    Ao = O.dense_to_csr(D, O.CSR(n, rp, ci, np.ones(ci.size)))
+    P = G.spai_build(A)
+    assert column_errors(G.precond_factor(P, 0).cpu().numpy(), O.spai(Ao)).max() <= 1e-10
+
+
 def test_update_same_matrix_is_identity(G):
     beam, M, K = setup_beam(G, 300)
     A = G.assemble_shifted(M, K, AL, BE, 4.0)

@@ -77,7 +77,11 @@ def test_noalloc_matches_pcg_solve_on_two_calls(G):
         Xn = X.cpu().numpy()
         for c in range(2):
             assert int(status[c]) == G.OK and int(ref["status"][c]) == G.OK
-            assert abs(int(iters[c]) - int(ref["iters"][c])) <= 1
+            # iteration counts within the PCG parity tolerance max(2, 5 %): the
+            # raw band runs the full 7-point stencil, the handle path the packed
+            # beam stencil, so rounding moves the step that crosses the threshold
+            it_ref = int(ref["iters"][c])
+            assert abs(int(iters[c]) - it_ref) <= max(2, it_ref // 20)
             assert np.linalg.norm(Xn[c] - Xr[c]) <= 1e-8 * np.linalg.norm(Xr[c])
             assert float(relres[c]) <= 2e-10
 
