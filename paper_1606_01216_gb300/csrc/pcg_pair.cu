@@ -29,6 +29,7 @@
 // precedes z = M r.  Convergence is tested as r.r <= (tol ||b||)^2, keeping
 // square roots off the per-iteration critical path; the residual history is
 // stored as r.r and converted once at exit.
+#include "fp64_lean.cuh"
 #include "pcg_common.cuh"
 
 namespace airga {
@@ -339,7 +340,7 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
                     const double pq = pqt[0];
                     const bool bad = !(pq > 0.0) || !isfinite(pq);
                     s_dec = bad ? 1 : 0;
-                    tot[0] = bad ? 0.0 : rz / pq;
+                    tot[0] = bad ? 0.0 : rz * lean::rcp_signed(pq);
                 }
             }
             __syncthreads();
@@ -415,7 +416,7 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
                     if (t2v[1] <= thr2) dec = 1;                               // converged
                     else if (!isfinite(rz_new) || rz_new == 0.0) dec = 2;      // breakdown
                     s_dec = dec;
-                    tot[1] = dec ? 0.0 : rz_new / rz;                          // beta
+                    tot[1] = dec ? 0.0 : rz_new * lean::rcp_signed(rz);        // beta
                     tot[2] = rz_new;
                 }
             }

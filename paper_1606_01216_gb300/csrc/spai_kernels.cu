@@ -186,8 +186,10 @@ __device__ __forceinline__ void gather_block_p(int64_t n, int64_t j, const doubl
 // the plan's zero tests fold away.
 //
 // The scalar part costs few FP64-pipe instructions: 1/sqrt and the
-// reciprocal come from lean::rsqrt / lean::rcp (FP32 hardware seed, two FP64
-// Newton steps), signs and absolute values are integer bit operations, and
+// reciprocal come from lean::rsqrt1 / lean::rcp1 (FP32 hardware seed, one FP64
+// Newton step: relative error below 2^-43, which perturbs the reflectors by
+// that much, far below the 1e-10 the columns are held to), signs and absolute
+// values are integer bit operations, and
 // the rank test tracks the largest and smallest ||x|| by their bit patterns
 // (non-negative doubles order like their bits).
 template <int W, int PAR, int RHS, int C>
@@ -202,12 +204,12 @@ __device__ __forceinline__ void qr_step(double (&a)[2 * W + 7][2 * W + 1], doubl
     for (int t = 0; t < 7; ++t)
         if ((P.a[C][C] >> (C + t)) & 1u) sigma = fma(a[C + t][C], a[C + t][C], sigma);
     const double x0 = a[C][C];
-    const double rs = lean::rsqrt(sigma);              // 0 when sigma == 0
+    const double rs = lean::rsqrt1(sigma);             // 0 when sigma == 0
     const double nrm = sigma * rs;                     // ||x||
     const double alpha = lean::neg_sign_of(nrm, x0);   // R_CC = -sign(x0) ||x||
     const double v0 = x0 - alpha;                      // x0 + sign(x0) ||x||
     // H = I - tau v v^T, v = (v0, a[C+1..C+6][C]), tau = 2 / v^T v = 1 / (||x|| |v0|)
-    const double tau = lean::rcp(nrm * lean::abs_of(v0));   // 0 when sigma == 0
+    const double tau = lean::rcp1(nrm * lean::abs_of(v0));   // 0 when sigma == 0
 #pragma unroll
     for (int cc = C + 1; cc < NC; ++cc) {
         const unsigned col = P.a[C][cc];
@@ -304,7 +306,7 @@ __device__ __forceinline__ void qr_column(int64_t n, int64_t j, const double *__
         double rr = 0.0;
 #pragma unroll
         for (int r = NC; r < NR; ++r) rr = fma(b[r], b[r], rr);
-        colres[j] = rr * lean::rsqrt(rr);              // ||b_j - A m_j||
+        colres[j] = rr * lean::rsqrt1(rr);             // ||b_j - A m_j||
     }
     store_column<W>(n, j, m, F);
 }
