@@ -38,9 +38,9 @@ FP64_FMA_PER_CLK_SM = 2          # GB300 FP64 pipe
 PCG_FLOP_PER_ROW_ITER = 40       # 20 FMA: A (7) + P_sym (7) + 3 dots + 3 axpys
 PCG_BYTES_PER_ROW_ITER = 160     # A 56 + P_sym 56 + x, r, p read+write 48
 # DRAM bytes per row and iteration of pcg_pair_kernel from one ncu capture of
-# the s = 0.1 launch on this workload (dram read + write / (229 x 1e6)); the
-# bands stay in L2, see profiles/pcg_pair_kernel_beam_n1e6_s0.1.md
-PCG_DRAM_BYTES_PER_ROW_ITER = 8.54
+# the s = 0.1 launch on this workload (dram read + write / (229 x 1e6)) of the
+# current kernel; the bands stay in L2
+PCG_DRAM_BYTES_PER_ROW_ITER = 10.28
 
 
 def peaks():
@@ -225,7 +225,7 @@ def gpu_arm(args, world, rank, local):
                           "frac": round(achieved_tf / fp64_peak, 4),
                           "traffic": round(sum(pcg_it) * n * PCG_DRAM_BYTES_PER_ROW_ITER /
                                            len(pcg_it)),
-                          "traffic_note": "ncu DRAM bytes per launch, 8.54 B/row/iter x the "
+                          "traffic_note": "ncu DRAM bytes per launch, 10.28 B/row/iter x the "
                                           "mean row-iterations of a launch",
                           "kernel": "pcg_pair_kernel (persistent row-pair PCG, FP64)",
                           "hbm_achieved_gbs": round(achieved_gbs, 1),
