@@ -155,7 +155,8 @@ def gpu_arm(args, world, rank, local):
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
             r = G.pcg_solve(A, P, F, opts)
-            cnt += 3                      # pcg, residual partial, residual final
+            cnt += 2                      # pack_pairs (packed beam stencil of the new A), pcg
+                                          # (true residual in the PCG kernel's epilogue)
             if record:
                 e1.record(stream)
                 pcg_events.append((e0, e1, r["iters"]))

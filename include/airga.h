@@ -190,7 +190,8 @@ void airga_precond_free(airga_precond P);
  * be NULL (M = I).  Outputs (device): X[n*m]; iters[m] (int32, iterations
  * done); status[m] (int32, AIRGA_OK / AIRGA_E_MAXIT / AIRGA_E_BREAKDOWN /
  * AIRGA_E_TIMEOUT); true_relres[m] (||f - A x|| / ||f|| recomputed from X at
- * exit); res_hist[(maxit+1)*m] (optional, may be NULL: column c holds
+ * exit in FP64; NaN for a column whose solve ended in AIRGA_E_TIMEOUT, after
+ * which no residual pass runs); res_hist[(maxit+1)*m] (optional, may be NULL: column c holds
  * ||r_k|| / ||f|| for k = 0..iters[c], the rest untouched).  A zero column f
  * gives x = 0, iters = 0, status OK, true_relres 0.  Uses a per-call device
  * workspace from the library pool (about 4 n doubles). */

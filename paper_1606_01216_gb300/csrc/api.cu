@@ -621,16 +621,18 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
     a.bar = ctl;
     a.abort_flag = (int *)(ctl + 1);
     cudaError_t e = cudaSuccess;
+    // the row-pair kernel computes the true residual in its epilogue
+    const bool relres_in_kernel = plan.kind == 2;
     for (int32_t c = 0; c < m && e == cudaSuccess; ++c) {
         if (fused_rhs) {
             a.b = nullptr;
             a.rhs_M = Mrhs->band->d;
             a.rhs_v = V + (size_t)c * n;
             a.rhs_scale = scale;
-            a.relres = true_relres + c;        // true residual in the kernel epilogue
         } else {
             a.b = F + (size_t)c * n;
         }
+        a.relres = relres_in_kernel ? true_relres + c : nullptr;
         a.x = X + (size_t)c * n;
         a.hist = res_hist ? res_hist + (size_t)c * (o.maxit + 1) : nullptr;
         a.iters = iters + c;
@@ -638,7 +640,7 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
         e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
         if (e == cudaSuccess) e = launch_pcg(plan, a, s);
     }
-    if (e == cudaSuccess && !fused_rhs)
+    if (e == cudaSuccess && !relres_in_kernel)
         e = launch_true_residual(n, A->band->d, X, F, m, true_relres, res_part, nblk, s);
     dev_free(ws, s);
     if (Fmat) dev_free(Fmat, s);

@@ -444,6 +444,8 @@ finish:
             *a.status = status;
         }
     }
+    if (a.relres && status == AIRGA_E_TIMEOUT && rank == 0 && tid == 0)
+        *a.relres = __longlong_as_double(0x7FF8000000000000ll);   // NaN: no residual pass after an abort
     if (a.relres && status != AIRGA_E_TIMEOUT) {
         // true residual ||b - A x|| / ||b|| of the final x, in FP64: the group
         // exchanges x through global memory (one barrier), each CTA sums its rows
