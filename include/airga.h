@@ -424,6 +424,22 @@ void airga_mlp_free(airga_mlp net);
 #define AIRGA_FAULT_SKIP_ARRIVAL 1
 int airga_debug_set_fault(int fault);
 
+/* Test hook: make the CG calls of this process (airga_pcg_solve,
+ * airga_pcg_solve_mv) use one kernel variant whenever it is applicable, so
+ * that every variant can be checked on small problems.  0 = automatic (the
+ * default): the node-pair kernel with the whole solve state in shared memory
+ * when even n fits, else the node-pair kernel with the r and p windows in
+ * shared memory and x, z/q in global memory, else the generic kernel.
+ * 1 = generic kernel with its state in global memory, 2 = node-pair kernel
+ * with shared-memory state, 3 = node-pair kernel with split state.  A variant
+ * that does not apply (odd n, unaligned operands, update chains, too little
+ * shared memory) falls through to the next one as in automatic mode. */
+#define AIRGA_PCG_KERNEL_AUTO 0
+#define AIRGA_PCG_KERNEL_GENERIC_GLOBAL 1
+#define AIRGA_PCG_KERNEL_PAIR 2
+#define AIRGA_PCG_KERNEL_PAIR_SPLIT 3
+int airga_debug_force_pcg_kernel(int kind);
+
 /* Release the library's cached device memory (pool trim) on the current
  * device; outstanding handles stay valid. */
 int airga_trim(void);

@@ -35,6 +35,7 @@ EXPORTS = (
     "airga_mlp_train_options_default", "airga_mlp_create", "airga_mlp_set_params",
     "airga_mlp_get_params", "airga_mlp_status", "airga_mlp_features", "airga_mlp_forward",
     "airga_mlp_grad", "airga_mlp_train", "airga_mlp_spai", "airga_mlp_free",
+    "airga_debug_force_pcg_kernel",
 )
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
@@ -123,6 +124,7 @@ def lib():
         "airga_pcg_solve_mv": (C.c_int, [vp, vp, vp, vp, C.c_double, i32, C.POINTER(Options), vp,
                                          vp, vp, vp, vp, vp]),
         "airga_debug_set_fault": (C.c_int, [C.c_int]),
+        "airga_debug_force_pcg_kernel": (C.c_int, [C.c_int]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
         "airga_trim": (C.c_int, []),
@@ -481,6 +483,12 @@ def true_residual(A: Mat, X: torch.Tensor, F: torch.Tensor, stream=None) -> torc
 
 
 FAULT_NONE, FAULT_SKIP_ARRIVAL = 0, 1
+PCG_KERNEL_AUTO, PCG_KERNEL_GENERIC_GLOBAL, PCG_KERNEL_PAIR, PCG_KERNEL_PAIR_SPLIT = 0, 1, 2, 3
+
+
+def debug_force_pcg_kernel(kind: int):
+    """Test hook: prefer one CG kernel variant (0 = automatic)."""
+    _check(lib().airga_debug_force_pcg_kernel(int(kind)), "debug_force_pcg_kernel")
 
 
 def debug_set_fault(fault: int):

@@ -131,7 +131,8 @@ cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_
 constexpr int kMaxChain = 16;
 
 struct PcgPlan {
-    int kind = 0;          // 0 generic (shared-memory state), 1 generic (global state), 2 node-pair
+    int kind = 0;          // 0 generic (shared-memory state), 1 generic (global state), 2 node-pair,
+                           // 3 node-pair with r, p in shared memory and x, z/q in global memory
     int grid = 0;          // CTAs (all co-resident)
     int threads = 0;
     int64_t rows = 0;      // rows per CTA (R)
@@ -180,8 +181,15 @@ int take_fault();
 // by the node-pair kernel together with an even n)
 int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgPlan *plan);
 cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
+// test hook: 0 = automatic kernel choice, 1 = generic kernel with global
+// state, 2 = node-pair kernel with shared-memory state, 3 = node-pair kernel
+// with split state (whenever the forced kind is feasible)
+int forced_pcg_kind();
 // node-pair kernel (pcg_pair.cu)
 size_t pcg_pair_smem(int64_t R);
+size_t pcg_pair_split_smem(int64_t R);       // r and p windows only
+size_t pcg_pair_split_slice(int64_t R);      // doubles of global workspace per CTA (z/q window)
+int pcg_pair_split_occupancy(int mode, size_t smem, int *per_sm);
 int pcg_pair_threads();
 int pcg_pair_occupancy(int mode, size_t smem, int *per_sm);
 cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);

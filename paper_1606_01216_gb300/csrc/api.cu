@@ -132,6 +132,10 @@ static std::atomic<int> g_fault{AIRGA_FAULT_NONE};
 
 int take_fault() { return g_fault.exchange(AIRGA_FAULT_NONE); }
 
+static std::atomic<int> g_forced_kind{0};
+
+int forced_pcg_kind() { return g_forced_kind.load(); }
+
 int check_options(const airga_options *o) {
     if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return fail(AIRGA_E_INVALID_ARG, "tol must be finite and >= 0");
     if (o->maxit < 0) return fail(AIRGA_E_INVALID_ARG, "maxit must be >= 0");
@@ -556,7 +560,7 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
     st = pcg_plan(n, nf, nf == 1 && o.symmetrize, al, dev, &plan);
     if (st) return st;
     cudaStream_t s = S(stream);
-    const bool fused_rhs = Mrhs && plan.kind == 2;
+    const bool fused_rhs = Mrhs && plan.kind >= 2;
     double *Fmat = nullptr;           // materialised scale M V when the fallback kernel runs
     if (Mrhs && !fused_rhs) {
         st = dev_alloc((void **)&Fmat, sizeof(double) * (size_t)n * m, s);
@@ -597,7 +601,7 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
     a.fault_skip_arrival = take_fault() == AIRGA_FAULT_SKIP_ARRIVAL ? 1 : 0;
     a.pairz = A->pairz ? (const int32_t *)A->pairz.get() : nullptr;
-    if (plan.kind == 2 && A->pairz) {
+    if (plan.kind >= 2 && A->pairz) {
         // packed beam entries for the row-pair stencil, made once per matrix
         if (!A->packed) {
             st = make_buf(sizeof(double) * 5 * (size_t)n, s, &A->packed);
@@ -622,7 +626,7 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
     a.abort_flag = (int *)(ctl + 1);
     cudaError_t e = cudaSuccess;
     // the row-pair kernel computes the true residual in its epilogue
-    const bool relres_in_kernel = plan.kind == 2;
+    const bool relres_in_kernel = plan.kind >= 2;
     for (int32_t c = 0; c < m && e == cudaSuccess; ++c) {
         if (fused_rhs) {
             a.b = nullptr;
@@ -684,6 +688,12 @@ int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m
     cudaError_t e = launch_true_residual(A->n, A->band->d, X, F, m, relres, (double *)tmp, nblk, s);
     dev_free(tmp, s);
     if (e != cudaSuccess) return cuda_fail(e, "true residual");
+    return AIRGA_OK;
+}
+
+int airga_debug_force_pcg_kernel(int kind) {
+    if (kind < 0 || kind > 3) return fail(AIRGA_E_INVALID_ARG, "kernel kind must be 0..3");
+    g_forced_kind.store(kind);
     return AIRGA_OK;
 }
 

@@ -316,29 +316,42 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
     int sms = 0, optin = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
-    // node-pair kernel: even n, aligned operands, state in shared memory
-    if (mode != kChain && aligned16 && n % 2 == 0) {
+    const int forced = forced_pcg_kind();
+    // node-pair kernel: even n, aligned operands, no update chain; state in
+    // shared memory (kind 2), or r and p in shared memory with x and z/q in
+    // global memory (kind 3).  Automatic order 2, 3, generic; a forced kind is
+    // taken first when it applies.
+    if (mode != kChain && aligned16 && n % 2 == 0 && forced != 1) {
         int64_t want_p = (n + kMinRowsPerCta - 1) / kMinRowsPerCta;
         int grid_p = (int)(want_p < sms ? want_p : sms);
         if (grid_p < 1) grid_p = 1;
         int64_t Rp = (n + grid_p - 1) / grid_p;
         Rp += Rp & 1;
-        const size_t smem_p = pcg_pair_smem(Rp);
+        const size_t smem_p = pcg_pair_smem(Rp), smem_s = pcg_pair_split_smem(Rp);
+        bool ok2 = false, ok3 = false;
         if (smem_p + 256 <= (size_t)optin) {
             int per_sm = 0;
             int st = pcg_pair_occupancy(mode == kIdentity ? 0 : 1, smem_p, &per_sm);
             if (st) return st;
-            if (per_sm >= 1 && grid_p <= per_sm * sms) {
-                plan->kind = 2;
-                plan->threads = pcg_pair_threads();
-                plan->halo = 8;
-                plan->grid = grid_p;
-                plan->rows = Rp;
-                plan->smem_state = true;
-                plan->smem_bytes = smem_p;
-                plan->scratch_doubles = 0;
-                return AIRGA_OK;
-            }
+            ok2 = per_sm >= 1 && grid_p <= per_sm * sms;
+        }
+        if (smem_s + 256 <= (size_t)optin) {
+            int per_sm = 0;
+            int st = pcg_pair_split_occupancy(mode == kIdentity ? 0 : 1, smem_s, &per_sm);
+            if (st) return st;
+            ok3 = per_sm >= 1 && grid_p <= per_sm * sms;
+        }
+        const int kind = (forced == 3 && ok3) ? 3 : (ok2 ? 2 : (ok3 ? 3 : 0));
+        if (kind) {
+            plan->kind = kind;
+            plan->threads = pcg_pair_threads();
+            plan->halo = 8;
+            plan->grid = grid_p;
+            plan->rows = Rp;
+            plan->smem_state = kind == 2;
+            plan->smem_bytes = kind == 2 ? smem_p : smem_s;
+            plan->scratch_doubles = kind == 2 ? 0 : pcg_pair_split_slice(Rp) * (size_t)grid_p;
+            return AIRGA_OK;
         }
     }
     const int H = mode == kIdentity ? 3 : (mode == kBand1 ? 6 : 3 + 3 * nf);
@@ -355,7 +368,7 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
     plan->halo = H;
     plan->grid = grid;
     plan->rows = R;
-    plan->smem_state = (mode != kChain) && (smem + static_smem <= (size_t)optin);
+    plan->smem_state = (mode != kChain) && (smem + static_smem <= (size_t)optin) && forced != 1;
     plan->kind = plan->smem_state ? 0 : 1;
     plan->smem_bytes = plan->smem_state ? smem : 0;
     const size_t slice = (size_t)(R + (R + 2 * H) + (R + 2 * H + 6) + (R + 6) + 2 * (R + 2 * H));
@@ -395,7 +408,7 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
 }
 
 cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
-    if (plan.kind == 2) return launch_pcg_pair(plan, args, s);
+    if (plan.kind == 2 || plan.kind == 3) return launch_pcg_pair(plan, args, s);
     const int mode = mode_of(args.nf, args.psym != nullptr);
     if (plan.smem_state) {
         if (mode == kIdentity) return launch_mode<true, kIdentity>(plan, args, s);

@@ -156,7 +156,7 @@ struct PairShared {
 // being `rank` (rows [rank R, rank R + R)).  The group's barriers, partials
 // and p boundary buffer come from `a`; the single-system kernel runs it with
 // the whole grid as the group, the batched kernel once per assignment.
-template <int MODE>   // 0: identity, 1: one symmetric band
+template <int MODE, int SPLIT = 0>   // MODE 0: identity, 1: one symmetric band
 __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem,
                           PairShared &sh) {
     double *tot = sh.tot;
@@ -169,11 +169,23 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
     const int hi = lo + R < n ? lo + R : n;
     if (tid == 0) s_nb = 0.0;
 
-    double *xs = smem;
-    double *rs = xs + R;
-    double *ps = rs + (R + 2 * HR);
-    double *zq = ps + (R + 2 * HZ);
-    double2 *ah = reinterpret_cast<double2 *>(zq + (R + 2 * HZ));   // A rows of the r halo
+    // SPLIT == 0: x, r, p, z/q windows all in shared memory.  SPLIT == 1 (n too
+    // large for four windows): r and p stay in shared memory, x is updated in
+    // place in the caller's X and the z/q window lives in this CTA's slice of
+    // the global workspace (L2 traffic of 48 B per row and iteration).
+    double *xs, *rs, *ps, *zq;
+    if (SPLIT) {
+        rs = smem;
+        ps = rs + (R + 2 * HR);
+        xs = a.x + lo;
+        zq = a.state + (size_t)rank * (size_t)(R + 2 * HZ);
+    } else {
+        xs = smem;
+        rs = xs + R;
+        ps = rs + (R + 2 * HR);
+        zq = ps + (R + 2 * HZ);
+    }
+    double2 *ah = reinterpret_cast<double2 *>(ps + (R + 2 * HZ) + (SPLIT ? 0 : R + 2 * HZ));   // A rows of the r halo
     double *red = reinterpret_cast<double *>(ah + kHaloPairs * kBand);
     const int xbase = lo, rbase = lo - HR, pbase = lo - HZ, zbase = lo - HZ;
     const int rlo = lo - HR > 0 ? lo - HR : 0, rhi = hi + HR < n ? hi + HR : n;
@@ -192,8 +204,10 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
 
     // zero every window (out-of-matrix slots must read as 0), cache A's halo rows
     {
-        const int total = 4 * R + 2 * (HR + 2 * HZ);
+        const int total = SPLIT ? 2 * R + 2 * (HR + HZ) : 4 * R + 2 * (HR + 2 * HZ);
         for (int k = tid; k < total; k += nt) smem[k] = 0.0;
+        if (SPLIT)
+            for (int k = tid; k < R + 2 * HZ; k += nt) zq[k] = 0.0;
         if (hvalid) {
             double2 t[kBand];
             load_band_pair(a.A, n, hpair, t);
@@ -434,7 +448,8 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
     }
 finish:
     __syncthreads();
-    for (int i = lo + tid; i < hi; i += nt) a.x[i] = xs[i - xbase];
+    if (!SPLIT)
+        for (int i = lo + tid; i < hi; i += nt) a.x[i] = xs[i - xbase];
     if (rank == 0) {
         if (a.hist && s_nb > 0.0)       // r.r -> ||r_k|| / ||b||
             for (int k = tid; k <= iters; k += nt) a.hist[k] = sqrt(a.hist[k]) / s_nb;
@@ -473,12 +488,12 @@ finish:
     }
 }
 
-template <int MODE>
+template <int MODE, int SPLIT>
 __global__ void __launch_bounds__(kThreads, 1)
 pcg_pair_kernel(PcgArgs a, int R) {
     extern __shared__ __align__(16) double smem[];
     __shared__ PairShared sh;
-    pair_body<MODE>(a, R, gridDim.x, blockIdx.x, smem, sh);
+    pair_body<MODE, SPLIT>(a, R, gridDim.x, blockIdx.x, smem, sh);
 }
 
 // Batched form: CTA c runs the assignments asg[off[c] .. off[c+1]) in order;
@@ -502,9 +517,9 @@ pcg_pair_batch_kernel(const PcgArgs *__restrict__ sys, const int4 *__restrict__ 
     }
 }
 
-template <int MODE>
+template <int MODE, int SPLIT>
 cudaError_t launch_pair_mode(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
-    auto kern = pcg_pair_kernel<MODE>;
+    auto kern = pcg_pair_kernel<MODE, SPLIT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)plan.smem_bytes);
     if (e != cudaSuccess) return e;
@@ -522,20 +537,26 @@ size_t pcg_pair_smem(int64_t R) {
            sizeof(double);
 }
 
+size_t pcg_pair_split_smem(int64_t R) {
+    return (size_t)(2 * R + 2 * (HR + HZ) + 2 * kHaloPairs * kBand + 3 * kThreads) * sizeof(double);
+}
+
+size_t pcg_pair_split_slice(int64_t R) { return (size_t)(R + 2 * HZ); }
+
 int pcg_pair_threads() { return kThreads; }
 
 int pcg_pair_occupancy(int mode, size_t smem, int *per_sm) {
     cudaError_t e;
     if (mode == 0) {
-        e = cudaFuncSetAttribute(pcg_pair_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(pcg_pair_kernel<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<0>, kThreads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<0, 0>, kThreads, smem);
     } else {
-        e = cudaFuncSetAttribute(pcg_pair_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        e = cudaFuncSetAttribute(pcg_pair_kernel<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<1>, kThreads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<1, 0>, kThreads, smem);
     }
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg pair occupancy");
 }
@@ -563,9 +584,29 @@ cudaError_t launch_pcg_pair_batch(int mode, int grid, size_t smem, const PcgArgs
     return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreads), kargs, smem, s);
 }
 
+int pcg_pair_split_occupancy(int mode, size_t smem, int *per_sm) {
+    cudaError_t e;
+    if (mode == 0) {
+        e = cudaFuncSetAttribute(pcg_pair_kernel<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<0, 1>, kThreads, smem);
+    } else {
+        e = cudaFuncSetAttribute(pcg_pair_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<1, 1>, kThreads, smem);
+    }
+    return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg pair split occupancy");
+}
+
 cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
-    if (args.nf == 0) return launch_pair_mode<0>(plan, args, s);
-    return launch_pair_mode<1>(plan, args, s);
+    if (plan.kind == 3) {
+        if (args.nf == 0) return launch_pair_mode<0, 1>(plan, args, s);
+        return launch_pair_mode<1, 1>(plan, args, s);
+    }
+    if (args.nf == 0) return launch_pair_mode<0, 0>(plan, args, s);
+    return launch_pair_mode<1, 0>(plan, args, s);
 }
 
 }  // namespace airga

@@ -540,6 +540,45 @@ def test_pcg_even_n_without_beam_structure(G):
     assert abs(int(res["iters"][0]) - it_o) <= 1
 
 
+@pytest.mark.parametrize("kind", [1, 3])
+@pytest.mark.parametrize("s", [0.1, 100.0])
+def test_pcg_forced_kernel_variants(G, kind, s):
+    """Every CG kernel variant against the oracle on a small beam: the
+    generic kernel with global state (kind 1) and the node-pair kernel with
+    the split state (kind 3, r and p in shared memory, x and z/q in global
+    memory; chosen automatically only when n is too large for the
+    shared-memory state), with and without a preconditioner."""
+    beam, M, K = setup_beam(G, 1237)
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    P = G.spai_build(A)
+    Ao = O.shifted_csr(beam, AL, BE, s)
+    F = W.loads(beam.n, 2, seed=5)
+    Fd = torch.from_numpy(np.ascontiguousarray(F.T)).cuda()
+    G.debug_force_pcg_kernel(kind)
+    try:
+        for prec in (P, None):
+            res = G.pcg_solve(A, prec, Fd.t(), G.options(tol=1e-10, maxit=5000), want_hist=True)
+            torch.cuda.synchronize()
+            X = res["X"].t().cpu().numpy()
+            for c in range(2):
+                facs = [O.spai(Ao)] if prec is not None else []
+                x_o, it_o, st_o, h_o = O.pcg(Ao, F[:, c], facs, tol=1e-10, maxit=5000)
+                assert int(res["status"][c]) == G.OK and st_o == O.OK
+                assert np.linalg.norm(X[c] - x_o) <= 1e-8 * np.linalg.norm(x_o)
+                assert abs(int(res["iters"][c]) - it_o) <= max(2, it_o // 20)
+                assert float(res["true_relres"][c]) <= 2e-10
+        # inner-loop right-hand sides through the same variant
+        V = torch.from_numpy(np.ascontiguousarray(F[:, 0])).cuda()
+        r = G.pcg_solve_mv(A, P, M, V, -1.0, G.options(tol=1e-10, maxit=5000))
+        torch.cuda.synchronize()
+        rhs = -O.spmv(O.from_beam(beam, "m"), F[:, 0])
+        x_o, it_o, st_o, _ = O.pcg(Ao, rhs, [O.spai(Ao)], tol=1e-10, maxit=5000)
+        assert int(r["status"][0]) == G.OK
+        assert np.linalg.norm(r["X"].cpu().numpy() - x_o) <= 1e-8 * np.linalg.norm(x_o)
+    finally:
+        G.debug_force_pcg_kernel(0)
+
+
 # ---------------------------------------------------------------------------
 # AIRGA inner-loop right-hand sides M V with the preconditioner reused
 # ---------------------------------------------------------------------------
