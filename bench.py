@@ -63,6 +63,24 @@ def dist_env():
     return world, rank, local
 
 
+def job_ms(ms: float, dist=None, device=None) -> float:
+    """The job's step time: the slowest rank's mean step time (ms).  Replicas
+    share nothing on the data path; this all-reduce of one scalar (MAX) and
+    the barrier after it are the only collectives."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_value(world: int, ms: float) -> float:
+    """Whole-job throughput: every rank solves the 8 shifts of its replica."""
+    return world * len(SHIFTS) / (ms * 1e-3)
+
+
 class Clocks:
     """nvidia-smi sampling during the timed region."""
 
@@ -185,12 +203,7 @@ def gpu_arm(args, world, rank, local):
         times.append(e0.elapsed_time(e1))
     torch.cuda.synchronize()
     ck = clocks.stop()
-    ms = sum(times) / len(times)
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dist.barrier()
-        ms = float(t.item())
+    ms = job_ms(sum(times) / len(times), dist, device="cuda")
     iters = [int(r["iters"][0]) for r in results]
     status = [int(r["status"][0]) for r in results]
     relres = [float(r["true_relres"][0]) for r in results]
@@ -846,7 +859,7 @@ def main():
         return
     r = gpu_arm(args, world, rank, local)
     if rank == 0:
-        value = world * len(SHIFTS) / (r["ms"] * 1e-3)
+        value = job_value(world, r["ms"])
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms"], 4),
