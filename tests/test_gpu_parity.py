@@ -540,6 +540,49 @@ def test_pcg_even_n_without_beam_structure(G):
     assert abs(int(res["iters"][0]) - it_o) <= 1
 
 
+@pytest.mark.parametrize("s", [1.0, 10.0, 100.0, 1000.0])
+def test_literal_scaling_config1(G, s):
+    """Config 1 in the literal scaling (L = 1, h = 1/500): the FP64 floor
+    phi(s) = ||F - A X_dir|| / ||F|| of the banded Cholesky solve makes 1e-10
+    unreachable, so both sides run PCG to tol_eff = max(1e-10, 10 phi(s)).  At
+    this conditioning (kappa ~ 1e11) the iteration total depends on rounding
+    order: rounding differences between the two recurrences roughly double
+    per iteration (2e-9 relative at iteration 4, 5e-8 at 10, at s = 1000),
+    and the totals end up 10-30 % apart.  Parity is therefore checked where it
+    is defined: the first 5 residual-history entries to 1e-6 (any wrong
+    operator or coefficient shows at iteration 1 at O(1)), reaching tol_eff
+    (s <= 100) or the iteration cap (s = 1000, where neither side gets there),
+    and the solution's error against the direct solve (within 10x of the
+    oracle's own)."""
+    beam, M, K = setup_beam(G, 500, "literal")
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    P = G.spai_build(A)
+    Ao = O.shifted_csr(beam, AL, BE, s)
+    F = W.loads(beam.n)[:, 0]
+    xd = O.chol_solve(Ao, F)[:, 0]
+    phi = np.linalg.norm(F - O.spmv(Ao, xd)) / np.linalg.norm(F)
+    tol = max(1e-10, 10 * phi)
+    cap = 30000 if s <= 100 else 4000
+    res = G.pcg_solve(A, P, torch.from_numpy(F).cuda(), G.options(tol=tol, maxit=cap),
+                      want_hist=True)
+    torch.cuda.synchronize()
+    x_o, it_o, st_o, h_o = O.pcg(Ao, F, [O.spai(Ao)], tol=tol, maxit=cap)
+    h = res["res_hist"][0].cpu().numpy()
+    k = min(5, it_o, int(res["iters"][0]))
+    it = int(res["iters"][0])
+    x = res["X"].cpu().numpy()
+    err = np.linalg.norm(x - xd) / np.linalg.norm(xd)
+    err_o = np.linalg.norm(x_o - xd) / np.linalg.norm(xd)
+    print("\nliteral s=%g phi=%.2e tol_eff=%.2e iters gpu %d oracle %d, |x-xd|/|xd| gpu %.2e oracle %.2e"
+          % (s, phi, tol, it, it_o, err, err_o))
+    assert np.allclose(h[:k + 1], h_o[:k + 1], rtol=1e-6, atol=0)
+    if s <= 100:
+        assert int(res["status"][0]) == G.OK and st_o == O.OK
+        assert err <= max(10 * err_o, 1e-9)
+    else:
+        assert int(res["status"][0]) == G.E_MAXIT and st_o == O.EMAXIT
+
+
 @pytest.mark.parametrize("kind", [1, 3])
 @pytest.mark.parametrize("s", [0.1, 100.0])
 def test_pcg_forced_kernel_variants(G, kind, s):
