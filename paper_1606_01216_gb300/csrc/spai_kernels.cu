@@ -375,13 +375,13 @@ spai_mr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
         double am = (q >= W && q <= W + 6) ? a[q][W] * alpha0 : 0.0;
         r[q] = b[q] - am;
     }
-    const double thr = tol * sqrt(bb);
+    // stop when ||r|| <= tol ||b||, tested on squares: no square root per step
+    const double thr2 = (tol * tol) * bb;
     double rn2 = 0.0;
 #pragma unroll
     for (int q = 0; q < NR; ++q) rn2 = fma(r[q], r[q], rn2);
-    double rn = sqrt(rn2);
     int k = 0;
-    while (rn > thr && k < kmax) {
+    while (rn2 > thr2 && k < kmax) {
         // d = r restricted to the pattern: column c's unknown sits on local row c+3
         double d[NC];
 #pragma unroll
@@ -400,7 +400,7 @@ spai_mr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
             rw = fma(r[q], w[q], rw);
         }
         if (ww == 0.0) break;                          // r vanishes on the pattern
-        const double al = rw / ww;
+        const double al = rw * lean::rcp_signed(ww);   // step length (r, w) / (w, w)
 #pragma unroll
         for (int c = 0; c < NC; ++c) m[c] = fma(al, d[c], m[c]);
         rn2 = 0.0;
@@ -409,11 +409,10 @@ spai_mr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
             r[q] = fma(-al, w[q], r[q]);
             rn2 = fma(r[q], r[q], rn2);
         }
-        rn = sqrt(rn2);
         ++k;
     }
     steps[j] = k;
-    if (colres) colres[j] = rn;
+    if (colres) colres[j] = sqrt(rn2);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
         if (!in[c]) m[c] = 0.0;
