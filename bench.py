@@ -168,7 +168,7 @@ def gpu_arm(args, world, rank, local):
         for s in SHIFTS:
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
             P = G.spai_build(A)
-            cnt += 3                      # assemble, spai_qr, symmetrize
+            cnt += 4                      # assemble, spai_qr_beam + spai_qr (general plan), symmetrize
             if record:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)

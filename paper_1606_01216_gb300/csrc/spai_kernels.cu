@@ -311,32 +311,49 @@ __device__ __forceinline__ void qr_column(int64_t n, int64_t j, const double *__
     store_column<W>(n, j, m, F);
 }
 
-// One column per thread.  For the full band pattern (W = 3) the warps take
-// columns of one parity each (warp w: j = 2 (32 (w / 2) + lane) + w mod 2),
-// so that on a beam matrix (device flags zA, zAold) the interior columns run
-// the beam plan without divergence; all other columns run the general plan.
+// Two launches per SPAI call, each with the registers of one plan only (the
+// general plan needs ~230, the beam plan ~155-170; one kernel holding both
+// runs at the larger count and fewer warps per SM):
+//  * spai_qr_beam_kernel: on a matrix carrying the beam zero-structure flag
+//    (and A_old too, for an update), the interior columns 3 <= j <= n - 9 of
+//    an even-n band-7 pattern, with warps taking columns of one parity
+//    (warp w: j = 2 (32 (w / 2) + lane) + w mod 2) so the two beam plans
+//    never diverge; it returns at once on other matrices.
+//  * spai_qr_kernel: every column the beam kernel does not take, with the
+//    general plan.
+__device__ __forceinline__ bool beam_interior(int64_t n, int64_t j, int upd, const int32_t *zA,
+                                              const int32_t *zAold) {
+    return zA && *zA != 0 && (!upd || (zAold && *zAold != 0)) && (n % 2 == 0) && j >= 3 &&
+           j <= n - 9;
+}
+
+template <int UPD>
+__global__ void __launch_bounds__(kThreadsSpai)
+spai_qr_beam_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
+                    double *__restrict__ F, double *__restrict__ colres, int32_t *rank_flag,
+                    const int32_t *__restrict__ zA, const int32_t *__restrict__ zAold) {
+    constexpr int W = 3;
+    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t w = gt >> 5;
+    const int64_t j = 2 * ((w >> 1) * 32 + (gt & 31)) + (w & 1);
+    if (j >= n || !beam_interior(n, j, UPD, zA, zAold)) return;
+    if (j & 1) qr_column<W, 1, UPD ? 2 : 0>(n, j, A, Aold, F, colres, rank_flag);
+    else qr_column<W, 0, UPD ? 2 : 0>(n, j, A, Aold, F, colres, rank_flag);
+}
+
 template <int W, int UPD>
 __global__ void __launch_bounds__(kThreadsSpai)
 spai_qr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
                double *__restrict__ F, double *__restrict__ colres, int32_t *rank_flag,
                const int32_t *__restrict__ zA, const int32_t *__restrict__ zAold) {
-    const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    int64_t j = gt;
-    if (W == 3) {
-        const int64_t w = gt >> 5;
-        j = 2 * ((w >> 1) * 32 + (gt & 31)) + (w & 1);
+    // grid-stride over one resident wave: on a beam matrix nearly every
+    // column is skipped, and one wave of blocks skips them far sooner than
+    // many waves of short-lived blocks would
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += stride) {
+        if (W == 3 && beam_interior(n, j, UPD, zA, zAold)) continue;   // the beam kernel's column
+        qr_column<W, -1, UPD ? 1 : 0>(n, j, A, Aold, F, colres, rank_flag);
     }
-    if (j >= n) return;
-    if (W == 3) {
-        const bool beam = zA && *zA != 0 && (!UPD || (zAold && *zAold != 0)) && (n % 2 == 0) &&
-                          j >= 3 && j <= n - 9;
-        if (beam) {
-            if (j & 1) qr_column<W, 1, UPD ? 2 : 0>(n, j, A, Aold, F, colres, rank_flag);
-            else qr_column<W, 0, UPD ? 2 : 0>(n, j, A, Aold, F, colres, rank_flag);
-            return;
-        }
-    }
-    qr_column<W, -1, UPD ? 1 : 0>(n, j, A, Aold, F, colres, rank_flag);
 }
 
 template <int W>
@@ -422,13 +439,39 @@ spai_mr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
 template <int W>
 cudaError_t qr_w(int64_t n, const double *A, const double *Aold, double *F, double *colres,
                  int32_t *flag, const int32_t *zA, const int32_t *zAold, cudaStream_t s) {
-    // W == 3 maps warps to columns of one parity: 64 columns per warp pair
-    const int64_t threads = W == 3 ? 64 * ((n + 63) / 64) : n;
-    const int64_t blocks = (threads + kThreadsSpai - 1) / kThreadsSpai;
-    if (Aold)
-        spai_qr_kernel<W, 1><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, zA, zAold);
+    if (W == 3 && zA) {
+        // parity-mapped warps: 64 columns per warp pair
+        const int64_t blocks_b = (64 * ((n + 63) / 64) + kThreadsSpai - 1) / kThreadsSpai;
+        if (Aold)
+            spai_qr_beam_kernel<1><<<(unsigned)blocks_b, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, zA, zAold);
+        else
+            spai_qr_beam_kernel<0><<<(unsigned)blocks_b, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, zA, zAold);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    // one resident wave of the general kernel (cached per device)
+    static int wave_dev[2] = {-1, -1}, wave_blocks[2] = {0, 0};
+    const int u = Aold ? 1 : 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (wave_dev[u] != dev) {
+        int sms = 0, per_sm = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = u ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spai_qr_kernel<W, 1>, kThreadsSpai, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, spai_qr_kernel<W, 0>, kThreadsSpai, 0);
+        if (e != cudaSuccess) return e;
+        wave_blocks[u] = sms * (per_sm > 0 ? per_sm : 1);
+        wave_dev[u] = dev;
+    }
+    int64_t blocks = (n + kThreadsSpai - 1) / kThreadsSpai;
+    if (blocks > wave_blocks[u]) blocks = wave_blocks[u];
+    const int32_t *za = W == 3 ? zA : nullptr;
+    if (u)
+        spai_qr_kernel<W, 1><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, za, zAold);
     else
-        spai_qr_kernel<W, 0><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, zA, zAold);
+        spai_qr_kernel<W, 0><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, za, zAold);
     return cudaGetLastError();
 }
 
