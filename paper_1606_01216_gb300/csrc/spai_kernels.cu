@@ -122,19 +122,33 @@ __host__ __device__ constexpr bool beam_zero(int W, int par, int r, int c) {
     return (g & 1) == 0 ? (d == -3 || d == 1) : (d == 3 || d == -1);
 }
 
-__host__ __device__ constexpr QrPlan make_plan(int W, int PAR, int RHS) {
+// Can local entry (r, c) of column j's block be nonzero?  E < 0: any column
+// away from the last rows; E >= 0: the column j = n - 1 - E of a beam matrix
+// (PAR >= 0), whose block reaches past the last row: there rows g >= n are
+// zero, columns k >= n are unit columns (only the diagonal entry), and the
+// last row pair (g = n - 2, n - 1) carries no beam zeros.
+__host__ __device__ constexpr bool plan_nz(int W, int PAR, int E, int r, int c) {
+    if (E >= 0) {
+        if (c >= E + W + 1) return r == c + 3;     // k = n - 1 - E - W + c >= n
+        if (r >= E + W + 4) return false;          // g = n - 1 - E - W - 3 + r >= n
+        if (r >= E + W + 2) return true;           // g in the last row pair
+    }
+    return PAR < 0 || !beam_zero(W, PAR, r, c);
+}
+
+__host__ __device__ constexpr QrPlan make_plan(int W, int PAR, int RHS, int E = -1) {
     QrPlan P{};
     const int NC = 2 * W + 1;
     unsigned a[7] = {0, 0, 0, 0, 0, 0, 0};
     unsigned b = 0;
     for (int c = 0; c < NC; ++c)
         for (int r = c; r < c + 7; ++r)
-            if (PAR < 0 || !beam_zero(W, PAR, r, c)) a[c] |= 1u << r;
+            if (plan_nz(W, PAR, E, r, c)) a[c] |= 1u << r;
     if (RHS == 0) {
         b = 1u << (W + 3);
     } else {
         for (int r = W; r <= W + 6; ++r)   // b_r = A_old(g, j): local column W of the block
-            if (RHS == 1 || !beam_zero(W, PAR, r, W)) b |= 1u << r;
+            if (RHS == 1 || plan_nz(W, PAR, E, r, W)) b |= 1u << r;
     }
     for (int C = 0; C < NC; ++C) {
         for (int c = 0; c < NC; ++c) P.a[C][c] = (unsigned short)a[c];
@@ -152,11 +166,11 @@ __host__ __device__ constexpr QrPlan make_plan(int W, int PAR, int RHS) {
 // Gather the block entries the plan says can be nonzero (the others are 0);
 // columns outside [0, n) become unit columns on local row c+3 (general plan
 // only).
-template <int W, int PAR>
+template <int W, int PAR, int E>
 __device__ __forceinline__ void gather_block_p(int64_t n, int64_t j, const double *__restrict__ A,
                                                double (&a)[2 * W + 7][2 * W + 1]) {
     constexpr int NC = 2 * W + 1;
-    constexpr QrPlan P = make_plan(W, PAR, 0);
+    constexpr QrPlan P = make_plan(W, PAR, 0, E);
 #pragma unroll
     for (int c = 0; c < NC; ++c)
 #pragma unroll
@@ -192,12 +206,12 @@ __device__ __forceinline__ void gather_block_p(int64_t n, int64_t j, const doubl
 // values are integer bit operations, and
 // the rank test tracks the largest and smallest ||x|| by their bit patterns
 // (non-negative doubles order like their bits).
-template <int W, int PAR, int RHS, int C>
+template <int W, int PAR, int RHS, int E, int C>
 __device__ __forceinline__ void qr_step(double (&a)[2 * W + 7][2 * W + 1], double (&b)[2 * W + 7],
                                         double (&rinv)[2 * W + 1], unsigned long long &rmax,
                                         unsigned long long &rmin) {
     constexpr int NC = 2 * W + 1;
-    constexpr QrPlan P = make_plan(W, PAR, RHS);
+    constexpr QrPlan P = make_plan(W, PAR, RHS, E);
     constexpr unsigned V = (P.a[C][C] & (0x7Fu << C)) | (1u << C);   // reflector support
     double sigma = 0.0;
 #pragma unroll
@@ -250,20 +264,20 @@ __device__ __forceinline__ void qr_step(double (&a)[2 * W + 7][2 * W + 1], doubl
     rmin = nb < rmin ? nb : rmin;
 }
 
-template <int W, int PAR, int RHS, int... Cs>
+template <int W, int PAR, int RHS, int E, int... Cs>
 __device__ __forceinline__ void qr_all(std::integer_sequence<int, Cs...>,
                                        double (&a)[2 * W + 7][2 * W + 1], double (&b)[2 * W + 7],
                                        double (&rinv)[2 * W + 1], unsigned long long &rmax,
                                        unsigned long long &rmin) {
-    (qr_step<W, PAR, RHS, Cs>(a, b, rinv, rmax, rmin), ...);
+    (qr_step<W, PAR, RHS, E, Cs>(a, b, rinv, rmax, rmin), ...);
 }
 
 // Right-hand side entries the plan says can be nonzero (RHS 1/2: A_old(I_j, j))
-template <int W, int PAR, int RHS>
+template <int W, int PAR, int RHS, int E>
 __device__ __forceinline__ void gather_rhs_p(int64_t n, int64_t j, const double *__restrict__ Aold,
                                              double (&b)[2 * W + 7]) {
     constexpr int NR = 2 * W + 7;
-    constexpr QrPlan P = make_plan(W, PAR, RHS);
+    constexpr QrPlan P = make_plan(W, PAR, RHS, E);
 #pragma unroll
     for (int r = 0; r < NR; ++r) b[r] = 0.0;
     if constexpr (RHS == 0) {
@@ -277,8 +291,8 @@ __device__ __forceinline__ void gather_rhs_p(int64_t n, int64_t j, const double 
     }
 }
 
-// Solve column j's least-squares problem with the plan (PAR, RHS) and store it.
-template <int W, int PAR, int RHS>
+// Solve column j's least-squares problem with the plan (PAR, RHS, E) and store it.
+template <int W, int PAR, int RHS, int E = -1>
 __device__ __forceinline__ void qr_column(int64_t n, int64_t j, const double *__restrict__ A,
                                           const double *__restrict__ Aold, double *__restrict__ F,
                                           double *__restrict__ colres, int32_t *rank_flag) {
@@ -286,11 +300,11 @@ __device__ __forceinline__ void qr_column(int64_t n, int64_t j, const double *__
     constexpr int NR = NC + 6;
     double a[NR][NC];
     double b[NR];
-    gather_block_p<W, PAR>(n, j, A, a);
-    gather_rhs_p<W, PAR, RHS>(n, j, Aold, b);
+    gather_block_p<W, PAR, E>(n, j, A, a);
+    gather_rhs_p<W, PAR, RHS, E>(n, j, Aold, b);
     double rinv[NC];
     unsigned long long rmax = 0ull, rmin = ~0ull;      // bit patterns of ||x|| >= 0
-    qr_all<W, PAR, RHS>(std::make_integer_sequence<int, NC>{}, a, b, rinv, rmax, rmin);
+    qr_all<W, PAR, RHS, E>(std::make_integer_sequence<int, NC>{}, a, b, rinv, rmax, rmin);
     double m[NC];
     const bool rank_ok = rmin != 0ull && lean::from_bits(rmin) >= 1e-14 * lean::from_bits(rmax);
 #pragma unroll
@@ -312,19 +326,28 @@ __device__ __forceinline__ void qr_column(int64_t n, int64_t j, const double *__
 }
 
 // Two launches per SPAI call, each with the registers of one plan only (the
-// general plan needs ~230, the beam plan ~155-170; one kernel holding both
+// general plan needs ~230, the beam plans ~155-170; one kernel holding both
 // runs at the larger count and fewer warps per SM):
-//  * spai_qr_beam_kernel: on a matrix carrying the beam zero-structure flag
-//    (and A_old too, for an update), the interior columns 3 <= j <= n - 9 of
-//    an even-n band-7 pattern, with warps taking columns of one parity
-//    (warp w: j = 2 (32 (w / 2) + lane) + w mod 2) so the two beam plans
-//    never diverge; it returns at once on other matrices.
-//  * spai_qr_kernel: every column the beam kernel does not take, with the
-//    general plan.
-__device__ __forceinline__ bool beam_interior(int64_t n, int64_t j, int upd, const int32_t *zA,
-                                              const int32_t *zAold) {
-    return zA && *zA != 0 && (!upd || (zAold && *zAold != 0)) && (n % 2 == 0) && j >= 3 &&
-           j <= n - 9;
+//  * spai_qr_beam_kernel: every column of a matrix carrying the beam
+//    zero-structure flag (and A_old too, for an update), n even and >= 16.
+//    Warps take columns of one parity (the two interior beam plans never
+//    diverge in a warp), and warp pairs run from the last columns down, so
+//    the warps holding the last 8 columns, each with a plan of its own, start
+//    first and their divergence stays off the critical path.  The first
+//    columns use the interior plan: their out-of-range rows and unit columns
+//    agree with it.  Returns at once on other matrices.
+//  * spai_qr_kernel: the general plan, for matrices without the flag; returns
+//    at once on flagged ones.
+__device__ __forceinline__ bool beam_matrix(int64_t n, int upd, const int32_t *zA,
+                                            const int32_t *zAold) {
+    return zA && *zA != 0 && (!upd || (zAold && *zAold != 0)) && (n % 2 == 0) && n >= 16;
+}
+
+template <int RHS, int PAR, int E>
+__device__ __forceinline__ void end_column(int64_t n, int64_t j, const double *__restrict__ A,
+                                           const double *__restrict__ Aold, double *__restrict__ F,
+                                           double *__restrict__ colres, int32_t *rank_flag) {
+    qr_column<3, PAR, RHS, E>(n, j, A, Aold, F, colres, rank_flag);
 }
 
 template <int UPD>
@@ -332,13 +355,28 @@ __global__ void __launch_bounds__(kThreadsSpai)
 spai_qr_beam_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
                     double *__restrict__ F, double *__restrict__ colres, int32_t *rank_flag,
                     const int32_t *__restrict__ zA, const int32_t *__restrict__ zAold) {
-    constexpr int W = 3;
+    constexpr int W = 3, RHS = UPD ? 2 : 0;
+    if (!beam_matrix(n, UPD, zA, zAold)) return;
     const int64_t gt = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t w = gt >> 5;
-    const int64_t j = 2 * ((w >> 1) * 32 + (gt & 31)) + (w & 1);
-    if (j >= n || !beam_interior(n, j, UPD, zA, zAold)) return;
-    if (j & 1) qr_column<W, 1, UPD ? 2 : 0>(n, j, A, Aold, F, colres, rank_flag);
-    else qr_column<W, 0, UPD ? 2 : 0>(n, j, A, Aold, F, colres, rank_flag);
+    const int64_t pair = (n + 63) / 64 - 1 - (w >> 1);   // 64 columns per warp pair
+    if (pair < 0) return;
+    const int64_t j = 2 * (pair * 32 + (gt & 31)) + (w & 1);
+    if (j >= n) return;
+    // n is even: j = n - 1 - e has parity (e + 1) mod 2
+    switch (n - 1 - j) {
+        case 0: end_column<RHS, 1, 0>(n, j, A, Aold, F, colres, rank_flag); return;
+        case 1: end_column<RHS, 0, 1>(n, j, A, Aold, F, colres, rank_flag); return;
+        case 2: end_column<RHS, 1, 2>(n, j, A, Aold, F, colres, rank_flag); return;
+        case 3: end_column<RHS, 0, 3>(n, j, A, Aold, F, colres, rank_flag); return;
+        case 4: end_column<RHS, 1, 4>(n, j, A, Aold, F, colres, rank_flag); return;
+        case 5: end_column<RHS, 0, 5>(n, j, A, Aold, F, colres, rank_flag); return;
+        case 6: end_column<RHS, 1, 6>(n, j, A, Aold, F, colres, rank_flag); return;
+        case 7: end_column<RHS, 0, 7>(n, j, A, Aold, F, colres, rank_flag); return;
+        default: break;
+    }
+    if (j & 1) qr_column<W, 1, RHS>(n, j, A, Aold, F, colres, rank_flag);
+    else qr_column<W, 0, RHS>(n, j, A, Aold, F, colres, rank_flag);
 }
 
 template <int W, int UPD>
@@ -346,14 +384,12 @@ __global__ void __launch_bounds__(kThreadsSpai)
 spai_qr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
                double *__restrict__ F, double *__restrict__ colres, int32_t *rank_flag,
                const int32_t *__restrict__ zA, const int32_t *__restrict__ zAold) {
-    // grid-stride over one resident wave: on a beam matrix nearly every
-    // column is skipped, and one wave of blocks skips them far sooner than
-    // many waves of short-lived blocks would
+    if (W == 3 && beam_matrix(n, UPD, zA, zAold)) return;   // the beam kernel's matrix
+    // grid-stride over one resident wave, so that on a flagged matrix the
+    // launch is one wave of blocks that return at once
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += stride) {
-        if (W == 3 && beam_interior(n, j, UPD, zA, zAold)) continue;   // the beam kernel's column
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += stride)
         qr_column<W, -1, UPD ? 1 : 0>(n, j, A, Aold, F, colres, rank_flag);
-    }
 }
 
 template <int W>
@@ -468,7 +504,7 @@ cudaError_t qr_w(int64_t n, const double *A, const double *Aold, double *F, doub
     int64_t blocks = (n + kThreadsSpai - 1) / kThreadsSpai;
     if (blocks > wave_blocks[u]) blocks = wave_blocks[u];
     const int32_t *za = W == 3 ? zA : nullptr;
-    if (u)
+    if (Aold)
         spai_qr_kernel<W, 1><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, za, zAold);
     else
         spai_qr_kernel<W, 0><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, F, colres, flag, za, zAold);

@@ -166,6 +166,26 @@ def test_spai_build_qr(G, n_e, s):
     assert np.allclose(colres.cpu().numpy(), colres_o, rtol=1e-8, atol=1e-14)
 
 
+@pytest.mark.parametrize("n_e", [7, 8, 9, 34, 35, 66])
+def test_spai_beam_boundary_columns(G, n_e):
+    # The beam-plan kernel takes every column of a flagged beam with n >= 16
+    # (n = 14 stays on the general plan); its last 8 columns have plans of
+    # their own (rows past n, unit columns, the last row pair without beam
+    # zeros).  n = 68, 70: those columns straddle two 64-column warp pairs.
+    beam, M, K = setup_beam(G, n_e)
+    A0 = G.assemble_shifted(M, K, AL, BE, 2.0)
+    A1 = G.assemble_shifted(M, K, AL, BE, 7.0)
+    P0 = G.spai_build(A0)
+    P1 = G.spai_update(P0, A0, A1)
+    Ao0, Ao1 = O.shifted_csr(beam, AL, BE, 2.0), O.shifted_csr(beam, AL, BE, 7.0)
+    Po, colres_o = O.spai(Ao0, want_colres=True)
+    assert column_errors(G.precond_factor(P0, 0).cpu().numpy(), Po).max() <= 1e-10
+    assert np.allclose(G.precond_status(P0)[1].cpu().numpy(), colres_o, rtol=1e-8, atol=1e-14)
+    Qo = O.spai(Ao1, A_old=Ao0)
+    assert column_errors(G.precond_factor(P1, 1).cpu().numpy(), Qo).max() <= 1e-10
+    assert G.precond_status(P1)[2] == G.OK
+
+
 @pytest.mark.parametrize("hbw", [0, 1, 2])
 def test_spai_narrow_patterns(G, hbw):
     beam, M, K = setup_beam(G, 600)
