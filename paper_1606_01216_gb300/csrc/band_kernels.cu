@@ -11,6 +11,7 @@
 // kernels sit near the FP64/HBM ridge (~0.18 flop/B).  Every kernel below
 // keeps its FP64 operation count at the minimum the formula needs.
 #include "airga_internal.cuh"
+#include "ieee_conv.cuh"
 
 namespace airga {
 namespace {
@@ -163,17 +164,26 @@ __global__ void band_apply_kernel(int64_t n, const double *__restrict__ band,
         y[i] = transpose ? band_row_t(band, n, i, x) : band_row(band, n, i, x);
 }
 
-// Psym(i, i+d) = 1/2 (P(i, i+d) + P(i+d, i)); P(i+d, i) = band[(3-d)*n + i+d]
+// Psym(i, i+d) = 1/2 (P(i, i+d) + P(i+d, i)); P(i+d, i) = band[(3-d)*n + i+d].
+// Thread i forms each of its pairs d = 1..3 once and writes both mirrored
+// entries (i, i+d) and (i+d, i); the diagonal is copied.  One FP64 add per
+// pair and an exact integer halving (ieee::half_of, = x / 2 bit for bit) —
+// on GB300 the FP64 pipe, not HBM, bound the one-entry-per-thread form.
 __global__ void symmetrize_kernel(int64_t n, const double *__restrict__ P,
                                   double *__restrict__ S) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
+        S[kHalf * n + i] = P[kHalf * n + i];
 #pragma unroll
-        for (int d = -kHalf; d <= kHalf; ++d) {
-            int64_t c = i + d;
-            double v = 0.0;
-            if (c >= 0 && c < n) v = 0.5 * (P[(d + kHalf) * n + i] + P[(kHalf - d) * n + c]);
-            S[(d + kHalf) * n + i] = v;
+        for (int d = 1; d <= kHalf; ++d) {
+            if (i + d < n) {
+                const double v = ieee::half_of(P[(kHalf + d) * n + i] + P[(kHalf - d) * n + i + d]);
+                S[(kHalf + d) * n + i] = v;             // (i, i+d)
+                S[(kHalf - d) * n + i + d] = v;         // (i+d, i)
+            } else {
+                S[(kHalf + d) * n + i] = 0.0;           // column outside the matrix
+            }
+            if (i < d) S[(kHalf - d) * n + i] = 0.0;    // column i-d outside the matrix
         }
     }
 }

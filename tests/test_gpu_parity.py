@@ -317,6 +317,30 @@ def test_precond_apply_single_and_chain(G):
             assert np.linalg.norm(z - ref) <= 1e-10 * np.linalg.norm(ref)
 
 
+@pytest.mark.parametrize("n_e", [700, 9])
+def test_psym_band_bit_exact(G, n_e):
+    # P_sym = (P + P^T) / 2 (Sec. 3.1, symmetric preconditioner for CG),
+    # bit for bit.  r = sum of e_j over j = k mod 7 meets each row's 7-entry
+    # window exactly once, so z = P_sym r returns entry (i, j) of every row
+    # exactly (the other products are with 0); seven applies read the band.
+    beam, M, K = setup_beam(G, n_e)
+    A = G.assemble_shifted(M, K, AL, BE, 3.0)
+    P = G.spai_build(A)
+    n = beam.n
+    r_, c_, v_ = factor_dense_cols(G.precond_factor(P, 0).cpu().numpy(), n)
+    Pd = np.zeros((n, n)); Pd[r_, c_] = v_
+    S = 0.5 * (Pd + Pd.T)
+    rows = np.arange(n)
+    for k in range(7):
+        rv = (rows % 7 == k).astype(np.float64)
+        z = G.precond_apply(P, torch.from_numpy(rv).cuda(), symmetrize=True).cpu().numpy()
+        j = rows - ((rows - k) % 7)                   # the column j = k mod 7 in i-3..i+3
+        j = np.where(rows - j > 3, j + 7, j)
+        ok = (j >= 0) & (j < n)
+        expect = np.where(ok, S[rows, np.clip(j, 0, n - 1)], 0.0)
+        assert np.array_equal(z, expect), k
+
+
 # ---------------------------------------------------------------------------
 # PCG
 # ---------------------------------------------------------------------------
@@ -498,6 +522,25 @@ def test_full_size_beam(G, s):
     assert int(res["status"][0]) == G.OK
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
     true = np.linalg.norm(F - O.spmv(Ao, x)) / np.linalg.norm(F)
+    assert true <= 2e-10
+
+
+def test_full_size_update(G):
+    # Sec. 3.2 update Q for the first shift step of the measured shift list,
+    # every column against the oracle's exact LS, then PCG with the chain
+    s0, s1 = 0.1, 0.5179474679231212
+    beam, M, K = setup_beam(G, 500_000)
+    A0 = G.assemble_shifted(M, K, AL, BE, s0)
+    A1 = G.assemble_shifted(M, K, AL, BE, s1)
+    P1 = G.spai_update(G.spai_build(A0), A0, A1)
+    Ao0, Ao1 = O.shifted_csr(beam, AL, BE, s0), O.shifted_csr(beam, AL, BE, s1)
+    Qo = O.spai(Ao1, A_old=Ao0)
+    assert column_errors(G.precond_factor(P1, 1).cpu().numpy(), Qo).max() <= 1e-10
+    F = W.loads(beam.n)[:, 0]
+    res = run_pcg(G, A1, P1, F)
+    x = res["X"].cpu().numpy()
+    assert int(res["status"][0]) == G.OK
+    true = np.linalg.norm(F - O.spmv(Ao1, x)) / np.linalg.norm(F)
     assert true <= 2e-10
 
 
