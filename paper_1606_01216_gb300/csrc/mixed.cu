@@ -2,14 +2,17 @@
 // refinement (airga_pcg_solve_mixed).
 //
 // Per right-hand side f, with x = 0:
-//   k = 0, 1, ...:  r = f - A x            FP64 (resid_* kernels, true residual)
-//                   stop if ||r|| <= tol ||f||
-//                   A d = r by FP32 PCG   (pcg32_pair_kernel: FP32 bands of A
-//                                          and P_sym, FP32 vectors)
-//                   x = x + d             FP64 (fused into the inner kernel's exit)
-// Every kernel reads a per-column state block in device memory; once the
-// column has converged (or failed) the remaining enqueued kernels return at
-// once, so the whole refinement is enqueued without host synchronisation.
+//   k = 0, 1, ...:  r = f - A x            FP64 (true residual)
+//                   stop if ||r|| <= tol ||f||  (or after max_outer steps)
+//                   A d = r by FP32 PCG   (FP32 bands of A and P_sym, FP32
+//                                          vectors, d_0 = 0)
+//                   x = x + d             FP64
+// One persistent launch per column runs the whole loop: the FP64 residual of
+// a CTA's rows (and of its r-halo rows) goes straight into its FP32 residual
+// window, the convergence test is a grid reduction, and the update of x is
+// followed by a grid barrier so the next residual sees the neighbours' rows.
+// A column therefore costs one launch however many steps it takes, and none
+// is spent on steps that are never needed.
 //
 // Why on GB300: an FP64 FMA issues at 2/clk/SM, an FP32 FMA at 128/clk/SM.
 // The inner iterations — the bulk of the work — leave the FP64 pipe for the
@@ -19,9 +22,10 @@
 // the reduction totals of the inner CG (per-thread FP32 partials are summed
 // in FP64).
 //
-// The inner kernel is the row-pair persistent PCG of pcg_pair.cu with float
+// The inner solve is the row-pair persistent PCG of pcg_pair.cu with float
 // data: same ownership, halo and barrier scheme, r halo recomputed beside
 // the x/r sweep, warp-0 scalar updates.
+#include "fp64_lean.cuh"
 #include "pcg_common.cuh"
 
 namespace airga {
@@ -31,15 +35,6 @@ using namespace pcgdev;
 
 constexpr int kThreads = 512;
 constexpr int HR = 8, HP = 12, HZ = 4, kHaloPairs = 8;
-
-struct MixState {
-    double nf2;      // ||f||^2
-    double rr;       // ||r||^2 of the latest FP64 residual
-    int done;        // 1: converged or failed; later kernels return at once
-    int outer;       // refinement steps taken
-    int inner;       // FP32 CG iterations, all steps
-    int status;
-};
 
 // ---------------------------------------------------------------------------
 // FP64 -> FP32 copies
@@ -51,97 +46,8 @@ __global__ void to_f32_kernel(int64_t total, const double *__restrict__ src,
         dst[i] = (float)src[i];
 }
 
-__global__ void state_init_kernel(MixState *st) {
-    st->nf2 = 0.0;
-    st->rr = 0.0;
-    st->done = 0;
-    st->outer = 0;
-    st->inner = 0;
-    st->status = AIRGA_E_MAXIT;
-}
-
-__device__ __forceinline__ double warp_sum_d(double v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
-
 // ---------------------------------------------------------------------------
-// FP64 residual r = f - A x, r32 = (float) r, per-block ||r||^2
-// ---------------------------------------------------------------------------
-__global__ void resid_partial_kernel(int64_t n, const double *__restrict__ A,
-                                     const double *__restrict__ x,
-                                     const double *__restrict__ f, float *__restrict__ r32,
-                                     double *__restrict__ partial, const MixState *st) {
-    if (st->done) return;
-    __shared__ double sh[32];
-    const int64_t per = (n + gridDim.x - 1) / gridDim.x;
-    const int64_t lo = blockIdx.x * per, hi = lo + per < n ? lo + per : n;
-    double rr = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
-        double ax = 0.0;
-#pragma unroll
-        for (int d = 0; d < kBand; ++d) {
-            const int64_t c = i + d - kHalf;
-            if (c >= 0 && c < n) ax = fma(A[(int64_t)d * n + i], x[c], ax);
-        }
-        const double r = f[i] - ax;
-        r32[i] = (float)r;
-        rr = fma(r, r, rr);
-    }
-    rr = warp_sum_d(rr);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = rr;
-    __syncthreads();
-    if (w == 0) {
-        double t = l < (int)(blockDim.x >> 5) ? sh[l] : 0.0;
-        t = warp_sum_d(t);
-        if (l == 0) partial[blockIdx.x] = t;
-    }
-}
-
-// Sum the partials; decide convergence of the column.  `k` is the number of
-// refinement steps done so far; after the last allowed step an unconverged
-// column is closed with AIRGA_E_MAXIT.
-__global__ void resid_final_kernel(int nblk, const double *__restrict__ partial, MixState *st,
-                                   double tol, int k, int max_outer, double *relres) {
-    if (st->done) return;
-    __shared__ double sh[32];
-    double t = 0.0;
-    for (int b = threadIdx.x; b < nblk; b += blockDim.x) t += partial[b];
-    t = warp_sum_d(t);
-    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    if (l == 0) sh[w] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double rr = 0.0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) rr += sh[q];
-        if (k == 0) st->nf2 = rr;                      // x = 0: r = f
-        st->rr = rr;
-        const double nf2 = st->nf2;
-        const bool conv = rr <= tol * tol * nf2;
-        *relres = nf2 > 0.0 ? sqrt(rr / nf2) : 0.0;
-        if (conv) {
-            st->done = 1;
-            st->status = AIRGA_OK;
-            st->outer = k;
-        } else if (k >= max_outer) {
-            st->done = 1;
-            st->status = AIRGA_E_MAXIT;
-            st->outer = k;
-        }
-    }
-}
-
-__global__ void state_out_kernel(const MixState *st, int32_t *outer, int32_t *inner,
-                                 int32_t *status) {
-    *outer = st->outer;
-    *inner = st->inner;
-    *status = st->status;
-}
-
-// ---------------------------------------------------------------------------
-// FP32 row-pair PCG (inner solve of A d = r32, d_0 = 0)
+// The refinement loop of one column (FP64 residual, FP32 row-pair PCG)
 // ---------------------------------------------------------------------------
 struct Args32 {
     int n;
@@ -149,17 +55,31 @@ struct Args32 {
     const float *Apk;     // FP32 packed beam nonzeros of A, or null
     const int32_t *pairz; // beam structure flag of A (device), or null
     const float *M;       // FP32 band-7 preconditioner (or null = identity)
-    const float *b;       // r32
-    double *x64;          // refinement iterate: x64 += d at exit
+    const double *A64;    // FP64 band-7 of A (outer residual)
+    const double *f;      // right-hand side column
+    double *x64;          // refinement iterate (zeroed by the kernel)
     float *pbuf;
     double *partials;
     unsigned *bar;
     int *abort_flag;
-    double tol;           // inner relative tolerance
-    int maxit;
+    double tol;           // outer (FP64) relative tolerance
+    double inner_tol;     // inner relative tolerance
+    int maxit;            // inner iterations per refinement step
+    int max_outer;        // refinement steps
     long long timeout_ns;
-    MixState *st;
+    double *relres;       // out: FP64 relative residual at exit
+    int32_t *outer_iters; // out: refinement steps taken
+    int32_t *inner_iters; // out: FP32 CG iterations, all steps
+    int32_t *status;      // out
 };
+
+// Warm L2 with the 8-byte rows of `count` FP32 band arrays at pair i (no
+// registers held; issued before a barrier so the next phase's first loads
+// find their lines in L2).
+__device__ __forceinline__ void prefetch_pair_f(const float *band, int n, int i, int count) {
+    for (int k = 0; k < count; ++k)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(band + (long long)k * n + i));
+}
 
 __device__ __forceinline__ void load_band_pair_f(const float *__restrict__ band, int n, int i,
                                                  float2 (&a)[kBand]) {
@@ -214,13 +134,11 @@ __device__ __forceinline__ float2 pair_packed_f(const float *__restrict__ pk,
 
 template <int MODE>   // 0: identity, 1: one band preconditioner
 __global__ void __launch_bounds__(kThreads, 1)
-pcg32_pair_kernel(Args32 a, int R) {
+mixed_pair_kernel(Args32 a, int R) {
     extern __shared__ __align__(16) double smem64[];
     __shared__ double tot[8];
     __shared__ int s_flag;
     __shared__ int s_dec;
-
-    if (a.st->done) return;                 // converged or failed column: nothing to do
 
     const int G = gridDim.x;
     const int n = a.n;
@@ -253,17 +171,18 @@ pcg32_pair_kernel(Args32 a, int R) {
 #pragma unroll
             for (int d = 0; d < kBand; ++d) ah[hslot * kBand + d] = t[d];
         }
+        for (int i = lo + tid; i < hi; i += nt) a.x64[i] = 0.0;   // x_0 = 0
     }
     __syncthreads();
 
     unsigned bar_no = 0;
     const long long tmo = a.timeout_ns;
     int status = AIRGA_E_MAXIT;
-    int iters = 0;
+    int inner_total = 0, outer = 0;
+    double relres = 0.0;
 
-    // r_0 = b (d_0 = 0) on own +- HR
-    for (int i = rlo + tid; i < rhi; i += nt) rs[i - rbase] = a.b[i];
-    __syncthreads();
+    // z = M r for the pairs [from, to) (stride 2 nt starting at this thread's
+    // slot); r.z and r.r of own pairs accumulate into v2
     auto apply_M = [&](int from, int to, float (&v2)[2]) {
         for (int i = from + 2 * tid; i < to; i += 2 * nt) {
             float2 z;
@@ -284,178 +203,240 @@ pcg32_pair_kernel(Args32 a, int R) {
             }
         }
     };
-    {
-        float v2[2] = {0.0f, 0.0f};
-        apply_M(zlo, zhi, v2);
-        double v[2] = {(double)v2[0], (double)v2[1]};
-        block_partials_tree<2>(v, red, a.partials, bar_no & 1, G, blockIdx.x);
-    }
-    if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
-        status = AIRGA_E_TIMEOUT;
-        goto finish;
-    }
-    if (tid < 32) {
-        double t0[2];
-        warp0_totals<2>(a.partials, bar_no & 1, G, t0);
-        if (tid == 0) {
-            tot[0] = t0[0];                                  // (r, z)
-            tot[1] = t0[1];                                  // (r, r) = ||b||^2
-            s_dec = t0[1] == 0.0 ? 1 : ((!isfinite(t0[0]) || t0[0] == 0.0) ? 2 : 0);
-        }
-    }
-    __syncthreads();
-    ++bar_no;
-    {
-        double rz = tot[0];
-        const double thr2 = a.tol * a.tol * tot[1];
-        if (s_dec == 1) { status = AIRGA_OK; goto finish; }
-        if (s_dec == 2) { status = AIRGA_E_BREAKDOWN; goto finish; }
-        float beta = 0.0f;
-        for (int k = 1; k <= a.maxit; ++k) {
-            for (int i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
-                float2 *pp = reinterpret_cast<float2 *>(ps + (i - pbase));
-                const float2 z = *reinterpret_cast<const float2 *>(zq + (i - zbase));
-                if (k == 1) {
-                    *pp = z;
-                } else {
-                    float2 p = *pp;
-                    p.x = fmaf(beta, p.x, z.x);
-                    p.y = fmaf(beta, p.y, z.y);
-                    *pp = p;
-                }
-            }
-            __syncthreads();
-            for (int t = tid; t < 2 * bw; t += nt) {
-                const int i = t < bw ? lo + t : hi - bw + (t - bw);
-                a.pbuf[i] = ps[i - pbase];
-            }
-            float vq = 0.0f;
-            for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
-                float v[10];
-                load_win_f(ps, pbase, i, v);
-                float2 q;
-                if (packed) {
-                    q = pair_packed_f(a.Apk, a.A, n, i, v);
-                } else {
-                    float2 ab[kBand];
-                    load_band_pair_f(a.A, n, i, ab);
-                    q = pair_full_f(ab, v);
-                }
-                *reinterpret_cast<float2 *>(zq + (i - zbase)) = q;
-                vq = fmaf(v[4], q.x, fmaf(v[5], q.y, vq));
-            }
-            {
-                double vv[1] = {(double)vq};
-                block_partials_tree<1>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
-            }
-            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
-                status = AIRGA_E_TIMEOUT;
-                iters = k - 1;
-                goto finish;
-            }
-            if (tid < 32) {
-                double pqt[1];
-                warp0_totals<1>(a.partials, bar_no & 1, G, pqt);
-                if (tid == 0) {
-                    const double pq = pqt[0];
-                    const bool bad = !(pq > 0.0) || !isfinite(pq);
-                    s_dec = bad ? 1 : 0;
-                    tot[2] = bad ? 0.0 : rz / pq;
-                }
-            }
-            __syncthreads();
-            ++bar_no;
-            if (s_dec) {
-                status = AIRGA_E_BREAKDOWN;
-                iters = k - 1;
-                goto finish;
-            }
-            const float alpha = (float)tot[2];
 
-            float pv[10];
-            if (hvalid) {
+    for (int ko = 0;; ++ko) {
+        // ---- FP64 residual r = f - A x on own +- HR into the FP32 window;
+        //      ||r||^2 of own rows; x's halo rows were written by the
+        //      neighbours before the barrier that ended the previous step ----
+        {
+            double rr = 0.0;
+            for (int i = rlo + tid; i < rhi; i += nt) {
+                double r = __ldg(a.f + i);
+                if (ko > 0) {
+                    double ax = 0.0;
 #pragma unroll
-                for (int q = 0; q < 10; ++q) {
-                    const int row = hpair - 4 + q;
-                    float v = 0.0f;
-                    if (row >= 0 && row < n)
-                        v = (row >= lo - HZ && row < hi + HZ) ? ps[row - pbase] : __ldcg(a.pbuf + row);
-                    pv[q] = v;
+                    for (int d = 0; d < kBand; ++d) {
+                        const int c = i + d - kHalf;
+                        if (c >= 0 && c < n)
+                            ax = fma(__ldg(a.A64 + (long long)d * n + i), __ldcg(a.x64 + c), ax);
+                    }
+                    r -= ax;
                 }
+                rs[i - rbase] = (float)r;
+                if (i >= lo && i < hi) rr = fma(r, r, rr);
             }
-            for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
-                float2 *xp = reinterpret_cast<float2 *>(xs + (i - xbase));
-                float2 *rp = reinterpret_cast<float2 *>(rs + (i - rbase));
-                const float2 p = *reinterpret_cast<const float2 *>(ps + (i - pbase));
-                const float2 q = *reinterpret_cast<const float2 *>(zq + (i - zbase));
-                float2 x = *xp, r = *rp;
-                x.x = fmaf(alpha, p.x, x.x);
-                x.y = fmaf(alpha, p.y, x.y);
-                r.x = fmaf(-alpha, q.x, r.x);
-                r.y = fmaf(-alpha, q.y, r.y);
-                *xp = x;
-                *rp = r;
+            double v[1] = {rr};
+            block_partials_tree<1>(v, red, a.partials, bar_no & 1, G, blockIdx.x);
+        }
+        if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+            status = AIRGA_E_TIMEOUT;
+            break;
+        }
+        if (tid < 32) {
+            double t[1];
+            warp0_totals<1>(a.partials, bar_no & 1, G, t);
+            if (tid == 0) {
+                const double rr = t[0];
+                if (ko == 0) tot[5] = rr;                       // x = 0: r = f
+                const double nf2 = tot[5];
+                tot[6] = nf2 > 0.0 ? sqrt(rr / nf2) : 0.0;
+                s_dec = rr <= a.tol * a.tol * nf2 ? 1 : (ko >= a.max_outer ? 2 : 0);
             }
-            if (hvalid) {
-                float2 t[kBand];
-#pragma unroll
-                for (int d = 0; d < kBand; ++d) t[d] = ah[hslot * kBand + d];
-                const float2 q = pair_full_f(t, pv);
-                float2 *rp = reinterpret_cast<float2 *>(rs + (hpair - rbase));
-                float2 r = *rp;
-                r.x = fmaf(-alpha, q.x, r.x);
-                r.y = fmaf(-alpha, q.y, r.y);
-                *rp = r;
-            }
-            __syncthreads();
+        }
+        __syncthreads();
+        ++bar_no;
+        relres = tot[6];
+        outer = ko;
+        if (s_dec == 1) { status = AIRGA_OK; break; }
+        if (s_dec == 2) { status = AIRGA_E_MAXIT; break; }
+
+        // ---- FP32 inner PCG: A d = r, d_0 = 0 ----
+        for (int i = lo + tid; i < hi; i += nt) xs[i - xbase] = 0.0f;
+        int istatus = AIRGA_E_MAXIT;
+        int iters = 0;
+        {
             float v2[2] = {0.0f, 0.0f};
             apply_M(zlo, zhi, v2);
-            {
-                double vv[2] = {(double)v2[0], (double)v2[1]};
-                block_partials_tree<2>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
+            double v[2] = {(double)v2[0], (double)v2[1]};
+            block_partials_tree<2>(v, red, a.partials, bar_no & 1, G, blockIdx.x);
+        }
+        if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+            status = AIRGA_E_TIMEOUT;
+            break;
+        }
+        if (tid < 32) {
+            double t0[2];
+            warp0_totals<2>(a.partials, bar_no & 1, G, t0);
+            if (tid == 0) {
+                tot[0] = t0[0];                                  // (r, z)
+                tot[1] = t0[1];                                  // (r, r)
+                s_dec = t0[1] == 0.0 ? 1 : ((!isfinite(t0[0]) || t0[0] == 0.0) ? 2 : 0);
             }
-            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
-                status = AIRGA_E_TIMEOUT;
-                iters = k;
-                goto finish;
-            }
-            if (tid < 32) {
-                double t2v[2];
-                warp0_totals<2>(a.partials, bar_no & 1, G, t2v);
-                if (tid == 0) {
-                    const double rz_new = t2v[0];
-                    int dec = 0;
-                    if (t2v[1] <= thr2) dec = 1;
-                    else if (!isfinite(rz_new) || rz_new == 0.0) dec = 2;
-                    s_dec = dec;
-                    tot[3] = dec ? 0.0 : rz_new / rz;
-                    tot[4] = rz_new;
+        }
+        __syncthreads();
+        ++bar_no;
+        if (s_dec == 2) istatus = AIRGA_E_BREAKDOWN;
+        if (s_dec == 0) {
+            double rz = tot[0];
+            const double thr2 = a.inner_tol * a.inner_tol * tot[1];
+            float beta = 0.0f;
+            for (int k = 1; k <= a.maxit; ++k) {
+                for (int i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
+                    float2 *pp = reinterpret_cast<float2 *>(ps + (i - pbase));
+                    const float2 z = *reinterpret_cast<const float2 *>(zq + (i - zbase));
+                    if (k == 1) {
+                        *pp = z;
+                    } else {
+                        float2 p = *pp;
+                        p.x = fmaf(beta, p.x, z.x);
+                        p.y = fmaf(beta, p.y, z.y);
+                        *pp = p;
+                    }
                 }
+                __syncthreads();
+                for (int t = tid; t < 2 * bw; t += nt) {
+                    const int i = t < bw ? lo + t : hi - bw + (t - bw);
+                    a.pbuf[i] = ps[i - pbase];
+                }
+                float vq = 0.0f;
+                for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                    float v[10];
+                    load_win_f(ps, pbase, i, v);
+                    float2 q;
+                    if (packed) {
+                        q = pair_packed_f(a.Apk, a.A, n, i, v);
+                    } else {
+                        float2 ab[kBand];
+                        load_band_pair_f(a.A, n, i, ab);
+                        q = pair_full_f(ab, v);
+                    }
+                    *reinterpret_cast<float2 *>(zq + (i - zbase)) = q;
+                    vq = fmaf(v[4], q.x, fmaf(v[5], q.y, vq));
+                }
+                if (MODE == 1 && zlo + 2 * tid < zhi) prefetch_pair_f(a.M, n, zlo + 2 * tid, kBand);
+                {
+                    double vv[1] = {(double)vq};
+                    block_partials_tree<1>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
+                }
+                if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+                    istatus = AIRGA_E_TIMEOUT;
+                    iters = k - 1;
+                    break;
+                }
+                if (tid < 32) {
+                    double pqt[1];
+                    warp0_totals<1>(a.partials, bar_no & 1, G, pqt);
+                    if (tid == 0) {
+                        const double pq = pqt[0];
+                        const bool bad = !(pq > 0.0) || !isfinite(pq);
+                        s_dec = bad ? 1 : 0;
+                        tot[2] = bad ? 0.0 : rz * lean::rcp_signed(pq);
+                    }
+                }
+                __syncthreads();
+                ++bar_no;
+                if (s_dec) {
+                    istatus = AIRGA_E_BREAKDOWN;
+                    iters = k - 1;
+                    break;
+                }
+                const float alpha = (float)tot[2];
+
+                float pv[10];
+                if (hvalid) {
+#pragma unroll
+                    for (int q = 0; q < 10; ++q) {
+                        const int row = hpair - 4 + q;
+                        float v = 0.0f;
+                        if (row >= 0 && row < n)
+                            v = (row >= lo - HZ && row < hi + HZ) ? ps[row - pbase] : __ldcg(a.pbuf + row);
+                        pv[q] = v;
+                    }
+                }
+                for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                    float2 *xp = reinterpret_cast<float2 *>(xs + (i - xbase));
+                    float2 *rp = reinterpret_cast<float2 *>(rs + (i - rbase));
+                    const float2 p = *reinterpret_cast<const float2 *>(ps + (i - pbase));
+                    const float2 q = *reinterpret_cast<const float2 *>(zq + (i - zbase));
+                    float2 x = *xp, r = *rp;
+                    x.x = fmaf(alpha, p.x, x.x);
+                    x.y = fmaf(alpha, p.y, x.y);
+                    r.x = fmaf(-alpha, q.x, r.x);
+                    r.y = fmaf(-alpha, q.y, r.y);
+                    *xp = x;
+                    *rp = r;
+                }
+                if (hvalid) {
+                    float2 t[kBand];
+#pragma unroll
+                    for (int d = 0; d < kBand; ++d) t[d] = ah[hslot * kBand + d];
+                    const float2 q = pair_full_f(t, pv);
+                    float2 *rp = reinterpret_cast<float2 *>(rs + (hpair - rbase));
+                    float2 r = *rp;
+                    r.x = fmaf(-alpha, q.x, r.x);
+                    r.y = fmaf(-alpha, q.y, r.y);
+                    *rp = r;
+                }
+                __syncthreads();
+                float v2[2] = {0.0f, 0.0f};
+                apply_M(zlo, zhi, v2);
+                if (lo + 2 * tid < hi) {
+                    if (packed) prefetch_pair_f(a.Apk, n, lo + 2 * tid, 5);
+                    else prefetch_pair_f(a.A, n, lo + 2 * tid, kBand);
+                }
+                {
+                    double vv[2] = {(double)v2[0], (double)v2[1]};
+                    block_partials_tree<2>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
+                }
+                if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+                    istatus = AIRGA_E_TIMEOUT;
+                    iters = k;
+                    break;
+                }
+                if (tid < 32) {
+                    double t2v[2];
+                    warp0_totals<2>(a.partials, bar_no & 1, G, t2v);
+                    if (tid == 0) {
+                        const double rz_new = t2v[0];
+                        int dec = 0;
+                        if (t2v[1] <= thr2) dec = 1;
+                        else if (!isfinite(rz_new) || rz_new == 0.0) dec = 2;
+                        s_dec = dec;
+                        tot[3] = dec ? 0.0 : rz_new * lean::rcp_signed(rz);
+                        tot[4] = rz_new;
+                    }
+                }
+                __syncthreads();
+                ++bar_no;
+                iters = k;
+                {
+                    const int dec = s_dec;
+                    if (dec == 1) { istatus = AIRGA_OK; break; }
+                    if (dec == 2) { istatus = AIRGA_E_BREAKDOWN; break; }
+                }
+                beta = (float)tot[3];
+                rz = tot[4];
             }
-            __syncthreads();
-            ++bar_no;
-            iters = k;
-            {
-                const int dec = s_dec;
-                if (dec == 1) { status = AIRGA_OK; break; }
-                if (dec == 2) { status = AIRGA_E_BREAKDOWN; break; }
-            }
-            beta = (float)tot[3];
-            rz = tot[4];
         }
+        inner_total += iters;
+        if (istatus == AIRGA_E_TIMEOUT) { status = istatus; break; }
+        // ---- x += d in FP64 (own rows); the barrier publishes x's rows to
+        //      the neighbours' next residual.  An inner solve that stopped on
+        //      its cap still improved x; a breakdown ends the column. ----
+        __syncthreads();
+        for (int i = lo + tid; i < hi; i += nt) a.x64[i] += (double)xs[i - xbase];
+        if (istatus == AIRGA_E_BREAKDOWN) { status = istatus; outer = ko + 1; break; }
+        if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+            status = AIRGA_E_TIMEOUT;
+            break;
+        }
+        ++bar_no;
     }
-finish:
-    __syncthreads();
-    // refinement update x += d in FP64 (own rows)
-    for (int i = lo + tid; i < hi; i += nt) a.x64[i] += (double)xs[i - xbase];
     if (blockIdx.x == 0 && tid == 0) {
-        a.st->inner += iters;
-        // an inner solve that stopped on its cap still improved x; breakdown
-        // and timeout end the column
-        if (status == AIRGA_E_BREAKDOWN || status == AIRGA_E_TIMEOUT) {
-            a.st->status = status;
-            a.st->done = 1;
-        }
+        *a.relres = relres;
+        *a.outer_iters = outer;
+        *a.inner_iters = inner_total;
+        *a.status = status;
     }
 }
 
@@ -466,7 +447,7 @@ size_t pcg32_smem(int64_t R) {
 
 template <int MODE>
 cudaError_t launch32(int grid, int64_t R, size_t smem, const Args32 &args, cudaStream_t s) {
-    auto kern = pcg32_pair_kernel<MODE>;
+    auto kern = mixed_pair_kernel<MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     Args32 a = args;
@@ -477,10 +458,10 @@ cudaError_t launch32(int grid, int64_t R, size_t smem, const Args32 &args, cudaS
 
 template <int MODE>
 int occupancy32(size_t smem, int *per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(pcg32_pair_kernel<MODE>,
+    cudaError_t e = cudaFuncSetAttribute(mixed_pair_kernel<MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg32_pair_kernel<MODE>, kThreads,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, mixed_pair_kernel<MODE>, kThreads,
                                                           smem);
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg32 occupancy");
 }
@@ -538,14 +519,12 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     if (per_sm < 1 || grid > per_sm * sms) return fail(AIRGA_E_INVALID_ARG, "mixed solve: grid not co-resident");
 
     cudaStream_t s = (cudaStream_t)stream;
-    const int rblk = (int)((n + 4095) / 4096 < 1216 ? (n + 4095) / 4096 : 1216);
-    // workspace: FP32 A band (7n), FP32 packed (5n), FP32 M band (7n), r32 (n),
-    // pbuf32 (n) as floats; partials, residual partials, states, control
+    // workspace: FP32 A band (7n), FP32 packed (5n), FP32 M band (7n), pbuf32 (n)
+    // as floats; partials, control
     const size_t nf = (size_t)n;
-    const size_t floats = 7 * nf + 5 * nf + (mode ? 7 * nf : 0) + nf + nf;
-    const size_t doubles = (size_t)8 * grid + (size_t)rblk + 4;
-    const size_t bytes = floats * sizeof(float) + 256 + doubles * sizeof(double) +
-                         (size_t)m * sizeof(MixState) + 256;
+    const size_t floats = 7 * nf + 5 * nf + (mode ? 7 * nf : 0) + nf;
+    const size_t doubles = (size_t)8 * grid + 4;
+    const size_t bytes = floats * sizeof(float) + 256 + doubles * sizeof(double) + 256;
     void *ws = nullptr;
     st = dev_alloc(&ws, bytes, s);
     if (st) return st;
@@ -553,13 +532,10 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     float *A32 = (float *)base;
     float *Apk32 = A32 + 7 * nf;
     float *M32 = Apk32 + 5 * nf;
-    float *r32 = M32 + (mode ? 7 * nf : 0);
-    float *pbuf = r32 + nf;
+    float *pbuf = M32 + (mode ? 7 * nf : 0);
     double *dbase = (double *)(((uintptr_t)(pbuf + nf) + 255) & ~(uintptr_t)255);
     double *partials = dbase;
-    double *rpart = partials + 8 * grid;
-    unsigned *ctl = (unsigned *)(rpart + rblk);
-    MixState *states = (MixState *)(((uintptr_t)(ctl + 8) + 15) & ~(uintptr_t)15);
+    unsigned *ctl = (unsigned *)(partials + 8 * grid);
 
     cudaError_t e = cudaSuccess;
     const int gconv = grid_for(7 * n);
@@ -589,36 +565,26 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     a.Apk = A->pairz ? Apk32 : nullptr;
     a.pairz = A->pairz ? (const int32_t *)A->pairz.get() : nullptr;
     a.M = mode ? M32 : nullptr;
-    a.b = r32;
+    a.A64 = A->band->d;
     a.pbuf = pbuf;
     a.partials = partials;
     a.bar = ctl;
     a.abort_flag = (int *)(ctl + 1);
-    a.tol = o.inner_tol;
+    a.tol = o.tol;
+    a.inner_tol = o.inner_tol;
     a.maxit = o.maxit;
+    a.max_outer = o.max_outer;
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
+    // one launch per column runs its whole refinement
     for (int32_t c = 0; c < m && e == cudaSuccess; ++c) {
-        const double *f = F + (size_t)c * nf;
-        double *x = X + (size_t)c * nf;
-        MixState *stc = states + c;
-        e = cudaMemsetAsync(x, 0, sizeof(double) * nf, s);
-        if (e != cudaSuccess) break;
-        state_init_kernel<<<1, 1, 0, s>>>(stc);
-        a.x64 = x;
-        a.st = stc;
-        for (int k = 0; k <= o.max_outer && e == cudaSuccess; ++k) {
-            resid_partial_kernel<<<rblk, 256, 0, s>>>(n, A->band->d, x, f, r32, rpart, stc);
-            resid_final_kernel<<<1, 256, 0, s>>>(rblk, rpart, stc, o.tol, k, o.max_outer,
-                                                 true_relres + c);
-            e = cudaGetLastError();
-            if (e != cudaSuccess || k == o.max_outer) break;
-            e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
-            if (e == cudaSuccess) e = mode ? launch32<1>(grid, R, smem, a, s) : launch32<0>(grid, R, smem, a, s);
-        }
-        if (e == cudaSuccess) {
-            state_out_kernel<<<1, 1, 0, s>>>(stc, outer_iters + c, inner_iters + c, status + c);
-            e = cudaGetLastError();
-        }
+        a.f = F + (size_t)c * nf;
+        a.x64 = X + (size_t)c * nf;
+        a.relres = true_relres + c;
+        a.outer_iters = outer_iters + c;
+        a.inner_iters = inner_iters + c;
+        a.status = status + c;
+        e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
+        if (e == cudaSuccess) e = mode ? launch32<1>(grid, R, smem, a, s) : launch32<0>(grid, R, smem, a, s);
     }
     dev_free(ws, s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed solve launch");
