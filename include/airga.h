@@ -247,10 +247,12 @@ void airga_batch_free(airga_batch b);
  * outer_iters[m] and inner_iters[m] (int32: refinement steps taken and
  * total FP32 CG iterations); status[m] (AIRGA_OK when the FP64 residual
  * reached tol, AIRGA_E_MAXIT when max_outer steps did not, AIRGA_E_BREAKDOWN
- * or AIRGA_E_TIMEOUT from an inner solve); true_relres[m] as for
- * airga_pcg_solve.  P must be NULL (no preconditioner) or a single factor.
- * Uses a per-call workspace from the library pool (about 3 n doubles plus
- * FP32 copies of A and P). */
+ * from an inner solve, AIRGA_E_TIMEOUT when a bounded grid barrier expired);
+ * true_relres[m] as for airga_pcg_solve.  P must be NULL (no preconditioner)
+ * or a single factor.  Each column is one persistent launch that runs its
+ * whole refinement loop (asynchronous on `stream`, no host synchronisation).
+ * Uses a per-call workspace from the library pool: FP32 copies of A, of its
+ * packed beam entries and of P, plus n floats. */
 int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double *F, int32_t m,
                           const airga_options *opt, double *X, int32_t *outer_iters,
                           int32_t *inner_iters, int32_t *status, double *true_relres,
