@@ -67,6 +67,7 @@ struct Args32 {
     int maxit;            // inner iterations per refinement step
     int max_outer;        // refinement steps
     long long timeout_ns;
+    int fault_skip_arrival; // test hook: CTA 0 skips its first inner barrier arrival
     double *relres;       // out: FP64 relative residual at exit
     int32_t *outer_iters; // out: refinement steps taken
     int32_t *inner_iters; // out: FP32 CG iterations, all steps
@@ -318,7 +319,9 @@ mixed_pair_kernel(Args32 a, int R) {
                     double vv[1] = {(double)vq};
                     block_partials_tree<1>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
                 }
-                if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+                const bool arrive = !(a.fault_skip_arrival && ko == 0 && k == 1 && blockIdx.x == 0);
+                if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
+                                  arrive)) {
                     istatus = AIRGA_E_TIMEOUT;
                     iters = k - 1;
                     break;
@@ -575,6 +578,7 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     a.maxit = o.maxit;
     a.max_outer = o.max_outer;
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
+    const int fault = take_fault() == AIRGA_FAULT_SKIP_ARRIVAL ? 1 : 0;
     // one launch per column runs its whole refinement
     for (int32_t c = 0; c < m && e == cudaSuccess; ++c) {
         a.f = F + (size_t)c * nf;
@@ -583,6 +587,7 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
         a.outer_iters = outer_iters + c;
         a.inner_iters = inner_iters + c;
         a.status = status + c;
+        a.fault_skip_arrival = c == 0 ? fault : 0;
         e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
         if (e == cudaSuccess) e = mode ? launch32<1>(grid, R, smem, a, s) : launch32<0>(grid, R, smem, a, s);
     }

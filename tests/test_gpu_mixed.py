@@ -93,3 +93,20 @@ def test_mixed_full_size_two_million(G, s):
         assert int(res["status"][c]) == G.OK
         assert np.linalg.norm(X[:, c] - Xd[:, c]) <= 1e-8 * np.linalg.norm(Xd[:, c])
         assert float(res["true_relres"][c]) <= 1e-10
+
+
+def test_mixed_barrier_timeout_reports_status(G):
+    """A CTA that never arrives at the first inner barrier (host-injected)
+    makes every bounded wait expire: the column ends with AIRGA_E_TIMEOUT,
+    x keeps its last refined value (here 0), later columns and later calls
+    solve normally."""
+    beam = W.beam(5000)
+    F = W.loads(beam.n, 2, seed=3)
+    G.debug_set_fault(G.FAULT_SKIP_ARRIVAL)
+    res = solve(G, beam, 1.0, F, barrier_timeout_ms=100)
+    assert int(res["status"][0]) == G.E_TIMEOUT
+    assert not res["X"][:, 0].any()
+    assert int(res["status"][1]) == G.OK
+    assert float(res["true_relres"][1]) <= 1e-10
+    res = solve(G, beam, 1.0, F)
+    assert all(int(v) == G.OK for v in res["status"])
