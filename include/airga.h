@@ -417,11 +417,12 @@ int airga_mlp_spai(airga_mlp net, airga_mat A, double s, double alpha, double be
 void airga_mlp_free(airga_mlp net);
 
 /* Test hook for failure detection (no GPU fault involved): arm a fault for
- * the next airga_pcg_solve or airga_pcg_solve_mixed call of this process.
- * AIRGA_FAULT_SKIP_ARRIVAL makes CTA 0 skip its arrival at the first
- * (inner) iteration barrier of the first column, so every CTA's bounded
- * barrier wait (opt->barrier_timeout_ms) expires, the kernel returns and that
- * column's status is AIRGA_E_TIMEOUT; the CUDA context stays usable.  The
+ * the next airga_pcg_solve, airga_pcg_solve_mixed or airga_batch_solve call
+ * of this process.  AIRGA_FAULT_SKIP_ARRIVAL makes CTA 0 (of system 0, in a
+ * batch) skip its arrival at the first (inner) iteration barrier of the
+ * first column, so every bounded barrier wait of that system
+ * (opt->barrier_timeout_ms) expires and its status is AIRGA_E_TIMEOUT; the
+ * other systems of a batch, the kernel and the CUDA context carry on.  The
  * fault is consumed by that call. */
 #define AIRGA_FAULT_NONE 0
 #define AIRGA_FAULT_SKIP_ARRIVAL 1

@@ -117,3 +117,22 @@ def test_batch_rejects(G):
     x = torch.zeros(beam.n, dtype=torch.float64, device="cuda")
     with pytest.raises(G.AirgaError):
         G.Batch([(A, P, f, x), (A, None, f, x)])      # mixed preconditioning
+
+
+def test_batch_barrier_timeout_is_per_system(G):
+    """A host-injected missing arrival in system 0 expires that system's
+    bounded barrier waits only: it reports AIRGA_E_TIMEOUT (relres NaN), every
+    other system of the launch still solves, and the next solve of the same
+    batch is clean."""
+    systems, ref, keep = make_systems(G, SPEC)
+    B = G.Batch(systems, G.options(tol=1e-10, maxit=20000, barrier_timeout_ms=100))
+    G.debug_set_fault(G.FAULT_SKIP_ARRIVAL)
+    B.solve()
+    torch.cuda.synchronize()
+    assert int(B.status[0]) == G.E_TIMEOUT
+    assert np.isnan(float(B.relres[0]))
+    assert all(int(v) == G.OK for v in B.status[1:])
+    assert float(B.relres[1:].max()) <= 2e-10
+    B.solve()
+    torch.cuda.synchronize()
+    assert all(int(v) == G.OK for v in B.status)
