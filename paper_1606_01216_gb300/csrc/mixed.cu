@@ -133,7 +133,44 @@ __device__ __forceinline__ float2 pair_packed_f(const float *__restrict__ pk,
     return make_float2(y0, y1);
 }
 
-template <int MODE>   // 0: identity, 1: one band preconditioner
+// Symmetric preconditioner stored by its upper diagonals only: U[d][i] =
+// P(i, i+d), d = 0..3 (16 B per row instead of the band's 28 B, so the inner
+// iteration's working set stays in L2 to larger n).  The lower entries of
+// pair (i, i+1) come from earlier rows, P(i, i-d) = U[d][i-d]; v[k] is window
+// row i-4+k.  Out-of-matrix entries multiply window zeros and are not loaded.
+__device__ __forceinline__ float2 pair_sym_f(const float *__restrict__ U, int n, int i,
+                                             const float (&v)[10]) {
+    const float2 z2 = make_float2(0.0f, 0.0f);
+    const float2 *U0 = reinterpret_cast<const float2 *>(U);
+    const float2 *U1 = reinterpret_cast<const float2 *>(U + n);
+    const float2 *U2 = reinterpret_cast<const float2 *>(U + 2 * (long long)n);
+    const float2 *U3 = reinterpret_cast<const float2 *>(U + 3 * (long long)n);
+    const int h = i >> 1;                                   // float2 index of rows (i, i+1)
+    const float2 u0 = __ldg(U0 + h), u1 = __ldg(U1 + h), u2 = __ldg(U2 + h), u3 = __ldg(U3 + h);
+    const float2 l1 = i >= 2 ? __ldg(U1 + h - 1) : z2;      // U1[i-2], U1[i-1]
+    const float2 l2 = i >= 2 ? __ldg(U2 + h - 1) : z2;      // U2[i-2], U2[i-1]
+    const float2 l3a = i >= 4 ? __ldg(U3 + h - 2) : z2;     // U3[i-4], U3[i-3]
+    const float2 l3b = i >= 2 ? __ldg(U3 + h - 1) : z2;     // U3[i-2], U3[i-1]
+    // offsets d = -3 .. 3 in the band kernel's order: for a symmetric band the
+    // result is the full-band product bit for bit
+    float y0 = l3a.y * v[1];
+    y0 = fmaf(l2.x, v[2], y0);
+    y0 = fmaf(l1.y, v[3], y0);
+    y0 = fmaf(u0.x, v[4], y0);
+    y0 = fmaf(u1.x, v[5], y0);
+    y0 = fmaf(u2.x, v[6], y0);
+    y0 = fmaf(u3.x, v[7], y0);
+    float y1 = l3b.x * v[2];
+    y1 = fmaf(l2.y, v[3], y1);
+    y1 = fmaf(u1.x, v[4], y1);
+    y1 = fmaf(u0.y, v[5], y1);
+    y1 = fmaf(u1.y, v[6], y1);
+    y1 = fmaf(u2.y, v[7], y1);
+    y1 = fmaf(u3.y, v[8], y1);
+    return make_float2(y0, y1);
+}
+
+template <int MODE>   // 0: identity, 1: band preconditioner, 2: symmetric (upper diagonals)
 __global__ void __launch_bounds__(kThreads, 1)
 mixed_pair_kernel(Args32 a, int R) {
     extern __shared__ __align__(16) double smem64[];
@@ -193,6 +230,10 @@ mixed_pair_kernel(Args32 a, int R) {
                 float v[10];
                 load_win_f(rs, rbase, i, v);
                 z = pair_full_f(pb, v);
+            } else if (MODE == 2) {
+                float v[10];
+                load_win_f(rs, rbase, i, v);
+                z = pair_sym_f(a.M, n, i, v);
             } else {
                 z = *reinterpret_cast<const float2 *>(rs + (i - rbase));
             }
@@ -314,7 +355,8 @@ mixed_pair_kernel(Args32 a, int R) {
                     *reinterpret_cast<float2 *>(zq + (i - zbase)) = q;
                     vq = fmaf(v[4], q.x, fmaf(v[5], q.y, vq));
                 }
-                if (MODE == 1 && zlo + 2 * tid < zhi) prefetch_pair_f(a.M, n, zlo + 2 * tid, kBand);
+                if (MODE != 0 && zlo + 2 * tid < zhi)
+                    prefetch_pair_f(a.M, n, zlo + 2 * tid, MODE == 2 ? 4 : kBand);
                 {
                     double vv[1] = {(double)vq};
                     block_partials_tree<1>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
@@ -507,7 +549,8 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     AIRGA_CUDA(cudaGetDevice(&dev));
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int mode = P ? 1 : 0;
+    // 2: P_sym stored by its upper diagonals; 1: a nonsymmetric band (symmetrize = 0)
+    const int mode = P ? ((o.symmetrize && P->psym) ? 2 : 1) : 0;
     int64_t want = (n + 127) / 128;
     int grid = (int)(want < sms ? want : sms);
     if (grid < 1) grid = 1;
@@ -517,7 +560,8 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     if (smem + 256 > (size_t)optin)
         return fail(AIRGA_E_INVALID_ARG, "mixed solve: the FP32 state does not fit in shared memory");
     int per_sm = 0;
-    st = mode ? occupancy32<1>(smem, &per_sm) : occupancy32<0>(smem, &per_sm);
+    st = mode == 2 ? occupancy32<2>(smem, &per_sm)
+                   : (mode ? occupancy32<1>(smem, &per_sm) : occupancy32<0>(smem, &per_sm));
     if (st) return st;
     if (per_sm < 1 || grid > per_sm * sms) return fail(AIRGA_E_INVALID_ARG, "mixed solve: grid not co-resident");
 
@@ -525,7 +569,8 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     // workspace: FP32 A band (7n), FP32 packed (5n), FP32 M band (7n), pbuf32 (n)
     // as floats; partials, control
     const size_t nf = (size_t)n;
-    const size_t floats = 7 * nf + 5 * nf + (mode ? 7 * nf : 0) + nf;
+    const size_t mfl = mode == 2 ? 4 * nf : (mode ? 7 * nf : 0);
+    const size_t floats = 7 * nf + 5 * nf + mfl + nf;
     const size_t doubles = (size_t)8 * grid + 4;
     const size_t bytes = floats * sizeof(float) + 256 + doubles * sizeof(double) + 256;
     void *ws = nullptr;
@@ -535,7 +580,7 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     float *A32 = (float *)base;
     float *Apk32 = A32 + 7 * nf;
     float *M32 = Apk32 + 5 * nf;
-    float *pbuf = M32 + (mode ? 7 * nf : 0);
+    float *pbuf = M32 + mfl;
     double *dbase = (double *)(((uintptr_t)(pbuf + nf) + 255) & ~(uintptr_t)255);
     double *partials = dbase;
     unsigned *ctl = (unsigned *)(partials + 8 * grid);
@@ -557,10 +602,10 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
         }
         to_f32_kernel<<<gconv, 256, 0, s>>>(5 * n, (const double *)A->packed.get(), Apk32);
     }
-    if (mode) {
-        const double *mb = (o.symmetrize && P->psym) ? P->psym->d : P->factors[0]->d;
-        to_f32_kernel<<<gconv, 256, 0, s>>>(7 * n, mb, M32);
-    }
+    if (mode == 2)   // diagonals d = 0..3 of the band are contiguous from row offset 3n
+        to_f32_kernel<<<gconv, 256, 0, s>>>(4 * n, P->psym->d + 3 * nf, M32);
+    else if (mode)
+        to_f32_kernel<<<gconv, 256, 0, s>>>(7 * n, P->factors[0]->d, M32);
     e = cudaGetLastError();
     Args32 a{};
     a.n = (int)n;
@@ -589,7 +634,9 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
         a.status = status + c;
         a.fault_skip_arrival = c == 0 ? fault : 0;
         e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
-        if (e == cudaSuccess) e = mode ? launch32<1>(grid, R, smem, a, s) : launch32<0>(grid, R, smem, a, s);
+        if (e == cudaSuccess)
+            e = mode == 2 ? launch32<2>(grid, R, smem, a, s)
+                          : (mode ? launch32<1>(grid, R, smem, a, s) : launch32<0>(grid, R, smem, a, s));
     }
     dev_free(ws, s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed solve launch");
