@@ -71,6 +71,43 @@ __device__ __forceinline__ double2 pair_full(const double2 (&a)[kBand], const do
     return make_double2(y0, y1);
 }
 
+// Symmetric band from its upper diagonals U[d][i] = P(i, i+d), d = 0..3 (the
+// rows 3n..7n of a band array): the lower entries of pair (i, i+1) are read
+// from earlier rows, P(i, i-d) = U[d][i-d], so the band's lower three
+// diagonals are never touched and the per-iteration L2 footprint of P_sym
+// drops from 56 to 32 B per row.  Products are summed in pair_full's order
+// (offsets -3 .. 3), so for a symmetric band the result is the same bit for
+// bit.  Out-of-matrix entries multiply window zeros and are not loaded.
+__device__ __forceinline__ double2 pair_sym(const double *__restrict__ U, int n, int i,
+                                            const double (&v)[10]) {
+    const double2 z2 = make_double2(0.0, 0.0);
+    const double2 *U0 = reinterpret_cast<const double2 *>(U);
+    const double2 *U1 = reinterpret_cast<const double2 *>(U + n);
+    const double2 *U2 = reinterpret_cast<const double2 *>(U + 2 * (long long)n);
+    const double2 *U3 = reinterpret_cast<const double2 *>(U + 3 * (long long)n);
+    const int h = i >> 1;                                   // double2 index of rows (i, i+1)
+    const double2 u0 = __ldg(U0 + h), u1 = __ldg(U1 + h), u2 = __ldg(U2 + h), u3 = __ldg(U3 + h);
+    const double2 l1 = i >= 2 ? __ldg(U1 + h - 1) : z2;     // U1[i-2], U1[i-1]
+    const double2 l2 = i >= 2 ? __ldg(U2 + h - 1) : z2;     // U2[i-2], U2[i-1]
+    const double2 l3a = i >= 4 ? __ldg(U3 + h - 2) : z2;    // U3[i-4], U3[i-3]
+    const double2 l3b = i >= 2 ? __ldg(U3 + h - 1) : z2;    // U3[i-2], U3[i-1]
+    double y0 = l3a.y * v[1];
+    y0 = fma(l2.x, v[2], y0);
+    y0 = fma(l1.y, v[3], y0);
+    y0 = fma(u0.x, v[4], y0);
+    y0 = fma(u1.x, v[5], y0);
+    y0 = fma(u2.x, v[6], y0);
+    y0 = fma(u3.x, v[7], y0);
+    double y1 = l3b.x * v[2];
+    y1 = fma(l2.y, v[3], y1);
+    y1 = fma(u1.x, v[4], y1);
+    y1 = fma(u0.y, v[5], y1);
+    y1 = fma(u1.y, v[6], y1);
+    y1 = fma(u2.y, v[7], y1);
+    y1 = fma(u3.y, v[8], y1);
+    return make_double2(y0, y1);
+}
+
 // Same with the beam's exact zeros skipped: even row drops d = 0 (-3) and
 // d = 4 (+1); odd row drops d = 6 (+3) and d = 2 (-1).  The free-end pair
 // (i = n-2) keeps its +-1 couplings.
@@ -194,6 +231,8 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
     const bool beam = a.pairz != nullptr && *a.pairz != 0;
     const bool packed = beam && a.Apk != nullptr;
     const double *Pb = MODE == 1 ? (a.psym ? a.psym : a.fac[0]) : nullptr;
+    // P_sym is symmetric: read its upper diagonals only (rows 3n.. of the band)
+    const double *Psu = MODE == 1 && a.psym ? a.psym + 3 * (long long)n : nullptr;
     // r-halo pairs are recomputed by the last kHaloPairs threads (they own
     // one pair fewer than the first threads when R/2 is not a multiple of nt)
     const int hslot = nt - 1 - tid;                  // 0..7 for the halo threads
@@ -243,7 +282,11 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
     auto apply_M = [&](int from, int to, double (&v2)[2]) {
         for (int i = from + 2 * tid; i < to; i += 2 * nt) {
             double2 z;
-            if (MODE == 1) {
+            if (MODE == 1 && Psu) {
+                double v[10];
+                load_win(rs, rbase, i, v);
+                z = pair_sym(Psu, n, i, v);
+            } else if (MODE == 1) {
                 double2 pb[kBand];
                 load_band_pair(Pb, n, i, pb);
                 double v[10];
@@ -339,7 +382,10 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
                     vq[0] = fma(v[4], q.x, fma(v[5], q.y, vq[0]));
                 }
             }
-            if (MODE == 1 && zlo + 2 * tid < zhi) prefetch_pair(Pb, n, zlo + 2 * tid, kBand);
+            if (MODE == 1 && zlo + 2 * tid < zhi) {
+                if (Psu) prefetch_pair(Psu, n, zlo + 2 * tid, 4);
+                else prefetch_pair(Pb, n, zlo + 2 * tid, kBand);
+            }
             block_partials_tree<1>(vq, red, a.partials, bar_no & 1, G, rank);
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
                 status = AIRGA_E_TIMEOUT;
