@@ -114,7 +114,11 @@ __device__ void apply_precond(const PcgArgs &a, int64_t lo, int64_t hi, int H, d
         zq[i - zbase] = 0.5 * (zq[i - zbase] + src[i - rbase]);
 }
 
-template <bool SMEM, int MODE>
+// SMEM: 0 every window in this CTA's slice of the global workspace; 1 every
+// window in shared memory; 2 (update chains) the windows the chain stencils
+// read and write — r, t1, t2 — in shared memory, x, p and z/q in the global
+// slice (the six windows of a chain do not fit shared memory at large n).
+template <int SMEM, int MODE>
 __global__ void __launch_bounds__(kPcgThreads, 1)
 pcg_kernel(PcgArgs a, int64_t R, int H) {
     extern __shared__ double smem[];
@@ -129,13 +133,25 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
 
     // window buffers (global row i of a window with base B sits at buf[i - B])
     const int64_t lenX = R, lenR = R + 2 * H, lenP = R + 2 * H + 6, lenZ = R + 6;
-    double *base = SMEM ? smem : a.state + (size_t)blockIdx.x * (lenX + lenR + lenP + lenZ + 2 * lenR);
-    double *xs = base;
-    double *rs = xs + lenX;
-    double *ps = rs + lenR;
-    double *zq = ps + lenP;
-    double *t1 = SMEM ? nullptr : zq + lenZ;
-    double *t2 = SMEM ? nullptr : t1 + lenR;
+    double *xs, *rs, *ps, *zq, *t1 = nullptr, *t2 = nullptr;
+    if (SMEM == 2) {
+        rs = smem;
+        t1 = rs + lenR;
+        t2 = t1 + lenR;
+        xs = a.state + (size_t)blockIdx.x * (lenX + lenP + lenZ);
+        ps = xs + lenX;
+        zq = ps + lenP;
+    } else {
+        double *base = SMEM ? smem : a.state + (size_t)blockIdx.x * (lenX + lenR + lenP + lenZ + 2 * lenR);
+        xs = base;
+        rs = xs + lenX;
+        ps = rs + lenR;
+        zq = ps + lenP;
+        if (!SMEM) {
+            t1 = zq + lenZ;
+            t2 = t1 + lenR;
+        }
+    }
     const int64_t xbase = lo, rbase = lo - H, pbase = lo - H - 3, zbase = lo - 3;
     const int64_t rlo = lo - H > 0 ? lo - H : 0, rhi = hi + H < n ? hi + H : n;
     const int64_t plo3 = lo - 3 > 0 ? lo - 3 : 0, phi3 = hi + 3 < n ? hi + 3 : n;
@@ -286,7 +302,7 @@ finish:
     }
 }
 
-template <bool SMEM, int MODE>
+template <int SMEM, int MODE>
 cudaError_t launch_mode(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
     auto kern = pcg_kernel<SMEM, MODE>;
     if (SMEM) {
@@ -362,43 +378,41 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
     int grid = (int)(want < sms ? want : sms);
     if (grid < 1) grid = 1;
     int64_t R = (n + grid - 1) / grid;
-    const size_t per_cta = (size_t)(R + (R + 2 * H) + (R + 2 * H + 6) + (R + 6));
+    // shared memory: all four windows (identity, one band), or for a chain the
+    // r, t1, t2 windows with x, p, z/q in a global slice
+    const size_t per_cta = mode == kChain ? (size_t)3 * (R + 2 * H)
+                                          : (size_t)(R + (R + 2 * H) + (R + 2 * H + 6) + (R + 6));
     const size_t smem = per_cta * sizeof(double);
     plan->threads = kPcgThreads;
     plan->halo = H;
     plan->grid = grid;
     plan->rows = R;
-    plan->smem_state = (mode != kChain) && (smem + static_smem <= (size_t)optin) && forced != 1;
+    plan->smem_state = (smem + static_smem <= (size_t)optin) && forced != 1;
     plan->kind = plan->smem_state ? 0 : 1;
     plan->smem_bytes = plan->smem_state ? smem : 0;
     const size_t slice = (size_t)(R + (R + 2 * H) + (R + 2 * H + 6) + (R + 6) + 2 * (R + 2 * H));
-    plan->scratch_doubles = plan->smem_state ? 0 : slice * (size_t)grid;
+    const size_t chain_slice = (size_t)(R + (R + 2 * H + 6) + (R + 6));
+    plan->scratch_doubles = !plan->smem_state ? slice * (size_t)grid
+                            : (mode == kChain ? chain_slice * (size_t)grid : 0);
     // co-residency check for the cooperative launch
     int per_sm = 0;
     cudaError_t e;
     if (plan->smem_state) {
-        if (mode == kIdentity)
-            e = cudaFuncSetAttribute(pcg_kernel<true, kIdentity>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        else
-            e = cudaFuncSetAttribute(pcg_kernel<true, kBand1>,
-                                     cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        const void *kern = mode == kIdentity ? (const void *)pcg_kernel<1, kIdentity>
+                         : mode == kBand1    ? (const void *)pcg_kernel<1, kBand1>
+                                             : (const void *)pcg_kernel<2, kChain>;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return fail(AIRGA_E_CUDA, "pcg: cannot reserve shared memory");
-        if (mode == kIdentity)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<true, kIdentity>,
-                                                              kPcgThreads, smem);
-        else
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<true, kBand1>,
-                                                              kPcgThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kPcgThreads, smem);
     } else {
         if (mode == kIdentity)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<false, kIdentity>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<0, kIdentity>,
                                                               kPcgThreads, 0);
         else if (mode == kBand1)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<false, kBand1>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<0, kBand1>,
                                                               kPcgThreads, 0);
         else
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<false, kChain>,
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pcg_kernel<0, kChain>,
                                                               kPcgThreads, 0);
     }
     if (e != cudaSuccess) return cuda_fail(e, "pcg occupancy");
@@ -411,12 +425,13 @@ cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s)
     if (plan.kind == 2 || plan.kind == 3) return launch_pcg_pair(plan, args, s);
     const int mode = mode_of(args.nf, args.psym != nullptr);
     if (plan.smem_state) {
-        if (mode == kIdentity) return launch_mode<true, kIdentity>(plan, args, s);
-        return launch_mode<true, kBand1>(plan, args, s);
+        if (mode == kIdentity) return launch_mode<1, kIdentity>(plan, args, s);
+        if (mode == kBand1) return launch_mode<1, kBand1>(plan, args, s);
+        return launch_mode<2, kChain>(plan, args, s);
     }
-    if (mode == kIdentity) return launch_mode<false, kIdentity>(plan, args, s);
-    if (mode == kBand1) return launch_mode<false, kBand1>(plan, args, s);
-    return launch_mode<false, kChain>(plan, args, s);
+    if (mode == kIdentity) return launch_mode<0, kIdentity>(plan, args, s);
+    if (mode == kBand1) return launch_mode<0, kBand1>(plan, args, s);
+    return launch_mode<0, kChain>(plan, args, s);
 }
 
 }  // namespace airga

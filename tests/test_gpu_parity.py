@@ -399,8 +399,20 @@ def test_pcg_multi_rhs_and_identity(G):
             assert abs(int(res["iters"][c]) - it_o) <= max(2, it_o // 20)
 
 
+@pytest.mark.parametrize("kind", [0, 1])
 @pytest.mark.parametrize("chain", [2, 3])
-def test_pcg_update_chain(G, chain):
+def test_pcg_update_chain(G, chain, kind):
+    """PCG with the update chain z = (C + C^T) r / 2 (Sec. 3.2), through the
+    generic kernel with r and the chain windows in shared memory (automatic,
+    kind 0) and with every window in global memory (kind 1)."""
+    G.debug_force_pcg_kernel(kind)
+    try:
+        _pcg_update_chain(G, chain)
+    finally:
+        G.debug_force_pcg_kernel(0)
+
+
+def _pcg_update_chain(G, chain):
     beam, M, K = setup_beam(G, 1237)
     shifts = W.log_shifts(-1, 4, 8)[2:2 + chain]
     As = [G.assemble_shifted(M, K, AL, BE, s) for s in shifts]
