@@ -254,6 +254,58 @@ def test_mr_residual_monotone_and_bounded_by_ls(ora):
         assert np.allclose(true, res, rtol=1e-9)
 
 
+def _random_band(ora, n, seed):
+    """Nonsymmetric, diagonally dominant band-7 CSR (structurally symmetric)."""
+    rng = np.random.default_rng(seed)
+    rp, ci = W.band_pattern(n)
+    rows = np.repeat(np.arange(n), np.diff(rp))
+    val = rng.uniform(-1.0, 1.0, ci.size)
+    val[ci == rows] = 8.0 + rng.uniform(0.0, 1.0, n)
+    return ora.CSR(n, rp, ci, val)
+
+
+@pytest.mark.parametrize("nonsym", [False, True])
+@pytest.mark.parametrize("update", [False, True])
+def test_mr_steps_are_minimal_residual_along_projected_residual(ora, update, nonsym):
+    """Each MR step of Algorithms 2/4 is fixed by two properties that do not
+    restate its formula.  The change m_{k+1} - m_k is parallel to Pi_J(r_k),
+    the current residual restricted to the column's pattern.  The new
+    residual is orthogonal to A Pi_J(r_k), i.e. minimal along that direction.
+    Both are checked on every column for the first two steps from
+    m_0 = alpha_0 e_j; the right-hand side is e_j (build) or A_old(:, j)
+    (update)."""
+    if nonsym:       # A != A^T: a transposed operand would break the pins
+        A = _random_band(ora, 24, 5)
+        A_old = _random_band(ora, 24, 6) if update else None
+    else:
+        b, A = _beamA(ora, 12, 1.3)
+        A_old = ora.shifted_csr(b, AL, BE, 0.9) if update else None
+    n = A.n
+    Ad = A.dense()
+    Bd = A_old.dense() if update else np.eye(n)
+    a0 = ora.alpha_update(A_old, A) if update else ora.alpha_build(A)
+    iters = [a0 * np.eye(n)]
+    for k in (1, 2):
+        P, steps, _, a0k = ora.spai_mr(A, tol=0.0, kmax=k, A_old=A_old)
+        assert a0k == a0 and np.all(steps == k)
+        iters.append(P.dense())
+    rows = np.repeat(np.arange(n), np.diff(A.rowptr))
+    mask = np.zeros((n, n), dtype=bool)
+    mask[rows, A.col] = True                      # column j's pattern: rows i with A(i, j) stored
+    for k in (0, 1):
+        R = Bd - Ad @ iters[k]
+        D = np.where(mask, R, 0.0)
+        W = Ad @ D
+        delta = iters[k + 1] - iters[k]
+        Rn = Bd - Ad @ iters[k + 1]
+        for j in range(n):
+            d, dj = D[:, j], delta[:, j]
+            a = (dj @ d) / (d @ d)
+            assert np.linalg.norm(dj - a * d) <= 1e-12 * np.linalg.norm(dj)
+            assert abs(Rn[:, j] @ W[:, j]) <= 1e-10 * np.linalg.norm(Rn[:, j]) * np.linalg.norm(W[:, j])
+            assert a * (R[:, j] @ W[:, j]) > 0        # the step decreases the residual
+
+
 # ---------------------------------------------------------------------------
 # PCG and the direct solve
 # ---------------------------------------------------------------------------
