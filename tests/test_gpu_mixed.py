@@ -110,3 +110,33 @@ def test_mixed_barrier_timeout_reports_status(G):
     assert float(res["true_relres"][1]) <= 1e-10
     res = solve(G, beam, 1.0, F)
     assert all(int(v) == G.OK for v in res["status"])
+
+
+def _psym_band(band, n):
+    """(P + P^T) / 2 of a band-7 factor, in the same band layout."""
+    B = band.reshape(7, n)
+    S = np.zeros_like(B)
+    for d in range(-3, 4):
+        i = np.arange(max(0, -d), min(n, n - d))
+        S[d + 3, i] = 0.5 * (B[d + 3, i] + B[3 - d, i + d])
+    return S.reshape(-1)
+
+
+def test_mixed_symmetric_read_is_bit_identical_to_full_band(G):
+    """The FP32 copy of P_sym keeps only its upper diagonals and reads the
+    lower entries from earlier rows, summing in the band order.  The same
+    matrix handed over as a plain band factor (symmetrize = 0, full 7-diagonal
+    FP32 copy) must give the same solve bit for bit."""
+    beam = W.beam(1237)
+    M, K = G.beam_mats(beam)
+    A = G.assemble_shifted(M, K, AL, BE, 0.5)
+    P = G.spai_build(A)
+    S = _psym_band(G.precond_factor(P, 0).cpu().numpy(), beam.n)
+    P2 = G.precond_from_bands([torch.from_numpy(S).cuda()])
+    F = torch.from_numpy(W.loads(beam.n)[:, 0]).cuda()
+    r1 = G.pcg_solve_mixed(A, P, F, G.options())
+    r2 = G.pcg_solve_mixed(A, P2, F, G.options(symmetrize=0))
+    torch.cuda.synchronize()
+    assert int(r1["status"][0]) == G.OK and int(r2["status"][0]) == G.OK
+    assert int(r1["inner_iters"][0]) == int(r2["inner_iters"][0])
+    assert torch.equal(r1["X"], r2["X"])

@@ -472,6 +472,28 @@ def test_pcg_deterministic(G):
     assert torch.equal(r1["X"], r2["X"]) and torch.equal(r1["iters"], r2["iters"])
 
 
+def test_pcg_symmetric_read_is_bit_identical_to_full_band(G):
+    """The CG kernel reads P_sym through its upper diagonals (lower entries
+    from earlier rows, band summation order).  The same matrix given as a
+    plain band factor with symmetrize = 0 is read in full: the solves must
+    agree bit for bit."""
+    beam, M, K = setup_beam(G, 1237)
+    A = G.assemble_shifted(M, K, AL, BE, 0.5)
+    P = G.spai_build(A)
+    n = beam.n
+    B = G.precond_factor(P, 0).cpu().numpy().reshape(7, n)
+    S = np.zeros_like(B)
+    for d in range(-3, 4):
+        i = np.arange(max(0, -d), min(n, n - d))
+        S[d + 3, i] = 0.5 * (B[d + 3, i] + B[3 - d, i + d])
+    P2 = G.precond_from_bands([torch.from_numpy(S.reshape(-1)).cuda()])
+    F = W.loads(n)[:, 0]
+    r1 = run_pcg(G, A, P, F)
+    r2 = run_pcg(G, A, P2, F, symmetrize=0)
+    assert int(r1["status"][0]) == G.OK and int(r1["iters"][0]) == int(r2["iters"][0])
+    assert torch.equal(r1["X"], r2["X"])
+
+
 def test_barrier_timeout_reports_status(G):
     """A CTA that never arrives (host-injected) makes every bounded barrier
     wait expire; the solve returns AIRGA_E_TIMEOUT and the context stays
