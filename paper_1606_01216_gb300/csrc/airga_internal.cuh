@@ -80,6 +80,10 @@ namespace airga {
 // ---------------------------------------------------------------------------
 cudaError_t launch_csr_to_band(int64_t n, const int64_t *rowptr, const int32_t *col,
                                const double *val, double *band, int32_t *flag, cudaStream_t s);
+// n even; packed: 5 n doubles, written when both flags are set
+cudaError_t launch_assemble_pack(int64_t n, const double *M, const double *K, double alpha,
+                                 double beta, double sh, double *A, double *packed, cudaStream_t s,
+                                 const int32_t *fm, const int32_t *fk, int32_t *fa);
 cudaError_t launch_assemble(int64_t n, const double *M, const double *K, double alpha,
                             double beta, double sh, double *A, cudaStream_t s,
                             const int32_t *fm = nullptr, const int32_t *fk = nullptr,

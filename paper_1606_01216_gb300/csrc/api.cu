@@ -328,14 +328,25 @@ int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, 
     std::shared_ptr<void> flag;
     st = make_buf(sizeof(int32_t), cs, &flag);
     if (st) return st;
-    AIRGA_CUDA(launch_assemble(M->n, M->band->d, K->band->d, alpha, beta, s, b->d, cs,
-                               (const int32_t *)(M->pairz ? M->pairz.get() : nullptr),
-                               (const int32_t *)(K->pairz ? K->pairz.get() : nullptr),
-                               (int32_t *)flag.get()));
+    const int32_t *fm = (const int32_t *)(M->pairz ? M->pairz.get() : nullptr);
+    const int32_t *fk = (const int32_t *)(K->pairz ? K->pairz.get() : nullptr);
+    std::shared_ptr<void> packed;
+    if (fm && fk && M->n % 2 == 0) {
+        // both inputs may be beams (decided on the device): assemble by row
+        // pairs and write the packed beam stencil the CG kernel reads
+        st = make_buf(sizeof(double) * 5 * (size_t)M->n, cs, &packed);
+        if (st) return st;
+        AIRGA_CUDA(launch_assemble_pack(M->n, M->band->d, K->band->d, alpha, beta, s, b->d,
+                                        (double *)packed.get(), cs, fm, fk, (int32_t *)flag.get()));
+    } else {
+        AIRGA_CUDA(launch_assemble(M->n, M->band->d, K->band->d, alpha, beta, s, b->d, cs, fm, fk,
+                                   (int32_t *)flag.get()));
+    }
     auto *m = new airga_mat_s;
     m->n = M->n;
     m->band = b;
     m->pairz = flag;
+    m->packed = packed;
     *A_out = m;
     return AIRGA_OK;
 }

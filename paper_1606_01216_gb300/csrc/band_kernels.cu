@@ -91,6 +91,45 @@ __global__ void assemble_kernel(int64_t total, const double *__restrict__ M,
         A[total - 1] = fma(cm, M[total - 1], ck * K[total - 1]);
 }
 
+// The same assembly by row pairs (n even), also writing the packed beam
+// nonzeros of A (layout of pack_pairs_kernel) when both inputs carry the beam
+// zero-structure flag: the CG kernel's packed stencil then needs no separate
+// packing pass over A.  Thread j owns rows (2j, 2j+1): seven double2 loads
+// of M and of K, seven double2 stores of A and, for a beam, five double2
+// stores of the packed entries (even row offsets -2,-1,0,2,3, odd row
+// -3,-2,0,1,2).
+__global__ void assemble_pack_kernel(int64_t n, const double *__restrict__ M,
+                                     const double *__restrict__ K, double cm, double ck,
+                                     double *__restrict__ A, double *__restrict__ packed,
+                                     const int32_t *fm, const int32_t *fk, int32_t *fa) {
+    const bool beam = fm && fk && *fm && *fk;
+    if (fa && blockIdx.x == 0 && threadIdx.x == 0) *fa = beam ? 1 : 0;
+    const int64_t pairs = n >> 1;
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < pairs;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        double2 a[kBand];
+#pragma unroll
+        for (int d = 0; d < kBand; ++d) {
+            const int64_t o = (int64_t)d * (n >> 1) + j;      // double2 index of rows (2j, 2j+1)
+            const double2 m = __ldcs(reinterpret_cast<const double2 *>(M) + o);
+            const double2 k = __ldcs(reinterpret_cast<const double2 *>(K) + o);
+            a[d].x = fma(cm, m.x, ck * k.x);
+            a[d].y = fma(cm, m.y, ck * k.y);
+            __stcs(reinterpret_cast<double2 *>(A) + o, a[d]);
+        }
+        if (beam) {
+            // band index = offset + 3; even row (x): 1,2,3,5,6; odd row (y): 0,1,3,4,5
+            double2 *P2 = reinterpret_cast<double2 *>(packed);
+            const int64_t h = n >> 1;
+            P2[0 * h + j] = make_double2(a[1].x, a[0].y);
+            P2[1 * h + j] = make_double2(a[2].x, a[1].y);
+            P2[2 * h + j] = make_double2(a[3].x, a[3].y);
+            P2[3 * h + j] = make_double2(a[5].x, a[4].y);
+            P2[4 * h + j] = make_double2(a[6].x, a[5].y);
+        }
+    }
+}
+
 // Beam zero structure: every row pair (2k, 2k+1) except the last has exact
 // zeros at offsets -3, +1 (even row) and +3, -1 (odd row).  `flag` arrives
 // nonzero; any violation clears it (all writers store the same 0).
@@ -310,6 +349,16 @@ __global__ void mr_alpha_final_kernel(int nblk, const double *__restrict__ parti
 cudaError_t launch_csr_to_band(int64_t n, const int64_t *rowptr, const int32_t *col,
                                const double *val, double *band, int32_t *flag, cudaStream_t s) {
     csr_to_band_kernel<<<grid_for(n), kThreads, 0, s>>>(n, rowptr, col, val, band, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_pack(int64_t n, const double *M, const double *K, double alpha,
+                                 double beta, double sh, double *A, double *packed, cudaStream_t s,
+                                 const int32_t *fm, const int32_t *fk, int32_t *fa) {
+    const double cm = sh * sh + alpha * sh;
+    const double ck = 1.0 + beta * sh;
+    assemble_pack_kernel<<<grid_for(n / 2 + 1), kThreads, 0, s>>>(n, M, K, cm, ck, A, packed, fm,
+                                                                   fk, fa);
     return cudaGetLastError();
 }
 

@@ -472,6 +472,22 @@ def test_pcg_deterministic(G):
     assert torch.equal(r1["X"], r2["X"]) and torch.equal(r1["iters"], r2["iters"])
 
 
+def test_assemble_writes_the_packed_beam_stencil(G):
+    """assemble_shifted on beam inputs also writes the packed beam nonzeros
+    the CG kernel reads (by row pairs, one pass); a matrix imported from the
+    same band has no packed copy and is packed by the CG call instead.  The
+    solves must agree bit for bit."""
+    beam, M, K = setup_beam(G, 1237)
+    A = G.assemble_shifted(M, K, AL, BE, 3.0)
+    A2 = G.mat_from_band(G.mat_to_band(A))
+    P = G.spai_build(A)
+    F = W.loads(beam.n)[:, 0]
+    r1 = run_pcg(G, A, P, F)
+    r2 = run_pcg(G, A2, P, F)
+    assert int(r1["status"][0]) == G.OK and int(r1["iters"][0]) == int(r2["iters"][0])
+    assert torch.equal(r1["X"], r2["X"])
+
+
 def test_pcg_symmetric_read_is_bit_identical_to_full_band(G):
     """The CG kernel reads P_sym through its upper diagonals (lower entries
     from earlier rows, band summation order).  The same matrix given as a
