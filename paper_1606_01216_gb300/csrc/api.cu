@@ -59,7 +59,7 @@ static int pool_for_current(cudaMemPool_t *out) {
 
 int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
-    cudaMemPool_t pool;
+    cudaMemPool_t pool = nullptr;
     int st = pool_for_current(&pool);
     if (st) return st;
     if (bytes == 0) bytes = 16;
@@ -716,7 +716,7 @@ int airga_debug_set_fault(int fault) {
 }
 
 int airga_trim(void) {
-    cudaMemPool_t pool;
+    cudaMemPool_t pool = nullptr;
     int st = pool_for_current(&pool);
     if (st) return st;
     AIRGA_CUDA(cudaMemPoolTrimTo(pool, 0));

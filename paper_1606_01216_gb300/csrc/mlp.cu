@@ -58,7 +58,6 @@ constexpr int kOffW1 = 0, kOffB1 = 1024, kOffW2 = 1088, kOffB2 = 5184, kOffW3 = 
 // W3^T [64 x 16] | W2^T [64 x 64] (backward B operands), bytes:
 constexpr int kImgW1 = 0, kImgW2 = 2048, kImgW3 = 10240, kImgW3t = 12288, kImgW2t = 14336,
               kImgFwd = 12288, kImgAll = 22528;
-constexpr int kNWeights = 6144;
 constexpr int kTile = 128;
 constexpr int kDistCap = 8;
 constexpr long long kWaitNs = 2000000000ll;   // bound on any tensor-core completion wait
