@@ -37,7 +37,7 @@ namespace {
 
 using namespace pcgdev;
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 384;
 constexpr int HR = 8, HP = 12, HZ = 4;
 constexpr int kHaloPairs = HR;   // 4 pairs of r halo on each side
 
