@@ -194,7 +194,7 @@ size_t pcg_pair_smem(int64_t R);
 size_t pcg_pair_split_smem(int64_t R);       // r and p windows only
 size_t pcg_pair_split_slice(int64_t R);      // doubles of global workspace per CTA (z/q window)
 int pcg_pair_split_occupancy(int mode, size_t smem, int *per_sm);
-int pcg_pair_threads();
+int pcg_pair_threads(int kind);   // threads per CTA of plan kind 2 or 3
 int pcg_pair_occupancy(int mode, size_t smem, int *per_sm);
 cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
 // batched node-pair kernel: systems `sys`, assignments asg (int4: system,

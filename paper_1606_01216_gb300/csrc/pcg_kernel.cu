@@ -360,7 +360,7 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
         const int kind = (forced == 3 && ok3) ? 3 : (ok2 ? 2 : (ok3 ? 3 : 0));
         if (kind) {
             plan->kind = kind;
-            plan->threads = pcg_pair_threads();
+            plan->threads = pcg_pair_threads(kind);
             plan->halo = 8;
             plan->grid = grid_p;
             plan->rows = Rp;

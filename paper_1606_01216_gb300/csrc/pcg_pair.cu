@@ -37,7 +37,11 @@ namespace {
 
 using namespace pcgdev;
 
-constexpr int kThreads = 384;
+// threads per CTA: the all-shared-memory kernel runs best at 384 (up to 168
+// registers per thread); the split-state and batched kernels, whose windows
+// partly live in L2, keep 512 warps' worth of latency hiding
+constexpr int kThreadsFull = 384, kThreadsSplit = 512, kThreadsBatch = 512;
+constexpr int kThreadsMax = 512;   // sizes the shared-memory reduction buffer
 constexpr int HR = 8, HP = 12, HZ = 4;
 constexpr int kHaloPairs = HR;   // 4 pairs of r halo on each side
 
@@ -535,7 +539,7 @@ finish:
 }
 
 template <int MODE, int SPLIT>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(SPLIT ? kThreadsSplit : kThreadsFull, 1)
 pcg_pair_kernel(PcgArgs a, int R) {
     extern __shared__ __align__(16) double smem[];
     __shared__ PairShared sh;
@@ -549,7 +553,7 @@ pcg_pair_kernel(PcgArgs a, int R) {
 // waiting at a group barrier only waits for CTAs that are at the same or an
 // earlier system in that order: the schedule cannot deadlock.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __launch_bounds__(kThreadsBatch, 1)
 pcg_pair_batch_kernel(const PcgArgs *__restrict__ sys, const int4 *__restrict__ asg,
                       const int *__restrict__ off) {
     extern __shared__ __align__(16) double smem[];
@@ -579,17 +583,17 @@ cudaError_t launch_pair_mode(const PcgPlan &plan, const PcgArgs &args, cudaStrea
 }  // namespace
 
 size_t pcg_pair_smem(int64_t R) {
-    return (size_t)(4 * R + 2 * (HR + 2 * HZ) + 2 * kHaloPairs * kBand + 3 * kThreads) *
+    return (size_t)(4 * R + 2 * (HR + 2 * HZ) + 2 * kHaloPairs * kBand + 3 * kThreadsMax) *
            sizeof(double);
 }
 
 size_t pcg_pair_split_smem(int64_t R) {
-    return (size_t)(2 * R + 2 * (HR + HZ) + 2 * kHaloPairs * kBand + 3 * kThreads) * sizeof(double);
+    return (size_t)(2 * R + 2 * (HR + HZ) + 2 * kHaloPairs * kBand + 3 * kThreadsSplit) * sizeof(double);
 }
 
 size_t pcg_pair_split_slice(int64_t R) { return (size_t)(R + 2 * HZ); }
 
-int pcg_pair_threads() { return kThreads; }
+int pcg_pair_threads(int kind) { return kind == 3 ? kThreadsSplit : kThreadsFull; }
 
 int pcg_pair_occupancy(int mode, size_t smem, int *per_sm) {
     cudaError_t e;
@@ -597,12 +601,12 @@ int pcg_pair_occupancy(int mode, size_t smem, int *per_sm) {
         e = cudaFuncSetAttribute(pcg_pair_kernel<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<0, 0>, kThreads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<0, 0>, kThreadsFull, smem);
     } else {
         e = cudaFuncSetAttribute(pcg_pair_kernel<1, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<1, 0>, kThreads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<1, 0>, kThreadsFull, smem);
     }
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg pair occupancy");
 }
@@ -617,9 +621,9 @@ int pcg_pair_batch_prepare(int mode, size_t smem) {
 
 int pcg_pair_batch_occupancy(int mode, size_t smem, int *per_sm) {
     cudaError_t e = mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_batch_kernel<1>,
-                                                                         kThreads, smem)
+                                                                         kThreadsBatch, smem)
                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_batch_kernel<0>,
-                                                                         kThreads, smem);
+                                                                         kThreadsBatch, smem);
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "batch occupancy");
 }
 
@@ -627,7 +631,7 @@ cudaError_t launch_pcg_pair_batch(int mode, int grid, size_t smem, const PcgArgs
                                   const int4 *asg, const int *off, cudaStream_t s) {
     void *kargs[] = {(void *)&sys, (void *)&asg, (void *)&off};
     const void *kern = mode ? (const void *)pcg_pair_batch_kernel<1> : (const void *)pcg_pair_batch_kernel<0>;
-    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreads), kargs, smem, s);
+    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreadsBatch), kargs, smem, s);
 }
 
 int pcg_pair_split_occupancy(int mode, size_t smem, int *per_sm) {
@@ -636,12 +640,12 @@ int pcg_pair_split_occupancy(int mode, size_t smem, int *per_sm) {
         e = cudaFuncSetAttribute(pcg_pair_kernel<0, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<0, 1>, kThreads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<0, 1>, kThreadsSplit, smem);
     } else {
         e = cudaFuncSetAttribute(pcg_pair_kernel<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<1, 1>, kThreads, smem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_kernel<1, 1>, kThreadsSplit, smem);
     }
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg pair split occupancy");
 }
