@@ -78,7 +78,7 @@ typedef struct {
     int32_t pattern_hbw;        /* SPAI pattern: band |i - j| <= pattern_hbw, 0..3 (default 3) */
     int32_t warm_start;         /* CG: nonzero = use X's content on entry as x_0 (default 0: x_0 = 0) */
     int32_t barrier_timeout_ms; /* bound on any single grid-barrier wait (default 2000) */
-    double inner_tol;           /* mixed precision: FP32 inner solve to ||r_in|| <= inner_tol ||r|| (default 1e-5) */
+    double inner_tol;           /* mixed precision: FP32 inner solve to ||r_in|| <= inner_tol ||r|| (default 3e-4) */
     int32_t max_outer;          /* mixed precision: FP64 refinement steps per column (default 12) */
 } airga_options;
 

@@ -211,7 +211,7 @@ void airga_options_default(airga_options *o) {
     o->pattern_hbw = 3;
     o->warm_start = 0;
     o->barrier_timeout_ms = 2000;
-    o->inner_tol = 1e-5;
+    o->inner_tol = 3e-4;   // fewest FP32 + FP64 iterations on the beam workloads (measured)
     o->max_outer = 12;
 }
 
