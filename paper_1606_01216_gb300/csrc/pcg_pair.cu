@@ -197,7 +197,9 @@ struct PairShared {
 // being `rank` (rows [rank R, rank R + R)).  The group's barriers, partials
 // and p boundary buffer come from `a`; the single-system kernel runs it with
 // the whole grid as the group, the batched kernel once per assignment.
-template <int MODE, int SPLIT = 0>   // MODE 0: identity, 1: one symmetric band
+// SYMU: read P_sym through its upper diagonals (pair_sym); the batched kernel
+// keeps the full-band read, which fits its registers without spills
+template <int MODE, int SPLIT = 0, bool SYMU = true>   // MODE 0: identity, 1: one symmetric band
 __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem,
                           PairShared &sh) {
     double *tot = sh.tot;
@@ -236,7 +238,7 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
     const bool packed = beam && a.Apk != nullptr;
     const double *Pb = MODE == 1 ? (a.psym ? a.psym : a.fac[0]) : nullptr;
     // P_sym is symmetric: read its upper diagonals only (rows 3n.. of the band)
-    const double *Psu = MODE == 1 && a.psym ? a.psym + 3 * (long long)n : nullptr;
+    const double *Psu = SYMU && MODE == 1 && a.psym ? a.psym + 3 * (long long)n : nullptr;
     // r-halo pairs are recomputed by the last kHaloPairs threads (they own
     // one pair fewer than the first threads when R/2 is not a multiple of nt)
     const int hslot = nt - 1 - tid;                  // 0..7 for the halo threads
@@ -562,7 +564,7 @@ pcg_pair_batch_kernel(const PcgArgs *__restrict__ sys, const int4 *__restrict__ 
     for (int k = b; k < e; ++k) {
         const int4 w = asg[k];                       // (system, group size, rank, rows per CTA)
         const PcgArgs a = sys[w.x];
-        if ((MODE == 1) == (a.nf == 1)) pair_body<MODE>(a, w.w, w.y, w.z, smem, sh);
+        if ((MODE == 1) == (a.nf == 1)) pair_body<MODE, 0, false>(a, w.w, w.y, w.z, smem, sh);
         __syncthreads();
     }
 }
