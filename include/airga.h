@@ -117,7 +117,11 @@ void airga_mat_free(airga_mat A);
 
 /* K(s) = s^2 M + s D + K with D = alpha M + beta K (Eq. 1.1; K_i of
  * Algorithms 3 and 5, Sec. 3).  M and K must have equal n.  *A_out is a new
- * handle on the same band. */
+ * handle on the same band layout.  When M and K both come from beam
+ * matrices (the Hermite-beam zero structure detected at import) and n is
+ * even, the same pass also stores the packed nonzeros the CG kernel reads
+ * (5 n doubles owned by the handle), so a later airga_pcg_solve needs no
+ * packing pass.  Asynchronous on `stream`. */
 int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, double s,
                            void *stream, airga_mat *A_out);
 
