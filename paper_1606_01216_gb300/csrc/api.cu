@@ -567,6 +567,7 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
                                   : nullptr;
     bool al = aligned16(A->band->d) && (!F || aligned16(F)) && aligned16(X) &&
               (!mband || aligned16(mband));
+    for (int f = 0; f < nf; ++f) al = al && aligned16(P->factors[f]->d);   // chain stencils: double2
     PcgPlan plan;
     st = pcg_plan(n, nf, nf == 1 && o.symmetrize, al, dev, &plan);
     if (st) return st;

@@ -63,13 +63,73 @@ __device__ __forceinline__ double stencil_t(const double *__restrict__ band, int
     return acc;
 }
 
-// z = M r on rows [lo-3, hi+3) (clipped to the matrix), written to zq.
-template <int MODE>
-__device__ void apply_precond(const PcgArgs &a, int64_t lo, int64_t hi, int H, double *rs,
-                              double *zq, double *t1, double *t2) {
+// Rows (i, i+1), i even, of (band) x and of (band)^T x from a window whose
+// out-of-matrix rows hold zeros (even n, even window base, 16-byte aligned
+// band).  Band entries are double2 loads where the pair is aligned (every
+// offset of the forward stencil; even offsets of the transposed one) and
+// scalar loads otherwise; products are summed in stencil()'s and
+// stencil_t()'s order, so each row equals the one-row form (out-of-matrix
+// terms are products with window zeros instead of skipped).
+__device__ __forceinline__ double2 stencil_pair(const double *__restrict__ band, int64_t n,
+                                                int64_t i, const double *win, int64_t wbase) {
+    double v[10];
+    const double2 *w2 = reinterpret_cast<const double2 *>(win + (i - 4 - wbase));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double2 t = w2[k];
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+    double y0 = 0.0, y1 = 0.0;
+#pragma unroll
+    for (int d = 0; d < kBand; ++d) {
+        const double2 b = __ldg(reinterpret_cast<const double2 *>(band + (int64_t)d * n + i));
+        y0 = fma(b.x, v[1 + d], y0);
+        y1 = fma(b.y, v[2 + d], y1);
+    }
+    return make_double2(y0, y1);
+}
+
+__device__ __forceinline__ double2 stencil_t_pair(const double *__restrict__ band, int64_t n,
+                                                  int64_t i, const double *win, int64_t wbase) {
+    double v[10];
+    const double2 *w2 = reinterpret_cast<const double2 *>(win + (i - 4 - wbase));
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+        const double2 t = w2[k];
+        v[2 * k] = t.x;
+        v[2 * k + 1] = t.y;
+    }
+    double y0 = 0.0, y1 = 0.0;
+#pragma unroll
+    for (int d = -kHalf; d <= kHalf; ++d) {
+        // F(i+d, i) and F(i+1+d, i+1): entries i+d and i+d+1 of band row 3-d
+        const double *p = band + (int64_t)(kHalf - d) * n + i + d;
+        double b0, b1;
+        if ((d & 1) == 0) {
+            const double2 b = __ldg(reinterpret_cast<const double2 *>(p));
+            b0 = b.x;
+            b1 = b.y;
+        } else {
+            b0 = __ldg(p);
+            b1 = __ldg(p + 1);
+        }
+        y0 = fma(b0, v[4 + d], y0);
+        y1 = fma(b1, v[5 + d], y1);
+    }
+    return make_double2(y0, y1);
+}
+
+// z = M r on rows [lo-3, hi+3) (clipped to the matrix), written to zq; the r
+// and chain windows hold row i at [i - rbase].  PAIRS: the chain stencils run
+// by row pairs over each stage's range widened to whole pairs (the extra row
+// reads only window rows inside the 2-row pad and feeds no needed row).
+template <int MODE, bool PAIRS>
+__device__ void apply_precond(const PcgArgs &a, int64_t lo, int64_t hi, int H, int64_t rbase,
+                              double *rs, double *zq, double *t1, double *t2) {
     const int64_t n = a.n;
     const int64_t zlo = lo - 3 > 0 ? lo - 3 : 0, zhi = hi + 3 < n ? hi + 3 : n;
-    const int64_t rbase = lo - H, zbase = lo - 3;
+    const int64_t zbase = lo - 3;
     if (MODE == kIdentity) {
         for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x) zq[i - zbase] = rs[i - rbase];
         return;
@@ -86,8 +146,13 @@ __device__ void apply_precond(const PcgArgs &a, int64_t lo, int64_t hi, int H, d
         const int h = H - 3 * (f + 1);
         const int64_t wlo = lo - h > 0 ? lo - h : 0, whi = hi + h < n ? hi + h : n;
         double *dst = (f & 1) ? t2 : t1;
-        for (int64_t i = wlo + threadIdx.x; i < whi; i += blockDim.x)
-            dst[i - rbase] = stencil(a.fac[f], n, i, src, rbase);
+        if (PAIRS) {
+            for (int64_t i = (wlo & ~(int64_t)1) + 2 * threadIdx.x; i < whi; i += 2 * blockDim.x)
+                *reinterpret_cast<double2 *>(dst + (i - rbase)) = stencil_pair(a.fac[f], n, i, src, rbase);
+        } else {
+            for (int64_t i = wlo + threadIdx.x; i < whi; i += blockDim.x)
+                dst[i - rbase] = stencil(a.fac[f], n, i, src, rbase);
+        }
         __syncthreads();
         src = dst;
     }
@@ -105,8 +170,13 @@ __device__ void apply_precond(const PcgArgs &a, int64_t lo, int64_t hi, int H, d
         const int h = H - 3 * (s + 1);
         const int64_t wlo = lo - h > 0 ? lo - h : 0, whi = hi + h < n ? hi + h : n;
         double *dst = (s & 1) ? t2 : t1;
-        for (int64_t i = wlo + threadIdx.x; i < whi; i += blockDim.x)
-            dst[i - rbase] = stencil_t(a.fac[f], n, i, src, rbase);
+        if (PAIRS) {
+            for (int64_t i = (wlo & ~(int64_t)1) + 2 * threadIdx.x; i < whi; i += 2 * blockDim.x)
+                *reinterpret_cast<double2 *>(dst + (i - rbase)) = stencil_t_pair(a.fac[f], n, i, src, rbase);
+        } else {
+            for (int64_t i = wlo + threadIdx.x; i < whi; i += blockDim.x)
+                dst[i - rbase] = stencil_t(a.fac[f], n, i, src, rbase);
+        }
         __syncthreads();
         src = dst;
     }
@@ -132,7 +202,11 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
     const int tid = threadIdx.x, nt = blockDim.x;
 
     // window buffers (global row i of a window with base B sits at buf[i - B])
-    const int64_t lenX = R, lenR = R + 2 * H, lenP = R + 2 * H + 6, lenZ = R + 6;
+    // chain windows in shared memory (SMEM == 2) run row-pair stencils: even
+    // base and a 2-row pad on each side, zeroed once (rows outside the
+    // matrix must read as zeros)
+    constexpr int64_t kPad = SMEM == 2 ? 2 : 0;
+    const int64_t lenX = R, lenR = R + 2 * H + 2 * kPad, lenP = R + 2 * H + 6, lenZ = R + 6;
     double *xs, *rs, *ps, *zq, *t1 = nullptr, *t2 = nullptr;
     if (SMEM == 2) {
         rs = smem;
@@ -152,7 +226,7 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
             t2 = t1 + lenR;
         }
     }
-    const int64_t xbase = lo, rbase = lo - H, pbase = lo - H - 3, zbase = lo - 3;
+    const int64_t xbase = lo, rbase = lo - H - kPad, pbase = lo - H - 3, zbase = lo - 3;
     const int64_t rlo = lo - H > 0 ? lo - H : 0, rhi = hi + H < n ? hi + H : n;
     const int64_t plo3 = lo - 3 > 0 ? lo - 3 : 0, phi3 = hi + 3 < n ? hi + 3 : n;
     const int64_t bw = (H + 3) < (hi - lo) ? (H + 3) : (hi - lo);   // boundary rows written
@@ -162,6 +236,10 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
     int status = AIRGA_E_MAXIT;
     int iters = 0;
 
+    if (SMEM == 2) {
+        for (int64_t k = tid; k < 3 * lenR; k += nt) smem[k] = 0.0;
+        __syncthreads();
+    }
     // ---- initial residual r_0 = b - A x_0 on own +- H, x_0 on own rows ----
     for (int64_t i = lo + tid; i < hi; i += nt) xs[i - xbase] = a.warm ? a.x[i] : 0.0;
     for (int64_t i = rlo + tid; i < rhi; i += nt) {
@@ -178,7 +256,7 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
         rs[i - rbase] = v;
     }
     __syncthreads();
-    apply_precond<MODE>(a, lo, hi, H, rs, zq, t1, t2);
+    apply_precond<MODE, SMEM == 2>(a, lo, hi, H, rbase, rs, zq, t1, t2);
     __syncthreads();
     {
         double v[3] = {0.0, 0.0, 0.0};
@@ -266,7 +344,7 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
                 rs[i - rbase] = fma(-alpha, stencil(a.A, n, i, ps, pbase), rs[i - rbase]);
             }
             __syncthreads();
-            apply_precond<MODE>(a, lo, hi, H, rs, zq, t1, t2);
+            apply_precond<MODE, SMEM == 2>(a, lo, hi, H, rbase, rs, zq, t1, t2);
             __syncthreads();
             double v2[2] = {0.0, 0.0};
             for (int64_t i = lo + tid; i < hi; i += nt) {
@@ -370,7 +448,11 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
             return AIRGA_OK;
         }
     }
-    const int H = mode == kIdentity ? 3 : (mode == kBand1 ? 6 : 3 + 3 * nf);
+    int H = mode == kIdentity ? 3 : (mode == kBand1 ? 6 : 3 + 3 * nf);
+    // update chains with even n and aligned operands run their stencils by row
+    // pairs in shared memory: even halo and even rows per CTA keep pairs aligned
+    const bool chain_pairs = mode == kChain && n % 2 == 0 && aligned16;
+    if (chain_pairs) H += H & 1;
     const size_t static_smem = 160 * sizeof(double) + 64;
     // grid: one CTA per SM at most (the state fills shared memory), fewer for
     // small n so that every CTA keeps at least kMinRowsPerCta rows
@@ -378,16 +460,18 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
     int grid = (int)(want < sms ? want : sms);
     if (grid < 1) grid = 1;
     int64_t R = (n + grid - 1) / grid;
+    if (chain_pairs) R += R & 1;
     // shared memory: all four windows (identity, one band), or for a chain the
-    // r, t1, t2 windows with x, p, z/q in a global slice
-    const size_t per_cta = mode == kChain ? (size_t)3 * (R + 2 * H)
+    // r, t1, t2 windows (2-row pads) with x, p, z/q in a global slice
+    const size_t per_cta = mode == kChain ? (size_t)3 * (R + 2 * H + 4)
                                           : (size_t)(R + (R + 2 * H) + (R + 2 * H + 6) + (R + 6));
     const size_t smem = per_cta * sizeof(double);
     plan->threads = kPcgThreads;
     plan->halo = H;
     plan->grid = grid;
     plan->rows = R;
-    plan->smem_state = (smem + static_smem <= (size_t)optin) && forced != 1;
+    plan->smem_state = (smem + static_smem <= (size_t)optin) && forced != 1 &&
+                       (mode != kChain || chain_pairs);
     plan->kind = plan->smem_state ? 0 : 1;
     plan->smem_bytes = plan->smem_state ? smem : 0;
     const size_t slice = (size_t)(R + (R + 2 * H) + (R + 2 * H + 6) + (R + 6) + 2 * (R + 2 * H));
