@@ -315,7 +315,10 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
         double v[3] = {v2[0], v2[1], 0.0};
         for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
             if (a.rhs_M) {
-                const double b0 = rhs_row(a, n, i), b1 = rhs_row(a, n, i + 1);
+                // b = c M v formed in the kernel: with x_0 = 0 the r_0 window
+                // already holds it (no second band product)
+                const double b0 = a.warm ? rhs_row(a, n, i) : rs[i - rbase];
+                const double b1 = a.warm ? rhs_row(a, n, i + 1) : rs[i + 1 - rbase];
                 v[2] = fma(b0, b0, fma(b1, b1, v[2]));
             } else {
                 const double2 b = *reinterpret_cast<const double2 *>(a.b + i);

@@ -631,6 +631,27 @@ def test_pcg_generic_odd_n(G, n):
     assert abs(int(res["iters"][0]) - it_o) <= 1
 
 
+def test_pcg_update_chain_odd_n(G):
+    """An update chain (Sec. 3.2) on an odd n: the chain stencils cannot run
+    by row pairs there, and the plan takes the one-row form with its windows
+    in global memory."""
+    n = 1001
+    A0o, A1o = random_spd_band(n, 11), random_spd_band(n, 12)
+    mk = lambda Ao: G.mat_from_csr(n, torch.from_numpy(Ao.rowptr).cuda(),
+                                   torch.from_numpy(Ao.col).cuda(), torch.from_numpy(Ao.val).cuda())
+    A0, A1 = mk(A0o), mk(A1o)
+    P = G.spai_update(G.spai_build(A0), A0, A1)
+    assert len(P) == 2
+    F = np.random.default_rng(2).standard_normal(n)
+    res = run_pcg(G, A1, P, F)
+    facs = [O.spai(A0o), O.spai(A1o, A_old=A0o)]
+    x_o, it_o, st_o, _ = O.pcg(A1o, F, facs, tol=1e-10, maxit=5000)
+    x = res["X"].cpu().numpy()
+    assert int(res["status"][0]) == G.OK and st_o == O.OK
+    assert np.linalg.norm(x - x_o) <= 1e-8 * np.linalg.norm(x_o)
+    assert abs(int(res["iters"][0]) - it_o) <= 1
+
+
 def test_pcg_even_n_without_beam_structure(G):
     beam = W.beam(2000)
     k_val = beam.k_val.copy()
