@@ -485,13 +485,13 @@ mixed_pair_kernel(Args32 a, int R) {
     }
 }
 
-size_t pcg32_smem(int64_t R) {
+size_t mixed_smem(int64_t R) {
     return (size_t)3 * kThreads * sizeof(double) +
            (size_t)(4 * R + 2 * (HR + 2 * HZ) + 2 * kHaloPairs * kBand) * sizeof(float);
 }
 
 template <int MODE>
-cudaError_t launch32(int grid, int64_t R, size_t smem, const Args32 &args, cudaStream_t s) {
+cudaError_t launch_mixed(int grid, int64_t R, size_t smem, const Args32 &args, cudaStream_t s) {
     auto kern = mixed_pair_kernel<MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -502,13 +502,13 @@ cudaError_t launch32(int grid, int64_t R, size_t smem, const Args32 &args, cudaS
 }
 
 template <int MODE>
-int occupancy32(size_t smem, int *per_sm) {
+int occupancy_mixed(size_t smem, int *per_sm) {
     cudaError_t e = cudaFuncSetAttribute(mixed_pair_kernel<MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, mixed_pair_kernel<MODE>, kThreads,
                                                           smem);
-    return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg32 occupancy");
+    return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "mixed-precision kernel occupancy");
 }
 
 int grid_for(int64_t work) {
@@ -556,12 +556,12 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     if (grid < 1) grid = 1;
     int64_t R = (n + grid - 1) / grid;
     R += R & 1;
-    const size_t smem = pcg32_smem(R);
+    const size_t smem = mixed_smem(R);
     if (smem + 256 > (size_t)optin)
         return fail(AIRGA_E_INVALID_ARG, "mixed solve: the FP32 state does not fit in shared memory");
     int per_sm = 0;
-    st = mode == 2 ? occupancy32<2>(smem, &per_sm)
-                   : (mode ? occupancy32<1>(smem, &per_sm) : occupancy32<0>(smem, &per_sm));
+    st = mode == 2 ? occupancy_mixed<2>(smem, &per_sm)
+                   : (mode ? occupancy_mixed<1>(smem, &per_sm) : occupancy_mixed<0>(smem, &per_sm));
     if (st) return st;
     if (per_sm < 1 || grid > per_sm * sms) return fail(AIRGA_E_INVALID_ARG, "mixed solve: grid not co-resident");
 
@@ -635,8 +635,8 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
         a.fault_skip_arrival = c == 0 ? fault : 0;
         e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
         if (e == cudaSuccess)
-            e = mode == 2 ? launch32<2>(grid, R, smem, a, s)
-                          : (mode ? launch32<1>(grid, R, smem, a, s) : launch32<0>(grid, R, smem, a, s));
+            e = mode == 2 ? launch_mixed<2>(grid, R, smem, a, s)
+                          : (mode ? launch_mixed<1>(grid, R, smem, a, s) : launch_mixed<0>(grid, R, smem, a, s));
     }
     dev_free(ws, s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed solve launch");
