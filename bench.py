@@ -21,6 +21,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -93,8 +94,9 @@ class Clocks:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % gpu_index) \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/airga_clocks_%d.csv" % os.getpid()
+        # raw samples (the summary goes into the JSON line); AIRGA_CLOCKS_DIR keeps them
+        out_dir = os.environ.get("AIRGA_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, "airga_clocks_rank%d_%d.csv" % (gpu_index, os.getpid()))
 
     def start(self):
         try:
