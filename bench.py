@@ -40,9 +40,9 @@ PCG_FLOP_PER_ROW_ITER = 40       # 20 FMA: A (7) + P_sym (7) + 3 dots + 3 axpys
 PCG_BYTES_PER_ROW_ITER = 160     # A 56 + P_sym 56 + x, r, p read+write 48
 # DRAM bytes per row and iteration of pcg_pair_kernel from one ncu capture of
 # the s = 0.1 launch on this workload (dram read + write / (229 x 1e6)) of the
-# current kernel: 147.2 MB, about one pass over the packed A, the upper half
+# current kernel: 146.7 MB, about one pass over the packed A, the upper half
 # of P_sym and the vectors; the bands stay in L2 after that
-PCG_DRAM_BYTES_PER_ROW_ITER = 0.643
+PCG_DRAM_BYTES_PER_ROW_ITER = 0.641
 SPAI_FLOP_PER_COLUMN_MODEL = 1250  # algorithmic SPAI work per column (band-7 QR + solve)
 
 
@@ -256,7 +256,7 @@ def gpu_arm(args, world, rank, local):
                           "frac": round(achieved_tf / fp64_peak, 4),
                           "traffic": round(sum(pcg_it) * n * PCG_DRAM_BYTES_PER_ROW_ITER /
                                            len(pcg_it)),
-                          "traffic_note": "ncu DRAM bytes per launch, 0.643 B/row/iter x the "
+                          "traffic_note": "ncu DRAM bytes per launch, 0.641 B/row/iter x the "
                                           "mean row-iterations of a launch",
                           "kernel": "pcg_pair_kernel (persistent row-pair PCG, FP64)",
                           "hbm_achieved_gbs": round(achieved_gbs, 1),
