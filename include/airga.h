@@ -72,7 +72,7 @@ typedef struct {
     double tol;                 /* CG stops when ||r_k||_2 <= tol ||F(:,c)||_2 (default 1e-10) */
     int32_t maxit;              /* CG iteration cap per column (default 20000) */
     int32_t spai_mode;          /* AIRGA_SPAI_QR (default) or AIRGA_SPAI_MR */
-    double mr_tol;              /* MR: stop a column when ||r|| <= mr_tol ||b_j|| (default 0.01, Sec. 5) */
+    double mr_tol;              /* MR: stop a column when ||r|| <= mr_tol (default 0.01, Sec. 5; see mr_relative) */
     int32_t mr_kmax;            /* MR: step cap per column (default 50) */
     int32_t symmetrize;         /* CG applies z = 1/2 (C + C^T) r instead of z = C r (default 1) */
     int32_t pattern_hbw;        /* SPAI pattern: band |i - j| <= pattern_hbw, 0..3 (default 3) */
@@ -80,6 +80,9 @@ typedef struct {
     int32_t barrier_timeout_ms; /* bound on any single grid-barrier wait (default 2000) */
     double inner_tol;           /* mixed precision: FP32 inner solve to ||r_in|| <= inner_tol ||r|| (default 3e-4) */
     int32_t max_outer;          /* mixed precision: FP64 refinement steps per column (default 12) */
+    int32_t mr_relative;        /* MR stop test: 0 = ||r|| <= mr_tol, the loop test of Algorithms 2 / 4
+                                   (default); 1 = ||r|| <= mr_tol ||b_j||, b_j = e_j (build) or
+                                   A_prev e_j (update) — the same for a build, scale-free for an update */
 } airga_options;
 
 void airga_options_default(airga_options *opt);
@@ -290,17 +293,20 @@ int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m
  * cudaMalloc/cudaFree or other allocating routine.
  *
  * Inputs are raw band-7 arrays instead of handles: A_band[7*n] (the shifted
- * matrix) and M_band[7*n] (the preconditioner applied as z = M r, e.g.
- * P_sym = 1/2 (P + P^T) of a SPAI; NULL = no preconditioner), all device
- * memory owned by the caller; F, X, res_hist, iters, status, true_relres and
- * the options mean the same as for airga_pcg_solve (chains of update factors
- * are not accepted here).
+ * matrix) and M_band[7*n] (the preconditioner, applied exactly as given:
+ * z = M r with all seven diagonals read, so M need not be symmetric — pass
+ * P_sym = 1/2 (P + P^T) of a SPAI to get airga_pcg_solve's default
+ * operator; NULL = no preconditioner), all device memory owned by the
+ * caller; F, X, res_hist, iters, status, true_relres and the options mean the
+ * same as for airga_pcg_solve (chains of update factors are not accepted
+ * here; opt->symmetrize is ignored).
  *
- * Its scratch is a fixed array of 8.1 MiB in the library's device image,
+ * Its scratch is a fixed array of 16.2 MiB in the library's device image,
  * which every GPU that loads the library holds until the process exits.
- * Limits: n <= 1048576 rows, and the solve state must fit in shared memory
- * (true on a GB300 up to that n); larger problems give AIRGA_E_INVALID_ARG
- * with an explanatory airga_last_error().  The first call on each device
+ * Limits: n <= 1048576 rows, and the solve must fit one of the plans that
+ * keep their windows in shared memory or in that array (true on a GB300 for
+ * every n up to the limit); larger problems give AIRGA_E_INVALID_ARG with an
+ * explanatory airga_last_error().  The first call on each device
  * looks up the array's device address (once per device, with that device
  * current); make that first call before any stream capture.  All calls share
  * the array and it keeps the previous call's contents (the barrier words are

@@ -44,7 +44,7 @@ def lib():
         L.ora_alpha_update.argtypes = [C.c_int64, ip64, dp, dp]
         L.ora_alpha_update.restype = C.c_double
         L.ora_spai_mr.argtypes = [C.c_int64, ip64, ip32, dp, dp, ip64, ip32, C.c_double,
-                                  C.c_double, C.c_int, dp, ip32, dp]
+                                  C.c_double, C.c_int, C.c_int, dp, ip32, dp]
         L.ora_spai_mr.restype = C.c_int
         L.ora_pcg.argtypes = [C.c_int64, ip64, ip32, dp, C.c_int, C.POINTER(ip64),
                               C.POINTER(ip32), C.POINTER(dp), C.c_int, dp, C.c_double, C.c_int,
@@ -177,10 +177,12 @@ def alpha_update(A_old: CSR, A_new: CSR):
     return lib().ora_alpha_update(A_new.n, _i64(A_new.rowptr), _d(A_old.val), _d(A_new.val))
 
 
-def spai_mr(A: CSR, tol=0.01, kmax=50, pattern: CSR | None = None, A_old: CSR | None = None):
+def spai_mr(A: CSR, tol=0.01, kmax=50, pattern: CSR | None = None, A_old: CSR | None = None,
+            relative: bool = False):
     """The paper's MR iteration (Algorithm 2, or Algorithm 4 when A_old is
-    given).  Returns (factor CSR, steps per column, final column residuals,
-    alpha0)."""
+    given).  A column stops when ||r|| <= tol (the paper's test), or with
+    relative=True when ||r|| <= tol ||b_j||.  Returns (factor CSR, steps per
+    column, final column residuals, alpha0)."""
     pat = pattern if pattern is not None else A
     alpha0 = alpha_build(A) if A_old is None else alpha_update(A_old, A)
     pval = np.zeros(pat.col.size)
@@ -188,7 +190,8 @@ def spai_mr(A: CSR, tol=0.01, kmax=50, pattern: CSR | None = None, A_old: CSR | 
     colres = np.empty(A.n)
     st = lib().ora_spai_mr(A.n, _i64(A.rowptr), _i32(A.col), _d(A.val),
                            _d(A_old.val) if A_old is not None else None,
-                           _i64(pat.rowptr), _i32(pat.col), alpha0, tol, kmax,
+                           _i64(pat.rowptr), _i32(pat.col), alpha0, tol,
+                           1 if relative else 0, kmax,
                            _d(pval), _i32(steps), _d(colres))
     if st != OK:
         raise RuntimeError("ora_spai_mr status %d" % st)

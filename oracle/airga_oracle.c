@@ -360,21 +360,24 @@ double ora_alpha_update(int64_t n, const int64_t *rp, const double *v_old, const
 /* Algorithm 2 (val_old == NULL) or Algorithm 4 (val_old != NULL), one sweep
  * over the columns, fixed pattern S (by columns, pcp/pcr):
  *   m = alpha0 e_j;  r = b_j - A m
- *   while ||r|| > tol ||b_j|| and k < kmax:
+ *   while ||r|| > thr and k < kmax:
  *       d = r restricted to J_j      (the paper's commented dropping rule:
  *                                     d keeps the pattern of m; the frozen
  *                                     P = alpha0 I only rescales r, which
  *                                     cancels in the step length)
  *       w = A d;  a = (r, w) / (w, w);  m = m + a d;  r = r - a w
- * The relative test ||r|| <= tol ||b_j|| equals the paper's ||r|| <= tol for
- * b_j = e_j and keeps the update scale-free.  alpha0 is ora_alpha_build or
- * ora_alpha_update.  Residuals are dense over the rows I_j (rows of A's
+ * thr = tol (relative == 0): the loop condition of Algorithms 2 and 4 as the
+ * paper writes it.  thr = tol ||b_j|| (relative != 0): a scale-free reading
+ * of the same test; both agree for b_j = e_j, and for the update (b_j =
+ * A_old e_j, norms far from 1) they differ.  The cap kmax bounds columns
+ * whose fixed-pattern residual never reaches thr.  alpha0 is ora_alpha_build
+ * or ora_alpha_update.  Residuals are dense over the rows I_j (rows of A's
  * columns in J_j together with the rows of b_j): outside them r stays b_j.
  * steps[j] receives the number of MR steps; colres[j] the final ||r||. */
 int ora_spai_mr(int64_t n, const int64_t *rp, const int32_t *ci, const double *val,
                 const double *val_old, const int64_t *pcp, const int32_t *pcr,
-                double alpha0, double tol, int kmax, double *pval, int32_t *steps,
-                double *colres)
+                double alpha0, double tol, int relative, int kmax, double *pval,
+                int32_t *steps, double *colres)
 {
     int64_t *acp = NULL, *ocp = NULL;
     int32_t *ari = NULL, *ori = NULL;
@@ -456,7 +459,7 @@ int ora_spai_mr(int64_t n, const int64_t *rp, const int32_t *ci, const double *v
                 am += Ah[q + (size_t)c * ni] * m[c];
             r[q] = bq - am;
         }
-        double thr = tol * sqrt(bb);
+        double thr = relative ? tol * sqrt(bb) : tol;
         int k = 0;
         double rn = sqrt(dot(ni, r, r));
         while (rn > thr && k < kmax) {

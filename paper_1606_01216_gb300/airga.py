@@ -54,6 +54,7 @@ class Options(C.Structure):
         ("barrier_timeout_ms", C.c_int32),
         ("inner_tol", C.c_double),
         ("max_outer", C.c_int32),
+        ("mr_relative", C.c_int32),
     ]
 
 

@@ -124,9 +124,10 @@ int mr_alpha_blocks(int64_t n);
 cudaError_t launch_spai_qr(int64_t n, int hbw, const double *A, const double *A_old, double *F,
                            double *colres, int32_t *rank_flag, const int32_t *zA,
                            const int32_t *zAold, cudaStream_t s);
-// MR mode (Algorithms 2 / 4); alpha0 read from device memory.
+// MR mode (Algorithms 2 / 4); alpha0 read from device memory.  A column
+// stops when ||r|| <= tol (relative == 0) or ||r|| <= tol ||b_j||.
 cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_old,
-                           const double *alpha0, double tol, int kmax, double *F,
+                           const double *alpha0, double tol, int relative, int kmax, double *F,
                            int32_t *steps, double *colres, cudaStream_t s);
 
 // ---------------------------------------------------------------------------

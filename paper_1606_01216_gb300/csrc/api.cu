@@ -187,7 +187,8 @@ static int spai_factor(airga_mat A, airga_mat A_old, const airga_options &o, cud
     double *partial = (double *)tmp, *alpha = partial + 2 * nblk;
     cudaError_t e = launch_mr_alpha(n, A->band->d, Aold, partial, nblk, alpha, s);
     if (e == cudaSuccess)
-        e = launch_spai_mr(n, o.pattern_hbw, A->band->d, Aold, alpha + 2, o.mr_tol, o.mr_kmax,
+        e = launch_spai_mr(n, o.pattern_hbw, A->band->d, Aold, alpha + 2, o.mr_tol,
+                           o.mr_relative ? 1 : 0, o.mr_kmax,
                            (*F)->d, (int32_t *)out->col_steps.get(), (double *)out->col_res.get(), s);
     dev_free(tmp, s);
     if (e != cudaSuccess) return cuda_fail(e, "spai MR launch");
@@ -213,6 +214,7 @@ void airga_options_default(airga_options *o) {
     o->barrier_timeout_ms = 2000;
     o->inner_tol = 3e-4;   // fewest FP32 + FP64 iterations on the beam workloads (measured)
     o->max_outer = 12;
+    o->mr_relative = 0;    // the paper's ||r|| <= tol
 }
 
 const char *airga_status_string(int s) {

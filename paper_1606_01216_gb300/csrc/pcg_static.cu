@@ -11,6 +11,8 @@
 // that loads the library.
 //
 // Scratch contents (doubles): the boundary rows of p (up to kNoallocMaxRows),
+// the per-CTA z/q window slices of the split-state plan (even n whose four
+// shared-memory windows no longer fit, from about 1.04e6 rows on 152 SMs),
 // the per-CTA reduction partials, the partials of the true residual and the
 // barrier control words.  Every call reuses the same array and it keeps the
 // previous call's contents, so the control words are cleared on the stream
@@ -28,12 +30,15 @@ constexpr int64_t kNoallocMaxRows = 1 << 20;                  // 1,048,576 rows
 constexpr int64_t kNoallocMaxCtas = 1024;
 constexpr int64_t kNoallocResidBlocks = 1216;
 constexpr int64_t kNoallocPbuf = kNoallocMaxRows;
+// split-state slices: (R + 8) doubles per CTA with R <= n / grid + 2
+constexpr int64_t kNoallocSlices = kNoallocMaxRows + 16 * kNoallocMaxCtas;
 constexpr int64_t kNoallocPartials = 2 * 4 * kNoallocMaxCtas;
 constexpr int64_t kNoallocResid = 2 * kNoallocResidBlocks;
 constexpr int64_t kNoallocCtl = 32;                           // barrier counter + abort flag, padded
-constexpr int64_t kNoallocDoubles = kNoallocPbuf + kNoallocPartials + kNoallocResid + kNoallocCtl;
+constexpr int64_t kNoallocDoubles =
+    kNoallocPbuf + kNoallocSlices + kNoallocPartials + kNoallocResid + kNoallocCtl;
 
-// 8.1 MiB, held by every GPU that loads the library until the process exits.
+// 16.2 MiB, held by every GPU that loads the library until the process exits.
 static __device__ __align__(256) double g_noalloc_scratch[kNoallocDoubles];
 
 std::mutex g_noalloc_mu;
@@ -88,9 +93,12 @@ extern "C" int airga_pcg_solve_noalloc(int64_t n, const double *A_band, const do
     const bool al = ((uintptr_t)A_band & 15u) == 0 && ((uintptr_t)F & 15u) == 0 &&
                     ((uintptr_t)X & 15u) == 0 && ((uintptr_t)M_band & 15u) == 0;
     PcgPlan plan;
-    st = pcg_plan(n, nf, nf == 1, al, dev, &plan);
+    st = pcg_plan(n, nf, false, al, dev, &plan);
     if (st) return st;
-    if (!plan.smem_state || plan.scratch_doubles != 0)
+    // every plan but the generic kernel with its whole state in global memory
+    // (kind 1) fits: shared-memory state, or the split state whose z/q slices
+    // live in the array
+    if (plan.kind == 1 || (int64_t)plan.scratch_doubles > kNoallocSlices)
         return fail(AIRGA_E_INVALID_ARG,
                     "pcg_solve_noalloc: the solve state does not fit in shared memory on this GPU");
     if (plan.grid > kNoallocMaxCtas)
@@ -104,17 +112,19 @@ extern "C" int airga_pcg_solve_noalloc(int64_t n, const double *A_band, const do
     a.n = n;
     a.A = A_band;
     a.nf = nf;
+    // the caller's band is applied as given, z = M r, by every kernel variant:
+    // a plain factor read through all seven diagonals, no symmetry assumed
     a.fac[0] = M_band;
-    a.psym = M_band;                 // the caller's band is applied as given: z = M r
-    a.symmetrize = 1;
+    a.psym = nullptr;
+    a.symmetrize = 0;
     a.tol = o.tol;
     a.maxit = o.maxit;
     a.warm = o.warm_start ? 1 : 0;
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
     a.fault_skip_arrival = 0;
     a.pbuf = scratch;
-    a.state = nullptr;
-    a.partials = scratch + kNoallocPbuf;
+    a.state = plan.scratch_doubles ? scratch + kNoallocPbuf : nullptr;
+    a.partials = scratch + kNoallocPbuf + kNoallocSlices;
     double *resid = a.partials + kNoallocPartials;
     unsigned *ctl = (unsigned *)(resid + kNoallocResid);
     a.bar = ctl;

@@ -395,7 +395,7 @@ spai_qr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
 template <int W>
 __global__ void __launch_bounds__(kThreadsSpai)
 spai_mr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
-               const double *__restrict__ alpha0p, double tol, int kmax,
+               const double *__restrict__ alpha0p, double tol, int relative, int kmax,
                double *__restrict__ F, int32_t *__restrict__ steps,
                double *__restrict__ colres) {
     constexpr int NC = 2 * W + 1;
@@ -428,8 +428,10 @@ spai_mr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
         double am = (q >= W && q <= W + 6) ? a[q][W] * alpha0 : 0.0;
         r[q] = b[q] - am;
     }
-    // stop when ||r|| <= tol ||b||, tested on squares: no square root per step
-    const double thr2 = (tol * tol) * bb;
+    // stop when ||r|| <= tol (the loop test of Algorithms 2 / 4) or, in the
+    // relative reading, ||r|| <= tol ||b_j||; tested on squares: no square
+    // root per step
+    const double thr2 = relative ? (tol * tol) * bb : tol * tol;
     double rn2 = 0.0;
 #pragma unroll
     for (int q = 0; q < NR; ++q) rn2 = fma(r[q], r[q], rn2);
@@ -513,11 +515,11 @@ cudaError_t qr_w(int64_t n, const double *A, const double *Aold, double *F, doub
 
 template <int W>
 cudaError_t mr_w(int64_t n, const double *A, const double *Aold, const double *alpha0,
-                 double tol, int kmax, double *F, int32_t *steps, double *colres,
+                 double tol, int relative, int kmax, double *F, int32_t *steps, double *colres,
                  cudaStream_t s) {
     int64_t blocks = (n + kThreadsSpai - 1) / kThreadsSpai;
-    spai_mr_kernel<W><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, alpha0, tol, kmax,
-                                                                 F, steps, colres);
+    spai_mr_kernel<W><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, Aold, alpha0, tol, relative,
+                                                                 kmax, F, steps, colres);
     return cudaGetLastError();
 }
 
@@ -535,13 +537,13 @@ cudaError_t launch_spai_qr(int64_t n, int hbw, const double *A, const double *A_
 }
 
 cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_old,
-                           const double *alpha0, double tol, int kmax, double *F,
+                           const double *alpha0, double tol, int relative, int kmax, double *F,
                            int32_t *steps, double *colres, cudaStream_t s) {
     switch (hbw) {
-        case 0: return mr_w<0>(n, A, A_old, alpha0, tol, kmax, F, steps, colres, s);
-        case 1: return mr_w<1>(n, A, A_old, alpha0, tol, kmax, F, steps, colres, s);
-        case 2: return mr_w<2>(n, A, A_old, alpha0, tol, kmax, F, steps, colres, s);
-        default: return mr_w<3>(n, A, A_old, alpha0, tol, kmax, F, steps, colres, s);
+        case 0: return mr_w<0>(n, A, A_old, alpha0, tol, relative, kmax, F, steps, colres, s);
+        case 1: return mr_w<1>(n, A, A_old, alpha0, tol, relative, kmax, F, steps, colres, s);
+        case 2: return mr_w<2>(n, A, A_old, alpha0, tol, relative, kmax, F, steps, colres, s);
+        default: return mr_w<3>(n, A, A_old, alpha0, tol, relative, kmax, F, steps, colres, s);
     }
 }
 

@@ -529,27 +529,49 @@ def test_barrier_timeout_reports_status(G):
 # MR mode (Algorithms 2 and 4)
 # ---------------------------------------------------------------------------
 
+def _near_threshold(res_a, res_b, thr):
+    """Columns whose final residual, on either side, lies within 1e-12
+    relative of the stop threshold: there rounding may move the step at
+    which ||r|| <= thr is first met, so step counts may differ by one."""
+    return (np.abs(res_a - thr) <= 1e-12 * thr) | (np.abs(res_b - thr) <= 1e-12 * thr)
+
+
+def _col_norms(A: O.CSR):
+    return np.sqrt(np.bincount(A.col, weights=A.val ** 2, minlength=A.n))
+
+
+@pytest.mark.parametrize("relative", [False, True], ids=["absolute", "relative"])
 @pytest.mark.parametrize("s", [0.5, 13.9, 373.0])
-def test_spai_mr_build_and_update(G, s):
+def test_spai_mr_build_and_update(G, s, relative):
+    """MR mode (Algorithms 2 and 4) against the oracle's step-by-step run.
+    Every column must take the oracle's number of steps and match its
+    entries to 1e-10; the only columns exempt from this are those whose final
+    residual lies within 1e-12 relative of the stop threshold (tol, or
+    tol ||b_j|| in the relative reading), where the first crossing can move
+    by one step under rounding.  Both stop tests run."""
+    tol, kmax = 0.01, 50
     beam, M, K = setup_beam(G, 700)
     A0 = G.assemble_shifted(M, K, AL, BE, s / 5.18)
     A1 = G.assemble_shifted(M, K, AL, BE, s)
-    opts = G.options(spai_mode=G.SPAI_MR, mr_tol=0.01, mr_kmax=50)
-    P = G.spai_build(A1, opts)
+    opts = G.options(spai_mode=G.SPAI_MR, mr_tol=tol, mr_kmax=kmax, mr_relative=int(relative))
     Ao0, Ao1 = O.shifted_csr(beam, AL, BE, s / 5.18), O.shifted_csr(beam, AL, BE, s)
-    Po, steps_o, res_o, a0 = O.spai_mr(Ao1, tol=0.01, kmax=50)
-    steps, colres, _ = G.precond_status(P)
-    steps = steps.cpu().numpy()
-    same = steps == steps_o
-    assert same.mean() >= 0.99
-    err = column_errors(G.precond_factor(P, 0).cpu().numpy(), Po)
-    assert err[same].max() <= 1e-10
-    Pu = G.spai_update(G.spai_build(A0), A0, A1, opts)
-    Qo, steps_uo, _, _ = O.spai_mr(Ao1, tol=0.01, kmax=50, A_old=Ao0)
-    steps_u = G.precond_status(Pu)[0].cpu().numpy()
-    same = steps_u == steps_uo
-    assert same.mean() >= 0.99
-    assert column_errors(G.precond_factor(Pu, 1).cpu().numpy(), Qo)[same].max() <= 1e-10
+    n = beam.n
+    cases = [("build", G.spai_build(A1, opts), 0, None, np.full(n, tol))]
+    thr_u = tol * _col_norms(Ao0) if relative else np.full(n, tol)
+    cases.append(("update", G.spai_update(G.spai_build(A0), A0, A1, opts), 1, Ao0, thr_u))
+    for name, P, k, A_old, thr in cases:
+        Fo, steps_o, res_o, _ = O.spai_mr(Ao1, tol=tol, kmax=kmax, A_old=A_old,
+                                          relative=relative)
+        steps, colres, _ = G.precond_status(P)
+        steps, colres = steps.cpu().numpy(), colres.cpu().numpy()
+        near = _near_threshold(res_o, colres, thr)
+        ok = ~near
+        assert np.array_equal(steps[ok], steps_o[ok]), (
+            name, int((steps[ok] != steps_o[ok]).sum()), "columns take other step counts")
+        assert np.all(np.abs(steps[near].astype(int) - steps_o[near]) <= 1)
+        err = column_errors(G.precond_factor(P, k).cpu().numpy(), Fo)
+        assert err[ok].max() <= 1e-10, (name, float(err[ok].max()))
+        np.testing.assert_allclose(colres[ok], res_o[ok], rtol=1e-9, atol=1e-14)
 
 
 # ---------------------------------------------------------------------------

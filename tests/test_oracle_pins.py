@@ -254,6 +254,60 @@ def test_mr_residual_monotone_and_bounded_by_ls(ora):
         assert np.allclose(true, res, rtol=1e-9)
 
 
+def _mr_threshold(ora, A, A_old, tol, relative):
+    """tol (Algorithms 2/4 as written) or tol ||b_j|| per column."""
+    n = A.n
+    B = A_old.dense() if A_old is not None else np.eye(n)
+    return tol * np.linalg.norm(B, axis=0) if relative else np.full(n, tol)
+
+
+@pytest.mark.parametrize("update,relative,tol", [(False, False, 0.5), (False, True, 0.5),
+                                                 (True, False, 0.02), (True, True, 0.003)])
+def test_mr_stop_test_is_the_first_crossing(ora, update, relative, tol):
+    """Algorithms 2 and 4 loop while ||r|| > tol.  A column's step count must
+    therefore be the first k at which its residual reaches the threshold:
+    the final residual is at or below it (unless the cap kmax ended the
+    column), and rerunning with kmax = steps - 1 leaves the residual above
+    it.  Checked against thresholds computed here from the definition (tol,
+    or tol ||b_j|| for the relative reading), not from the oracle."""
+    b, A = _beamA(ora, 30, 1.0)
+    A_old = ora.shifted_csr(b, AL, BE, 0.8) if update else None
+    kmax = 50
+    thr = _mr_threshold(ora, A, A_old, tol, relative)
+    P, steps, res, _ = ora.spai_mr(A, tol=tol, kmax=kmax, A_old=A_old, relative=relative)
+    done = steps < kmax
+    assert done.any() and (steps > 0).any(), "the case must exercise the stop test"
+    assert np.all(res[done] <= thr[done])
+    for k in np.unique(steps[(steps > 0)]):
+        _, st_k, res_k, _ = ora.spai_mr(A, tol=tol, kmax=int(k) - 1, A_old=A_old,
+                                        relative=relative)
+        sel = steps == k
+        assert np.all(res_k[sel] > thr[sel])
+
+
+def test_mr_absolute_and_relative_readings(ora):
+    """The paper's absolute test ||r|| <= tol and the relative reading
+    ||r|| <= tol ||b_j|| agree whenever ||b_j|| = 1, i.e. for every column of
+    the build (b_j = e_j): identical steps and entries.  For the update the
+    relative reading is invariant under scaling A_old and A_new by a power of
+    two (every operation scales exactly in FP64), while the absolute one is
+    not: scaled residuals cross a fixed tol later."""
+    b, A = _beamA(ora, 30, 1.0)
+    Ao = ora.shifted_csr(b, AL, BE, 0.8)
+    P1, s1, r1, _ = ora.spai_mr(A, tol=0.5, kmax=50, relative=False)
+    P2, s2, r2, _ = ora.spai_mr(A, tol=0.5, kmax=50, relative=True)
+    assert np.array_equal(s1, s2) and np.array_equal(P1.val, P2.val) and (s1 < 50).any()
+    c = 2.0 ** 10
+    As = ora.CSR(A.n, A.rowptr, A.col, c * A.val)
+    Aos = ora.CSR(A.n, Ao.rowptr, Ao.col, c * Ao.val)
+    Q1, q1, _, _ = ora.spai_mr(A, tol=0.003, A_old=Ao, relative=True)
+    Q2, q2, _, _ = ora.spai_mr(As, tol=0.003, A_old=Aos, relative=True)
+    assert np.array_equal(q1, q2) and np.array_equal(Q1.val, Q2.val)
+    Q3, q3, _, _ = ora.spai_mr(A, tol=0.02, A_old=Ao, relative=False)
+    Q4, q4, _, _ = ora.spai_mr(As, tol=0.02, A_old=Aos, relative=False)
+    assert np.all(q4 >= q3) and q4.sum() > q3.sum()
+
+
 def _random_band(ora, n, seed):
     """Nonsymmetric, diagonally dominant band-7 CSR (structurally symmetric)."""
     rng = np.random.default_rng(seed)
