@@ -26,8 +26,17 @@
  *   library-owned stream-ordered memory pool on the device that was current
  *   at creation; it is released on the stream that created the handle, so
  *   free a handle before destroying that stream.
- * - Matrices are stored as band-7 diagonals ("DIA"): band[(d+3)*n + i] =
- *   A(i, i+d) for d = -3..3, entries outside the matrix held as 0.
+ * - A matrix handle has one of two storages, chosen at import:
+ *   band-7 diagonals ("DIA") when every entry has |col - row| <= 3:
+ *   band[(d+3)*n + i] = A(i, i+d) for d = -3..3, entries outside the matrix
+ *   held as 0 (the fast path: node-pair CG kernels, band SPAI plans); or
+ *   general sparse CSR (rows sorted, no duplicates) otherwise.  Matrices of
+ *   the two storages mix freely in the calls below that say so (a band
+ *   operand then takes part with the pattern of its nonzero entries, so a
+ *   lumped, diagonal mass matrix stays diagonal; this view is made once per
+ *   handle and SYNCHRONISES the stream that makes it); the
+ *   mixed-precision, batched, no-alloc and learned-SPAI calls need band
+ *   storage and give AIRGA_E_UNSUPPORTED for CSR.
  * - Return value: AIRGA_OK or an AIRGA_E_* code for argument, shape, CUDA or
  *   allocation errors detected when the call is made.  Numerical outcomes of
  *   a solve (converged, iteration cap, breakdown, barrier timeout) are written
@@ -55,7 +64,7 @@ extern "C" {
 #define AIRGA_E_RANK 6          /* SPAI: a column least-squares block is rank deficient */
 #define AIRGA_E_CUDA 7          /* a CUDA runtime call failed */
 #define AIRGA_E_OOM 8           /* device allocation failed */
-#define AIRGA_E_NOT_BANDED 9    /* CSR input has an entry with |col - row| > 3 */
+#define AIRGA_E_UNSUPPORTED 9   /* operation not available for this storage (CSR where band is needed) */
 
 /* SPAI modes */
 #define AIRGA_SPAI_QR 0         /* exact fixed-pattern least squares, Householder QR */
@@ -94,19 +103,35 @@ int airga_version(void);        /* 100 * major + minor */
 /* matrices                                                                */
 /* ---------------------------------------------------------------------- */
 
-/* Import a square n x n CSR matrix (device arrays: rowptr[n+1] int64,
- * col[nnz] int32, val[nnz] double) into band-7 storage.  Duplicate entries
- * are summed.  Entries with |col - row| > 3 give AIRGA_E_NOT_BANDED, column
- * indices outside [0, n) or a malformed rowptr give AIRGA_E_INVALID_ARG.
- * SYNCHRONISES `stream` (to read back the validation flag).  n >= 1. */
+/* Import a square n x n CSR matrix (device arrays: rowptr[n+1] int64 with
+ * rowptr[0] = 0 and rowptr[n] = nnz, col[nnz] int32, val[nnz] double; the
+ * columns of a row in any order).  Duplicate entries are summed (in input
+ * order).  When every entry satisfies |col - row| <= 3 the matrix is stored
+ * as band-7 (explicit zeros inside the band kept); otherwise it is kept as
+ * general sparse CSR with the rows sorted.  Column indices outside [0, n) or
+ * malformed rowptr give AIRGA_E_INVALID_ARG.  SYNCHRONISES `stream` (to read
+ * back the validation flag and, for CSR, the sizes).  n >= 1. */
 int airga_mat_from_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
                        const double *val, void *stream, airga_mat *out);
+
+/* 1 if the matrix is stored as band-7, 0 if as general sparse CSR (or NULL). */
+int airga_mat_is_banded(airga_mat A);
+
+/* Stored entries: the CSR nnz, or for a band matrix the entries of its full
+ * band pattern inside the matrix (7 n - 12 for n >= 3). */
+int64_t airga_mat_nnz(airga_mat A);
+
+/* Copy the matrix as CSR (rows sorted): rowptr[n+1], col[nnz], val[nnz]
+ * with nnz = airga_mat_nnz(A); a band matrix is written on its full band
+ * pattern.  Any pointer may be NULL to skip that array. */
+int airga_mat_to_csr(airga_mat A, int64_t *rowptr, int32_t *col, double *val, void *stream);
 
 /* Import band-7 storage band[7*n] (layout above; entries outside the matrix
  * must be 0).  The data are copied. */
 int airga_mat_from_band(int64_t n, const double *band, void *stream, airga_mat *out);
 
-/* Copy a matrix's band-7 storage into band[7*n]. */
+/* Copy a band matrix's band-7 storage into band[7*n] (AIRGA_E_UNSUPPORTED
+ * for a CSR matrix). */
 int airga_mat_to_band(airga_mat A, double *band, void *stream);
 
 /* Rows of a matrix (0 for NULL). */
@@ -120,7 +145,11 @@ void airga_mat_free(airga_mat A);
 
 /* K(s) = s^2 M + s D + K with D = alpha M + beta K (Eq. 1.1; K_i of
  * Algorithms 3 and 5, Sec. 3).  M and K must have equal n.  *A_out is a new
- * handle on the same band layout.  When M and K both come from beam
+ * handle: band-7 when both are band matrices; otherwise CSR on the union of
+ * the two patterns (one pattern shared by every shift assembled from the
+ * same M and K; forming a new union SYNCHRONISES `stream` once, later shifts
+ * reuse it).  Each stored entry is fma(s^2 + alpha s, m, (1 + beta s) k).
+ * When M and K both come from beam
  * matrices (the Hermite-beam zero structure detected at import) and n is
  * even, the same pass also stores the packed nonzeros the CG kernel reads
  * (5 n doubles owned by the handle), so a later airga_pcg_solve needs no
@@ -128,19 +157,33 @@ void airga_mat_free(airga_mat A);
 int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, double s,
                            void *stream, airga_mat *A_out);
 
-/* Y = A X for m columns (X, Y: n x m column-major, distinct buffers). */
+/* Y = A X for m columns (X, Y: n x m column-major, distinct buffers); either
+ * storage. */
 int airga_spmv(airga_mat A, const double *X, double *Y, int32_t m, void *stream);
 
 /* SPAI of Sec. 3.1: P minimising ||I - A P||_F = sum_j ||e_j - A p_j||_2
- * (Eq. 3.1) over matrices whose column j is supported on
- * J_j = {k : |k - j| <= hbw}, hbw = opt->pattern_hbw (band-7 pattern of A for
- * hbw = 3).  opt->spai_mode selects the exact per-column least-squares
+ * (Eq. 3.1) over matrices whose column j is supported on J_j, the row
+ * indices of column j of the sparsity pattern S:
+ *   - pattern NULL: S = the pattern of A;
+ *   - pattern a matrix handle: S = its stored pattern (values unused); for
+ *     a band-7 handle, the pattern of its nonzero entries.
+ * For a band A with a band (or NULL) pattern, J_j = {k : |k - j| <= hbw},
+ * hbw = opt->pattern_hbw, and P is band-7.  Otherwise P is stored as CSR on
+ * S (pattern_hbw is not used) and each column's block is limited to
+ * |J_j| <= 32 entries and |I_j| <= 64 rows, I_j the rows of A's columns in
+ * J_j (AIRGA_E_INVALID_ARG otherwise); the row sets are computed once per
+ * pair of patterns, which SYNCHRONISES `stream` on the first build (later
+ * builds on matrices of the same pattern, e.g. every shift of one problem,
+ * reuse them).  opt->spai_mode selects the exact per-column least-squares
  * solution (Householder QR of the |I_j| x |J_j| block A(I_j, J_j)) or the
  * paper's MR iteration of Algorithm 2 (initial P = alpha I, alpha =
- * trace(A) / trace(A A^T); steps capped by opt->mr_kmax).  The new handle
- * holds P and, for CG, P_sym = 1/2 (P + P^T) on the same band.  A rank
+ * trace(A) / trace(A A^T); direction r restricted to J_j; stop test as
+ * opt->mr_relative says; steps capped by opt->mr_kmax).  The new handle
+ * holds P and, for CG, P_sym = 1/2 (P + P^T) (on S's pattern, or on its
+ * union with the transpose when S is not structurally symmetric).  A rank
  * deficient column block is reported through airga_precond_status. */
-int airga_spai_build(airga_mat A, const airga_options *opt, void *stream, airga_precond *P_out);
+int airga_spai_build(airga_mat A, airga_mat pattern, const airga_options *opt, void *stream,
+                     airga_precond *P_out);
 
 /* SPAI update of Sec. 3.2 / Algorithm 4: Q minimising
  * ||A_prev - A_next Q||_F = sum_j ||A_prev e_j - A_next q_j||_2 over the same
@@ -149,7 +192,11 @@ int airga_spai_build(airga_mat A, const airga_options *opt, void *stream, airga_
  * The new handle is the chain [P_prev's factors..., Q], i.e. the
  * preconditioner Q P_prev of Algorithm 5, applied by mat-vecs and never
  * formed.  The new handle keeps P_prev's factors alive (reference counted),
- * so P_prev may be freed at any time. */
+ * so P_prev may be freed at any time.  When A_prev, A_next and P_prev are all
+ * band-7, Q is band-7 on the band pattern of opt->pattern_hbw; otherwise Q
+ * is CSR on the pattern of A_next, A_prev must share A_next's pattern
+ * (AIRGA_E_SHAPE otherwise; matrices assembled from the same M and K do),
+ * and band factors of P_prev are carried over as CSR. */
 int airga_spai_update(airga_precond P_prev, airga_mat A_prev, airga_mat A_next,
                       const airga_options *opt, void *stream, airga_precond *P_out);
 
@@ -165,8 +212,29 @@ int32_t airga_precond_length(airga_precond P);
 int64_t airga_precond_rows(airga_precond P);
 
 /* Copy factor k (0 = the built SPAI P, k >= 1 the update factors Q in
- * order) into band[7*n]. */
+ * order) of a band-7 chain into band[7*n] (AIRGA_E_UNSUPPORTED for a CSR
+ * chain: use airga_precond_factor_csr). */
 int airga_precond_factor(airga_precond P, int32_t k, double *band, void *stream);
+
+/* 1 if the chain's factors are band-7, 0 if CSR (or NULL). */
+int airga_precond_is_banded(airga_precond P);
+
+/* Stored entries of factor k (band factors: their full band pattern). */
+int64_t airga_precond_factor_nnz(airga_precond P, int32_t k);
+
+/* Copy factor k as CSR (rows sorted): rowptr[n+1], col[nnz], val[nnz], nnz =
+ * airga_precond_factor_nnz(P, k); any pointer may be NULL. */
+int airga_precond_factor_csr(airga_precond P, int32_t k, int64_t *rowptr, int32_t *col,
+                             double *val, void *stream);
+
+/* Build a CSR chain handle from nfactors CSR matrices (host arrays of
+ * nfactors device pointers / sizes, factor 0 first; CSR arrays as for
+ * airga_mat_from_csr); the data are copied.  A single factor also gets its
+ * symmetric part for CG.  With airga_precond_factor_csr this saves and
+ * restores a CSR preconditioner.  SYNCHRONISES `stream`. */
+int airga_precond_from_csr(int64_t n, int32_t nfactors, const int64_t *nnz,
+                           const int64_t *const *rowptr, const int32_t *const *col,
+                           const double *const *val, void *stream, airga_precond *P_out);
 
 /* Build a chain handle from nfactors band-7 arrays (device pointers, each
  * 7*n doubles, factor 0 first); the data are copied.  Together with
@@ -201,7 +269,11 @@ void airga_precond_free(airga_precond P);
  * which no residual pass runs); res_hist[(maxit+1)*m] (optional, may be NULL: column c holds
  * ||r_k|| / ||f|| for k = 0..iters[c], the rest untouched).  A zero column f
  * gives x = 0, iters = 0, status OK, true_relres 0.  Uses a per-call device
- * workspace from the library pool (about 4 n doubles). */
+ * workspace from the library pool (about 4 n doubles).  Storage: a band-7 A
+ * with a band-7 (or no) preconditioner runs the band kernels; any CSR
+ * operand runs the general sparse kernel (vectors in global memory, three
+ * grid barriers per iteration and one more per further chain factor, about
+ * 9 n doubles of workspace). */
 int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
                     const airga_options *opt, double *X, double *res_hist, int32_t *iters,
                     int32_t *status, double *true_relres, void *stream);

@@ -19,7 +19,7 @@ LIB_PATH = os.path.join(HERE, "libairga.so")
 
 OK = 0
 E_INVALID_ARG, E_SHAPE, E_BREAKDOWN, E_MAXIT, E_TIMEOUT = 1, 2, 3, 4, 5
-E_RANK, E_CUDA, E_OOM, E_NOT_BANDED = 6, 7, 8, 9
+E_RANK, E_CUDA, E_OOM, E_UNSUPPORTED = 6, 7, 8, 9
 SPAI_QR, SPAI_MR = 0, 1
 
 # every symbol include/airga.h declares
@@ -35,7 +35,9 @@ EXPORTS = (
     "airga_mlp_train_options_default", "airga_mlp_create", "airga_mlp_set_params",
     "airga_mlp_get_params", "airga_mlp_status", "airga_mlp_features", "airga_mlp_forward",
     "airga_mlp_grad", "airga_mlp_train", "airga_mlp_spai", "airga_mlp_free",
-    "airga_debug_force_pcg_kernel",
+    "airga_debug_force_pcg_kernel", "airga_mat_is_banded", "airga_mat_nnz", "airga_mat_to_csr",
+    "airga_precond_is_banded", "airga_precond_factor_nnz", "airga_precond_factor_csr",
+    "airga_precond_from_csr",
 )
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
@@ -101,7 +103,15 @@ def lib():
         "airga_assemble_shifted": (C.c_int, [vp, vp, C.c_double, C.c_double, C.c_double, vp,
                                              C.POINTER(vp)]),
         "airga_spmv": (C.c_int, [vp, vp, vp, i32, vp]),
-        "airga_spai_build": (C.c_int, [vp, C.POINTER(Options), vp, C.POINTER(vp)]),
+        "airga_spai_build": (C.c_int, [vp, vp, C.POINTER(Options), vp, C.POINTER(vp)]),
+        "airga_mat_is_banded": (C.c_int, [vp]),
+        "airga_mat_nnz": (i64, [vp]),
+        "airga_mat_to_csr": (C.c_int, [vp, vp, vp, vp, vp]),
+        "airga_precond_is_banded": (C.c_int, [vp]),
+        "airga_precond_factor_nnz": (i64, [vp, i32]),
+        "airga_precond_factor_csr": (C.c_int, [vp, i32, vp, vp, vp, vp]),
+        "airga_precond_from_csr": (C.c_int, [i64, i32, C.POINTER(i64), C.POINTER(vp), C.POINTER(vp),
+                                             C.POINTER(vp), vp, C.POINTER(vp)]),
         "airga_spai_update": (C.c_int, [vp, vp, vp, C.POINTER(Options), vp, C.POINTER(vp)]),
         "airga_precond_apply": (C.c_int, [vp, vp, vp, i32, vp]),
         "airga_precond_length": (i32, [vp]),
@@ -250,6 +260,21 @@ def mat_from_band(band: torch.Tensor, stream=None) -> Mat:
     return Mat(out.value, n)
 
 
+def mat_is_banded(A: Mat) -> bool:
+    return bool(lib().airga_mat_is_banded(A.h))
+
+
+def mat_to_csr(A: Mat, stream=None):
+    """(rowptr int64, col int32, val float64) device tensors of A (rows sorted)."""
+    nnz = int(lib().airga_mat_nnz(A.h))
+    rp = torch.empty(A.n + 1, dtype=torch.int64, device="cuda")
+    ci = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+    va = torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")
+    _check(lib().airga_mat_to_csr(A.h, _ptr(rp), _ptr(ci), _ptr(va), _stream(stream)),
+           "mat_to_csr")
+    return rp, ci[:nnz], va[:nnz]
+
+
 def mat_to_band(A: Mat, stream=None) -> torch.Tensor:
     band = torch.empty(7 * A.n, dtype=torch.float64, device="cuda")
     _check(lib().airga_mat_to_band(A.h, _ptr(band), _stream(stream)), "mat_to_band")
@@ -289,9 +314,12 @@ def spmv(A: Mat, X: torch.Tensor, Y: torch.Tensor | None = None, stream=None) ->
     return Y
 
 
-def spai_build(A: Mat, opts: Options | None = None, stream=None) -> Precond:
+def spai_build(A: Mat, opts: Options | None = None, stream=None,
+               pattern: Mat | None = None) -> Precond:
+    """SPAI of A on the pattern of `pattern` (default: A's own pattern)."""
     out = C.c_void_p()
-    _check(lib().airga_spai_build(A.h, C.byref(opts) if opts else None, _stream(stream),
+    _check(lib().airga_spai_build(A.h, pattern.h if pattern is not None else None,
+                                  C.byref(opts) if opts else None, _stream(stream),
                                   C.byref(out)), "spai_build")
     return Precond(out.value, A.n)
 
@@ -319,6 +347,37 @@ def precond_factor(P: Precond, k: int, stream=None) -> torch.Tensor:
     _check(lib().airga_precond_factor(P.h, int(k), _ptr(band), _stream(stream)),
            "precond_factor")
     return band
+
+
+def precond_is_banded(P: Precond) -> bool:
+    return bool(lib().airga_precond_is_banded(P.h))
+
+
+def precond_factor_csr(P: Precond, k: int, stream=None):
+    """Factor k as (rowptr, col, val) device tensors (rows sorted)."""
+    nnz = int(lib().airga_precond_factor_nnz(P.h, int(k)))
+    rp = torch.empty(P.n + 1, dtype=torch.int64, device="cuda")
+    ci = torch.empty(max(nnz, 1), dtype=torch.int32, device="cuda")
+    va = torch.empty(max(nnz, 1), dtype=torch.float64, device="cuda")
+    _check(lib().airga_precond_factor_csr(P.h, int(k), _ptr(rp), _ptr(ci), _ptr(va),
+                                          _stream(stream)), "precond_factor_csr")
+    return rp, ci[:nnz], va[:nnz]
+
+
+def precond_from_csr(n: int, factors, stream=None) -> Precond:
+    """Chain handle from [(rowptr, col, val), ...] device tensors, factor 0 first."""
+    factors = list(factors)
+    k = len(factors)
+    for rp, ci, va in factors:
+        _ptr(rp, torch.int64), _ptr(ci, torch.int32), _ptr(va, torch.float64)
+    nnz = (C.c_int64 * k)(*[int(ci.numel()) for _, ci, _ in factors])
+    rps = (C.c_void_p * k)(*[rp.data_ptr() for rp, _, _ in factors])
+    cis = (C.c_void_p * k)(*[ci.data_ptr() for _, ci, _ in factors])
+    vas = (C.c_void_p * k)(*[va.data_ptr() for _, _, va in factors])
+    out = C.c_void_p()
+    _check(lib().airga_precond_from_csr(int(n), k, nnz, rps, cis, vas, _stream(stream),
+                                        C.byref(out)), "precond_from_csr")
+    return Precond(out.value, n)
 
 
 def precond_from_bands(bands, stream=None) -> Precond:

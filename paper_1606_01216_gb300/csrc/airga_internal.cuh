@@ -50,11 +50,51 @@ struct Band {
 using BandPtr = std::shared_ptr<Band>;
 int make_band(int64_t n, cudaStream_t s, BandPtr *out);
 
+// A sparsity pattern in CSR form together with its transpose (CSC) and the
+// map between the two, on the device; shared by every matrix and factor with
+// that structure (assemble_shifted keeps it, so the per-shift matrices of
+// one problem share one pattern).  Column indices are sorted within rows,
+// row indices within columns, no duplicates.
+struct CsrPat {
+    int64_t n = 0, nnz = 0;
+    int64_t *rowptr = nullptr;   // [n+1], rowptr[0] = 0
+    int32_t *col = nullptr;      // [nnz]
+    int64_t *colptr = nullptr;   // [n+1]
+    int32_t *rowidx = nullptr;   // [nnz]
+    int64_t *tperm = nullptr;    // [nnz]: CSR index of CSC entry f
+    int32_t max_row = 0, max_col = 0;   // longest row / column (host copies)
+    bool symmetric = false;      // structurally symmetric: CSC arrays equal the CSR arrays
+    std::shared_ptr<void> mem;   // owns the arrays
+    // symbolic SPAI data, made on the first SPAI with this pattern as the
+    // matrix: keyed by the pattern S whose columns are J_j
+    struct Rows {
+        std::weak_ptr<CsrPat> S;             // the pattern the sets belong to
+        std::shared_ptr<void> buf;           // owns iptr and irows
+        const int64_t *iptr = nullptr;       // [n+1]
+        const int32_t *irows = nullptr;      // [iptr[n]]: I_j, sorted
+        int32_t max_i = 0, max_j = 0;
+    };
+    std::vector<Rows> spai_rows;
+    // cached union patterns with other patterns (assemble_shifted of matrices
+    // with different structure; the symmetric part of a factor on a
+    // structurally nonsymmetric pattern)
+    struct Union {
+        std::weak_ptr<CsrPat> other;
+        bool other_transposed = false;
+        std::shared_ptr<CsrPat> result;
+    };
+    std::vector<Union> unions;
+};
+using CsrPatPtr = std::shared_ptr<CsrPat>;
+
 }  // namespace airga
 
 struct airga_mat_s {
     int64_t n = 0;
     airga::BandPtr band;
+    // general sparse storage (band == nullptr): pattern + values in CSR order
+    airga::CsrPatPtr csr;
+    std::shared_ptr<void> cval;          // double[csr->nnz]
     // device int32: nonzero when every row pair (2k, 2k+1) but the last has the
     // Hermite-beam zeros (even rows: offsets -3, +1; odd rows: +3, -1)
     std::shared_ptr<void> pairz;
@@ -63,10 +103,24 @@ struct airga_mat_s {
     std::shared_ptr<void> packed;
 };
 
+namespace airga {
+// One CSR factor of a preconditioner chain: pattern (with its transpose, for
+// C^T r) and values in CSR order.
+struct CsrFactor {
+    CsrPatPtr pat;
+    std::shared_ptr<void> val;
+    const double *v() const { return (const double *)val.get(); }
+};
+}  // namespace airga
+
 struct airga_precond_s {
     int64_t n = 0;
     std::vector<airga::BandPtr> factors;  // factor 0 = built P, then Q_2, Q_3, ...
     airga::BandPtr psym;                  // 1/2 (P + P^T) when factors.size() == 1
+    // general sparse chain (factors empty): CSR factors and, for a single
+    // factor, its symmetric part
+    std::vector<airga::CsrFactor> cfactors;
+    airga::CsrFactor csym;
     // per-column results of the SPAI call that made the newest factor
     std::shared_ptr<void> col_steps;      // int32[n]
     std::shared_ptr<void> col_res;        // double[n]
@@ -129,6 +183,55 @@ cudaError_t launch_spai_qr(int64_t n, int hbw, const double *A, const double *A_
 cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_old,
                            const double *alpha0, double tol, int relative, int kmax, double *F,
                            int32_t *steps, double *colres, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// general sparse storage (csr_kernels.cu, spai_csr.cu, pcg_csr.cu)
+// ---------------------------------------------------------------------------
+struct RowView;
+// canonical copy of a caller's CSR (rows sorted, duplicates summed in input
+// order) with its pattern; SYNCHRONISES s.  Arrays must be validated first.
+int csr_import(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
+               const double *val, cudaStream_t s, CsrPatPtr *pat, std::shared_ptr<void> *vals);
+// pattern of the full band |i - j| <= 3 (7 n - 12 entries for n >= 4); SYNCHRONISES s
+int band_pattern(int64_t n, cudaStream_t s, CsrPatPtr *out);
+// values of a band-7 array on band_pattern(n)
+cudaError_t launch_band_values(const CsrPat &p, const double *band, double *val, cudaStream_t s);
+// the nonzero entries of a band-7 array as CSR with its own pattern; SYNCHRONISES s
+int band_nonzero_csr(int64_t n, const double *band, cudaStream_t s, CsrPatPtr *pat,
+                     std::shared_ptr<void> *vals);
+// equal n, nnz, rowptr and col; SYNCHRONISES s (unless sizes differ)
+int csr_same_structure(const CsrPat &a, const CsrPat &b, cudaStream_t s, bool *same);
+// union of the row patterns of X and Y; SYNCHRONISES s
+int csr_union(int64_t n, const RowView &X, const RowView &Y, cudaStream_t s, CsrPatPtr *out);
+// Z = a X + b Y on Z's pattern (a superset of both), fma(a, x, b y) per entry
+cudaError_t launch_csr_add(const CsrPat &Z, double a, const RowView &X, double b,
+                           const RowView &Y, double *val, cudaStream_t s);
+cudaError_t launch_csr_spmv(int64_t n, const RowView &A, const double *X, double *Y, int32_t m,
+                            cudaStream_t s);
+int csr_blocks(int64_t n);
+// relres[c] = ||F_c - A X_c|| / ||F_c||; `partial` holds 2 * nblk * m doubles
+cudaError_t launch_csr_true_residual(int64_t n, const RowView &A, const double *X,
+                                     const double *F, int32_t m, double *relres,
+                                     double *partial, int nblk, cudaStream_t s);
+// out[0..2] as launch_mr_alpha, over the stored entries (A_old on A's pattern)
+cudaError_t launch_csr_mr_alpha(const CsrPat &p, const double *A, const double *A_old,
+                                double *partial, int nblk, double *out, cudaStream_t s);
+
+// Symbolic SPAI: the row sets I_j (rows of A's columns in J_j, J_j = column
+// j of S) of every column, cached on A's pattern (SYNCHRONISES s the first
+// time for a pattern pair).  AIRGA_E_INVALID_ARG when a column exceeds the
+// kernel's limits (|J_j| <= kSpaiMaxJ, |I_j| <= kSpaiMaxI).
+constexpr int kSpaiMaxJ = 32, kSpaiMaxI = 64;
+int csr_spai_rows(const CsrPatPtr &A, const CsrPatPtr &S, cudaStream_t s,
+                  const CsrPat::Rows **out);
+// Numeric SPAI on a general pattern, one warp per column: QR (mr == 0) or
+// the MR iteration (mr != 0; alpha0 on the device).  A_old (values on A's
+// pattern) selects the update right-hand side A_old e_j.  F: values on S's
+// pattern in CSR order.  flag bit 1: rank-deficient column block.
+cudaError_t launch_spai_csr(const CsrPat &A, const double *Av, const double *Aold,
+                            const CsrPat &S, const CsrPat::Rows &rows, int mr,
+                            const double *alpha0, double tol, int relative, int kmax, double *F,
+                            int32_t *steps, double *colres, int32_t *flag, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // persistent PCG (pcg_kernel.cu)
@@ -205,4 +308,31 @@ int pcg_pair_batch_occupancy(int mode, size_t smem, int *per_sm);
 cudaError_t launch_pcg_pair_batch(int mode, int grid, size_t smem, const PcgArgs *sys,
                                   const int4 *asg, const int *off, cudaStream_t s);
 
+}  // namespace airga
+
+namespace airga {
+// ---------------------------------------------------------------------------
+// host paths for general sparse storage (api_csr.cu)
+// ---------------------------------------------------------------------------
+int check_any(airga_mat A, const char *name);          // either storage
+int csr_check(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
+              cudaStream_t s, int32_t *hflag);          // SYNCHRONISES s
+int csr_view(airga_mat A, cudaStream_t s, CsrPatPtr *pat, const double **val);
+int mat_from_csr_general(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
+                         const double *val, cudaStream_t s, airga_mat *out);
+int assemble_general(airga_mat M, airga_mat K, double alpha, double beta, double sh,
+                     cudaStream_t s, airga_mat *A_out);
+int spmv_general(airga_mat A, const double *X, double *Y, int32_t m, cudaStream_t s);
+int true_residual_general(airga_mat A, const double *X, const double *F, int32_t m,
+                          double *relres, cudaStream_t s);
+int spai_general(airga_mat A, airga_mat A_old, airga_mat pattern, const airga_options &o,
+                 cudaStream_t s, airga_precond_s *out, CsrFactor *F);
+int csr_symmetric_part(const CsrFactor &F, cudaStream_t s, CsrFactor *out);
+int spai_update_general(airga_precond P_prev, airga_mat A_prev, airga_mat A_next,
+                        const airga_options &o, cudaStream_t s, airga_precond_s *P);
+int precond_apply_general(airga_precond P, const double *r, double *z, int symmetrize,
+                          cudaStream_t s);
+int pcg_general(airga_mat A, airga_precond P, const double *F, int32_t m, const airga_options &o,
+                double *X, double *res_hist, int32_t *iters, int32_t *status, double *relres,
+                int fault, cudaStream_t s);
 }  // namespace airga

@@ -152,8 +152,21 @@ int check_options(const airga_options *o) {
     return AIRGA_OK;
 }
 
+// a matrix in either storage
+int check_any(airga_mat A, const char *name) {
+    if (!A || (!A->band && !A->csr) || A->n < 1)
+        return fail(AIRGA_E_INVALID_ARG, std::string(name) + " is not a valid matrix");
+    return AIRGA_OK;
+}
+
+// a band-7 matrix (calls with no general sparse form)
 int check_mat(airga_mat A, const char *name) {
-    if (!A || !A->band || A->n < 1) return fail(AIRGA_E_INVALID_ARG, std::string(name) + " is not a valid matrix");
+    int st = check_any(A, name);
+    if (st) return st;
+    if (!A->band)
+        return fail(AIRGA_E_UNSUPPORTED, std::string(name) +
+                                             " is stored as a general sparse (CSR) matrix; this "
+                                             "call needs band-7 storage");
     return AIRGA_OK;
 }
 
@@ -228,7 +241,7 @@ const char *airga_status_string(int s) {
         case AIRGA_E_RANK: return "rank-deficient least-squares block";
         case AIRGA_E_CUDA: return "CUDA error";
         case AIRGA_E_OOM: return "out of device memory";
-        case AIRGA_E_NOT_BANDED: return "matrix has entries outside the band |i-j| <= 3";
+        case AIRGA_E_UNSUPPORTED: return "operation not available for this matrix storage";
         default: return "unknown status";
     }
 }
@@ -245,24 +258,27 @@ int airga_mat_from_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int3
     if (!out) return fail(AIRGA_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > (int64_t)INT32_MAX) return fail(AIRGA_E_INVALID_ARG, "n must be in [1, 2^31)");
-    if (nnz < 0 || !rowptr || (nnz > 0 && (!col || !val)))
+    if (nnz < 0 || nnz > (int64_t)INT32_MAX * 64 || !rowptr || (nnz > 0 && (!col || !val)))
         return fail(AIRGA_E_INVALID_ARG, "bad CSR arrays");
     cudaStream_t s = S(stream);
+    int32_t hflag = 0;
+    int st = csr_check(n, nnz, rowptr, col, s, &hflag);
+    if (st) return st;
+    if (hflag & 2)
+        return fail(AIRGA_E_INVALID_ARG,
+                    "CSR arrays malformed (rowptr[0] != 0, rowptr[n] != nnz, decreasing rowptr "
+                    "or a column index outside [0, n))");
+    if (hflag & 1) return mat_from_csr_general(n, nnz, rowptr, col, val, s, out);
     BandPtr b;
-    int st = make_band(n, s, &b);
+    st = make_band(n, s, &b);
     if (st) return st;
     void *flag = nullptr;
     st = dev_alloc(&flag, sizeof(int32_t), s);
     if (st) return st;
-    int32_t hflag = 0;
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) e = launch_csr_to_band(n, rowptr, col, val, b->d, (int32_t *)flag, s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hflag, flag, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     dev_free(flag, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "mat_from_csr");
-    if (hflag & 2) return fail(AIRGA_E_INVALID_ARG, "CSR column index out of range or rowptr decreasing");
-    if (hflag & 1) return fail(AIRGA_E_NOT_BANDED, "CSR entry with |col - row| > 3");
     auto *m = new airga_mat_s;
     m->n = n;
     m->band = b;
@@ -317,13 +333,14 @@ int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, 
                            void *stream, airga_mat *A_out) {
     if (!A_out) return fail(AIRGA_E_INVALID_ARG, "A_out is NULL");
     *A_out = nullptr;
-    int st = check_mat(M, "M");
-    if (!st) st = check_mat(K, "K");
+    int st = check_any(M, "M");
+    if (!st) st = check_any(K, "K");
     if (st) return st;
     if (M->n != K->n) return fail(AIRGA_E_SHAPE, "M and K differ in size");
     if (!std::isfinite(alpha) || !std::isfinite(beta) || !std::isfinite(s))
         return fail(AIRGA_E_INVALID_ARG, "alpha, beta and s must be finite");
     cudaStream_t cs = S(stream);
+    if (!M->band || !K->band) return assemble_general(M, K, alpha, beta, s, cs, A_out);
     BandPtr b;
     st = make_band(M->n, cs, &b);
     if (st) return st;
@@ -354,19 +371,23 @@ int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, 
 }
 
 int airga_spmv(airga_mat A, const double *X, double *Y, int32_t m, void *stream) {
-    int st = check_mat(A, "A");
+    int st = check_any(A, "A");
     if (st) return st;
     if (m < 0 || (m > 0 && (!X || !Y))) return fail(AIRGA_E_INVALID_ARG, "bad spmv operands");
     if (m == 0) return AIRGA_OK;
+    if (!A->band) return spmv_general(A, X, Y, m, S(stream));
     AIRGA_CUDA(launch_spmv(A->n, A->band->d, X, Y, m, S(stream)));
     return AIRGA_OK;
 }
 
-int airga_spai_build(airga_mat A, const airga_options *opt, void *stream, airga_precond *P_out) {
+int airga_spai_build(airga_mat A, airga_mat pattern, const airga_options *opt, void *stream,
+                     airga_precond *P_out) {
     if (!P_out) return fail(AIRGA_E_INVALID_ARG, "P_out is NULL");
     *P_out = nullptr;
-    int st = check_mat(A, "A");
+    int st = check_any(A, "A");
+    if (!st && pattern) st = check_any(pattern, "pattern");
     if (st) return st;
+    if (pattern && pattern->n != A->n) return fail(AIRGA_E_SHAPE, "pattern and A differ in size");
     airga_options o;
     airga_options_default(&o);
     if (opt) o = *opt;
@@ -375,6 +396,19 @@ int airga_spai_build(airga_mat A, const airga_options *opt, void *stream, airga_
     cudaStream_t s = S(stream);
     auto *P = new airga_precond_s;
     P->n = A->n;
+    if (!A->band || (pattern && !pattern->band)) {
+        // general pattern: CSR factor and its symmetric part
+        CsrFactor F;
+        st = spai_general(A, nullptr, pattern, o, s, P, &F);
+        if (!st) st = csr_symmetric_part(F, s, &P->csym);
+        if (st) {
+            delete P;
+            return st;
+        }
+        P->cfactors.push_back(F);
+        *P_out = P;
+        return AIRGA_OK;
+    }
     BandPtr F;
     st = spai_factor(A, nullptr, o, s, P, &F);
     if (!st) st = make_band(A->n, s, &P->psym);
@@ -395,13 +429,14 @@ int airga_spai_update(airga_precond P_prev, airga_mat A_prev, airga_mat A_next,
                       const airga_options *opt, void *stream, airga_precond *P_out) {
     if (!P_out) return fail(AIRGA_E_INVALID_ARG, "P_out is NULL");
     *P_out = nullptr;
-    if (!P_prev || P_prev->factors.empty()) return fail(AIRGA_E_INVALID_ARG, "P_prev is not a valid preconditioner");
-    int st = check_mat(A_prev, "A_prev");
-    if (!st) st = check_mat(A_next, "A_next");
+    if (!P_prev || (P_prev->factors.empty() && P_prev->cfactors.empty()))
+        return fail(AIRGA_E_INVALID_ARG, "P_prev is not a valid preconditioner");
+    int st = check_any(A_prev, "A_prev");
+    if (!st) st = check_any(A_next, "A_next");
     if (st) return st;
     if (A_prev->n != A_next->n || P_prev->n != A_next->n)
         return fail(AIRGA_E_SHAPE, "P_prev, A_prev and A_next differ in size");
-    if ((int)P_prev->factors.size() + 1 > kMaxChain)
+    if ((int)(P_prev->factors.size() + P_prev->cfactors.size()) + 1 > kMaxChain)
         return fail(AIRGA_E_INVALID_ARG, "preconditioner chain longer than 16 factors");
     airga_options o;
     airga_options_default(&o);
@@ -411,6 +446,15 @@ int airga_spai_update(airga_precond P_prev, airga_mat A_prev, airga_mat A_next,
     cudaStream_t s = S(stream);
     auto *P = new airga_precond_s;
     P->n = A_next->n;
+    if (P_prev->factors.empty() || !A_prev->band || !A_next->band) {
+        st = spai_update_general(P_prev, A_prev, A_next, o, s, P);
+        if (st) {
+            delete P;
+            return st;
+        }
+        *P_out = P;
+        return AIRGA_OK;
+    }
     BandPtr Q;
     st = spai_factor(A_next, A_prev, o, s, P, &Q);
     if (st) {
@@ -425,8 +469,10 @@ int airga_spai_update(airga_precond P_prev, airga_mat A_prev, airga_mat A_next,
 
 int airga_precond_apply(airga_precond P, const double *r, double *z, int32_t symmetrize,
                         void *stream) {
-    if (!P || P->factors.empty() || !r || !z) return fail(AIRGA_E_INVALID_ARG, "bad apply operands");
+    if (!P || (P->factors.empty() && P->cfactors.empty()) || !r || !z)
+        return fail(AIRGA_E_INVALID_ARG, "bad apply operands");
     cudaStream_t s = S(stream);
+    if (P->factors.empty()) return precond_apply_general(P, r, z, symmetrize, s);
     const int64_t n = P->n;
     if (P->factors.size() == 1 && symmetrize && P->psym) {
         AIRGA_CUDA(launch_band_apply(n, P->psym->d, r, z, false, s));
@@ -461,11 +507,16 @@ int airga_precond_apply(airga_precond P, const double *r, double *z, int32_t sym
     return AIRGA_OK;
 }
 
-int32_t airga_precond_length(airga_precond P) { return P ? (int32_t)P->factors.size() : 0; }
+int32_t airga_precond_length(airga_precond P) {
+    return P ? (int32_t)(P->factors.size() + P->cfactors.size()) : 0;
+}
 
 int64_t airga_precond_rows(airga_precond P) { return P ? P->n : 0; }
 
 int airga_precond_factor(airga_precond P, int32_t k, double *band, void *stream) {
+    if (P && k >= 0 && k < (int32_t)P->cfactors.size() && P->factors.empty())
+        return fail(AIRGA_E_UNSUPPORTED,
+                    "factor is stored as a general sparse matrix: use airga_precond_factor_csr");
     if (!P || k < 0 || k >= (int32_t)P->factors.size() || !band)
         return fail(AIRGA_E_INVALID_ARG, "bad factor request");
     AIRGA_CUDA(cudaMemcpyAsync(band, P->factors[k]->d, sizeof(double) * kBand * (size_t)P->n,
@@ -547,19 +598,42 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
                           const double *V, double scale, int32_t m, const airga_options *opt,
                           double *X, double *res_hist, int32_t *iters, int32_t *status,
                           double *true_relres, void *stream) {
-    int st = check_mat(A, "A");
+    int st = check_any(A, "A");
     if (st) return st;
     if (m < 0) return fail(AIRGA_E_INVALID_ARG, "m must be >= 0");
     if (m == 0) return AIRGA_OK;
     if ((!F && !V) || !X || !iters || !status || !true_relres)
         return fail(AIRGA_E_INVALID_ARG, "F (or M and V), X, iters, status and true_relres are required");
     if (Mrhs && Mrhs->n != A->n) return fail(AIRGA_E_SHAPE, "M and A differ in size");
-    if (P && (P->n != A->n || P->factors.empty())) return fail(AIRGA_E_SHAPE, "P does not match A");
+    if (P && (P->n != A->n || (P->factors.empty() && P->cfactors.empty())))
+        return fail(AIRGA_E_SHAPE, "P does not match A");
     airga_options o;
     airga_options_default(&o);
     if (opt) o = *opt;
     st = check_options(&o);
     if (st) return st;
+    if (!A->band || (P && P->factors.empty()) || (Mrhs && !Mrhs->band)) {
+        // general sparse storage somewhere: the CSR kernel (right-hand sides
+        // scale M V formed once into a temporary)
+        cudaStream_t s = S(stream);
+        double *Fmat = nullptr;
+        if (Mrhs) {
+            st = dev_alloc((void **)&Fmat, sizeof(double) * (size_t)A->n * m, s);
+            if (st) return st;
+            st = airga_spmv(Mrhs, V, Fmat, m, stream);
+            for (int32_t c = 0; c < m && !st && scale != 1.0; ++c) {
+                cudaError_t fe = launch_axpby(A->n, 0.0, Fmat + (size_t)c * A->n, scale,
+                                              Fmat + (size_t)c * A->n, s);
+                if (fe != cudaSuccess) st = cuda_fail(fe, "rhs scale");
+            }
+            F = Fmat;
+        }
+        if (!st)
+            st = pcg_general(A, P, F, m, o, X, res_hist, iters, status, true_relres,
+                             take_fault() == AIRGA_FAULT_SKIP_ARRIVAL ? 1 : 0, s);
+        if (Fmat) dev_free(Fmat, s);
+        return st;
+    }
     const int nf = P ? (int)P->factors.size() : 0;
     if (nf > kMaxChain) return fail(AIRGA_E_INVALID_ARG, "chain too long");
     int dev = 0;
@@ -680,7 +754,7 @@ int airga_pcg_solve_mv(airga_mat A, airga_precond P, airga_mat M, const double *
                        double rhs_scale, int32_t m, const airga_options *opt, double *X,
                        double *res_hist, int32_t *iters, int32_t *status, double *true_relres,
                        void *stream) {
-    int st = check_mat(M, "M");
+    int st = check_any(M, "M");
     if (st) return st;
     if (!V) return fail(AIRGA_E_INVALID_ARG, "V is required");
     if (!std::isfinite(rhs_scale)) return fail(AIRGA_E_INVALID_ARG, "rhs_scale must be finite");
@@ -690,11 +764,12 @@ int airga_pcg_solve_mv(airga_mat A, airga_precond P, airga_mat M, const double *
 
 int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m,
                         double *relres, void *stream) {
-    int st = check_mat(A, "A");
+    int st = check_any(A, "A");
     if (st) return st;
     if (m < 0 || (m > 0 && (!X || !F || !relres))) return fail(AIRGA_E_INVALID_ARG, "bad residual operands");
     if (m == 0) return AIRGA_OK;
     cudaStream_t s = S(stream);
+    if (!A->band) return true_residual_general(A, X, F, m, relres, s);
     const int nblk = true_residual_blocks(A->n);
     void *tmp = nullptr;
     st = dev_alloc(&tmp, sizeof(double) * 2 * (size_t)nblk * m, s);

@@ -173,6 +173,79 @@ def batched_beams(seed: int = 20261203, count: int = 32,
     return out
 
 
+@dataclass
+class SparseCSR:
+    """A general sparse (M, K) pair, each with its own CSR pattern."""
+    n: int
+    m_rowptr: np.ndarray
+    m_col: np.ndarray
+    m_val: np.ndarray
+    k_rowptr: np.ndarray
+    k_col: np.ndarray
+    k_val: np.ndarray
+    meta: dict = field(default_factory=dict)
+
+
+def _coo_to_csr(n, rows, cols, vals):
+    """Sorted CSR with duplicates summed (input assembly, no method arithmetic)."""
+    order = np.lexsort((cols, rows))
+    r, c, v = rows[order], cols[order], vals[order]
+    key = r.astype(np.int64) * n + c
+    first = np.ones(key.size, dtype=bool)
+    first[1:] = key[1:] != key[:-1]
+    idx = np.cumsum(first) - 1
+    val = np.zeros(int(first.sum()))
+    np.add.at(val, idx, v)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(r[first], minlength=n), out=rowptr[1:])
+    return rowptr, c[first].astype(np.int32), val
+
+
+def membrane(nx: int, ny: int, seed: int = 0, lumped_mass: bool = False,
+             permute: bool = True) -> SparseCSR:
+    """A second-order system whose matrices leave every narrow band: a square
+    membrane of nx x ny bilinear quadrilateral elements (unit size), clamped
+    along the edge x = 0, with per-element stiffness and density drawn from
+    U(0.5, 2) (seed).  Textbook element matrices of the Laplace operator,
+    K_e = [[4,-1,-2,-1],[-1,4,-1,-2],[-2,-1,4,-1],[-1,-2,-1,4]] / 6 and
+    M_e = [[4,2,1,2],[2,4,2,1],[1,2,4,2],[2,1,2,4]] / 36 (nodes counter-
+    clockwise); a 9-point pattern per free node.  lumped_mass replaces M by
+    the diagonal of its row sums (a different pattern from K).  permute
+    renumbers the free nodes by a seeded random permutation, so the
+    pattern has no band structure.  n = nx * (ny + 1)."""
+    rng = np.random.default_rng(seed)
+    ke = np.array([[4, -1, -2, -1], [-1, 4, -1, -2], [-2, -1, 4, -1], [-1, -2, -1, 4]]) / 6.0
+    me = np.array([[4, 2, 1, 2], [2, 4, 2, 1], [1, 2, 4, 2], [2, 1, 2, 4]]) / 36.0
+    # grid nodes (i, j), i = 0..nx along x, j = 0..ny; nodes with i = 0 clamped
+    free = np.arange(nx * (ny + 1))
+    perm = rng.permutation(free.size) if permute else free
+    def dof(i, j):
+        return perm[(i - 1) * (ny + 1) + j] if i > 0 else -1
+    E = rng.uniform(0.5, 2.0, (nx, ny))
+    rho = rng.uniform(0.5, 2.0, (nx, ny))
+    rows, cols, kv, mv = [], [], [], []
+    for ex in range(nx):
+        for ey in range(ny):
+            nodes = [dof(ex, ey), dof(ex + 1, ey), dof(ex + 1, ey + 1), dof(ex, ey + 1)]
+            for a in range(4):
+                for b in range(4):
+                    if nodes[a] < 0 or nodes[b] < 0:
+                        continue
+                    rows.append(nodes[a]); cols.append(nodes[b])
+                    kv.append(E[ex, ey] * ke[a, b]); mv.append(rho[ex, ey] * me[a, b])
+    n = free.size
+    rows = np.array(rows, dtype=np.int64)
+    cols = np.array(cols, dtype=np.int64)
+    krp, kci, kva = _coo_to_csr(n, rows, cols, np.array(kv))
+    mrp, mci, mva = _coo_to_csr(n, rows, cols, np.array(mv))
+    if lumped_mass:
+        diag = np.zeros(n)
+        np.add.at(diag, np.repeat(np.arange(n), np.diff(mrp)), mva)
+        mrp, mci, mva = np.arange(n + 1, dtype=np.int64), np.arange(n, dtype=np.int32), diag
+    return SparseCSR(n, mrp, mci, mva, krp, kci, kva,
+                     meta=dict(nx=nx, ny=ny, seed=seed, lumped_mass=lumped_mass))
+
+
 def cantilever_beta_l(k: int) -> float:
     """k-th root (1-based) of 1 + cos x cosh x = 0 by bisection (closed form
     used to pin the assembled M, K; not part of the method)."""

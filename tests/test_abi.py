@@ -46,7 +46,7 @@ def test_host_only_calls(G):
     assert o.tol == 1e-10 and o.maxit == 20000 and o.pattern_hbw == 3 and o.symmetrize == 1
     assert o.mr_tol == 0.01 and o.mr_kmax == 50 and o.spai_mode == G.SPAI_QR
     assert o.inner_tol == 3e-4 and o.max_outer == 12 and o.mr_relative == 0
-    assert G.status_string(G.E_NOT_BANDED).startswith("matrix has entries")
+    assert G.status_string(G.E_UNSUPPORTED).startswith("operation not available")
     assert G.status_string(1234) == "unknown status"
 
 
@@ -58,7 +58,13 @@ def test_argument_checks_need_no_gpu(G):
     assert "n must be" in G.last_error()
     assert L.airga_mat_from_csr(5, 3, None, None, None, None, C.byref(out)) == G.E_INVALID_ARG
     assert L.airga_assemble_shifted(None, None, 0.1, 1e-4, 1.0, None, C.byref(out)) == G.E_INVALID_ARG
-    assert L.airga_spai_build(None, None, None, C.byref(out)) == G.E_INVALID_ARG
+    assert L.airga_spai_build(None, None, None, None, C.byref(out)) == G.E_INVALID_ARG
+    assert L.airga_mat_to_csr(None, None, None, None, None) == G.E_INVALID_ARG
+    assert L.airga_mat_is_banded(None) == 0 and L.airga_mat_nnz(None) == 0
+    assert L.airga_precond_factor_nnz(None, 0) == 0 and L.airga_precond_is_banded(None) == 0
+    assert L.airga_precond_factor_csr(None, 0, None, None, None, None) == G.E_INVALID_ARG
+    assert L.airga_precond_from_csr(0, 1, None, None, None, None, None, C.byref(out)) \
+        == G.E_INVALID_ARG
     assert L.airga_spai_update(None, None, None, None, None, C.byref(out)) == G.E_INVALID_ARG
     assert L.airga_pcg_solve(None, None, None, 1, None, None, None, None, None, None, None) \
         == G.E_INVALID_ARG

@@ -102,9 +102,11 @@ def test_csr_import_rejects(G):
     rp = torch.tensor([0, 1, 2, 3, 4, 5, 6], dtype=torch.int64, device="cuda")
     ci = torch.tensor([0, 1, 2, 3, 4, 0], dtype=torch.int32, device="cuda")   # (5, 0): |d| = 5
     v = torch.ones(6, dtype=torch.float64, device="cuda")
+    A = G.mat_from_csr(n, rp, ci, v)            # kept as general sparse storage
+    assert not G.mat_is_banded(A)
     with pytest.raises(G.AirgaError) as e:
-        G.mat_from_csr(n, rp, ci, v)
-    assert e.value.code == G.E_NOT_BANDED
+        G.mat_to_band(A)
+    assert e.value.code == G.E_UNSUPPORTED
     ci2 = torch.tensor([0, 1, 2, 3, 4, 9], dtype=torch.int32, device="cuda")
     with pytest.raises(G.AirgaError) as e:
         G.mat_from_csr(n, rp, ci2, v)

@@ -82,3 +82,44 @@ def test_loads_and_shifts():
     assert len(batch) == 32
     assert all(5000 <= c["n_e"] <= 500000 and 4 <= len(c["shifts"]) <= 16 and c["m"] in (1, 4)
                for c in batch)
+
+
+# ---------------------------------------------------------------------------
+# general sparse inputs (membrane family)
+# ---------------------------------------------------------------------------
+
+def test_membrane_matrices_are_spd_and_not_banded():
+    w = W.membrane(6, 5, seed=3)
+    assert w.n == 6 * 6
+    Kd = np.zeros((w.n, w.n))
+    Md = np.zeros((w.n, w.n))
+    Kd[np.repeat(np.arange(w.n), np.diff(w.k_rowptr)), w.k_col] = w.k_val
+    Md[np.repeat(np.arange(w.n), np.diff(w.m_rowptr)), w.m_col] = w.m_val
+    assert np.array_equal(Kd, Kd.T) and np.array_equal(Md, Md.T)
+    assert np.linalg.eigvalsh(Kd)[0] > 0 and np.linalg.eigvalsh(Md)[0] > 0
+    rows = np.repeat(np.arange(w.n), np.diff(w.k_rowptr))
+    assert np.abs(w.k_col - rows).max() > 3                    # leaves every narrow band
+    assert np.diff(w.k_rowptr).max() <= 9                      # bilinear quads: 9-point rows
+
+
+def test_membrane_element_sums():
+    """Unpermuted grid: each stiffness row of a node away from the clamped
+    edge sums to zero (the Laplace operator annihilates constants), and the
+    consistent mass of the free nodes plus their coupling to the clamp adds
+    up to the element masses (sum of M_e entries = rho_e for a unit square)."""
+    w = W.membrane(5, 4, seed=7, permute=False)
+    rows = np.repeat(np.arange(w.n), np.diff(w.k_rowptr))
+    rsum = np.bincount(rows, weights=w.k_val, minlength=w.n)
+    ny1 = 4 + 1
+    away = np.arange(w.n) >= ny1                                 # nodes with i >= 2
+    assert np.allclose(rsum[away], 0.0, atol=1e-14)
+    lumped = W.membrane(5, 4, seed=7, permute=False, lumped_mass=True)
+    mrows = np.repeat(np.arange(w.n), np.diff(w.m_rowptr))
+    assert np.allclose(lumped.m_val, np.bincount(mrows, weights=w.m_val, minlength=w.n))
+    rng = np.random.default_rng(7)                               # unpermuted: E, then rho
+    rng.uniform(0.5, 2.0, (5, 4))
+    rho = rng.uniform(0.5, 2.0, (5, 4))
+    # elements off the clamp keep all four nodes (entries of M_e sum to 1);
+    # the clamp-side column keeps nodes 1 and 2 of each element: 12/36 of it
+    expected = rho[1:].sum() + rho[0].sum() * 12.0 / 36.0
+    assert abs(w.m_val.sum() - expected) <= 1e-13 * expected
