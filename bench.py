@@ -35,8 +35,12 @@ METRIC = "shifted-system PCG solves/s at 1e-10 rel. residual, n=1e6 beam; % HBM 
 N_E = 500_000
 SHIFTS = W.log_shifts(-1, 4, 8)
 TOL = 1e-10
-FP64_FMA_PER_CLK_SM = 2          # GB300 FP64 pipe
-PCG_FLOP_PER_ROW_ITER = 40       # 20 FMA: A (7) + P_sym (7) + 3 dots + 3 axpys
+FP64_FMA_PER_CLK_SM = 2          # GB300 FP64 pipe (nominal; the bench measures it)
+# FP64 work the PCG kernel issues per row and iteration: 18 FMA = A's five
+# beam nonzeros + P_sym's seven + 3 dots + 3 axpys (the survey's 20-FMA model
+# counts A's two structural zeros too)
+PCG_FLOP_PER_ROW_ITER = 36
+PCG_FLOP_PER_ROW_ITER_MODEL = 40
 PCG_BYTES_PER_ROW_ITER = 160     # A 56 + P_sym 56 + x, r, p read+write 48
 # DRAM bytes per row and iteration of pcg_pair_kernel from one ncu capture of
 # the s = 0.1 launch on this workload (dram read + write / (229 x 1e6)) of the
@@ -57,6 +61,23 @@ def peaks():
     else:
         p["sm_max_mhz"] = 2070.0
     return p
+
+
+def fp64_peak(G, sm_max_mhz, sms=152):
+    """FP64 roofline: SMs x measured FMAs per SM clock x 2 flop x max SM clock.
+    The per-clock rate comes from the library's cycle-counter probe (best of
+    three), so the peak follows the recipe's unit-count x clock form with the
+    unit count measured on this GPU."""
+    best = None
+    for _ in range(3):
+        f, tf, ms = G.probe_fp64_rate(1 << 15)
+        if best is None or f > best[0]:
+            best = (f, tf, ms)
+    f, tf, ms = best
+    return {"tflops": sms * f * 2 * sm_max_mhz * 1e6 / 1e12, "fma_per_clk_sm": round(f, 4),
+            "probe_tflops_at_run_clock": round(tf, 4), "probe_ms": round(ms, 3),
+            "source": "derived: 152 SMs x %.3f FP64 FMA/clk/SM (measured, cycle counters) x 2 "
+                      "flop x %.0f MHz" % (f, sm_max_mhz)}
 
 
 def dist_env():
@@ -220,12 +241,13 @@ def gpu_arm(args, world, rank, local):
     flops = sum(pcg_it) * n * PCG_FLOP_PER_ROW_ITER
     byts = sum(pcg_it) * n * PCG_BYTES_PER_ROW_ITER
     pk = peaks()
-    fp64_peak = 152 * FP64_FMA_PER_CLK_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12   # TFLOP/s
+    f64 = fp64_peak(G, pk["sm_max_mhz"])
+    fp64_peak_tf = f64["tflops"]
     achieved_tf = flops / (tot_ms * 1e-3) / 1e12
     achieved_gbs = byts / (tot_ms * 1e-3) / 1e9
 
-    # per-shift split of one step (untimed diagnostics)
-    detail = None if args.profile else split_timings(G, torch, M, K, F, opts, stream)
+    # per-shift split of one step and the method's arms (untimed diagnostics)
+    detail = None if args.profile else method_arms(G, torch, stream, M, K, F, SHIFTS, opts)
     # the survey's solves/s counts PCG time only, SPAI reported beside it
     pcg_step_ms = tot_ms / max(1, args.steps)
     pcg_only = {"solves_per_s": round(len(SHIFTS) / (pcg_step_ms * 1e-3), 3),
@@ -236,14 +258,15 @@ def gpu_arm(args, world, rank, local):
         pcg_only["spai_build"] = {
             "ms_median": round(spai_ms, 4),
             "gflops_model": round(model_gf, 1),
-            "frac_fp64_peak_model": round(model_gf / (fp64_peak * 1e3), 4),
+            "frac_fp64_peak_model": round(model_gf / (fp64_peak_tf * 1e3), 4),
             "model": "1.25 kflop per column (Householder QR of the 12x7 block + solve, full "
                      "band); the kernel issues fewer (structural zeros skipped)"}
     forms = None
     if not args.profile and not args.no_forms:
         del M, K
-        makers = {"precision": precision_form, "batching": batching_form,
-                  "learned": learned_form, "inner_loop": inner_loop_form}
+        makers = {"c1": c1_form, "c2": c2_form, "precision": precision_form,
+                  "batching": batching_form, "learned": learned_form,
+                  "inner_loop": inner_loop_form}
         forms = {k: makers[k](G, torch, stream) for k in args.forms.split(",") if k}
 
     # end to end through the public API with host buffers
@@ -252,8 +275,12 @@ def gpu_arm(args, world, rank, local):
     return dict(ms=ms, iters=iters, status=status, relres=relres, ok=ok, clocks=ck,
                 launches=launches_per_step * args.steps, n=n,
                 roofline={"bound": "alu", "achieved": round(achieved_tf, 4),
-                          "peak": round(fp64_peak, 4), "unit": "TFLOP/s",
-                          "frac": round(achieved_tf / fp64_peak, 4),
+                          "peak": round(fp64_peak_tf, 4), "unit": "TFLOP/s",
+                          "frac": round(achieved_tf / fp64_peak_tf, 4),
+                          "flop_per_row_iter": PCG_FLOP_PER_ROW_ITER,
+                          "frac_20fma_model": round(achieved_tf * PCG_FLOP_PER_ROW_ITER_MODEL /
+                                                    PCG_FLOP_PER_ROW_ITER / fp64_peak_tf, 4),
+                          "fp64_probe": f64,
                           "traffic": round(sum(pcg_it) * n * PCG_DRAM_BYTES_PER_ROW_ITER /
                                            len(pcg_it)),
                           "traffic_note": "ncu DRAM bytes per launch, 0.641 B/row/iter x the "
@@ -262,14 +289,22 @@ def gpu_arm(args, world, rank, local):
                           "hbm_achieved_gbs": round(achieved_gbs, 1),
                           "hbm_peak_gbs": pk["hbm_gbs"],
                           "hbm_frac": round(achieved_gbs / pk["hbm_gbs"], 4),
-                          "peak_source": "derived: 152 SMs x 2 FP64 FMA/clk x 2 flop x %.0f MHz"
-                                         % pk["sm_max_mhz"]},
+                          "peak_source": f64["source"]},
                 detail=detail, e2e=e2e, dist=dist, forms=forms, pcg_only=pcg_only)
 
 
-def split_timings(G, torch, M, K, F, opts, stream):
-    """Per-phase device times of one pass (assemble / SPAI build / PCG), the
-    SPAI-update arm and the MR arm (paper's Algorithms 2 / 4)."""
+def method_arms(G, torch, stream, M, K, F, shifts, opts):
+    """The paper's comparison on one beam and shift list (Tables 2-5 and 8):
+      rebuild      assemble -> SPAI (QR) -> PCG per shift;
+      update_qr    the exact-LS update Q of Sec. 3.2 from the previous shift,
+                   chained (Algorithm 5, horizontal);
+      mr_absolute  the paper's MR iteration (Algorithms 2 / 4) stopping at
+                   ||r|| <= tol = 0.01 per column, as the algorithms state;
+      mr_relative  the same with ||r|| <= tol ||b_j||.
+    An update arm's CG run is capped at 2 x (previous iterations) + 20; past
+    the cap the shift falls back to a fresh build (time of both counted) and
+    the chain restarts there.  Every phase is timed on the device (CUDA
+    events); totals are preconditioner + CG time, as in Table 8."""
     def timed(fn):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -279,61 +314,113 @@ def split_timings(G, torch, M, K, F, opts, stream):
         torch.cuda.synchronize()
         return out, e0.elapsed_time(e1)
 
+    n = M.n
+    As = []
     rows = []
-    for s in SHIFTS:
+    for s in shifts:
         A, ta = timed(lambda: G.assemble_shifted(M, K, W.ALPHA, W.BETA, s))
         P, tb = timed(lambda: G.spai_build(A))
         r, tc = timed(lambda: G.pcg_solve(A, P, F, opts))
-        rows.append(dict(s=float(s), assemble_ms=round(ta, 4), spai_ms=round(tb, 4),
-                         pcg_ms=round(tc, 4), iters=int(r["iters"][0])))
-    # SPAI update arm (Algorithm 5, horizontal): P_1 built, then Q_i from the
-    # previous shift.  An update solve is capped at 2 x (previous iterations)
-    # + 20; if it does not converge within that the shift falls back to a
-    # fresh SPAI (time of both counted) and the chain restarts there.
-    upd = []
-    A_prev, P_prev, it_prev = None, None, None
-    for s in SHIFTS:
-        A, _ = timed(lambda: G.assemble_shifted(M, K, W.ALPHA, W.BETA, s))
-        tot_pc, tot_cg, kind = 0.0, 0.0, "build"
-        if P_prev is not None:
-            P, tb = timed(lambda: G.spai_update(P_prev, A_prev, A))
-            cap = G.options(tol=TOL, maxit=2 * it_prev + 20)
-            r, tc = timed(lambda: G.pcg_solve(A, P, F, cap))
-            tot_pc, tot_cg, kind = tb, tc, "update"
-            if int(r["status"][0]) != G.OK:
-                kind = "update->rebuild"
-                P = None
-        else:
-            P = None
-        if P is None:
-            P, tb = timed(lambda: G.spai_build(A))
-            r, tc = timed(lambda: G.pcg_solve(A, P, F, opts))
-            tot_pc += tb
-            tot_cg += tc
         it = int(r["iters"][0])
-        upd.append(dict(s=float(s), kind=kind, chain=len(P), precond_ms=round(tot_pc, 4),
-                        pcg_ms=round(tot_cg, 4), iters=it, status=int(r["status"][0])))
-        P_prev, A_prev, it_prev = P, A, it
-    upd_ms = sum(u["precond_ms"] + u["pcg_ms"] for u in upd)
+        rows.append(dict(s=float(s), assemble_ms=round(ta, 4), spai_ms=round(tb, 4),
+                         pcg_ms=round(tc, 4), iters=it, status=int(r["status"][0]),
+                         hbm_gbs=round(it * n * PCG_BYTES_PER_ROW_ITER / (tc * 1e-3) / 1e9, 1)))
+        As.append(A)
+
+    def chain_arm(build_opts, upd_opts):
+        out, steps_b, steps_u = [], [], []
+        A_prev, P_prev, it_prev = None, None, None
+        for s, A in zip(shifts, As):
+            tot_pc, tot_cg, kind, r = 0.0, 0.0, "build", None
+            upd_steps = None
+            if P_prev is not None:
+                P, tb = timed(lambda: G.spai_update(P_prev, A_prev, A, upd_opts))
+                upd_steps = G.precond_status(P)[0].double().mean().item()
+                cap = G.options(tol=TOL, maxit=2 * it_prev + 20)
+                r, tc = timed(lambda: G.pcg_solve(A, P, F, cap))
+                tot_pc, tot_cg, kind = tb, tc, "update"
+                if int(r["status"][0]) != G.OK:
+                    kind, P = "update->rebuild", None
+            else:
+                P = None
+            build_steps = None
+            if P is None:
+                P, tb = timed(lambda: G.spai_build(A, build_opts))
+                build_steps = G.precond_status(P)[0].double().mean().item()
+                r, tc = timed(lambda: G.pcg_solve(A, P, F, opts))
+                tot_pc += tb
+                tot_cg += tc
+            it = int(r["iters"][0])
+            row = dict(s=float(s), kind=kind, chain=len(P), precond_ms=round(tot_pc, 4),
+                       pcg_ms=round(tot_cg, 4), iters=it, status=int(r["status"][0]))
+            if upd_steps is not None:
+                row["update_steps_mean"] = round(upd_steps, 2)
+                steps_u.append(upd_steps)
+            if build_steps is not None:
+                row["build_steps_mean"] = round(build_steps, 2)
+                steps_b.append(build_steps)
+            out.append(row)
+            P_prev, A_prev, it_prev = P, A, it
+        tot = sum(u["precond_ms"] + u["pcg_ms"] for u in out)
+        return dict(per_shift=out, precond_plus_cg_ms=round(tot, 3),
+                    solves_per_s=round(sum(u["status"] == G.OK for u in out) / (tot * 1e-3), 2))
+
+    def mr_arm(relative):
+        mo = G.options(spai_mode=G.SPAI_MR, mr_tol=0.01, mr_kmax=50, mr_relative=int(relative))
+        # builds at every shift (the rebuild side of Tables 4/5) ...
+        builds = []
+        for s, A in zip(shifts, As):
+            P, tb = timed(lambda: G.spai_build(A, mo))
+            st = G.precond_status(P)[0]
+            r, tc = timed(lambda: G.pcg_solve(A, P, F, opts))
+            builds.append(dict(s=float(s), build_ms=round(tb, 4),
+                               build_steps_mean=round(st.double().mean().item(), 2),
+                               capped_columns=int((st >= 50).sum()), pcg_ms=round(tc, 4),
+                               iters=int(r["iters"][0]), status=int(r["status"][0])))
+        # ... and the update chain with MR factors (the update side)
+        chain = chain_arm(mo, mo)
+        tot_b = sum(b["build_ms"] + b["pcg_ms"] for b in builds)
+        return dict(stop_test="||r|| <= 0.01 ||b_j||" if relative else "||r|| <= 0.01",
+                    build=builds, build_precond_plus_cg_ms=round(tot_b, 3), update=chain)
+
+    upd = chain_arm(None, None)
     reb_ms = sum(u["spai_ms"] + u["pcg_ms"] for u in rows)
-    # MR arm: the paper's iteration, build vs update (Tables 4/5 analogue)
-    mr = []
-    mo = G.options(spai_mode=G.SPAI_MR, mr_tol=0.01, mr_kmax=50)
-    A_prev = None
-    for s in SHIFTS:
-        A, _ = timed(lambda: G.assemble_shifted(M, K, W.ALPHA, W.BETA, s))
-        P, tb = timed(lambda: G.spai_build(A, mo))
-        steps_b = G.precond_status(P)[0].double().mean().item()
-        row = dict(s=float(s), build_ms=round(tb, 4), build_steps_mean=round(steps_b, 2))
-        if A_prev is not None:
-            Q, tu = timed(lambda: G.spai_update(P, A_prev, A, mo))
-            row.update(update_ms=round(tu, 4),
-                       update_steps_mean=round(G.precond_status(Q)[0].double().mean().item(), 2))
-        mr.append(row)
-        A_prev = A
-    return dict(rebuild=rows, update_arm=upd, mr_arm=mr,
+    pcg_ms = sum(u["pcg_ms"] for u in rows)
+    its = sum(u["iters"] for u in rows)
+    return dict(n=n, shifts=[float(s) for s in shifts], rebuild=rows,
                 rebuild_precond_plus_cg_ms=round(reb_ms, 3),
-                update_precond_plus_cg_ms=round(upd_ms, 3))
+                rebuild_pcg_solves_per_s=round(len(shifts) / (pcg_ms * 1e-3), 2),
+                rebuild_hbm_gbs=round(its * n * PCG_BYTES_PER_ROW_ITER / (pcg_ms * 1e-3) / 1e9, 1),
+                update_qr=upd, mr_absolute=mr_arm(False), mr_relative=mr_arm(True))
+
+
+def _plain_config_form(G, torch, stream, n_e, shifts, note):
+    beam = W.beam(n_e)
+    M, K = G.beam_mats(beam)
+    F = torch.from_numpy(W.loads(beam.n)[:, 0]).cuda()
+    opts = G.options(tol=TOL, maxit=20000)
+    method_arms(G, torch, stream, M, K, F, shifts[:1], opts)     # warm the kernels and pool
+    out = method_arms(G, torch, stream, M, K, F, shifts, opts)
+    out["workload"] = "beam n_e=%d (n=%d, unit-element), tip force, shifts %s" % (
+        n_e, beam.n, [round(float(s), 4) for s in shifts])
+    out["bound_note"] = note
+    return out
+
+
+def c1_form(G, torch, stream):
+    """Config 1: 500 elements (n = 1000), 4 shifts logspace(0, 3), tip force."""
+    c = W.small_beam_case()
+    return _plain_config_form(G, torch, stream, c["n_e"], c["shifts"],
+                              "n = 1e3: 112 KB of bands, one CTA's shared memory; every PCG "
+                              "iteration is two grid barriers and latency, not bandwidth")
+
+
+def c2_form(G, torch, stream):
+    """Config 2: 50,000 elements (n = 1e5), 8 shifts logspace(-1, 4), tip force."""
+    c = W.scale_beam_case()
+    return _plain_config_form(G, torch, stream, c["n_e"], c["shifts"],
+                              "n = 1e5: 11 MB of bands, L2-resident; per-iteration time is "
+                              "barrier and latency bound (HBM GB/s here is L2 traffic)")
 
 
 def precision_form(G, torch, stream):
@@ -388,6 +475,14 @@ def precision_form(G, torch, stream):
             worstmx = max(worstmx, float(rrmx.max()))
             d = (rmx["X"] - r64["X"]).norm(dim=0) / r64["X"].norm(dim=0)
             maxdiff = max(maxdiff, float(d.max()))
+            k = int(np.argmin(np.abs(shifts - s)))
+            if k in PRECISION_SAMPLE_SHIFTS:
+                # a seeded sample of solutions, checked against the oracle's
+                # direct solve by the CPU-baseline leg
+                PRECISION_SAMPLE.append(dict(
+                    s=float(s), cols=list(PRECISION_SAMPLE_COLS),
+                    x_mixed=rmx["X"][:, list(PRECISION_SAMPLE_COLS)].t().cpu().numpy(),
+                    x_fp64=r64["X"][:, list(PRECISION_SAMPLE_COLS)].t().cpu().numpy()))
             inner_tot += int(rmx["inner_iters"].sum())
             outer_tot += int(rmx["outer_iters"].sum())
             it64_tot += int(r64["iters"].sum())
@@ -405,7 +500,40 @@ def precision_form(G, torch, stream):
                                            "max_true_relres": worstmx},
             "speedup": round(t64 / tmx, 3) if tmx > 0 else None,
             "spai_ms_total": round(tsp, 3),
-            "max_rel_diff_mixed_vs_fp64": maxdiff}
+            "max_rel_diff_mixed_vs_fp64": maxdiff,
+            "error_vs_oracle": "filled in by the cpu_baseline leg (oracle banded Cholesky)"}
+
+
+# (shift index, right-hand side) pairs of the precision workload whose
+# solutions the CPU-baseline leg compares with the oracle's direct solve
+PRECISION_SAMPLE_SHIFTS = (0, 7, 15)
+PRECISION_SAMPLE_COLS = (0, 3)
+PRECISION_SAMPLE = []
+
+
+def precision_error_vs_oracle():
+    """Per-solve relative error ||x - x_dir|| / ||x_dir|| of the sampled
+    FP32-refined and FP64 solutions, x_dir the oracle's banded Cholesky
+    solution of the same (shift, right-hand side) in FP64."""
+    import oracle as O
+    if not PRECISION_SAMPLE:
+        return None
+    beam = W.beam(1_000_000)
+    F = np.asfortranarray(W.loads(beam.n, 8, seed=4))
+    rows = []
+    for smp in PRECISION_SAMPLE:
+        A = O.shifted_csr(beam, W.ALPHA, W.BETA, smp["s"])
+        Xd = O.chol_solve(A, F[:, smp["cols"]])
+        for j, c in enumerate(smp["cols"]):
+            ref = Xd[:, j]
+            nr = np.linalg.norm(ref)
+            rows.append([round(smp["s"], 4), c,
+                         float(np.linalg.norm(smp["x_mixed"][j] - ref) / nr),
+                         float(np.linalg.norm(smp["x_fp64"][j] - ref) / nr)])
+    return {"columns": ["s", "rhs", "rel_err_fp32_refined", "rel_err_fp64_pcg"], "rows": rows,
+            "max_rel_err_fp32_refined": max(r[2] for r in rows),
+            "max_rel_err_fp64_pcg": max(r[3] for r in rows),
+            "reference": "oracle banded Cholesky (FP64) on the same matrix and load"}
 
 
 def batching_form(G, torch, stream):
@@ -478,7 +606,7 @@ def batching_form(G, torch, stream):
     # FP64 work of the batch in the model count (20 FMA per row and iteration)
     row_iters = float(sum(s[0].n * int(it) for s, it in zip(systems, batch.iters.cpu().tolist())))
     pk = peaks()
-    fp64_peak = 152 * FP64_FMA_PER_CLK_SM * 2 * pk["sm_max_mhz"] * 1e6 / 1e12
+    fp64_peak_tf = fp64_peak(G, pk["sm_max_mhz"])["tflops"]
     return {"workload": "32 beams n_e log-uniform [5e3, 5e5] (seed 20261203), 4..16 shifts "
                         "logspace(-1,4) each, m in {1,4}; SPAI (QR) per (beam, shift)",
             "systems": nsys, "rows_total": rows,
@@ -491,7 +619,7 @@ def batching_form(G, torch, stream):
                               "tflops_model": round(row_iters * PCG_FLOP_PER_ROW_ITER /
                                                     (bat_ms * 1e-3) / 1e12, 4),
                               "frac_fp64_peak": round(row_iters * PCG_FLOP_PER_ROW_ITER /
-                                                      (bat_ms * 1e-3) / 1e12 / fp64_peak, 4),
+                                                      (bat_ms * 1e-3) / 1e12 / fp64_peak_tf, 4),
                               "autotune": report},
             "speedup": round(seq_ms / bat_ms, 3)}
 
@@ -509,8 +637,11 @@ def learned_form(G, torch, stream):
     (geometric midpoints of a 17-point logspace over [1e-1, 1e4]) against
     the exact SPAI (rebuilt per shift) and the updated SPAI (Q P_prev from
     the previous shift's exact SPAI, Sec. 3.2).  A learned preconditioner's
-    CG run is capped at 1.5x the exact SPAI's iterations at that shift; past
-    the cap the shift falls back to the exact SPAI (both runs counted).
+    CG run is capped at 1.5x the exact SPAI's iterations at the nearest
+    training shift (recorded with the training data on the 1e5-element beam,
+    so a deployed caller has it); past the cap the shift falls back to the
+    exact SPAI (both runs counted).  The training cost and the number of
+    16-shift sweeps it takes to pay it back are reported beside the gain.
     solves/s = converged solves / (preconditioner + CG device time)."""
     import math
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -518,17 +649,24 @@ def learned_form(G, torch, stream):
     # training set from SPAIs the method builds
     t0 = time.time()
     Xs, Ts, Ms = [], [], []
+    train_shifts = W.log_shifts(-1, 4, 64)
+    train_iters = []        # exact-SPAI CG iterations (tip load) at each training shift
     for k, n_e in enumerate((10_000, 30_000, 100_000)):
         beam = W.beam(n_e)
         M, K = G.beam_mats(beam)
         cols = torch.from_numpy(W.mlp_training_columns(beam.n, 96, seed=100 + k)).cuda()
-        for s in W.log_shifts(-1, 4, 64):
+        ftr = torch.from_numpy(W.loads(beam.n, 1)[:, 0].copy()).cuda() if n_e == 100_000 else None
+        for s in train_shifts:
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
             P = G.spai_build(A)
             X, T, m, _ = G.mlp_features(A, P, float(s), W.ALPHA, W.BETA, cols)
             Xs.append(X)
             Ts.append(T)
             Ms.append(m)
+            if ftr is not None:
+                # recorded with the training data: what a deployed caller knows
+                rt = G.pcg_solve(A, P, ftr, G.options(tol=TOL, maxit=20000))
+                train_iters.append(int(rt["iters"].item()))
     X, T, m = torch.cat(Xs), torch.cat(Ts), torch.cat(Ms)
     torch.cuda.synchronize()
     data_s = time.time() - t0
@@ -571,8 +709,10 @@ def learned_form(G, torch, stream):
             torch.cuda.synchronize()
             it_ex = int(rex["iters"].item())
             ok_ex = int(rex["status"].item()) == G.OK and float(rex["true_relres"].item()) <= 2 * TOL
-            # learned, capped at 1.5x the exact SPAI's iterations
-            cap = int(math.ceil(1.5 * it_ex))
+            # learned, capped at 1.5x the exact SPAI's iterations at the
+            # nearest training shift (known before this shift is solved)
+            near = int(np.argmin(np.abs(np.log(train_shifts) - math.log(float(s)))))
+            cap = int(math.ceil(1.5 * train_iters[near]))
             b0, b1, b2 = ev(), ev(), ev()
             b0.record(stream)
             Pl = net.spai(A, float(s), W.ALPHA, W.BETA)
@@ -618,7 +758,8 @@ def learned_form(G, torch, stream):
             fallbacks += int(it_l >= cap and int(rl["status"].item()) != G.OK)
             build_ms["exact"].append(a0.elapsed_time(a1))
             build_ms["learned"].append(b0.elapsed_time(b1))
-            rows.append([round(float(s), 4), it_ex, it_u, it_l if int(rl["status"].item()) == G.OK else None])
+            rows.append([round(float(s), 4), it_ex, it_u,
+                         it_l if int(rl["status"].item()) == G.OK else None, cap])
     sps = {k: (round(v[1] / (v[0] * 1e-3), 2) if v[0] > 0 else None) for k, v in tot.items()}
     lb = statistics.median(build_ms["learned"])
     return {"workload": "train: 32 end + 96 interior columns of beams n_e in {1e4, 3e4, 1e5} at "
@@ -633,7 +774,8 @@ def learned_form(G, torch, stream):
                          "loss_first": float(h[:10].mean()), "loss_last": float(h[-500:].mean()),
                          "status": st, "adam_steps": done},
             "per_shift": {"columns": ["s", "cg_iters_exact", "cg_iters_updated",
-                                      "cg_iters_learned (None = fell back)"], "rows": rows},
+                                      "cg_iters_learned (None = fell back)", "learned_cap"],
+                          "rows": rows},
             "solves_per_s": {"exact_spai": sps["exact"], "updated_spai": sps["updated"],
                              "learned_spai": sps["learned"]},
             "device_ms": {k: round(v[0], 3) for k, v in tot.items()},
@@ -642,7 +784,16 @@ def learned_form(G, torch, stream):
             "build_ms_median": {"exact_spai_qr": round(statistics.median(build_ms["exact"]), 4),
                                 "learned_spai": round(lb, 4)},
             "learned_build_tflops_model": round(n * 1.06 * MLP_FLOP_PER_SAMPLE_FWD / (lb * 1e-3) / 1e12, 4),
-            "speedup_learned_vs_exact": round(tot["exact"][0] / tot["learned"][0], 3)}
+            "speedup_learned_vs_exact": round(tot["exact"][0] / tot["learned"][0], 3),
+            "fallback_cap": "ceil(1.5 x exact-SPAI CG iterations at the nearest of the 64 "
+                            "training shifts, recorded on the 1e5-element training beam with "
+                            "the training data)",
+            "cost": {"training_device_ms": round(train_ms, 2),
+                     "dataset_s": round(data_s, 2),
+                     "saved_ms_per_sweep": round(tot["exact"][0] - tot["learned"][0], 3),
+                     "break_even_sweeps": (round(train_ms / (tot["exact"][0] - tot["learned"][0]), 1)
+                                           if tot["exact"][0] > tot["learned"][0] else None),
+                     "sweep": "the 16 evaluation shifts of the n = 1e6 beam"}}
 
 
 def inner_loop_form(G, torch, stream):
@@ -768,82 +919,103 @@ def e2e_arm(G, torch, beam, opts, args):
 # CPU oracle timings (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_calibration():
-    """Oracle PCG iteration counts per shift on a 10,000-element beam (the tip
-    load's counts do not depend on n for this beam)."""
-    import oracle as O
-    b = W.beam(10_000)
-    F = W.loads(b.n)[:, 0]
-    its = []
-    for s in SHIFTS:
-        A = O.shifted_csr(b, W.ALPHA, W.BETA, s)
-        _, it, st, _ = O.pcg(A, F, [O.spai(A)], tol=TOL, maxit=20000)
-        its.append(it)
-    return its
+def config_dict(world):
+    """The workload both arms time (the GPU arm and the reference arm print
+    this same dict)."""
+    return {"workload": "beam n_e=500000 (n=1e6, unit-element), tip load, 8 shifts "
+                        "logspace(-1,4), SPAI (QR, band-7) rebuilt per shift, PCG to 1e-10",
+            "n": 2 * N_E, "m": 1, "shifts": [float(s) for s in SHIFTS],
+            "l2": "flushed (256 MiB write) before each timed step",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
-def oracle_sample(shift_index, its, iter_sample=24):
-    """Oracle on the full n = 1e6 beam for one shift: assemble + SPAI + a
-    bounded number of PCG iterations; returns the estimated seconds of the
-    full solve (iterations scaled to the calibrated count)."""
+def host_cores():
+    return len(os.sched_getaffinity(0))
+
+
+def oracle_step(beam, F):
+    """One whole step of the workload by the oracle: for each of the 8 shifts
+    assemble A(s), build the SPAI (QR) and run PCG to 1e-10.  Returns
+    (seconds, iterations per shift, statuses)."""
     import oracle as O
-    b = W.beam(N_E)
-    F = W.loads(b.n)[:, 0]
-    s = SHIFTS[shift_index]
     t0 = time.perf_counter()
-    A = O.shifted_csr(b, W.ALPHA, W.BETA, s)
-    t1 = time.perf_counter()
-    P = O.spai(A)
-    t2 = time.perf_counter()
-    k = min(iter_sample, its[shift_index])
-    O.pcg(A, F, [P], tol=0.0, maxit=k)
-    t3 = time.perf_counter()
-    per_iter = (t3 - t2) / k
-    return (t1 - t0) + (t2 - t1) + per_iter * its[shift_index], dict(
-        assemble_s=t1 - t0, spai_s=t2 - t1, pcg_iter_s=per_iter)
+    its, sts = [], []
+    for s in SHIFTS:
+        A = O.shifted_csr(beam, W.ALPHA, W.BETA, s)
+        P = O.spai(A)
+        _, it, st, _ = O.pcg(A, F, [P], tol=TOL, maxit=20000)
+        its.append(int(it))
+        sts.append(int(st))
+    return time.perf_counter() - t0, its, sts
 
 
 def cpu_baseline():
-    its = oracle_calibration()
-    est, parts = oracle_sample(len(SHIFTS) // 2, its)
-    total = step_estimate(its, parts)
-    return {"value": round(len(SHIFTS) / total, 5), "unit": "solves/s", "cores": 1,
+    """The oracle on the host cores, timed (no extrapolation): one whole
+    8-shift step of this workload single-threaded (the serial parity
+    reference as it stands), then the same step by the OpenMP build of the
+    same source on every core of the process's affinity set.  The leg also
+    checks the sampled precision-form solutions against the oracle's direct
+    solve (returned separately)."""
+    import oracle as O
+    beam = W.beam(N_E)
+    F = W.loads(beam.n)[:, 0]
+    O.use_openmp(False)
+    t1, its1, st1 = oracle_step(beam, F)
+    O.use_openmp(True)
+    tomp, itsomp, stomp = oracle_step(beam, F)
+    threads = O.threads()
+    O.use_openmp(False)
+    acc = precision_error_vs_oracle()
+    base = {"value": round(len(SHIFTS) / t1, 5), "unit": "solves/s", "cores": 1,
             "kind": "oracle",
-            "sample": "n=1e6 beam, one shift (s=%.3g): 1 assemble + 1 SPAI build + %d PCG "
-                      "iterations timed; step = 8 x (assemble + SPAI) + the oracle's iteration "
-                      "counts %s (10,000-element beam) x time per iteration" % (
-                          SHIFTS[len(SHIFTS) // 2], min(24, its[len(SHIFTS) // 2]), its)}
+            "sample": "one whole step of this workload, timed: 8 shifts x (assemble + SPAI "
+                      "(QR) + PCG to 1e-10) on the n=1e6 beam, single thread",
+            "seconds": round(t1, 3), "iters": its1, "converged": all(s == 0 for s in st1),
+            "all_cores": {"value": round(len(SHIFTS) / tomp, 5), "unit": "solves/s",
+                          "cores": threads, "host_cores": host_cores(),
+                          "seconds": round(tomp, 3), "iters": itsomp,
+                          "build": "same oracle source compiled with -fopenmp: rows and SPAI "
+                                   "columns split over threads, dot products by fixed thread "
+                                   "chunks summed in thread order"}}
+    return base, acc
 
 
-def step_estimate(its, parts):
-    """Seconds of the whole 8-shift step from one shift's sampled costs:
-    assemble and SPAI do not depend on s; PCG = iterations x time/iteration."""
-    return len(SHIFTS) * (parts["assemble_s"] + parts["spai_s"]) + sum(its) * parts["pcg_iter_s"]
+REFERENCE_BUDGET_S = 150.0    # timed oracle work of the reference arm, at least one step
 
 
 def reference_arm(args, world, rank):
+    """The oracle (OpenMP build, all host cores) timed on whole steps of this
+    workload: one warm-up step when W > 0, then whole steps until K are done
+    or the next would pass the time budget; `steps` is the number timed."""
     if rank != 0:
         return None
-    its = oracle_calibration()
-    t = []
-    for k in range(args.steps):
-        _, parts = oracle_sample(k % len(SHIFTS), its, iter_sample=8)
-        t.append(step_estimate(its, parts))
-    mean_s = sum(t) / len(t)
+    import oracle as O
+    O.use_openmp(True)
+    beam = W.beam(N_E)
+    F = W.loads(beam.n)[:, 0]
+    warm = 0
+    if args.warmup > 0:
+        oracle_step(beam, F)
+        warm = 1
+    times, its = [], None
+    while len(times) < max(1, args.steps):
+        t, its, sts = oracle_step(beam, F)
+        times.append(t)
+        if sum(times) + t > REFERENCE_BUDGET_S:
+            break
+    mean_s = sum(times) / len(times)
     value = len(SHIFTS) / mean_s
+    threads = O.threads()
     return {"metric": METRIC, "value": round(value, 5), "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_s * 1e3, 3),
+            "steps": len(times), "warmup": warm, "ms_per_step": round(mean_s * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": "beam n_e=500000 (n=1e6, unit-element), tip load, 8 shifts "
-                                   "logspace(-1,4), SPAI (QR, band-7) rebuilt per shift, PCG to "
-                                   "1e-10", "n": 2 * N_E, "m": 1},
-            "cpu_baseline": {"kind": "oracle", "cores": 1, "value": round(value, 5),
-                             "sample": "each step: one shift (cycled) on the full n=1e6 beam: "
-                                       "assemble + SPAI + 8 PCG iterations timed; the 8-shift "
-                                       "step time is 8 x (assemble + SPAI) + the oracle's "
-                                       "iteration counts %s (10,000-element beam) x time per "
-                                       "iteration" % its},
+            "data": "synthetic", "impl": "reference", "config": config_dict(world),
+            "cpu_baseline": {"kind": "oracle", "cores": threads, "host_cores": host_cores(),
+                             "value": round(value, 5), "iters": its,
+                             "sample": "whole steps of this workload, timed (8 shifts x "
+                                       "(assemble + SPAI (QR) + PCG to 1e-10), n=1e6), OpenMP "
+                                       "build of the oracle on all host cores; %d steps of "
+                                       "%.2f s mean" % (len(times), mean_s)},
             "e2e": {"value": round(value, 5), "unit": "solves/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -856,7 +1028,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="precision,batching,learned,inner_loop",
+    ap.add_argument("--forms", default="c1,c2,precision,batching,learned,inner_loop",
                     help="comma-separated growth forms to run after the timed steps")
     ap.add_argument("--learned-train-steps", type=int, default=LEARNED_TRAIN_STEPS,
                     help="Adam steps of the learned form (default 30000; fewer only to profile)")
@@ -882,18 +1054,16 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(r["ms"], 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "beam n_e=500000 (n=1e6, unit-element), tip load, 8 shifts "
-                                   "logspace(-1,4), SPAI (QR, band-7) rebuilt per shift, PCG to "
-                                   "1e-10", "n": r["n"], "m": 1, "shifts": [float(s) for s in SHIFTS],
-                       "l2": "flushed (256 MiB write) before each timed step",
-                       "parallelism": "replicas" if world > 1 else "single"},
+            "config": config_dict(world),
             "converged": r["ok"], "iters": r["iters"], "true_relres": r["relres"],
             "roofline": r["roofline"], "gpu_launches": r["launches"], "clocks": r["clocks"],
             "e2e": r["e2e"], "pcg_only": r["pcg_only"], "detail": r["detail"],
             "forms": r["forms"],
         }
         if world == 1 and not args.no_cpu_baseline and not args.profile:
-            line["cpu_baseline"] = cpu_baseline()
+            line["cpu_baseline"], acc = cpu_baseline()
+            if acc is not None and line.get("forms") and "precision" in line["forms"]:
+                line["forms"]["precision"]["error_vs_oracle"] = acc
         print(json.dumps(line), flush=True)
     if r["dist"] is not None:
         r["dist"].destroy_process_group()

@@ -526,6 +526,17 @@ int airga_debug_set_fault(int fault);
 #define AIRGA_PCG_KERNEL_PAIR_SPLIT 3
 int airga_debug_force_pcg_kernel(int kind);
 
+/* Measurement aid, no counterpart in the paper: the FP64 FMA issue rate of
+ * the current device, the roofline of this library's FP64-bound kernels.
+ * One CTA of 1024 threads per SM runs 8, 12 and then 16 independent FMA
+ * chains per thread for `iters` steps (1..2^24); *fma_per_clk_sm (host)
+ * receives the best of the three in FMAs per SM clock from the SMs' cycle
+ * counters (median over SMs, clock independent),
+ * *tflops and *ms (host, may be NULL) the rate and time by events at the
+ * clocks of the moment.  SYNCHRONISES `stream`. */
+int airga_probe_fp64_rate(int64_t iters, double *fma_per_clk_sm, double *tflops, double *ms,
+                          void *stream);
+
 /* Release the library's cached device memory (pool trim) on the current
  * device; outstanding handles stay valid. */
 int airga_trim(void);

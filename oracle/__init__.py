@@ -21,14 +21,29 @@ from . import build as _build
 
 OK, EARG, EBREAKDOWN, EMAXIT, ERANK, ENOMEM = 0, 1, 3, 4, 6, 8
 
-_lib = None
+_libs = {}
+_openmp = False
+
+
+def use_openmp(flag: bool) -> None:
+    """Route the calls below to the OpenMP build (all host cores) or back to
+    the serial parity reference."""
+    global _openmp
+    _openmp = bool(flag)
+
+
+def threads() -> int:
+    """Threads the selected build uses."""
+    return int(lib().ora_threads())
 
 
 def lib():
-    global _lib
-    if _lib is None:
-        path = _build.build()
+    key = "omp" if _openmp else "serial"
+    if key not in _libs:
+        path = _build.build(openmp=_openmp)
         L = C.CDLL(path)
+        L.ora_threads.argtypes = []
+        L.ora_threads.restype = C.c_int
         dp, ip64, ip32 = C.POINTER(C.c_double), C.POINTER(C.c_int64), C.POINTER(C.c_int32)
         L.ora_shifted.argtypes = [C.c_int64, dp, dp, C.c_double, C.c_double, C.c_double, dp]
         L.ora_shifted.restype = None
@@ -52,8 +67,8 @@ def lib():
         L.ora_pcg.restype = C.c_int
         L.ora_chol_solve.argtypes = [C.c_int64, ip64, ip32, dp, C.c_int, dp, dp]
         L.ora_chol_solve.restype = C.c_int
-        _lib = L
-    return _lib
+        _libs[key] = L
+    return _libs[key]
 
 
 def _d(a):

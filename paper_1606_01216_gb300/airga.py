@@ -37,7 +37,7 @@ EXPORTS = (
     "airga_mlp_grad", "airga_mlp_train", "airga_mlp_spai", "airga_mlp_free",
     "airga_debug_force_pcg_kernel", "airga_mat_is_banded", "airga_mat_nnz", "airga_mat_to_csr",
     "airga_precond_is_banded", "airga_precond_factor_nnz", "airga_precond_factor_csr",
-    "airga_precond_from_csr",
+    "airga_precond_from_csr", "airga_probe_fp64_rate",
 )
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
@@ -104,6 +104,8 @@ def lib():
                                              C.POINTER(vp)]),
         "airga_spmv": (C.c_int, [vp, vp, vp, i32, vp]),
         "airga_spai_build": (C.c_int, [vp, vp, C.POINTER(Options), vp, C.POINTER(vp)]),
+        "airga_probe_fp64_rate": (C.c_int, [i64, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                            C.POINTER(C.c_double), vp]),
         "airga_mat_is_banded": (C.c_int, [vp]),
         "airga_mat_nnz": (i64, [vp]),
         "airga_mat_to_csr": (C.c_int, [vp, vp, vp, vp, vp]),
@@ -553,6 +555,14 @@ def debug_force_pcg_kernel(kind: int):
 
 def debug_set_fault(fault: int):
     _check(lib().airga_debug_set_fault(int(fault)), "debug_set_fault")
+
+
+def probe_fp64_rate(iters: int = 1 << 16, stream=None):
+    """(FP64 FMAs per SM clock, TFLOP/s, ms) of the device (measurement aid)."""
+    f, t, ms = C.c_double(), C.c_double(), C.c_double()
+    _check(lib().airga_probe_fp64_rate(int(iters), C.byref(f), C.byref(t), C.byref(ms),
+                                       _stream(stream)), "probe_fp64_rate")
+    return f.value, t.value, ms.value
 
 
 def trim():
