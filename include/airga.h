@@ -505,10 +505,23 @@ void airga_mlp_free(airga_mlp net);
  * first column, so every bounded barrier wait of that system
  * (opt->barrier_timeout_ms) expires and its status is AIRGA_E_TIMEOUT; the
  * other systems of a batch, the kernel and the CUDA context carry on.  The
- * fault is consumed by that call. */
+ * fault is consumed by that call.  Two more faults are host-side only and
+ * are consumed by the next call that reaches their point:
+ * AIRGA_FAULT_ALLOC makes the next device allocation of the library fail
+ * (the call returns AIRGA_E_OOM); AIRGA_FAULT_LAUNCH makes the next PCG or
+ * SPAI kernel launch report a launch failure (AIRGA_E_CUDA, nothing is
+ * launched).  Either way the call releases what it had allocated and later
+ * calls work normally. */
 #define AIRGA_FAULT_NONE 0
 #define AIRGA_FAULT_SKIP_ARRIVAL 1
+#define AIRGA_FAULT_ALLOC 2
+#define AIRGA_FAULT_LAUNCH 3
 int airga_debug_set_fault(int fault);
+
+/* Test hook: bytes of the library's device pool in use on the current
+ * device (allocations not yet released; after a stream synchronise this
+ * shows leaks). */
+int airga_debug_pool_used(int64_t *bytes);
 
 /* Test hook: make the CG calls of this process (airga_pcg_solve,
  * airga_pcg_solve_mv) use one kernel variant whenever it is applicable, so

@@ -37,7 +37,7 @@ EXPORTS = (
     "airga_mlp_grad", "airga_mlp_train", "airga_mlp_spai", "airga_mlp_free",
     "airga_debug_force_pcg_kernel", "airga_mat_is_banded", "airga_mat_nnz", "airga_mat_to_csr",
     "airga_precond_is_banded", "airga_precond_factor_nnz", "airga_precond_factor_csr",
-    "airga_precond_from_csr", "airga_probe_fp64_rate",
+    "airga_precond_from_csr", "airga_probe_fp64_rate", "airga_debug_pool_used",
 )
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
@@ -137,6 +137,7 @@ def lib():
         "airga_pcg_solve_mv": (C.c_int, [vp, vp, vp, vp, C.c_double, i32, C.POINTER(Options), vp,
                                          vp, vp, vp, vp, vp]),
         "airga_debug_set_fault": (C.c_int, [C.c_int]),
+        "airga_debug_pool_used": (C.c_int, [C.POINTER(i64)]),
         "airga_debug_force_pcg_kernel": (C.c_int, [C.c_int]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
@@ -544,7 +545,7 @@ def true_residual(A: Mat, X: torch.Tensor, F: torch.Tensor, stream=None) -> torc
     return out
 
 
-FAULT_NONE, FAULT_SKIP_ARRIVAL = 0, 1
+FAULT_NONE, FAULT_SKIP_ARRIVAL, FAULT_ALLOC, FAULT_LAUNCH = 0, 1, 2, 3
 PCG_KERNEL_AUTO, PCG_KERNEL_GENERIC_GLOBAL, PCG_KERNEL_PAIR, PCG_KERNEL_PAIR_SPLIT = 0, 1, 2, 3
 
 
@@ -563,6 +564,13 @@ def probe_fp64_rate(iters: int = 1 << 16, stream=None):
     _check(lib().airga_probe_fp64_rate(int(iters), C.byref(f), C.byref(t), C.byref(ms),
                                        _stream(stream)), "probe_fp64_rate")
     return f.value, t.value, ms.value
+
+
+def debug_pool_used() -> int:
+    """Bytes of the library's device pool in use (synchronise first)."""
+    v = C.c_int64()
+    _check(lib().airga_debug_pool_used(C.byref(v)), "debug_pool_used")
+    return v.value
 
 
 def trim():

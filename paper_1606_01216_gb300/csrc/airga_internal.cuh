@@ -283,7 +283,11 @@ struct PcgArgs {
 };
 
 // process-wide test fault consumed by the next pcg_solve (airga_debug_set_fault)
-int take_fault();
+// (consumes it and returns true when the armed fault is `kind`)
+bool take_fault(int kind);
+// cudaErrorLaunchOutOfResources when AIRGA_FAULT_LAUNCH is armed (consumed),
+// else cudaSuccess: called where a solve or SPAI kernel is about to launch
+cudaError_t injected_launch_error();
 
 // aligned16: A, the preconditioner band, b and x are 16-byte aligned (needed
 // by the node-pair kernel together with an even n)

@@ -59,6 +59,8 @@ static int pool_for_current(cudaMemPool_t *out) {
 
 int dev_alloc(void **p, size_t bytes, cudaStream_t s) {
     *p = nullptr;
+    if (take_fault(AIRGA_FAULT_ALLOC))
+        return fail(AIRGA_E_OOM, "device allocation: injected failure (AIRGA_FAULT_ALLOC)");
     cudaMemPool_t pool = nullptr;
     int st = pool_for_current(&pool);
     if (st) return st;
@@ -130,7 +132,14 @@ bool aligned16(const void *p) { return ((uintptr_t)p & 15u) == 0; }
 
 static std::atomic<int> g_fault{AIRGA_FAULT_NONE};
 
-int take_fault() { return g_fault.exchange(AIRGA_FAULT_NONE); }
+bool take_fault(int kind) {
+    int expected = kind;
+    return g_fault.compare_exchange_strong(expected, AIRGA_FAULT_NONE);
+}
+
+cudaError_t injected_launch_error() {
+    return take_fault(AIRGA_FAULT_LAUNCH) ? cudaErrorLaunchOutOfResources : cudaSuccess;
+}
 
 static std::atomic<int> g_forced_kind{0};
 
@@ -630,7 +639,7 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
         }
         if (!st)
             st = pcg_general(A, P, F, m, o, X, res_hist, iters, status, true_relres,
-                             take_fault() == AIRGA_FAULT_SKIP_ARRIVAL ? 1 : 0, s);
+                             take_fault(AIRGA_FAULT_SKIP_ARRIVAL) ? 1 : 0, s);
         if (Fmat) dev_free(Fmat, s);
         return st;
     }
@@ -687,7 +696,7 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
     a.maxit = o.maxit;
     a.warm = o.warm_start ? 1 : 0;
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
-    a.fault_skip_arrival = take_fault() == AIRGA_FAULT_SKIP_ARRIVAL ? 1 : 0;
+    a.fault_skip_arrival = take_fault(AIRGA_FAULT_SKIP_ARRIVAL) ? 1 : 0;
     a.pairz = A->pairz ? (const int32_t *)A->pairz.get() : nullptr;
     if (plan.kind >= 2 && A->pairz) {
         // packed beam entries for the row-pair stencil, made once per matrix
@@ -787,9 +796,21 @@ int airga_debug_force_pcg_kernel(int kind) {
 }
 
 int airga_debug_set_fault(int fault) {
-    if (fault != AIRGA_FAULT_NONE && fault != AIRGA_FAULT_SKIP_ARRIVAL)
+    if (fault != AIRGA_FAULT_NONE && fault != AIRGA_FAULT_SKIP_ARRIVAL &&
+        fault != AIRGA_FAULT_ALLOC && fault != AIRGA_FAULT_LAUNCH)
         return fail(AIRGA_E_INVALID_ARG, "unknown fault");
     g_fault.store(fault);
+    return AIRGA_OK;
+}
+
+int airga_debug_pool_used(int64_t *bytes) {
+    if (!bytes) return fail(AIRGA_E_INVALID_ARG, "bytes is NULL");
+    cudaMemPool_t pool = nullptr;
+    int st = pool_for_current(&pool);
+    if (st) return st;
+    uint64_t used = 0;
+    AIRGA_CUDA(cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used));
+    *bytes = (int64_t)used;
     return AIRGA_OK;
 }
 

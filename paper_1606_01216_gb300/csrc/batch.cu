@@ -242,7 +242,7 @@ int airga_batch_solve(airga_batch B, void *stream) {
     // test hook: an armed fault makes system 0 skip one barrier arrival in
     // this solve only (its flag is set before the launch and cleared after)
     static const int kOne = 1, kZero = 0;
-    const bool fault = take_fault() == AIRGA_FAULT_SKIP_ARRIVAL;
+    const bool fault = take_fault(AIRGA_FAULT_SKIP_ARRIVAL);
     int *flag0 = &B->sys[0].fault_skip_arrival;
     if (fault) AIRGA_CUDA(cudaMemcpyAsync(flag0, &kOne, sizeof(int), cudaMemcpyHostToDevice, cs));
     AIRGA_CUDA(launch_pcg_pair_batch(B->mode, B->grid, B->smem, B->sys, B->asg, B->off, cs));

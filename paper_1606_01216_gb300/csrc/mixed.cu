@@ -623,7 +623,7 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     a.maxit = o.maxit;
     a.max_outer = o.max_outer;
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
-    const int fault = take_fault() == AIRGA_FAULT_SKIP_ARRIVAL ? 1 : 0;
+    const int fault = take_fault(AIRGA_FAULT_SKIP_ARRIVAL) ? 1 : 0;
     // one launch per column runs its whole refinement
     for (int32_t c = 0; c < m && e == cudaSuccess; ++c) {
         a.f = F + (size_t)c * nf;

@@ -325,6 +325,7 @@ int launch_pcg_csr(int64_t n, int grid, const RowView &A, int nf, const RowView 
         a.relres = relres + c;
         a.fault_skip_arrival = (fault && c == 0) ? 1 : 0;
         cudaError_t e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
+        if (e == cudaSuccess) e = injected_launch_error();   // host-side test fault only
         if (e == cudaSuccess) {
             void *kargs[] = {(void *)&a};
             e = cudaLaunchCooperativeKernel((const void *)pcg_csr_kernel, dim3(grid), dim3(kThreads),

@@ -489,6 +489,8 @@ cudaError_t launch_spai_csr(const CsrPat &A, const double *Av, const double *Aol
                             const CsrPat &S, const CsrPat::Rows &rows, int mr,
                             const double *alpha0, double tol, int relative, int kmax, double *F,
                             int32_t *steps, double *colres, int32_t *flag, cudaStream_t s) {
+    const cudaError_t fe = injected_launch_error();   // host-side test fault only
+    if (fe != cudaSuccess) return fe;
     SpaiCsrArgs a;
     a.n = A.n;
     a.Acp = A.colptr;

@@ -528,6 +528,8 @@ cudaError_t mr_w(int64_t n, const double *A, const double *Aold, const double *a
 cudaError_t launch_spai_qr(int64_t n, int hbw, const double *A, const double *A_old, double *F,
                            double *colres, int32_t *rank_flag, const int32_t *zA,
                            const int32_t *zAold, cudaStream_t s) {
+    const cudaError_t fe = injected_launch_error();   // host-side test fault only
+    if (fe != cudaSuccess) return fe;
     switch (hbw) {
         case 0: return qr_w<0>(n, A, A_old, F, colres, rank_flag, zA, zAold, s);
         case 1: return qr_w<1>(n, A, A_old, F, colres, rank_flag, zA, zAold, s);
