@@ -19,8 +19,10 @@
 // FP32 one and halve the band and vector bytes (FP32 copies of A and P_sym
 // stay resident in L2 up to n of about 2.3e6); FP64 is kept where accuracy
 // is decided: the outer residual, the refinement update, the SPAI QR, and
-// the reduction totals of the inner CG (per-thread FP32 partials are summed
-// in FP64).
+// the grid totals and step lengths of the inner CG.  Each CTA sums its
+// threads' FP32 partials in FP32 (a tree of FP32 adds instead of FP64 ones,
+// whose latency the otherwise idle inner loop would wait on); the 152 CTA
+// sums are added in FP64.
 //
 // The inner solve is the row-pair persistent PCG of pcg_pair.cu with float
 // data: same ownership, halo and barrier scheme, r halo recomputed beside
@@ -170,6 +172,45 @@ __device__ __forceinline__ float2 pair_sym_f(const float *__restrict__ U, int n,
     return make_float2(y0, y1);
 }
 
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block-sum NV FP32 values of the inner solve with a shared-memory tree in
+// FP32 (the FMA pipe: a handful of cycles per level, where an FP64 level
+// occupies a sub-partition's FP64 pipe for 64 cycles); thread 0 of warp q
+// writes the CTA's sum of value q, widened to FP64, to partials[slot][q][cta].
+// The grid totals and the step lengths stay FP64: summed or divided in FP32
+// they cost the inner solve a third more iterations on the precision
+// workload.  `red` holds NV * nt floats; blockDim.x must be a multiple of 128.
+template <int NV>
+__device__ void block_partials_tree_f(float (&v)[NV], float *red, double *partials, int slot,
+                                      int grid, int rank) {
+    const int tid = threadIdx.x, nt = blockDim.x;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[q * nt + tid] = v[q];
+    __syncthreads();
+    const int quarter = nt >> 2;
+    if (tid < quarter) {
+#pragma unroll
+        for (int q = 0; q < NV; ++q) {
+            float *r = red + q * nt;
+            r[tid] = (r[tid] + r[tid + quarter]) + (r[tid + 2 * quarter] + r[tid + 3 * quarter]);
+        }
+    }
+    __syncthreads();
+    const int w = tid >> 5, l = tid & 31;
+    if (w < NV) {
+        const float *r = red + w * nt;
+        float t = 0.0f;
+        for (int k = l; k < quarter; k += 32) t += r[k];
+        t = warp_sum_f(t);
+        if (l == 0) partials[(slot * 4 + w) * grid + rank] = (double)t;
+    }
+}
+
 template <int MODE>   // 0: identity, 1: band preconditioner, 2: symmetric (upper diagonals)
 __global__ void __launch_bounds__(kThreads, 1)
 mixed_pair_kernel(Args32 a, int R) {
@@ -185,6 +226,7 @@ mixed_pair_kernel(Args32 a, int R) {
     const int hi = lo + R < n ? lo + R : n;
 
     double *red = smem64;                                        // 3 * nt doubles
+    float *redf = reinterpret_cast<float *>(red);                // the inner loop's FP32 trees
     float *xs = reinterpret_cast<float *>(red + 3 * nt);
     float *rs = xs + R;
     float *ps = rs + (R + 2 * HR);
@@ -299,8 +341,7 @@ mixed_pair_kernel(Args32 a, int R) {
         {
             float v2[2] = {0.0f, 0.0f};
             apply_M(zlo, zhi, v2);
-            double v[2] = {(double)v2[0], (double)v2[1]};
-            block_partials_tree<2>(v, red, a.partials, bar_no & 1, G, blockIdx.x);
+            block_partials_tree_f<2>(v2, redf, a.partials, bar_no & 1, G, blockIdx.x);
         }
         if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
             status = AIRGA_E_TIMEOUT;
@@ -358,8 +399,8 @@ mixed_pair_kernel(Args32 a, int R) {
                 if (MODE != 0 && zlo + 2 * tid < zhi)
                     prefetch_pair_f(a.M, n, zlo + 2 * tid, MODE == 2 ? 4 : kBand);
                 {
-                    double vv[1] = {(double)vq};
-                    block_partials_tree<1>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
+                    float vv[1] = {vq};
+                    block_partials_tree_f<1>(vv, redf, a.partials, bar_no & 1, G, blockIdx.x);
                 }
                 const bool arrive = !(a.fault_skip_arrival && ko == 0 && k == 1 && blockIdx.x == 0);
                 if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
@@ -429,10 +470,7 @@ mixed_pair_kernel(Args32 a, int R) {
                     if (packed) prefetch_pair_f(a.Apk, n, lo + 2 * tid, 5);
                     else prefetch_pair_f(a.A, n, lo + 2 * tid, kBand);
                 }
-                {
-                    double vv[2] = {(double)v2[0], (double)v2[1]};
-                    block_partials_tree<2>(vv, red, a.partials, bar_no & 1, G, blockIdx.x);
-                }
+                block_partials_tree_f<2>(v2, redf, a.partials, bar_no & 1, G, blockIdx.x);
                 if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
                     istatus = AIRGA_E_TIMEOUT;
                     iters = k;
