@@ -289,7 +289,11 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
  * (0 = 4096) and fit shared memory; systems are placed largest cost first on
  * the CTAs that become free first.  cost[s] (host, may be NULL = rows) is
  * the caller's work estimate, e.g. rows x CG iterations of an earlier run —
- * the hook an autotuner uses.  Requirements: every n even, F[s] and X[s]
+ * the hook an autotuner uses.  group[s] (host, may be NULL): systems with
+ * the same group id (and the same CTA-group size) are scheduled as one job,
+ * back to back on one CTA group, e.g. the right-hand sides of one (A, P),
+ * which then reuse its bands while they sit in L2; NULL schedules every
+ * system on its own.  Requirements: every n even, F[s] and X[s]
  * (device, n-vectors) 16-byte aligned, either every P[s] a single factor of
  * matching size or P NULL / every P[s] NULL.  Results of each solve go to the
  * caller's device arrays iters[s], status[s] and relres[s] (true residual).
@@ -297,8 +301,10 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
  * plan and SYNCHRONISES `stream`. */
 int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
                        const double *const *F, double *const *X, const double *cost,
-                       int32_t rows_per_cta, const airga_options *opt, int32_t *iters,
-                       int32_t *status, double *relres, void *stream, airga_batch *out);
+                       const int32_t *group, int32_t rows_per_cta, const airga_options *opt,
+                       int32_t *iters, int32_t *status, double *relres, void *stream,
+                       airga_batch *out);
+
 
 /* Run the planned solves: one memset and one cooperative launch on `stream`,
  * no allocation (the call may be captured in a CUDA graph and replayed; each

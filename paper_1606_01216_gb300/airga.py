@@ -128,8 +128,9 @@ def lib():
         "airga_pcg_solve_mixed": (C.c_int, [vp, vp, vp, i32, C.POINTER(Options), vp, vp, vp, vp,
                                             vp, vp]),
         "airga_batch_create": (C.c_int, [i32, C.POINTER(vp), C.POINTER(vp), C.POINTER(vp),
-                                         C.POINTER(vp), C.POINTER(C.c_double), i32,
-                                         C.POINTER(Options), vp, vp, vp, vp, C.POINTER(vp)]),
+                                         C.POINTER(vp), C.POINTER(C.c_double),
+                                         C.POINTER(C.c_int32), i32, C.POINTER(Options), vp, vp,
+                                         vp, vp, C.POINTER(vp)]),
         "airga_batch_solve": (C.c_int, [vp, vp]),
         "airga_batch_info": (C.c_int, [vp, C.POINTER(i32), C.POINTER(i32), C.POINTER(i32),
                                        C.POINTER(C.c_double)]),
@@ -499,7 +500,7 @@ class Batch:
     n-vectors (x receives the solution)."""
 
     def __init__(self, systems, opts: Options | None = None, cost=None, rows_per_cta: int = 0,
-                 stream=None):
+                 stream=None, group=None):
         k = len(systems)
         self.systems = systems           # keep handles and buffers alive
         self.iters = torch.zeros(k, dtype=torch.int32, device="cuda")
@@ -511,10 +512,11 @@ class Batch:
         Fp = (C.c_void_p * k)(*[s[2].data_ptr() for s in systems])
         Xp = (C.c_void_p * k)(*[s[3].data_ptr() for s in systems])
         cst = (C.c_double * k)(*cost) if cost is not None else None
+        grp = (C.c_int32 * k)(*[int(g) for g in group]) if group is not None else None
         o = opts if opts is not None else options()
         self.opts = o
         out = C.c_void_p()
-        _check(lib().airga_batch_create(k, Ah, Ph if any_p else None, Fp, Xp, cst,
+        _check(lib().airga_batch_create(k, Ah, Ph if any_p else None, Fp, Xp, cst, grp,
                                         int(rows_per_cta), C.byref(o), _ptr(self.iters),
                                         _ptr(self.status), _ptr(self.relres), _stream(stream),
                                         C.byref(out)), "batch_create")

@@ -1,15 +1,23 @@
 """Schedule autotuner for batched solves (airga_batch_*).
 
-The batched launch needs two choices the library cannot know in advance:
-the rows each CTA of a system's group owns (small groups mean fewer barrier
-participants and more systems side by side; large groups finish one system
-sooner) and the cost of each system (rows x CG iterations decides the list
-schedule).  The tuner measures instead of guessing:
+The batched launch needs choices the library cannot know in advance:
+  * rows per CTA of a system's group, i.e. how many CTAs a system gets
+    (small groups mean fewer barrier participants and more systems side by
+    side; large groups finish one system sooner).  The target is capped by
+    shared memory: every target at or above the cap (`rows_max` of the
+    largest candidate) gives the same plan, which is where the sweep ends;
+  * right-hand-side grouping: the systems that share one (A, P) — the
+    right-hand sides of one shift — either scheduled one by one wherever CTAs
+    free up, or as one job back to back on one CTA group, so that they reuse
+    the bands while these sit in L2;
+  * the cost of each system (rows x CG iterations decides the list schedule).
+The tuner measures instead of guessing:
 
   1. plan with cost = rows and the default rows per CTA, solve once, read the
      CG iterations of every system;
-  2. for each candidate rows-per-CTA, plan with cost = rows x iterations and
-     time the solve on the device (CUDA events, best of `reps`);
+  2. for each (rows per CTA, grouping) candidate, plan with cost = rows x
+     iterations and time the solve on the device (CUDA events, best of
+     `reps`);
   3. keep the fastest plan.
 
 All timing goes through the C ABI; the tuner holds no compute of its own.
@@ -20,7 +28,8 @@ import torch
 
 from . import airga as G
 
-DEFAULT_CANDIDATES = (512, 1024, 2048, 4096, 8192)
+DEFAULT_CANDIDATES = (512, 1024, 2048, 4096, 5120, 6144, 8192)
+GROUPING = (False, True)
 
 
 def _time_solve(batch, stream, reps):
@@ -36,7 +45,18 @@ def _time_solve(batch, stream, reps):
     return best
 
 
-def tune(systems, opts=None, candidates=DEFAULT_CANDIDATES, reps=2, stream=None):
+def rhs_groups(systems):
+    """Group id per system: systems with the same matrix and preconditioner
+    handles (the right-hand sides of one shift) share an id."""
+    ids, out = {}, []
+    for s in systems:
+        key = (s[0].h.value, s[1].h.value if s[1] is not None else 0)
+        out.append(ids.setdefault(key, len(ids)))
+    return out
+
+
+def tune(systems, opts=None, candidates=DEFAULT_CANDIDATES, grouping=GROUPING, reps=2,
+         stream=None):
     """Return (best Batch, report).  systems: list of (A, P, f, x)."""
     stream = stream or torch.cuda.current_stream()
     first = G.Batch(systems, opts=opts, stream=stream)
@@ -45,17 +65,24 @@ def tune(systems, opts=None, candidates=DEFAULT_CANDIDATES, reps=2, stream=None)
     iters = first.iters.cpu().tolist()
     cost = [float(s[0].n) * max(1, it) for s, it in zip(systems, iters)]
     del first
+    groups = rhs_groups(systems)
     report = []
-    best, best_ms = None, float("inf")
-    for rows in candidates:
-        b = G.Batch(systems, opts=opts, cost=cost, rows_per_cta=rows, stream=stream)
-        ms = _time_solve(b, stream, reps)
-        info = b.info()
-        report.append(dict(rows_per_cta=rows, ms=round(ms, 4), rows_max=info["rows_max"],
-                           est_makespan=info["makespan"]))
-        if ms < best_ms:
-            best, best_ms = b, ms
-        else:
-            del b
+    best, best_ms, best_key = None, float("inf"), None
+    for grouped in grouping:
+        for rows in candidates:
+            b = G.Batch(systems, opts=opts, cost=cost, rows_per_cta=rows, stream=stream,
+                        group=groups if grouped else None)
+            ms = _time_solve(b, stream, reps)
+            info = b.info()
+            report.append(dict(rows_per_cta=rows, rhs_grouped=grouped, ms=round(ms, 4),
+                               rows_max=info["rows_max"], est_makespan=info["makespan"]))
+            if ms < best_ms:
+                best, best_ms, best_key = b, ms, (rows, grouped)
+            else:
+                del b
+    cap = max(r["rows_max"] for r in report)
     return best, dict(candidates=report, best_rows_per_cta=best.info()["rows_target"],
-                      best_ms=round(best_ms, 4))
+                      best_rhs_grouped=best_key[1], best_ms=round(best_ms, 4),
+                      rows_cap=cap, rhs_groups=max(groups) + 1,
+                      note="targets at or above the shared-memory cap give the same plan "
+                           "(rows_max = %d): the sweep ends there" % cap)

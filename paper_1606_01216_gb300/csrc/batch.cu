@@ -42,8 +42,9 @@ extern "C" {
 
 int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
                        const double *const *F, double *const *X, const double *cost,
-                       int32_t rows_per_cta, const airga_options *opt, int32_t *iters,
-                       int32_t *status, double *relres, void *stream, airga_batch *out) {
+                       const int32_t *group, int32_t rows_per_cta, const airga_options *opt,
+                       int32_t *iters, int32_t *status, double *relres, void *stream,
+                       airga_batch *out) {
     if (!out) return fail(AIRGA_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (nsys < 1 || !A || !F || !X || !iters || !status || !relres)
@@ -96,26 +97,54 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
     }
     const int64_t rbig = *std::max_element(R.begin(), R.end());
     const size_t smem = pcg_pair_smem(rbig);
+    // jobs: one system each, or (group given) the systems of one group id with
+    // the same group size, placed back to back on one CTA group so that the
+    // right-hand sides of one (A, P) reuse its bands while they are in L2
+    std::vector<std::vector<int>> jobs;
+    if (group) {
+        std::vector<std::pair<int64_t, int>> key(nsys);   // (group id, group size) -> job
+        std::vector<int> job_of(nsys, -1);
+        for (int s = 0; s < nsys; ++s) {
+            int found = -1;
+            for (int t = 0; t < s && found < 0; ++t)
+                if (group[t] == group[s] && g[t] == g[s]) found = job_of[t];
+            if (found < 0) {
+                found = (int)jobs.size();
+                jobs.emplace_back();
+            }
+            job_of[s] = found;
+            jobs[found].push_back(s);
+        }
+    } else {
+        for (int s = 0; s < nsys; ++s) jobs.push_back({s});
+    }
+    std::vector<double> jc(jobs.size(), 0.0);
+    for (size_t j = 0; j < jobs.size(); ++j)
+        for (int s : jobs[j]) jc[j] += c[s];
     // list scheduling, largest cost first
-    std::vector<int> order(nsys);
+    std::vector<int> order(jobs.size());
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return c[a] > c[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jc[a] > jc[b]; });
     std::vector<double> avail(G, 0.0);
     std::vector<std::vector<int4>> lists(G);
     std::vector<int> idx(G);
-    for (int s : order) {
+    for (int j : order) {
+        const int gj = g[jobs[j][0]];
         std::iota(idx.begin(), idx.end(), 0);
-        std::partial_sort(idx.begin(), idx.begin() + g[s], idx.end(), [&](int a, int b) {
+        std::partial_sort(idx.begin(), idx.begin() + gj, idx.end(), [&](int a, int b) {
             return avail[a] < avail[b] || (avail[a] == avail[b] && a < b);
         });
-        std::sort(idx.begin(), idx.begin() + g[s]);
+        std::sort(idx.begin(), idx.begin() + gj);
         double start = 0.0;
-        for (int k = 0; k < g[s]; ++k) start = std::max(start, avail[idx[k]]);
-        const double end = start + c[s] / g[s];
-        for (int k = 0; k < g[s]; ++k) {
-            avail[idx[k]] = end;
-            lists[idx[k]].push_back(make_int4(s, g[s], k, (int)R[s]));
+        for (int k = 0; k < gj; ++k) start = std::max(start, avail[idx[k]]);
+        // members in one global order: every CTA of the group appends them in
+        // the same sequence, which keeps the group barriers deadlock free
+        for (int s : jobs[j]) {
+            const double end = start + c[s] / gj;
+            for (int k = 0; k < gj; ++k) lists[idx[k]].push_back(make_int4(s, gj, k, (int)R[s]));
+            start = end;
         }
+        for (int k = 0; k < gj; ++k) avail[idx[k]] = start;
     }
     const double makespan = *std::max_element(avail.begin(), avail.end());
 

@@ -37,10 +37,11 @@ namespace {
 
 using namespace pcgdev;
 
-// threads per CTA: the all-shared-memory kernel runs best at 384 (up to 168
-// registers per thread); the split-state and batched kernels, whose windows
-// partly live in L2, keep 512 warps' worth of latency hiding
-constexpr int kThreadsFull = 384, kThreadsSplit = 512, kThreadsBatch = 512;
+// threads per CTA: the all-shared-memory kernels (single system and batched)
+// run at 384, which leaves up to 168 registers per thread for the
+// upper-diagonal P_sym read; the split-state kernel, whose windows partly
+// live in L2, keeps 512 warps' worth of latency hiding
+constexpr int kThreadsFull = 384, kThreadsSplit = 512, kThreadsBatch = 384;
 constexpr int kThreadsMax = 512;   // sizes the shared-memory reduction buffer
 constexpr int HR = 8, HP = 12, HZ = 4;
 constexpr int kHaloPairs = HR;   // 4 pairs of r halo on each side
@@ -197,8 +198,8 @@ struct PairShared {
 // being `rank` (rows [rank R, rank R + R)).  The group's barriers, partials
 // and p boundary buffer come from `a`; the single-system kernel runs it with
 // the whole grid as the group, the batched kernel once per assignment.
-// SYMU: read P_sym through its upper diagonals (pair_sym); the batched kernel
-// keeps the full-band read, which fits its registers without spills
+// SYMU: read P_sym through its upper diagonals (pair_sym; every kernel that
+// has P_sym does)
 template <int MODE, int SPLIT = 0, bool SYMU = true>   // MODE 0: identity, 1: one symmetric band
 __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem,
                           PairShared &sh) {
@@ -567,7 +568,7 @@ pcg_pair_batch_kernel(const PcgArgs *__restrict__ sys, const int4 *__restrict__ 
     for (int k = b; k < e; ++k) {
         const int4 w = asg[k];                       // (system, group size, rank, rows per CTA)
         const PcgArgs a = sys[w.x];
-        if ((MODE == 1) == (a.nf == 1)) pair_body<MODE, 0, false>(a, w.w, w.y, w.z, smem, sh);
+        if ((MODE == 1) == (a.nf == 1)) pair_body<MODE, 0, true>(a, w.w, w.y, w.z, smem, sh);
         __syncthreads();
     }
 }

@@ -46,10 +46,13 @@ def make_systems(G, spec, seed=3):
 SPEC = [(37, [0.3, 20.0], 1), (900, [0.1, 2.0, 500.0], 2), (5000, [1.0], 3), (12, [5.0], 1)]
 
 
+@pytest.mark.parametrize("grouped", [False, True], ids=["single", "rhs_grouped"])
 @pytest.mark.parametrize("rows", [0, 64, 700])
-def test_batch_matches_oracle(G, rows):
+def test_batch_matches_oracle(G, rows, grouped):
+    from paper_1606_01216_gb300 import autotune
     systems, ref, keep = make_systems(G, SPEC)
-    B = G.Batch(systems, rows_per_cta=rows)
+    group = autotune.rhs_groups(systems) if grouped else None
+    B = G.Batch(systems, rows_per_cta=rows, group=group)
     info = B.info()
     assert info["grid"] >= 1 and info["rows_max"] % 2 == 0
     B.solve()
