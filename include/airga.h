@@ -529,6 +529,27 @@ int airga_debug_set_fault(int fault);
  * shows leaks). */
 int airga_debug_pool_used(int64_t *bytes);
 
+/* Bounds-checked builds.  The library compiled with -DAIRGA_CHECKED
+ * (libairga_checked.so beside libairga.so) tests every instrumented index of
+ * its PCG, mixed-precision, SPAI and general-sparse kernels against the
+ * buffer it addresses before the access: window and band rows, row
+ * pointers, column indices, transposition maps and factor positions.  An
+ * index outside is counted and the access skipped (a load reads 0), so a
+ * wrong index shows up as a count instead of a memory fault.
+ *
+ * airga_debug_checked waits for the device, then writes the number of
+ * violations since the last call to *violations (host) and, when non-zero,
+ * the check site and offending index of one of them to *first_site and
+ * *first_index (host, may be NULL); the record is then cleared.  Normal
+ * builds set *violations to 0 and return AIRGA_E_UNSUPPORTED.
+ *
+ * airga_debug_check_selftest launches one thread on `stream` that tests
+ * `index` against [0, bound) with the kernels' check and touches no memory
+ * at `index` (any value is safe); an index outside is recorded with `site`.
+ * Normal builds return AIRGA_E_UNSUPPORTED. */
+int airga_debug_checked(int64_t *violations, int32_t *first_site, int64_t *first_index);
+int airga_debug_check_selftest(int64_t index, int64_t bound, int32_t site, void *stream);
+
 /* Test hook: make the CG calls of this process (airga_pcg_solve,
  * airga_pcg_solve_mv) use one kernel variant whenever it is applicable, so
  * that every variant can be checked on small problems.  0 = automatic (the

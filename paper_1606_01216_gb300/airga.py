@@ -6,6 +6,8 @@ Function names follow the C entry points without the ``airga_`` prefix.
 
 The library is loaded from this package directory; if it is missing the
 import of any compute function raises instead of falling back to anything.
+With AIRGA_LIB=checked in the environment the bounds-checked build
+(libairga_checked.so, see build.build(checked=True)) is loaded instead.
 """
 from __future__ import annotations
 
@@ -16,6 +18,7 @@ import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libairga.so")
+LIB_CHECKED_PATH = os.path.join(HERE, "libairga_checked.so")
 
 OK = 0
 E_INVALID_ARG, E_SHAPE, E_BREAKDOWN, E_MAXIT, E_TIMEOUT = 1, 2, 3, 4, 5
@@ -38,6 +41,7 @@ EXPORTS = (
     "airga_debug_force_pcg_kernel", "airga_mat_is_banded", "airga_mat_nnz", "airga_mat_to_csr",
     "airga_precond_is_banded", "airga_precond_factor_nnz", "airga_precond_factor_csr",
     "airga_precond_from_csr", "airga_probe_fp64_rate", "airga_debug_pool_used",
+    "airga_debug_checked", "airga_debug_check_selftest",
 )
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
@@ -81,14 +85,22 @@ class AirgaError(RuntimeError):
 _lib = None
 
 
+def lib_path() -> str:
+    """The library this process loads: libairga.so, or the bounds-checked
+    libairga_checked.so when AIRGA_LIB=checked."""
+    return LIB_CHECKED_PATH if os.environ.get("AIRGA_LIB", "") == "checked" else LIB_PATH
+
+
 def lib():
-    """Load libairga.so once; raises if it has not been built."""
+    """Load the library once; raises if it has not been built."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise RuntimeError("libairga.so is not built (run paper_1606_01216_gb300.build.build())")
-    L = C.CDLL(LIB_PATH)
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built (run paper_1606_01216_gb300.build.build(%s))"
+                           % (os.path.basename(path), "checked=True" if path == LIB_CHECKED_PATH else ""))
+    L = C.CDLL(path)
     vp, dp, i64, i32 = C.c_void_p, C.c_void_p, C.c_int64, C.c_int32
     sig = {
         "airga_options_default": (None, [C.POINTER(Options)]),
@@ -139,6 +151,8 @@ def lib():
                                          vp, vp, vp, vp, vp]),
         "airga_debug_set_fault": (C.c_int, [C.c_int]),
         "airga_debug_pool_used": (C.c_int, [C.POINTER(i64)]),
+        "airga_debug_checked": (C.c_int, [C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]),
+        "airga_debug_check_selftest": (C.c_int, [i64, i64, i32, vp]),
         "airga_debug_force_pcg_kernel": (C.c_int, [C.c_int]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
@@ -573,6 +587,22 @@ def debug_pool_used() -> int:
     v = C.c_int64()
     _check(lib().airga_debug_pool_used(C.byref(v)), "debug_pool_used")
     return v.value
+
+
+def debug_checked():
+    """Bounds-check record of a checked build since the last call:
+    (violations, site, index); raises AirgaError (E_UNSUPPORTED) on a normal
+    build."""
+    v, site, idx = C.c_int64(), C.c_int32(), C.c_int64()
+    _check(lib().airga_debug_checked(C.byref(v), C.byref(site), C.byref(idx)), "debug_checked")
+    return v.value, site.value, idx.value
+
+
+def debug_check_selftest(index, bound, site, stream=None):
+    """Run the kernels' bounds check once on (index, [0, bound)) in a checked
+    build; no memory is accessed at `index`."""
+    _check(lib().airga_debug_check_selftest(int(index), int(bound), int(site), _stream(stream)),
+           "debug_check_selftest")
 
 
 def trim():

@@ -8,6 +8,7 @@
 #pragma once
 
 #include "airga_internal.cuh"
+#include "check.cuh"
 
 namespace airga {
 
@@ -16,20 +17,44 @@ struct RowView {
     const int32_t *idx;
     const double *val;
     const int64_t *perm;   // null: values in entry order
+    int64_t n, nnz;        // rows (= columns) and entries: the bounds checked builds test
 };
 
 RowView rows_of(const CsrPat &p, const double *val);   // A
 RowView cols_of(const CsrPat &p, const double *val);   // A^T
 
 __device__ __forceinline__ double rv_val(const RowView &v, int64_t e) {
-    return v.perm ? __ldg(v.val + __ldg(v.perm + e)) : __ldg(v.val + e);
+    if (!AIRGA_CK(e, 0, v.nnz, 301)) return 0.0;
+    if (!v.perm) return __ldg(v.val + e);
+    const int64_t f = __ldg(v.perm + e);
+    return AIRGA_CK(f, 0, v.nnz, 302) ? __ldg(v.val + f) : 0.0;
+}
+
+// column of entry k, or -1 (checked builds, out of range: recorded)
+__device__ __forceinline__ int64_t rv_col(const RowView &v, int64_t k) {
+    const int64_t c = __ldg(v.idx + k);
+    return AIRGA_CK(c, 0, v.n, 303) ? c : -1;
+}
+
+// entry range of row i; checked builds record a row or pointer out of range
+// and give an empty range
+__device__ __forceinline__ void rv_range(const RowView &v, int64_t i, int64_t &b, int64_t &e) {
+    b = e = 0;
+    if (!AIRGA_CK(i, 0, v.n, 304)) return;
+    b = __ldg(v.ptr + i);
+    e = __ldg(v.ptr + i + 1);
+    if (!AIRGA_CK(b, 0, v.nnz + 1, 305) || !AIRGA_CK(e, b, v.nnz + 1, 305)) b = e = 0;
 }
 
 // (A x)_i, entries summed in stored (column) order
 __device__ __forceinline__ double rv_dot(const RowView &v, int64_t i, const double *x) {
     double acc = 0.0;
-    const int64_t b = __ldg(v.ptr + i), e = __ldg(v.ptr + i + 1);
-    for (int64_t k = b; k < e; ++k) acc = fma(rv_val(v, k), x[__ldg(v.idx + k)], acc);
+    int64_t b, e;
+    rv_range(v, i, b, e);
+    for (int64_t k = b; k < e; ++k) {
+        const int64_t c = rv_col(v, k);
+        if (c >= 0) acc = fma(rv_val(v, k), x[c], acc);
+    }
     return acc;
 }
 
@@ -37,8 +62,12 @@ __device__ __forceinline__ double rv_dot(const RowView &v, int64_t i, const doub
 // kernel between grid barriers)
 __device__ __forceinline__ double rv_dot_cg(const RowView &v, int64_t i, const double *x) {
     double acc = 0.0;
-    const int64_t b = __ldg(v.ptr + i), e = __ldg(v.ptr + i + 1);
-    for (int64_t k = b; k < e; ++k) acc = fma(rv_val(v, k), __ldcg(x + __ldg(v.idx + k)), acc);
+    int64_t b, e;
+    rv_range(v, i, b, e);
+    for (int64_t k = b; k < e; ++k) {
+        const int64_t c = rv_col(v, k);
+        if (c >= 0) acc = fma(rv_val(v, k), __ldcg(x + c), acc);
+    }
     return acc;
 }
 

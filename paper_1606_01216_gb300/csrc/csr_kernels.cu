@@ -482,11 +482,11 @@ cudaError_t scan_inclusive(int64_t *a, int64_t len, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 
 RowView rows_of(const CsrPat &p, const double *val) {
-    return RowView{p.rowptr, p.col, val, nullptr};
+    return RowView{p.rowptr, p.col, val, nullptr, p.n, p.nnz};
 }
 
 RowView cols_of(const CsrPat &p, const double *val) {
-    return RowView{p.colptr, p.rowidx, val, p.tperm};
+    return RowView{p.colptr, p.rowidx, val, p.tperm, p.n, p.nnz};
 }
 
 // Pattern from canonical CSR arrays already on the device (rowptr[n+1] with
@@ -763,3 +763,5 @@ cudaError_t launch_csr_mr_alpha(const CsrPat &p, const double *A, const double *
 }
 
 }  // namespace airga
+
+AIRGA_CHECK_READER(csr_kernels)

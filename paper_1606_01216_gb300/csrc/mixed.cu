@@ -27,6 +27,7 @@
 // The inner solve is the row-pair persistent PCG of pcg_pair.cu with float
 // data: same ownership, halo and barrier scheme, r halo recomputed beside
 // the x/r sweep, warp-0 scalar updates.
+#include "check.cuh"
 #include "fp64_lean.cuh"
 #include "pcg_common.cuh"
 
@@ -86,12 +87,24 @@ __device__ __forceinline__ void prefetch_pair_f(const float *band, int n, int i,
 
 __device__ __forceinline__ void load_band_pair_f(const float *__restrict__ band, int n, int i,
                                                  float2 (&a)[kBand]) {
+    if (!AIRGA_CK(i, 0, n - 1, 601)) {
+#pragma unroll
+        for (int d = 0; d < kBand; ++d) a[d] = make_float2(0.0f, 0.0f);
+        return;
+    }
 #pragma unroll
     for (int d = 0; d < kBand; ++d)
         a[d] = __ldg(reinterpret_cast<const float2 *>(band + (long long)d * n + i));
 }
 
-__device__ __forceinline__ void load_win_f(const float *w, int wbase, int i, float (&v)[10]) {
+// wlen: the window's length (checked builds test the ten rows against it)
+__device__ __forceinline__ void load_win_f(const float *w, int wbase, int i, float (&v)[10],
+                                           int wlen) {
+    if (!AIRGA_CK(i - 4 - wbase, 0, wlen - 9, 602)) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) v[k] = 0.0f;
+        return;
+    }
     const float2 *w2 = reinterpret_cast<const float2 *>(w + (i - 4 - wbase));
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -116,6 +129,7 @@ __device__ __forceinline__ float2 pair_packed_f(const float *__restrict__ pk,
                                                 const float *__restrict__ band, int n, int i,
                                                 const float (&v)[10]) {
     float2 c[5];
+    if (!AIRGA_CK(i, 0, n - 1, 603)) return make_float2(0.0f, 0.0f);
 #pragma unroll
     for (int k = 0; k < 5; ++k) c[k] = __ldg(reinterpret_cast<const float2 *>(pk + (long long)k * n + i));
     float y0 = c[0].x * v[2];
@@ -143,6 +157,7 @@ __device__ __forceinline__ float2 pair_packed_f(const float *__restrict__ pk,
 __device__ __forceinline__ float2 pair_sym_f(const float *__restrict__ U, int n, int i,
                                              const float (&v)[10]) {
     const float2 z2 = make_float2(0.0f, 0.0f);
+    if (!AIRGA_CK(i, 0, n - 1, 604)) return z2;
     const float2 *U0 = reinterpret_cast<const float2 *>(U);
     const float2 *U1 = reinterpret_cast<const float2 *>(U + n);
     const float2 *U2 = reinterpret_cast<const float2 *>(U + 2 * (long long)n);
@@ -233,6 +248,9 @@ mixed_pair_kernel(Args32 a, int R) {
     float *zq = ps + (R + 2 * HZ);
     float2 *ah = reinterpret_cast<float2 *>(zq + (R + 2 * HZ));  // A rows of the r halo
     const int xbase = lo, rbase = lo - HR, pbase = lo - HZ, zbase = lo - HZ;
+    const int lenR = R + 2 * HR, lenZ = R + 2 * HZ;      // window lengths (r; p and z/q)
+    (void)lenR;
+    (void)lenZ;
     const int rlo = lo - HR > 0 ? lo - HR : 0, rhi = hi + HR < n ? hi + HR : n;
     const int zlo = lo - HZ > 0 ? lo - HZ : 0, zhi = hi + HZ < n ? hi + HZ : n;
     const int bw = HP < (hi - lo) ? HP : (hi - lo);
@@ -270,16 +288,19 @@ mixed_pair_kernel(Args32 a, int R) {
                 float2 pb[kBand];
                 load_band_pair_f(a.M, n, i, pb);
                 float v[10];
-                load_win_f(rs, rbase, i, v);
+                load_win_f(rs, rbase, i, v, lenR);
                 z = pair_full_f(pb, v);
             } else if (MODE == 2) {
                 float v[10];
-                load_win_f(rs, rbase, i, v);
+                load_win_f(rs, rbase, i, v, lenR);
                 z = pair_sym_f(a.M, n, i, v);
             } else {
-                z = *reinterpret_cast<const float2 *>(rs + (i - rbase));
+                z = AIRGA_CK(i - rbase, 0, lenR - 1, 605)
+                        ? *reinterpret_cast<const float2 *>(rs + (i - rbase))
+                        : make_float2(0.0f, 0.0f);
             }
-            *reinterpret_cast<float2 *>(zq + (i - zbase)) = z;
+            if (AIRGA_CK(i - zbase, 0, lenZ - 1, 606))
+                *reinterpret_cast<float2 *>(zq + (i - zbase)) = z;
             if (i >= lo && i < hi) {
                 const float2 r = *reinterpret_cast<const float2 *>(rs + (i - rbase));
                 v2[0] = fmaf(r.x, z.x, fmaf(r.y, z.y, v2[0]));
@@ -306,7 +327,7 @@ mixed_pair_kernel(Args32 a, int R) {
                     }
                     r -= ax;
                 }
-                rs[i - rbase] = (float)r;
+                if (AIRGA_CK(i - rbase, 0, lenR, 607)) rs[i - rbase] = (float)r;
                 if (i >= lo && i < hi) rr = fma(r, r, rr);
             }
             double v[1] = {rr};
@@ -365,6 +386,7 @@ mixed_pair_kernel(Args32 a, int R) {
             float beta = 0.0f;
             for (int k = 1; k <= a.maxit; ++k) {
                 for (int i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
+                    if (!AIRGA_CK(i - pbase, 0, lenZ - 1, 608)) continue;
                     float2 *pp = reinterpret_cast<float2 *>(ps + (i - pbase));
                     const float2 z = *reinterpret_cast<const float2 *>(zq + (i - zbase));
                     if (k == 1) {
@@ -379,12 +401,13 @@ mixed_pair_kernel(Args32 a, int R) {
                 __syncthreads();
                 for (int t = tid; t < 2 * bw; t += nt) {
                     const int i = t < bw ? lo + t : hi - bw + (t - bw);
-                    a.pbuf[i] = ps[i - pbase];
+                    if (AIRGA_CK(i, 0, n, 609) && AIRGA_CK(i - pbase, 0, lenZ, 609))
+                        a.pbuf[i] = ps[i - pbase];
                 }
                 float vq = 0.0f;
                 for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
                     float v[10];
-                    load_win_f(ps, pbase, i, v);
+                    load_win_f(ps, pbase, i, v, lenZ);
                     float2 q;
                     if (packed) {
                         q = pair_packed_f(a.Apk, a.A, n, i, v);
@@ -393,7 +416,8 @@ mixed_pair_kernel(Args32 a, int R) {
                         load_band_pair_f(a.A, n, i, ab);
                         q = pair_full_f(ab, v);
                     }
-                    *reinterpret_cast<float2 *>(zq + (i - zbase)) = q;
+                    if (AIRGA_CK(i - zbase, 0, lenZ - 1, 610))
+                        *reinterpret_cast<float2 *>(zq + (i - zbase)) = q;
                     vq = fmaf(v[4], q.x, fmaf(v[5], q.y, vq));
                 }
                 if (MODE != 0 && zlo + 2 * tid < zhi)
@@ -440,6 +464,8 @@ mixed_pair_kernel(Args32 a, int R) {
                     }
                 }
                 for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                    if (!AIRGA_CK(i - xbase, 0, R - 1, 611) || !AIRGA_CK(i - rbase, 0, lenR - 1, 611))
+                        continue;
                     float2 *xp = reinterpret_cast<float2 *>(xs + (i - xbase));
                     float2 *rp = reinterpret_cast<float2 *>(rs + (i - rbase));
                     const float2 p = *reinterpret_cast<const float2 *>(ps + (i - pbase));
@@ -457,11 +483,13 @@ mixed_pair_kernel(Args32 a, int R) {
 #pragma unroll
                     for (int d = 0; d < kBand; ++d) t[d] = ah[hslot * kBand + d];
                     const float2 q = pair_full_f(t, pv);
-                    float2 *rp = reinterpret_cast<float2 *>(rs + (hpair - rbase));
-                    float2 r = *rp;
-                    r.x = fmaf(-alpha, q.x, r.x);
-                    r.y = fmaf(-alpha, q.y, r.y);
-                    *rp = r;
+                    if (AIRGA_CK(hpair - rbase, 0, lenR - 1, 612)) {
+                        float2 *rp = reinterpret_cast<float2 *>(rs + (hpair - rbase));
+                        float2 r = *rp;
+                        r.x = fmaf(-alpha, q.x, r.x);
+                        r.y = fmaf(-alpha, q.y, r.y);
+                        *rp = r;
+                    }
                 }
                 __syncthreads();
                 float v2[2] = {0.0f, 0.0f};
@@ -680,3 +708,5 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     if (e != cudaSuccess) return cuda_fail(e, "mixed solve launch");
     return AIRGA_OK;
 }
+
+AIRGA_CHECK_READER(mixed)

@@ -161,10 +161,12 @@ __global__ void __launch_bounds__(kThreads) pcg_csr_kernel(CsrPcgArgs a) {
             // ---- q = A p, p = z + beta p_prev formed per entry ----
             double vq[1] = {0.0};
             for (int64_t i = g0; i < n; i += gs) {
-                const int64_t rb = __ldg(a.A.ptr + i), re = __ldg(a.A.ptr + i + 1);
+                int64_t rb, re;
+                rv_range(a.A, i, rb, re);
                 double acc = 0.0;
                 for (int64_t e = rb; e < re; ++e) {
-                    const int64_t c = __ldg(a.A.idx + e);
+                    const int64_t c = rv_col(a.A, e);
+                    if (c < 0) continue;
                     const double pcv = k == 1 ? __ldcg(a.z + c) : fma(beta, __ldcg(pp + c), __ldcg(a.z + c));
                     acc = fma(rv_val(a.A, e), pcv, acc);
                 }
@@ -337,3 +339,5 @@ int launch_pcg_csr(int64_t n, int grid, const RowView &A, int nf, const RowView 
 }
 
 }  // namespace airga
+
+AIRGA_CHECK_READER(pcg_csr)

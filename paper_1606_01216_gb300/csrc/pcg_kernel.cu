@@ -26,6 +26,7 @@
 // * The barrier is a monotone arrival counter with a bounded wait (global
 //   timer); a CTA that gives up sets an abort flag that ends the others'
 //   waits, and the column's status becomes AIRGA_E_TIMEOUT.
+#include "check.cuh"
 #include "pcg_common.cuh"
 
 namespace airga {
@@ -38,26 +39,30 @@ constexpr int kMinRowsPerCta = 128;
 
 enum Mode { kIdentity = 0, kBand1 = 1, kChain = 2 };
 
-// One row of (band) x from a window buffer holding rows [wbase, ...).
+// One row of (band) x from a window buffer holding rows [wbase, wbase+wlen).
 __device__ __forceinline__ double stencil(const double *__restrict__ band, int64_t n, int64_t i,
-                                          const double *win, int64_t wbase) {
+                                          const double *win, int64_t wbase, int64_t wlen) {
     double acc = 0.0;
+    if (!AIRGA_CK(i, 0, n, 201)) return acc;
 #pragma unroll
     for (int d = 0; d < kBand; ++d) {
         const int64_t c = i + d - kHalf;
-        if (c >= 0 && c < n) acc = fma(__ldg(band + (int64_t)d * n + i), win[c - wbase], acc);
+        if (c >= 0 && c < n && AIRGA_CK(c - wbase, 0, wlen, 202))
+            acc = fma(__ldg(band + (int64_t)d * n + i), win[c - wbase], acc);
     }
     return acc;
 }
 
 // One row of (band)^T x: sum_d F(i+d, i) x_{i+d}, F(i+d, i) = band[(3-d) n + i + d].
 __device__ __forceinline__ double stencil_t(const double *__restrict__ band, int64_t n,
-                                            int64_t i, const double *win, int64_t wbase) {
+                                            int64_t i, const double *win, int64_t wbase,
+                                            int64_t wlen) {
     double acc = 0.0;
+    if (!AIRGA_CK(i, 0, n, 203)) return acc;
 #pragma unroll
     for (int d = -kHalf; d <= kHalf; ++d) {
         const int64_t c = i + d;
-        if (c >= 0 && c < n)
+        if (c >= 0 && c < n && AIRGA_CK(c - wbase, 0, wlen, 204))
             acc = fma(__ldg(band + (int64_t)(kHalf - d) * n + c), win[c - wbase], acc);
     }
     return acc;
@@ -71,7 +76,10 @@ __device__ __forceinline__ double stencil_t(const double *__restrict__ band, int
 // stencil_t()'s order, so each row equals the one-row form (out-of-matrix
 // terms are products with window zeros instead of skipped).
 __device__ __forceinline__ double2 stencil_pair(const double *__restrict__ band, int64_t n,
-                                                int64_t i, const double *win, int64_t wbase) {
+                                                int64_t i, const double *win, int64_t wbase,
+                                                int64_t wlen) {
+    if (!AIRGA_CK(i, 0, n - 1, 205) || !AIRGA_CK(i - 4 - wbase, 0, wlen - 9, 206))
+        return make_double2(0.0, 0.0);
     double v[10];
     const double2 *w2 = reinterpret_cast<const double2 *>(win + (i - 4 - wbase));
 #pragma unroll
@@ -91,7 +99,12 @@ __device__ __forceinline__ double2 stencil_pair(const double *__restrict__ band,
 }
 
 __device__ __forceinline__ double2 stencil_t_pair(const double *__restrict__ band, int64_t n,
-                                                  int64_t i, const double *win, int64_t wbase) {
+                                                  int64_t i, const double *win, int64_t wbase,
+                                                  int64_t wlen) {
+    // band reads (3-d) n + i + d .. +1 stay inside the 7 n array for i + 1 < n
+    // (entries past a diagonal's ends multiply window zeros)
+    if (!AIRGA_CK(i, 0, n - 1, 207) || !AIRGA_CK(i - 4 - wbase, 0, wlen - 9, 208))
+        return make_double2(0.0, 0.0);
     double v[10];
     const double2 *w2 = reinterpret_cast<const double2 *>(win + (i - 4 - wbase));
 #pragma unroll
@@ -121,23 +134,28 @@ __device__ __forceinline__ double2 stencil_t_pair(const double *__restrict__ ban
 }
 
 // z = M r on rows [lo-3, hi+3) (clipped to the matrix), written to zq; the r
-// and chain windows hold row i at [i - rbase].  PAIRS: the chain stencils run
+// and chain windows hold row i at [i - rbase] (lenR rows each), zq row i at
+// [i - lo + 3] (lenZ rows).  PAIRS: the chain stencils run
 // by row pairs over each stage's range widened to whole pairs (the extra row
 // reads only window rows inside the 2-row pad and feeds no needed row).
 template <int MODE, bool PAIRS>
 __device__ void apply_precond(const PcgArgs &a, int64_t lo, int64_t hi, int H, int64_t rbase,
-                              double *rs, double *zq, double *t1, double *t2) {
+                              double *rs, double *zq, double *t1, double *t2, int64_t lenR,
+                              int64_t lenZ) {
+    (void)lenZ;
     const int64_t n = a.n;
     const int64_t zlo = lo - 3 > 0 ? lo - 3 : 0, zhi = hi + 3 < n ? hi + 3 : n;
     const int64_t zbase = lo - 3;
     if (MODE == kIdentity) {
-        for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x) zq[i - zbase] = rs[i - rbase];
+        for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x)
+            if (AIRGA_CK(i - zbase, 0, lenZ, 209) && AIRGA_CK(i - rbase, 0, lenR, 210))
+                zq[i - zbase] = rs[i - rbase];
         return;
     }
     if (MODE == kBand1) {
         const double *Pb = a.psym ? a.psym : a.fac[0];
         for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x)
-            zq[i - zbase] = stencil(Pb, n, i, rs, rbase);
+            if (AIRGA_CK(i - zbase, 0, lenZ, 211)) zq[i - zbase] = stencil(Pb, n, i, rs, rbase, lenR);
         return;
     }
     // chain: C r with C = F_{nf-1} ... F_0, windows shrink by 3 per factor
@@ -148,20 +166,27 @@ __device__ void apply_precond(const PcgArgs &a, int64_t lo, int64_t hi, int H, i
         double *dst = (f & 1) ? t2 : t1;
         if (PAIRS) {
             for (int64_t i = (wlo & ~(int64_t)1) + 2 * threadIdx.x; i < whi; i += 2 * blockDim.x)
-                *reinterpret_cast<double2 *>(dst + (i - rbase)) = stencil_pair(a.fac[f], n, i, src, rbase);
+                if (AIRGA_CK(i - rbase, 0, lenR - 1, 212))
+                    *reinterpret_cast<double2 *>(dst + (i - rbase)) =
+                        stencil_pair(a.fac[f], n, i, src, rbase, lenR);
         } else {
             for (int64_t i = wlo + threadIdx.x; i < whi; i += blockDim.x)
-                dst[i - rbase] = stencil(a.fac[f], n, i, src, rbase);
+                if (AIRGA_CK(i - rbase, 0, lenR, 213))
+                    dst[i - rbase] = stencil(a.fac[f], n, i, src, rbase, lenR);
         }
         __syncthreads();
         src = dst;
     }
     if (!a.symmetrize) {
-        for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x) zq[i - zbase] = src[i - rbase];
+        for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x)
+            if (AIRGA_CK(i - zbase, 0, lenZ, 214) && AIRGA_CK(i - rbase, 0, lenR, 214))
+                zq[i - zbase] = src[i - rbase];
         __syncthreads();
         return;
     }
-    for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x) zq[i - zbase] = src[i - rbase];
+    for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x)
+        if (AIRGA_CK(i - zbase, 0, lenZ, 214) && AIRGA_CK(i - rbase, 0, lenR, 214))
+            zq[i - zbase] = src[i - rbase];
     __syncthreads();
     // C^T r = F_0^T ... F_{nf-1}^T r
     src = rs;
@@ -172,16 +197,20 @@ __device__ void apply_precond(const PcgArgs &a, int64_t lo, int64_t hi, int H, i
         double *dst = (s & 1) ? t2 : t1;
         if (PAIRS) {
             for (int64_t i = (wlo & ~(int64_t)1) + 2 * threadIdx.x; i < whi; i += 2 * blockDim.x)
-                *reinterpret_cast<double2 *>(dst + (i - rbase)) = stencil_t_pair(a.fac[f], n, i, src, rbase);
+                if (AIRGA_CK(i - rbase, 0, lenR - 1, 215))
+                    *reinterpret_cast<double2 *>(dst + (i - rbase)) =
+                        stencil_t_pair(a.fac[f], n, i, src, rbase, lenR);
         } else {
             for (int64_t i = wlo + threadIdx.x; i < whi; i += blockDim.x)
-                dst[i - rbase] = stencil_t(a.fac[f], n, i, src, rbase);
+                if (AIRGA_CK(i - rbase, 0, lenR, 216))
+                    dst[i - rbase] = stencil_t(a.fac[f], n, i, src, rbase, lenR);
         }
         __syncthreads();
         src = dst;
     }
     for (int64_t i = zlo + threadIdx.x; i < zhi; i += blockDim.x)
-        zq[i - zbase] = 0.5 * (zq[i - zbase] + src[i - rbase]);
+        if (AIRGA_CK(i - zbase, 0, lenZ, 217) && AIRGA_CK(i - rbase, 0, lenR, 217))
+            zq[i - zbase] = 0.5 * (zq[i - zbase] + src[i - rbase]);
 }
 
 // SMEM: 0 every window in this CTA's slice of the global workspace; 1 every
@@ -253,10 +282,10 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
             }
             v -= ax;
         }
-        rs[i - rbase] = v;
+        if (AIRGA_CK(i - rbase, 0, lenR, 218)) rs[i - rbase] = v;
     }
     __syncthreads();
-    apply_precond<MODE, SMEM == 2>(a, lo, hi, H, rbase, rs, zq, t1, t2);
+    apply_precond<MODE, SMEM == 2>(a, lo, hi, H, rbase, rs, zq, t1, t2, lenR, lenZ);
     __syncthreads();
     {
         double v[3] = {0.0, 0.0, 0.0};
@@ -292,20 +321,24 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
         for (int k = 1; k <= a.maxit; ++k) {
             // ---- phase 1: p = z + beta p on own +- 3; boundary rows out; q = A p ----
             if (k == 1) {
-                for (int64_t i = plo3 + tid; i < phi3; i += nt) ps[i - pbase] = zq[i - zbase];
+                for (int64_t i = plo3 + tid; i < phi3; i += nt)
+                    if (AIRGA_CK(i - pbase, 0, lenP, 219) && AIRGA_CK(i - zbase, 0, lenZ, 219))
+                        ps[i - pbase] = zq[i - zbase];
             } else {
                 for (int64_t i = plo3 + tid; i < phi3; i += nt)
-                    ps[i - pbase] = fma(beta, ps[i - pbase], zq[i - zbase]);
+                    if (AIRGA_CK(i - pbase, 0, lenP, 219) && AIRGA_CK(i - zbase, 0, lenZ, 219))
+                        ps[i - pbase] = fma(beta, ps[i - pbase], zq[i - zbase]);
             }
             __syncthreads();
             for (int64_t t = tid; t < 2 * bw; t += nt) {
                 const int64_t i = t < bw ? lo + t : hi - bw + (t - bw);
-                a.pbuf[i] = ps[i - pbase];
+                if (AIRGA_CK(i, 0, n, 220) && AIRGA_CK(i - pbase, 0, lenP, 220))
+                    a.pbuf[i] = ps[i - pbase];
             }
             double vq[1] = {0.0};
             for (int64_t i = lo + tid; i < hi; i += nt) {
-                const double q = stencil(a.A, n, i, ps, pbase);
-                zq[i - zbase] = q;
+                const double q = stencil(a.A, n, i, ps, pbase, lenP);
+                if (AIRGA_CK(i - zbase, 0, lenZ, 221)) zq[i - zbase] = q;
                 vq[0] = fma(ps[i - pbase], q, vq[0]);
             }
             block_partials<1>(vq, red, a.partials, bar_no & 1, G);
@@ -330,21 +363,22 @@ pcg_kernel(PcgArgs a, int64_t R, int H) {
             // ---- phase 2: outer p halo in; x, r updates; z = M r ----
             for (int64_t t = tid; t < 2 * (int64_t)H; t += nt) {
                 const int64_t i = t < H ? lo - H - 3 + t : hi + 3 + (t - H);
-                if (i < 0 || i >= n) continue;
+                if (i < 0 || i >= n || !AIRGA_CK(i - pbase, 0, lenP, 222)) continue;
                 ps[i - pbase] = __ldcg(a.pbuf + i);
             }
             for (int64_t i = lo + tid; i < hi; i += nt) {
+                if (!AIRGA_CK(i - xbase, 0, lenX, 223)) continue;
                 xs[i - xbase] = fma(alpha, ps[i - pbase], xs[i - xbase]);
                 rs[i - rbase] = fma(-alpha, zq[i - zbase], rs[i - rbase]);
             }
             __syncthreads();
             for (int64_t t = tid; t < 2 * (int64_t)H; t += nt) {
                 const int64_t i = t < H ? lo - H + t : hi + (t - H);
-                if (i < 0 || i >= n) continue;
-                rs[i - rbase] = fma(-alpha, stencil(a.A, n, i, ps, pbase), rs[i - rbase]);
+                if (i < 0 || i >= n || !AIRGA_CK(i - rbase, 0, lenR, 224)) continue;
+                rs[i - rbase] = fma(-alpha, stencil(a.A, n, i, ps, pbase, lenP), rs[i - rbase]);
             }
             __syncthreads();
-            apply_precond<MODE, SMEM == 2>(a, lo, hi, H, rbase, rs, zq, t1, t2);
+            apply_precond<MODE, SMEM == 2>(a, lo, hi, H, rbase, rs, zq, t1, t2, lenR, lenZ);
             __syncthreads();
             double v2[2] = {0.0, 0.0};
             for (int64_t i = lo + tid; i < hi; i += nt) {
@@ -521,3 +555,5 @@ cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s)
 }
 
 }  // namespace airga
+
+AIRGA_CHECK_READER(pcg_kernel)

@@ -29,6 +29,7 @@
 // precedes z = M r.  Convergence is tested as r.r <= (tol ||b||)^2, keeping
 // square roots off the per-iteration critical path; the residual history is
 // stored as r.r and converted once at exit.
+#include "check.cuh"
 #include "fp64_lean.cuh"
 #include "pcg_common.cuh"
 
@@ -48,14 +49,25 @@ constexpr int kHaloPairs = HR;   // 4 pairs of r halo on each side
 
 __device__ __forceinline__ void load_band_pair(const double *__restrict__ band, int n,
                                                int i, double2 (&a)[kBand]) {
+    if (!AIRGA_CK(i, 0, n - 1, 101)) {          // rows (i, i+1) inside the band arrays
+#pragma unroll
+        for (int d = 0; d < kBand; ++d) a[d] = make_double2(0.0, 0.0);
+        return;
+    }
 #pragma unroll
     for (int d = 0; d < kBand; ++d)
         a[d] = __ldg(reinterpret_cast<const double2 *>(band + (long long)d * n + i));
 }
 
-// v[k] = window row i-4+k, k = 0..9 (five aligned double2 loads)
+// v[k] = window row i-4+k, k = 0..9 (five aligned double2 loads); wlen is
+// the window's length (checked builds test the ten rows against it)
 __device__ __forceinline__ void load_win(const double *w, int wbase, int i,
-                                         double (&v)[10]) {
+                                         double (&v)[10], int wlen) {
+    if (!AIRGA_CK(i - 4 - wbase, 0, wlen - 9, 102)) {
+#pragma unroll
+        for (int k = 0; k < 10; ++k) v[k] = 0.0;
+        return;
+    }
     const double2 *w2 = reinterpret_cast<const double2 *>(w + (i - 4 - wbase));
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
@@ -86,6 +98,7 @@ __device__ __forceinline__ double2 pair_full(const double2 (&a)[kBand], const do
 __device__ __forceinline__ double2 pair_sym(const double *__restrict__ U, int n, int i,
                                             const double (&v)[10]) {
     const double2 z2 = make_double2(0.0, 0.0);
+    if (!AIRGA_CK(i, 0, n - 1, 103)) return z2;
     const double2 *U0 = reinterpret_cast<const double2 *>(U);
     const double2 *U1 = reinterpret_cast<const double2 *>(U + n);
     const double2 *U2 = reinterpret_cast<const double2 *>(U + 2 * (long long)n);
@@ -148,6 +161,11 @@ __device__ __forceinline__ void prefetch_pair(const double *band, int n, int i, 
 // (-3,-2,0,+1,+2); the free-end pair adds its +-1 couplings from the band.
 __device__ __forceinline__ void load_packed(const double *__restrict__ pk, int n, int i,
                                             double2 (&c)[5]) {
+    if (!AIRGA_CK(i, 0, n - 1, 104)) {
+#pragma unroll
+        for (int k = 0; k < 5; ++k) c[k] = make_double2(0.0, 0.0);
+        return;
+    }
 #pragma unroll
     for (int k = 0; k < 5; ++k) c[k] = __ldg(reinterpret_cast<const double2 *>(pk + (long long)k * n + i));
 }
@@ -176,6 +194,7 @@ __device__ __forceinline__ double2 pair_packed_c(const double2 (&c)[5],
 // on the fly from a band matrix M and a vector v (the AIRGA inner-loop
 // right-hand sides M V_j, Alg. 3 / Alg. 5), so M V is never stored.
 __device__ __forceinline__ double rhs_row(const PcgArgs &a, int n, int i) {
+    if (!AIRGA_CK(i, 0, n, 105)) return 0.0;
     if (!a.rhs_M) return a.b[i];
     double acc = 0.0;
 #pragma unroll
@@ -232,6 +251,9 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
     double2 *ah = reinterpret_cast<double2 *>(ps + (R + 2 * HZ) + (SPLIT ? 0 : R + 2 * HZ));   // A rows of the r halo
     double *red = reinterpret_cast<double *>(ah + kHaloPairs * kBand);
     const int xbase = lo, rbase = lo - HR, pbase = lo - HZ, zbase = lo - HZ;
+    const int lenR = R + 2 * HR, lenZ = R + 2 * HZ;      // window lengths (r; p and z/q)
+    (void)lenR;
+    (void)lenZ;
     const int rlo = lo - HR > 0 ? lo - HR : 0, rhi = hi + HR < n ? hi + HR : n;
     const int zlo = lo - HZ > 0 ? lo - HZ : 0, zhi = hi + HZ < n ? hi + HZ : n;
     const int bw = HP < (hi - lo) ? HP : (hi - lo);
@@ -291,18 +313,21 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
             double2 z;
             if (MODE == 1 && Psu) {
                 double v[10];
-                load_win(rs, rbase, i, v);
+                load_win(rs, rbase, i, v, lenR);
                 z = pair_sym(Psu, n, i, v);
             } else if (MODE == 1) {
                 double2 pb[kBand];
                 load_band_pair(Pb, n, i, pb);
                 double v[10];
-                load_win(rs, rbase, i, v);
+                load_win(rs, rbase, i, v, lenR);
                 z = pair_full(pb, v);
             } else {
-                z = *reinterpret_cast<const double2 *>(rs + (i - rbase));
+                z = AIRGA_CK(i - rbase, 0, lenR - 1, 106)
+                        ? *reinterpret_cast<const double2 *>(rs + (i - rbase))
+                        : make_double2(0.0, 0.0);
             }
-            *reinterpret_cast<double2 *>(zq + (i - zbase)) = z;
+            if (AIRGA_CK(i - zbase, 0, lenZ - 1, 107))
+                *reinterpret_cast<double2 *>(zq + (i - zbase)) = z;
             if (i >= lo && i < hi) {
                 const double2 r = *reinterpret_cast<const double2 *>(rs + (i - rbase));
                 v2[0] = fma(r.x, z.x, fma(r.y, z.y, v2[0]));
@@ -354,6 +379,7 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
         for (int k = 1; k <= a.maxit; ++k) {
             // ---- phase 1: p = z + beta p on own +- 4; boundary rows out; q = A p ----
             for (int i = zlo + 2 * tid; i < zhi; i += 2 * nt) {
+                if (!AIRGA_CK(i - pbase, 0, lenZ - 1, 108)) continue;
                 double2 *pp = reinterpret_cast<double2 *>(ps + (i - pbase));
                 const double2 z = *reinterpret_cast<const double2 *>(zq + (i - zbase));
                 if (k == 1) {
@@ -368,7 +394,8 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
             __syncthreads();
             for (int t = tid; t < 2 * bw; t += nt) {
                 const int i = t < bw ? lo + t : hi - bw + (t - bw);
-                a.pbuf[i] = ps[i - pbase];
+                if (AIRGA_CK(i, 0, n, 109) && AIRGA_CK(i - pbase, 0, lenZ, 110))
+                    a.pbuf[i] = ps[i - pbase];
             }
             double vq[1] = {0.0};
             if (packed) {
@@ -376,9 +403,10 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
                     double2 c[5];
                     load_packed(a.Apk, n, i, c);
                     double v[10];
-                    load_win(ps, pbase, i, v);
+                    load_win(ps, pbase, i, v, lenZ);
                     const double2 q = pair_packed_c(c, a.A, n, i, v);
-                    *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
+                    if (AIRGA_CK(i - zbase, 0, lenZ - 1, 111))
+                        *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
                     vq[0] = fma(v[4], q.x, fma(v[5], q.y, vq[0]));
                 }
             } else {
@@ -386,9 +414,10 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
                     double2 ab[kBand];
                     load_band_pair(a.A, n, i, ab);
                     double v[10];
-                    load_win(ps, pbase, i, v);
+                    load_win(ps, pbase, i, v, lenZ);
                     const double2 q = beam ? pair_beam(ab, v, i == n - 2) : pair_full(ab, v);
-                    *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
+                    if (AIRGA_CK(i - zbase, 0, lenZ - 1, 112))
+                        *reinterpret_cast<double2 *>(zq + (i - zbase)) = q;
                     vq[0] = fma(v[4], q.x, fma(v[5], q.y, vq[0]));
                 }
             }
@@ -436,6 +465,8 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
                 }
             }
             for (int i = lo + 2 * tid; i < hi; i += 2 * nt) {
+                if (!AIRGA_CK(i - xbase, 0, R - 1, 113) || !AIRGA_CK(i - rbase, 0, lenR - 1, 114))
+                    continue;
                 double2 *xp = reinterpret_cast<double2 *>(xs + (i - xbase));
                 double2 *rp = reinterpret_cast<double2 *>(rs + (i - rbase));
                 const double2 p = *reinterpret_cast<const double2 *>(ps + (i - pbase));
@@ -454,11 +485,13 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
 #pragma unroll
                 for (int d = 0; d < kBand; ++d) t[d] = ah[hslot * kBand + d];
                 const double2 q = beam ? pair_beam(t, pv, hpair == n - 2) : pair_full(t, pv);
-                double2 *rp = reinterpret_cast<double2 *>(rs + (hpair - rbase));
-                double2 r = *rp;
-                r.x = fma(-alpha, q.x, r.x);
-                r.y = fma(-alpha, q.y, r.y);
-                *rp = r;
+                if (AIRGA_CK(hpair - rbase, 0, lenR - 1, 115)) {
+                    double2 *rp = reinterpret_cast<double2 *>(rs + (hpair - rbase));
+                    double2 r = *rp;
+                    r.x = fma(-alpha, q.x, r.x);
+                    r.y = fma(-alpha, q.y, r.y);
+                    *rp = r;
+                }
             }
             __syncthreads();
             double v2[2] = {0.0, 0.0};
@@ -666,3 +699,5 @@ cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream
 }
 
 }  // namespace airga
+
+AIRGA_CHECK_READER(pcg_pair)

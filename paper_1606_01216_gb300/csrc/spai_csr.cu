@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(1024) scan_kernel(int64_t *a, int64_t len) {
 
 struct SpaiCsrArgs {
     int64_t n;
+    int64_t nnz_a, nnz_s;   // entries of A and of S (bounds of checked builds)
     // A by columns: entries of column k are [Acp[k], Acp[k+1]) with rows Ari
     // and values Av[Atp[e]] (A_old: Aold[Atp[e]], same pattern)
     const int64_t *Acp;
@@ -230,7 +231,11 @@ spai_csr_kernel(SpaiCsrArgs a, int max_j) {
         const int nj = (int)(a.Scp[j + 1] - sb);
         const int64_t ib = a.iptr[j];
         const int ni = (int)(a.iptr[j + 1] - ib);
-        if (lane < nj) Jcol[lane] = a.Sri[sb + lane];
+        if (!AIRGA_CK(nj, 0, max_j + 1, 401) || !AIRGA_CK(ni, 0, kLd + 1, 402)) continue;
+        if (lane < nj) {
+            const int32_t c = a.Sri[sb + lane];
+            Jcol[lane] = AIRGA_CK(c, 0, a.n, 403) ? c : 0;
+        }
         for (int r = lane; r < kLd; r += 32) Irow[r] = r < ni ? a.irows[ib + r] : INT32_MAX;
         for (int c = 0; c < nj; ++c)
             for (int r = lane; r < kLd; r += 32) Ah[c * kLd + r] = 0.0;
@@ -240,14 +245,17 @@ spai_csr_kernel(SpaiCsrArgs a, int max_j) {
         for (int c = 0; c < nj; ++c) {
             const int64_t k = Jcol[c];
             for (int64_t e = a.Acp[k] + lane; e < a.Acp[k + 1]; e += 32) {
+                if (!AIRGA_CK(e, 0, a.nnz_a, 404)) break;
                 const int p = find_row(Irow, ni, a.Ari[e]);
-                if (p >= 0) Ah[c * kLd + p] = a.Av[a.Atp[e]];
+                const int64_t t = a.Atp[e];
+                if (p >= 0 && AIRGA_CK(t, 0, a.nnz_a, 405)) Ah[c * kLd + p] = a.Av[t];
             }
         }
         // right-hand side on I_j; ||b||^2 outside I_j
         double bo2 = 0.0;
         if (a.Aold) {
             for (int64_t e = a.Acp[j] + lane; e < a.Acp[j + 1]; e += 32) {
+                if (!AIRGA_CK(e, 0, a.nnz_a, 406) || !AIRGA_CK(a.Atp[e], 0, a.nnz_a, 406)) break;
                 const double v = a.Aold[a.Atp[e]];
                 const int p = find_row(Irow, ni, a.Ari[e]);
                 if (p >= 0) bv[p] = v;
@@ -420,7 +428,10 @@ spai_csr_kernel(SpaiCsrArgs a, int max_j) {
             }
         }
         __syncwarp();
-        if (lane < nj) a.F[a.Stp[sb + lane]] = xs[lane];
+        if (lane < nj) {
+            const int64_t t = a.Stp[sb + lane];
+            if (AIRGA_CK(t, 0, a.nnz_s, 407)) a.F[t] = xs[lane];
+        }
         __syncwarp();
     }
 }
@@ -493,6 +504,8 @@ cudaError_t launch_spai_csr(const CsrPat &A, const double *Av, const double *Aol
     if (fe != cudaSuccess) return fe;
     SpaiCsrArgs a;
     a.n = A.n;
+    a.nnz_a = A.nnz;
+    a.nnz_s = S.nnz;
     a.Acp = A.colptr;
     a.Ari = A.rowidx;
     a.Atp = A.tperm;
@@ -535,3 +548,5 @@ cudaError_t launch_spai_csr(const CsrPat &A, const double *Av, const double *Aol
 }
 
 }  // namespace airga
+
+AIRGA_CHECK_READER(spai_csr)

@@ -24,6 +24,7 @@
 // the same block, with the direction restricted to the pattern.
 #include <utility>
 
+#include "check.cuh"
 #include "airga_internal.cuh"
 #include "fp64_lean.cuh"
 
@@ -51,7 +52,8 @@ __device__ __forceinline__ void gather_block(int64_t n, int64_t j, const double 
             const int r = c + t;                       // local row
             const int64_t g = j - W - 3 + r;           // global row
             double v = 0.0;
-            if (col_ok && g >= 0 && g < n) v = __ldg(A + (int64_t)(c - r + 6) * n + g);
+            if (col_ok && g >= 0 && g < n && AIRGA_CK((int64_t)(c - r + 6) * n + g, 0, 7 * n, 501))
+                v = __ldg(A + (int64_t)(c - r + 6) * n + g);
             if (!col_ok && t == 3) v = 1.0;            // decoupled unit column
             a[r][c] = v;
         }
@@ -72,7 +74,8 @@ __device__ __forceinline__ void gather_rhs(int64_t n, int64_t j, const double *_
 #pragma unroll
     for (int r = W; r <= W + 6; ++r) {
         const int64_t g = j - W - 3 + r;               // row of A_old(:, j)
-        if (g >= 0 && g < n) b[r] = __ldg(Aold + (int64_t)(W + 6 - r) * n + g);
+        if (g >= 0 && g < n && AIRGA_CK((int64_t)(W + 6 - r) * n + g, 0, 7 * n, 502))
+            b[r] = __ldg(Aold + (int64_t)(W + 6 - r) * n + g);
     }
 }
 
@@ -86,13 +89,15 @@ __device__ __forceinline__ void store_column(int64_t n, int64_t j, const double 
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
         const int64_t i = j - W + c;                   // row of F
-        if (i >= 0 && i < n) F[(int64_t)(W - c + 3) * n + i] = m[c];
+        if (i >= 0 && i < n && AIRGA_CK((int64_t)(W - c + 3) * n + i, 0, 7 * n, 503))
+            F[(int64_t)(W - c + 3) * n + i] = m[c];
     }
 #pragma unroll
     for (int d = -3; d <= 3; ++d) {
         const int64_t c = j + d;
         const bool outside = (c < 0 || c >= n);
-        if (d < -W || d > W || outside) F[(int64_t)(d + 3) * n + j] = 0.0;
+        if ((d < -W || d > W || outside) && AIRGA_CK((int64_t)(d + 3) * n + j, 0, 7 * n, 504))
+            F[(int64_t)(d + 3) * n + j] = 0.0;
     }
 }
 
@@ -185,7 +190,8 @@ __device__ __forceinline__ void gather_block_p(int64_t n, int64_t j, const doubl
             const int64_t g = j - W - 3 + r;           // global row
             double v = 0.0;
             if ((P.a[0][c] >> r) & 1u) {
-                if (col_ok && g >= 0 && g < n) v = __ldg(A + (int64_t)(c - r + 6) * n + g);
+                if (col_ok && g >= 0 && g < n && AIRGA_CK((int64_t)(c - r + 6) * n + g, 0, 7 * n, 505))
+                    v = __ldg(A + (int64_t)(c - r + 6) * n + g);
                 if (!col_ok && t == 3) v = 1.0;        // decoupled unit column
             }
             a[r][c] = v;
@@ -286,7 +292,9 @@ __device__ __forceinline__ void gather_rhs_p(int64_t n, int64_t j, const double 
 #pragma unroll
         for (int r = W; r <= W + 6; ++r) {
             const int64_t g = j - W - 3 + r;           // row of A_old(:, j)
-            if (((P.b[0] >> r) & 1u) && g >= 0 && g < n) b[r] = __ldg(Aold + (int64_t)(W + 6 - r) * n + g);
+            if (((P.b[0] >> r) & 1u) && g >= 0 && g < n &&
+                AIRGA_CK((int64_t)(W + 6 - r) * n + g, 0, 7 * n, 506))
+                b[r] = __ldg(Aold + (int64_t)(W + 6 - r) * n + g);
         }
     }
 }
@@ -550,3 +558,5 @@ cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_
 }
 
 }  // namespace airga
+
+AIRGA_CHECK_READER(spai_kernels)
