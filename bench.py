@@ -933,20 +933,42 @@ def host_cores():
     return len(os.sched_getaffinity(0))
 
 
-def oracle_step(beam, F):
+def oracle_step(beam, F, phases=None):
     """One whole step of the workload by the oracle: for each of the 8 shifts
     assemble A(s), build the SPAI (QR) and run PCG to 1e-10.  Returns
-    (seconds, iterations per shift, statuses)."""
+    (seconds, iterations per shift, statuses); `phases` (a dict), when given,
+    receives the seconds spent in assembly, SPAI and PCG."""
     import oracle as O
     t0 = time.perf_counter()
     its, sts = [], []
+    ph = {"assemble": 0.0, "spai": 0.0, "pcg": 0.0}
     for s in SHIFTS:
+        ta = time.perf_counter()
         A = O.shifted_csr(beam, W.ALPHA, W.BETA, s)
+        tb = time.perf_counter()
         P = O.spai(A)
+        tc = time.perf_counter()
         _, it, st, _ = O.pcg(A, F, [P], tol=TOL, maxit=20000)
+        td = time.perf_counter()
+        ph["assemble"] += tb - ta
+        ph["spai"] += tc - tb
+        ph["pcg"] += td - tc
         its.append(int(it))
         sts.append(int(st))
+    if phases is not None:
+        phases.update(ph)
     return time.perf_counter() - t0, its, sts
+
+
+def _phase_rates(ph, its, n):
+    """Per-phase figures of one timed oracle step: time per PCG iteration,
+    PCG-only solves/s and SPAI columns/s."""
+    it = max(1, sum(its))
+    return {"assemble_s": round(ph["assemble"], 3), "spai_s": round(ph["spai"], 3),
+            "pcg_s": round(ph["pcg"], 3),
+            "pcg_ms_per_iteration": round(1e3 * ph["pcg"] / it, 3),
+            "pcg_only_solves_per_s": round(len(its) / ph["pcg"], 4) if ph["pcg"] > 0 else None,
+            "spai_columns_per_s": round(len(its) * n / ph["spai"], 1) if ph["spai"] > 0 else None}
 
 
 def cpu_baseline():
@@ -960,9 +982,10 @@ def cpu_baseline():
     beam = W.beam(N_E)
     F = W.loads(beam.n)[:, 0]
     O.use_openmp(False)
-    t1, its1, st1 = oracle_step(beam, F)
+    ph1, phomp = {}, {}
+    t1, its1, st1 = oracle_step(beam, F, ph1)
     O.use_openmp(True)
-    tomp, itsomp, stomp = oracle_step(beam, F)
+    tomp, itsomp, stomp = oracle_step(beam, F, phomp)
     threads = O.threads()
     O.use_openmp(False)
     acc = precision_error_vs_oracle()
@@ -971,9 +994,11 @@ def cpu_baseline():
             "sample": "one whole step of this workload, timed: 8 shifts x (assemble + SPAI "
                       "(QR) + PCG to 1e-10) on the n=1e6 beam, single thread",
             "seconds": round(t1, 3), "iters": its1, "converged": all(s == 0 for s in st1),
+            "phases": _phase_rates(ph1, its1, beam.n),
             "all_cores": {"value": round(len(SHIFTS) / tomp, 5), "unit": "solves/s",
                           "cores": threads, "host_cores": host_cores(),
                           "seconds": round(tomp, 3), "iters": itsomp,
+                          "phases": _phase_rates(phomp, itsomp, beam.n),
                           "build": "same oracle source compiled with -fopenmp: rows and SPAI "
                                    "columns split over threads, dot products by fixed thread "
                                    "chunks summed in thread order"}}
