@@ -69,6 +69,8 @@ extern "C" {
 /* SPAI modes */
 #define AIRGA_SPAI_QR 0         /* exact fixed-pattern least squares, Householder QR */
 #define AIRGA_SPAI_MR 1         /* the paper's minimal-residual iteration (Algorithms 2 / 4) */
+#define AIRGA_SPAI_NE 2         /* exact fixed-pattern least squares by the normal equations: the
+                                   same minimiser as AIRGA_SPAI_QR (see airga_spai_build) */
 
 typedef struct airga_mat_s *airga_mat;
 typedef struct airga_precond_s *airga_precond;
@@ -80,7 +82,7 @@ typedef struct airga_batch_s *airga_batch;
 typedef struct {
     double tol;                 /* CG stops when ||r_k||_2 <= tol ||F(:,c)||_2 (default 1e-10) */
     int32_t maxit;              /* CG iteration cap per column (default 20000) */
-    int32_t spai_mode;          /* AIRGA_SPAI_QR (default) or AIRGA_SPAI_MR */
+    int32_t spai_mode;          /* AIRGA_SPAI_QR (default), AIRGA_SPAI_MR or AIRGA_SPAI_NE */
     double mr_tol;              /* MR: stop a column when ||r|| <= mr_tol (default 0.01, Sec. 5; see mr_relative) */
     int32_t mr_kmax;            /* MR: step cap per column (default 50) */
     int32_t symmetrize;         /* CG applies z = 1/2 (C + C^T) r instead of z = C r (default 1) */
@@ -178,7 +180,17 @@ int airga_spmv(airga_mat A, const double *X, double *Y, int32_t m, void *stream)
  * solution (Householder QR of the |I_j| x |J_j| block A(I_j, J_j)) or the
  * paper's MR iteration of Algorithm 2 (initial P = alpha I, alpha =
  * trace(A) / trace(A A^T); direction r restricted to J_j; stop test as
- * opt->mr_relative says; steps capped by opt->mr_kmax).  The new handle
+ * opt->mr_relative says; steps capped by opt->mr_kmax).
+ * AIRGA_SPAI_NE solves the same least-squares problems as AIRGA_SPAI_QR
+ * through G m = A(I_j,J_j)^T b_j, G = (A^T A)(J_j, J_j) taken from one
+ * band-13 product for all columns, by L D L^T (about half the FP64 work of
+ * the Householder solve).  It applies to band storage with pattern_hbw = 3;
+ * elsewhere the QR solver runs.  A column whose Gram block is
+ * ill-conditioned (a pivot <= 0, or smallest pivot < 1e-6 x largest
+ * diagonal entry) is solved by Householder QR instead, so the result is the
+ * QR result to within the rounding of a well-conditioned solve; those
+ * columns have steps[j] = 1 in airga_precond_status (0 elsewhere).  It
+ * takes 7 n doubles and n int32 of pool scratch for the call.  The new handle
  * holds P and, for CG, P_sym = 1/2 (P + P^T) (on S's pattern, or on its
  * union with the transpose when S is not structurally symmetric).  A rank
  * deficient column block is reported through airga_precond_status. */

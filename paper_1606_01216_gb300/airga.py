@@ -23,7 +23,7 @@ LIB_CHECKED_PATH = os.path.join(HERE, "libairga_checked.so")
 OK = 0
 E_INVALID_ARG, E_SHAPE, E_BREAKDOWN, E_MAXIT, E_TIMEOUT = 1, 2, 3, 4, 5
 E_RANK, E_CUDA, E_OOM, E_UNSUPPORTED = 6, 7, 8, 9
-SPAI_QR, SPAI_MR = 0, 1
+SPAI_QR, SPAI_MR, SPAI_NE = 0, 1, 2
 
 # every symbol include/airga.h declares
 EXPORTS = (

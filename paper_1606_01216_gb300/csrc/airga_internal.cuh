@@ -183,6 +183,13 @@ cudaError_t launch_spai_qr(int64_t n, int hbw, const double *A, const double *A_
 cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_old,
                            const double *alpha0, double tol, int relative, int kmax, double *F,
                            int32_t *steps, double *colres, cudaStream_t s);
+// Normal-equations mode (half-width 3): Gram band of A^T A into U (7 n
+// doubles of scratch), L D L^T per column; columns whose Gram block is
+// ill-conditioned are solved by the Householder kernel instead and marked
+// steps[j] = 1 (steps zeroed by the caller).  fb: n + 1 int32 of scratch.
+cudaError_t launch_spai_ne(int64_t n, const double *A, const double *A_old, double *F,
+                           double *colres, int32_t *rank_flag, int32_t *steps, double *U,
+                           int32_t *fb, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // general sparse storage (csr_kernels.cu, spai_csr.cu, pcg_csr.cu)

@@ -148,8 +148,9 @@ int forced_pcg_kind() { return g_forced_kind.load(); }
 int check_options(const airga_options *o) {
     if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return fail(AIRGA_E_INVALID_ARG, "tol must be finite and >= 0");
     if (o->maxit < 0) return fail(AIRGA_E_INVALID_ARG, "maxit must be >= 0");
-    if (o->spai_mode != AIRGA_SPAI_QR && o->spai_mode != AIRGA_SPAI_MR)
-        return fail(AIRGA_E_INVALID_ARG, "spai_mode must be AIRGA_SPAI_QR or AIRGA_SPAI_MR");
+    if (o->spai_mode != AIRGA_SPAI_QR && o->spai_mode != AIRGA_SPAI_MR &&
+        o->spai_mode != AIRGA_SPAI_NE)
+        return fail(AIRGA_E_INVALID_ARG, "spai_mode must be AIRGA_SPAI_QR, AIRGA_SPAI_MR or AIRGA_SPAI_NE");
     if (!(o->mr_tol >= 0.0)) return fail(AIRGA_E_INVALID_ARG, "mr_tol must be >= 0");
     if (o->mr_kmax < 0) return fail(AIRGA_E_INVALID_ARG, "mr_kmax must be >= 0");
     if (o->pattern_hbw < 0 || o->pattern_hbw > 3)
@@ -194,7 +195,21 @@ static int spai_factor(airga_mat A, airga_mat A_old, const airga_options &o, cud
     if (st) return st;
     AIRGA_CUDA(cudaMemsetAsync(out->rank_flag.get(), 0, sizeof(int32_t), s));
     const double *Aold = A_old ? A_old->band->d : nullptr;
-    if (o.spai_mode == AIRGA_SPAI_QR) {
+    if (o.spai_mode == AIRGA_SPAI_NE && o.pattern_hbw == 3) {
+        AIRGA_CUDA(cudaMemsetAsync(out->col_steps.get(), 0, sizeof(int32_t) * (size_t)n, s));
+        void *tmp = nullptr;
+        st = dev_alloc(&tmp, sizeof(double) * 7 * (size_t)n + sizeof(int32_t) * (size_t)(n + 2), s);
+        if (st) return st;
+        double *U = (double *)tmp;
+        int32_t *fb = (int32_t *)(U + 7 * (size_t)n);
+        const cudaError_t e = launch_spai_ne(n, A->band->d, Aold, (*F)->d, (double *)out->col_res.get(),
+                                             (int32_t *)out->rank_flag.get(),
+                                             (int32_t *)out->col_steps.get(), U, fb, s);
+        dev_free(tmp, s);
+        if (e != cudaSuccess) return cuda_fail(e, "spai NE launch");
+        return AIRGA_OK;
+    }
+    if (o.spai_mode == AIRGA_SPAI_QR || o.spai_mode == AIRGA_SPAI_NE) {
         AIRGA_CUDA(cudaMemsetAsync(out->col_steps.get(), 0, sizeof(int32_t) * (size_t)n, s));
         AIRGA_CUDA(launch_spai_qr(n, o.pattern_hbw, A->band->d, Aold, (*F)->d,
                                   (double *)out->col_res.get(), (int32_t *)out->rank_flag.get(),
