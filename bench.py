@@ -3,8 +3,10 @@ n = 1e6 beam (500,000 Hermite-cubic elements, unit-element scaling), tip
 force, 8 real shifts log-spaced in [1e-1, 1e4], SPAI rebuilt per shift.
 
 One step = the whole plain path over the 8 shifts: for each shift
-assemble_shifted -> spai_build (exact QR SPAI + P_sym) -> pcg_solve (PCG to
-1e-10 plus the true FP64 residual).  value = 8 solves / device time of a step
+assemble_shifted -> spai_build (exact fixed-pattern SPAI, least squares by
+the normal equations with the Householder fallback, + P_sym) -> pcg_solve
+(PCG to 1e-10 plus the true FP64 residual).  The Householder (QR) build is
+timed beside it in `detail`.  value = 8 solves / device time of a step
 (CUDA events on the launching stream; L2 flushed before every timed step by
 writing a 256 MiB buffer outside the timed interval).
 
@@ -48,6 +50,10 @@ PCG_BYTES_PER_ROW_ITER = 160     # A 56 + P_sym 56 + x, r, p read+write 48
 # of P_sym and the vectors; the bands stay in L2 after that
 PCG_DRAM_BYTES_PER_ROW_ITER = 0.641
 SPAI_FLOP_PER_COLUMN_MODEL = 1250  # algorithmic SPAI work per column (band-7 QR + solve)
+# FP64 instructions per interior column of the normal-equation SPAI build:
+# Gram band 28 FMA; L D L^T 35 + 21 FMA, 21 MUL, 7 x 4 for the reciprocals;
+# solves 42 FMA + 7 MUL; explicit residual 49 + 13 FMA; square root 4
+SPAI_NE_FP64_INSTR_PER_COLUMN = 248
 
 
 def peaks():
@@ -179,6 +185,7 @@ def gpu_arm(args, world, rank, local):
     M, K = G.beam_mats(beam)
     F = torch.from_numpy(W.loads(n)[:, 0]).cuda()
     opts = G.options(tol=TOL, maxit=20000)
+    spai_opts = G.options(spai_mode=G.SPAI_NE)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -191,9 +198,10 @@ def gpu_arm(args, world, rank, local):
         cnt = 0
         for s in SHIFTS:
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
-            P = G.spai_build(A)
-            cnt += 4                      # assemble (also writes the packed beam stencil),
-                                          # spai_qr_beam + spai_qr (general plan), symmetrize
+            P = G.spai_build(A, spai_opts)
+            cnt += 5                      # assemble (also writes the packed beam stencil),
+                                          # Gram band, normal-equation columns, Householder
+                                          # pass over the (empty) fallback list, symmetrize
             if record:
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -254,13 +262,22 @@ def gpu_arm(args, world, rank, local):
                 "pcg_ms_per_step": round(pcg_step_ms, 4)}
     if detail is not None:
         spai_ms = statistics.median([row["spai_ms"] for row in detail["rebuild"]])
-        model_gf = n * SPAI_FLOP_PER_COLUMN_MODEL / (spai_ms * 1e-3) / 1e9
+        qr_ms = statistics.median([row["spai_qr_ms"] for row in detail["rebuild"]])
+        model_gf = n * SPAI_FLOP_PER_COLUMN_MODEL / (qr_ms * 1e-3) / 1e9
+        # FP64 issue floor of the normal-equation build: its instructions per
+        # column at the device's FP64 rate (TFLOP/s = 2 x FMA rate)
+        floor_ms = n * SPAI_NE_FP64_INSTR_PER_COLUMN / (fp64_peak_tf * 1e12 / 2) * 1e3
         pcg_only["spai_build"] = {
+            "solver": "normal equations, L D L^T per column (Householder fallback)",
             "ms_median": round(spai_ms, 4),
-            "gflops_model": round(model_gf, 1),
-            "frac_fp64_peak_model": round(model_gf / (fp64_peak_tf * 1e3), 4),
-            "model": "1.25 kflop per column (Householder QR of the 12x7 block + solve, full "
-                     "band); the kernel issues fewer (structural zeros skipped)"}
+            "fp64_instr_per_column": SPAI_NE_FP64_INSTR_PER_COLUMN,
+            "fp64_issue_floor_ms": round(floor_ms, 4),
+            "frac_fp64_issue": round(floor_ms / spai_ms, 4),
+            "fallback_columns": sum(row["spai_fallback_columns"] for row in detail["rebuild"]),
+            "qr": {"ms_median": round(qr_ms, 4), "gflops_model": round(model_gf, 1),
+                   "frac_fp64_peak_model": round(model_gf / (fp64_peak_tf * 1e3), 4),
+                   "model": "1.25 kflop per column (Householder QR of the 12x7 block + solve, "
+                            "full band); the kernel issues fewer (structural zeros skipped)"}}
     forms = None
     if not args.profile and not args.no_forms:
         del M, K
@@ -315,14 +332,19 @@ def method_arms(G, torch, stream, M, K, F, shifts, opts):
         return out, e0.elapsed_time(e1)
 
     n = M.n
+    ne_opts = G.options(spai_mode=G.SPAI_NE)
     As = []
     rows = []
     for s in shifts:
         A, ta = timed(lambda: G.assemble_shifted(M, K, W.ALPHA, W.BETA, s))
-        P, tb = timed(lambda: G.spai_build(A))
+        P, tb = timed(lambda: G.spai_build(A, ne_opts))
+        fallback = int(G.precond_status(P)[0].sum())
+        Pq, tq = timed(lambda: G.spai_build(A))        # the Householder build, beside it
+        del Pq
         r, tc = timed(lambda: G.pcg_solve(A, P, F, opts))
         it = int(r["iters"][0])
         rows.append(dict(s=float(s), assemble_ms=round(ta, 4), spai_ms=round(tb, 4),
+                         spai_qr_ms=round(tq, 4), spai_fallback_columns=fallback,
                          pcg_ms=round(tc, 4), iters=it, status=int(r["status"][0]),
                          hbm_gbs=round(it * n * PCG_BYTES_PER_ROW_ITER / (tc * 1e-3) / 1e9, 1)))
         As.append(A)
@@ -384,14 +406,21 @@ def method_arms(G, torch, stream, M, K, F, shifts, opts):
                     build=builds, build_precond_plus_cg_ms=round(tot_b, 3), update=chain)
 
     upd = chain_arm(None, None)
+    upd_ne = chain_arm(ne_opts, ne_opts)
     reb_ms = sum(u["spai_ms"] + u["pcg_ms"] for u in rows)
     pcg_ms = sum(u["pcg_ms"] for u in rows)
     its = sum(u["iters"] for u in rows)
-    return dict(n=n, shifts=[float(s) for s in shifts], rebuild=rows,
+    return dict(n=n, shifts=[float(s) for s in shifts],
+                spai_solver="rebuild: normal equations (spai_mode NE, Householder fallback); "
+                            "spai_qr_ms: the Householder build of the same matrix",
+                rebuild=rows,
                 rebuild_precond_plus_cg_ms=round(reb_ms, 3),
+                rebuild_qr_precond_plus_cg_ms=round(
+                    sum(u["spai_qr_ms"] + u["pcg_ms"] for u in rows), 3),
                 rebuild_pcg_solves_per_s=round(len(shifts) / (pcg_ms * 1e-3), 2),
                 rebuild_hbm_gbs=round(its * n * PCG_BYTES_PER_ROW_ITER / (pcg_ms * 1e-3) / 1e9, 1),
-                update_qr=upd, mr_absolute=mr_arm(False), mr_relative=mr_arm(True))
+                update_qr=upd, update_ne=upd_ne, mr_absolute=mr_arm(False),
+                mr_relative=mr_arm(True))
 
 
 def _plain_config_form(G, torch, stream, n_e, shifts, note):
@@ -455,7 +484,7 @@ def precision_form(G, torch, stream):
         for s in shifts:
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
             e0 = ev()
-            P = G.spai_build(A)
+            P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
             e1 = ev()
             r64 = G.pcg_solve(A, P, Fd, o64)
             e2 = ev()
@@ -556,7 +585,7 @@ def batching_form(G, torch, stream):
         keep.append((M, K, Fd))
         for s in cfg["shifts"]:
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
-            P = G.spai_build(A)
+            P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
             Xd = torch.zeros_like(Fd)
             per_shift.append((A, P, Fd, Xd))
             for c in range(cfg["m"]):
@@ -658,7 +687,7 @@ def learned_form(G, torch, stream):
         ftr = torch.from_numpy(W.loads(beam.n, 1)[:, 0].copy()).cuda() if n_e == 100_000 else None
         for s in train_shifts:
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
-            P = G.spai_build(A)
+            P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
             X, T, m, _ = G.mlp_features(A, P, float(s), W.ALPHA, W.BETA, cols)
             Xs.append(X)
             Ts.append(T)
@@ -702,7 +731,7 @@ def learned_form(G, torch, stream):
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
             a0, a1, a2 = ev(), ev(), ev()
             a0.record(stream)
-            Pex = G.spai_build(A)
+            Pex = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
             a1.record(stream)
             rex = G.pcg_solve(A, Pex, f, opts)
             a2.record(stream)
@@ -726,7 +755,7 @@ def learned_form(G, torch, stream):
             if not ok_l:            # fallback: exact SPAI and a fresh solve
                 c0, c1 = ev(), ev()
                 c0.record(stream)
-                Pfb = G.spai_build(A)
+                Pfb = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
                 rfb = G.pcg_solve(A, Pfb, f, opts)
                 c1.record(stream)
                 torch.cuda.synchronize()
@@ -820,7 +849,7 @@ def inner_loop_form(G, torch, stream):
             ms, ok, its, worst = 0.0, 0, [], 0.0
             for s in shifts:
                 A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
-                P = G.spai_build(A)
+                P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
                 y = torch.empty(n, dtype=torch.float64, device="cuda")
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -883,7 +912,7 @@ def e2e_arm(G, torch, beam, opts, args):
         keep = []
         for i, s in enumerate(SHIFTS):
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
-            P = G.spai_build(A)
+            P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
             r = G.pcg_solve(A, P, dev["f"], opts)
             done = torch.cuda.Event()
             done.record(stream)
@@ -923,7 +952,8 @@ def config_dict(world):
     """The workload both arms time (the GPU arm and the reference arm print
     this same dict)."""
     return {"workload": "beam n_e=500000 (n=1e6, unit-element), tip load, 8 shifts "
-                        "logspace(-1,4), SPAI (QR, band-7) rebuilt per shift, PCG to 1e-10",
+                        "logspace(-1,4), exact band-7 SPAI (fixed-pattern least squares) rebuilt "
+                        "per shift, PCG to 1e-10",
             "n": 2 * N_E, "m": 1, "shifts": [float(s) for s in SHIFTS],
             "l2": "flushed (256 MiB write) before each timed step",
             "parallelism": "replicas" if world > 1 else "single"}

@@ -139,7 +139,8 @@ def test_ne_random_band_and_pcg(G):
     r_ne = G.pcg_solve(As, G.spai_build(As, ne(G)), F)
     r_qr = G.pcg_solve(As, G.spai_build(As), F)
     assert int(r_ne["status"][0]) == G.OK
-    assert abs(int(r_ne["iters"][0]) - int(r_qr["iters"][0])) <= 1
+    it_qr = int(r_qr["iters"][0])                    # the parity tests' iteration bar
+    assert abs(int(r_ne["iters"][0]) - it_qr) <= max(2, it_qr // 20)
     assert float(r_ne["true_relres"][0]) <= 2e-10
     Fo = W.loads(beam.n)[:, :1]
     xd = O.chol_solve(O.shifted_csr(beam, AL, BE, 0.5), Fo)[:, 0]
