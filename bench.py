@@ -50,10 +50,18 @@ PCG_BYTES_PER_ROW_ITER = 160     # A 56 + P_sym 56 + x, r, p read+write 48
 # of P_sym and the vectors; the bands stay in L2 after that
 PCG_DRAM_BYTES_PER_ROW_ITER = 0.641
 SPAI_FLOP_PER_COLUMN_MODEL = 1250  # algorithmic SPAI work per column (band-7 QR + solve)
-# FP64 instructions per interior column of the normal-equation SPAI build:
-# Gram band 28 FMA; L D L^T 35 + 21 FMA, 21 MUL, 7 x 4 for the reciprocals;
-# solves 42 FMA + 7 MUL; explicit residual 49 + 13 FMA; square root 4
-SPAI_NE_FP64_INSTR_PER_COLUMN = 248
+# FP64 instructions per interior column of the normal-equation SPAI build
+# as the bench runs it (no per-column residuals): Gram band 28 FMA; L D L^T
+# 35 + 21 FMA, 21 MUL, 7 x 4 for the reciprocals; solves 42 FMA + 7 MUL
+SPAI_NE_FP64_INSTR_PER_COLUMN = 182
+
+
+def spai_options(G):
+    """The SPAI build every GPU arm of the bench uses: the exact band-7 SPAI
+    by the normal equations (Householder fallback for ill-conditioned Gram
+    blocks); the per-column residual diagnostic is not requested, as the CG
+    calls request no residual history."""
+    return G.options(spai_mode=G.SPAI_NE, want_colres=0)
 
 
 def peaks():
@@ -185,7 +193,7 @@ def gpu_arm(args, world, rank, local):
     M, K = G.beam_mats(beam)
     F = torch.from_numpy(W.loads(n)[:, 0]).cuda()
     opts = G.options(tol=TOL, maxit=20000)
-    spai_opts = G.options(spai_mode=G.SPAI_NE)
+    spai_opts = spai_options(G)
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -268,7 +276,8 @@ def gpu_arm(args, world, rank, local):
         # column at the device's FP64 rate (TFLOP/s = 2 x FMA rate)
         floor_ms = n * SPAI_NE_FP64_INSTR_PER_COLUMN / (fp64_peak_tf * 1e12 / 2) * 1e3
         pcg_only["spai_build"] = {
-            "solver": "normal equations, L D L^T per column (Householder fallback)",
+            "solver": "normal equations, L D L^T per column (Householder fallback); per-column "
+                      "residuals not requested (want_colres = 0)",
             "ms_median": round(spai_ms, 4),
             "fp64_instr_per_column": SPAI_NE_FP64_INSTR_PER_COLUMN,
             "fp64_issue_floor_ms": round(floor_ms, 4),
@@ -332,7 +341,7 @@ def method_arms(G, torch, stream, M, K, F, shifts, opts):
         return out, e0.elapsed_time(e1)
 
     n = M.n
-    ne_opts = G.options(spai_mode=G.SPAI_NE)
+    ne_opts = spai_options(G)
     As = []
     rows = []
     for s in shifts:
@@ -484,7 +493,7 @@ def precision_form(G, torch, stream):
         for s in shifts:
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
             e0 = ev()
-            P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
+            P = G.spai_build(A, spai_options(G))
             e1 = ev()
             r64 = G.pcg_solve(A, P, Fd, o64)
             e2 = ev()
@@ -585,7 +594,7 @@ def batching_form(G, torch, stream):
         keep.append((M, K, Fd))
         for s in cfg["shifts"]:
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
-            P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
+            P = G.spai_build(A, spai_options(G))
             Xd = torch.zeros_like(Fd)
             per_shift.append((A, P, Fd, Xd))
             for c in range(cfg["m"]):
@@ -687,7 +696,7 @@ def learned_form(G, torch, stream):
         ftr = torch.from_numpy(W.loads(beam.n, 1)[:, 0].copy()).cuda() if n_e == 100_000 else None
         for s in train_shifts:
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
-            P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
+            P = G.spai_build(A, spai_options(G))
             X, T, m, _ = G.mlp_features(A, P, float(s), W.ALPHA, W.BETA, cols)
             Xs.append(X)
             Ts.append(T)
@@ -731,7 +740,7 @@ def learned_form(G, torch, stream):
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
             a0, a1, a2 = ev(), ev(), ev()
             a0.record(stream)
-            Pex = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
+            Pex = G.spai_build(A, spai_options(G))
             a1.record(stream)
             rex = G.pcg_solve(A, Pex, f, opts)
             a2.record(stream)
@@ -755,7 +764,7 @@ def learned_form(G, torch, stream):
             if not ok_l:            # fallback: exact SPAI and a fresh solve
                 c0, c1 = ev(), ev()
                 c0.record(stream)
-                Pfb = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
+                Pfb = G.spai_build(A, spai_options(G))
                 rfb = G.pcg_solve(A, Pfb, f, opts)
                 c1.record(stream)
                 torch.cuda.synchronize()
@@ -849,7 +858,7 @@ def inner_loop_form(G, torch, stream):
             ms, ok, its, worst = 0.0, 0, [], 0.0
             for s in shifts:
                 A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(s))
-                P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
+                P = G.spai_build(A, spai_options(G))
                 y = torch.empty(n, dtype=torch.float64, device="cuda")
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
@@ -912,7 +921,7 @@ def e2e_arm(G, torch, beam, opts, args):
         keep = []
         for i, s in enumerate(SHIFTS):
             A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
-            P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
+            P = G.spai_build(A, spai_options(G))
             r = G.pcg_solve(A, P, dev["f"], opts)
             done = torch.cuda.Event()
             done.record(stream)

@@ -89,6 +89,11 @@ typedef struct {
     int32_t pattern_hbw;        /* SPAI pattern: band |i - j| <= pattern_hbw, 0..3 (default 3) */
     int32_t warm_start;         /* CG: nonzero = use X's content on entry as x_0 (default 0: x_0 = 0) */
     int32_t barrier_timeout_ms; /* bound on any single grid-barrier wait (default 2000) */
+    int32_t want_colres;        /* SPAI: 1 = keep ||b_j - A m_j|| per column for
+                                   airga_precond_status (default); 0 = the normal-equation solver
+                                   skips forming it (its residual pass is a quarter of that
+                                   solver's FP64 work) and those entries read NaN; the Householder
+                                   and MR solvers get it as a by-product and always keep it */
     double inner_tol;           /* mixed precision: FP32 inner solve to ||r_in|| <= inner_tol ||r|| (default 3e-4) */
     int32_t max_outer;          /* mixed precision: FP64 refinement steps per column (default 12) */
     int32_t mr_relative;        /* MR stop test: 0 = ||r|| <= mr_tol, the loop test of Algorithms 2 / 4

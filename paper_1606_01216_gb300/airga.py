@@ -58,6 +58,7 @@ class Options(C.Structure):
         ("pattern_hbw", C.c_int32),
         ("warm_start", C.c_int32),
         ("barrier_timeout_ms", C.c_int32),
+        ("want_colres", C.c_int32),
         ("inner_tol", C.c_double),
         ("max_outer", C.c_int32),
         ("mr_relative", C.c_int32),

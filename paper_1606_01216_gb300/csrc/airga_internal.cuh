@@ -187,9 +187,11 @@ cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_
 // doubles of scratch), L D L^T per column; columns whose Gram block is
 // ill-conditioned are solved by the Householder kernel instead and marked
 // steps[j] = 1 (steps zeroed by the caller).  fb: n + 1 int32 of scratch.
+// want_colres false: the NE columns' colres entries are set to NaN instead
+// of forming the residual (the Householder columns still write theirs).
 cudaError_t launch_spai_ne(int64_t n, const double *A, const double *A_old, double *F,
-                           double *colres, int32_t *rank_flag, int32_t *steps, double *U,
-                           int32_t *fb, cudaStream_t s);
+                           double *colres, bool want_colres, int32_t *rank_flag, int32_t *steps,
+                           double *U, int32_t *fb, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // general sparse storage (csr_kernels.cu, spai_csr.cu, pcg_csr.cu)

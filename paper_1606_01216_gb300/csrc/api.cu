@@ -203,7 +203,7 @@ static int spai_factor(airga_mat A, airga_mat A_old, const airga_options &o, cud
         double *U = (double *)tmp;
         int32_t *fb = (int32_t *)(U + 7 * (size_t)n);
         const cudaError_t e = launch_spai_ne(n, A->band->d, Aold, (*F)->d, (double *)out->col_res.get(),
-                                             (int32_t *)out->rank_flag.get(),
+                                             o.want_colres != 0, (int32_t *)out->rank_flag.get(),
                                              (int32_t *)out->col_steps.get(), U, fb, s);
         dev_free(tmp, s);
         if (e != cudaSuccess) return cuda_fail(e, "spai NE launch");
@@ -249,6 +249,7 @@ void airga_options_default(airga_options *o) {
     o->pattern_hbw = 3;
     o->warm_start = 0;
     o->barrier_timeout_ms = 2000;
+    o->want_colres = 1;
     o->inner_tol = 3e-4;   // fewest FP32 + FP64 iterations on the beam workloads (measured)
     o->max_outer = 12;
     o->mr_relative = 0;    // the paper's ||r|| <= tol

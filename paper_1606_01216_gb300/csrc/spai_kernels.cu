@@ -558,7 +558,7 @@ template <int UPD>
 __global__ void __launch_bounds__(kThreadsSpai)
 spai_ne_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
                const double *__restrict__ U, double *__restrict__ F, double *__restrict__ colres,
-               int32_t *__restrict__ fb_count, int32_t *__restrict__ fb_list) {
+               int want_colres, int32_t *__restrict__ fb_count, int32_t *__restrict__ fb_list) {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= n) return;
     bool in[7];
@@ -638,7 +638,9 @@ spai_ne_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
         for (int k = i + 1; k < 7; ++k) s = fma(-L[k][i], m[k], s);
         m[i] = s;
     }
-    if (colres) {
+    if (colres && !want_colres) {
+        colres[j] = __longlong_as_double(0x7FF8000000000000ll);   // not formed: NaN
+    } else if (colres) {
         // ||b_j - Ahat m|| from the explicit residual over the 13 rows
         double rr = 0.0;
 #pragma unroll
@@ -749,8 +751,9 @@ cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_
 }
 
 cudaError_t launch_spai_ne(int64_t n, const double *A, const double *A_old, double *F,
-                           double *colres, int32_t *rank_flag, int32_t *steps, double *U,
-                           int32_t *fb, cudaStream_t s) {
+                           double *colres, bool want_colres, int32_t *rank_flag, int32_t *steps,
+                           double *U, int32_t *fb, cudaStream_t s) {
+    const int want = want_colres ? 1 : 0;
     const cudaError_t fe = injected_launch_error();   // host-side test fault only
     if (fe != cudaSuccess) return fe;
     const int64_t gb = (n + kGramRows - 1) / kGramRows;
@@ -761,9 +764,9 @@ cudaError_t launch_spai_ne(int64_t n, const double *A, const double *A_old, doub
     if (e != cudaSuccess) return e;
     const int64_t blocks = (n + kThreadsSpai - 1) / kThreadsSpai;
     if (A_old)
-        spai_ne_kernel<1><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, A_old, U, F, colres, fb, fb + 1);
+        spai_ne_kernel<1><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, A_old, U, F, colres, want, fb, fb + 1);
     else
-        spai_ne_kernel<0><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, nullptr, U, F, colres, fb, fb + 1);
+        spai_ne_kernel<0><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, nullptr, U, F, colres, want, fb, fb + 1);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the Householder pass over the listed columns: one resident wave

@@ -80,7 +80,8 @@ def test_options_layout_matches_header(G):
     # offsets follow C's natural alignment of the struct in airga.h
     O = G.Options
     assert O.tol.offset == 0 and O.maxit.offset == 8 and O.mr_tol.offset == 16
-    assert O.barrier_timeout_ms.offset == 40 and O.inner_tol.offset == 48
+    assert O.barrier_timeout_ms.offset == 40 and O.want_colres.offset == 44
+    assert O.inner_tol.offset == 48
     assert O.max_outer.offset == 56 and O.mr_relative.offset == 60 and C.sizeof(O) == 64
 
 

@@ -157,3 +157,26 @@ def test_ne_narrow_patterns_fall_back_to_qr(G):
         a = G.precond_factor(G.spai_build(A, G.options(spai_mode=G.SPAI_NE, pattern_hbw=hbw)), 0)
         b = G.precond_factor(G.spai_build(A, G.options(pattern_hbw=hbw)), 0)
         assert torch.equal(a, b)
+
+
+def test_ne_without_column_residuals(G):
+    """want_colres = 0 skips only the residual pass: the factor is the same
+    bit for bit, the NE columns' residual entries read NaN and the columns
+    the Householder kernel took keep theirs."""
+    beam = W.beam(200)
+    D = O.shifted_csr(beam, AL, BE, 1.0).dense()
+    D[:, 40:42] *= 1e-3                              # columns 37..44 take the Householder pass
+    A = G.mat_from_band(torch.from_numpy(band_of(D).ravel()).cuda())
+    P1 = G.spai_build(A, G.options(spai_mode=G.SPAI_NE))
+    P0 = G.spai_build(A, G.options(spai_mode=G.SPAI_NE, want_colres=0))
+    assert torch.equal(G.precond_factor(P0, 0), G.precond_factor(P1, 0))
+    r = torch.from_numpy(np.random.default_rng(5).standard_normal(beam.n)).cuda()
+    assert torch.equal(G.precond_apply(P0, r), G.precond_apply(P1, r))      # P_sym r
+    c0, c1 = G.precond_status(P0)[1].cpu().numpy(), G.precond_status(P1)[1].cpu().numpy()
+    fb = np.zeros(c0.size, dtype=bool)
+    fb[37:45] = True
+    assert np.all(np.isnan(c0[~fb]))
+    assert np.array_equal(c0[fb], c1[fb])
+    # the Householder solver keeps its by-product residuals either way
+    Pq = G.spai_build(A, G.options(want_colres=0))
+    assert not np.any(np.isnan(G.precond_status(Pq)[1].cpu().numpy()))
