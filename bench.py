@@ -49,6 +49,10 @@ PCG_BYTES_PER_ROW_ITER = 160     # A 56 + P_sym 56 + x, r, p read+write 48
 # current kernel: 146.7 MB, about one pass over the packed A, the upper half
 # of P_sym and the vectors; the bands stay in L2 after that
 PCG_DRAM_BYTES_PER_ROW_ITER = 0.641
+# L2 traffic of pcg_pair_kernel per row and iteration: the packed beam A
+# (40 B) and the upper diagonals of P_sym (32 B); the vectors live in shared
+# memory
+PCG_L2_BYTES_PER_ROW_ITER = 72
 SPAI_FLOP_PER_COLUMN_MODEL = 1250  # algorithmic SPAI work per column (band-7 QR + solve)
 # FP64 instructions per interior column of the normal-equation SPAI build
 # as the bench runs it (no per-column residuals): Gram band 28 FMA; L D L^T
@@ -92,6 +96,17 @@ def fp64_peak(G, sm_max_mhz, sms=152):
             "probe_tflops_at_run_clock": round(tf, 4), "probe_ms": round(ms, 3),
             "source": "derived: 152 SMs x %.3f FP64 FMA/clk/SM (measured, cycle counters) x 2 "
                       "flop x %.0f MHz" % (f, sm_max_mhz)}
+
+
+def read_bw(G):
+    """Measured read bandwidths of this GPU for the rooflines of L2-resident
+    working sets: a 64 MiB buffer (inside L2: L2 reads) and a 4 GiB one
+    (DRAM), best of three probes each."""
+    l2 = max(G.probe_read_bw(64 << 20, 100)[0] for _ in range(3))
+    dram = max(G.probe_read_bw(4 << 30, 4)[0] for _ in range(3))
+    return {"l2_read_gbs": round(l2, 1), "dram_read_gbs": round(dram, 1),
+            "method": "airga_probe_read_bw: 16-byte L1-bypassing loads, 4 x 512 threads per SM, "
+                      "64 MiB x 100 passes (L2) and 4 GiB x 4 passes (DRAM), best of 3"}
 
 
 def dist_env():
@@ -258,6 +273,8 @@ def gpu_arm(args, world, rank, local):
     byts = sum(pcg_it) * n * PCG_BYTES_PER_ROW_ITER
     pk = peaks()
     f64 = fp64_peak(G, pk["sm_max_mhz"])
+    rb = read_bw(G)
+    l2_gbs = sum(pcg_it) * n * PCG_L2_BYTES_PER_ROW_ITER / (tot_ms * 1e-3) / 1e9
     fp64_peak_tf = f64["tflops"]
     achieved_tf = flops / (tot_ms * 1e-3) / 1e12
     achieved_gbs = byts / (tot_ms * 1e-3) / 1e9
@@ -315,7 +332,14 @@ def gpu_arm(args, world, rank, local):
                           "hbm_achieved_gbs": round(achieved_gbs, 1),
                           "hbm_peak_gbs": pk["hbm_gbs"],
                           "hbm_frac": round(achieved_gbs / pk["hbm_gbs"], 4),
-                          "peak_source": f64["source"]},
+                          "peak_source": f64["source"],
+                          "read_bw": rb,
+                          "l2_view": {"bytes_per_row_iter": PCG_L2_BYTES_PER_ROW_ITER,
+                                      "achieved_gbs": round(l2_gbs, 1),
+                                      "frac_of_l2_read": round(l2_gbs / rb["l2_read_gbs"], 4),
+                                      "note": "packed A 40 B + P_sym upper diagonals 32 B per "
+                                              "row and iteration, the bands' L2-resident "
+                                              "traffic (vectors stay in shared memory)"}},
                 detail=detail, e2e=e2e, dist=dist, forms=forms, pcg_only=pcg_only)
 
 
@@ -540,8 +564,23 @@ def precision_form(G, torch, stream):
             outer_tot += int(rmx["outer_iters"].sum())
             it64_tot += int(r64["iters"].sum())
     nsol = len(shifts) * 8
+    # L2 view of the inner iteration: 36 B per row of FP32 bands (packed A
+    # 20 B + P_sym upper diagonals 16 B) read from L2, vectors in shared memory
+    l2 = max(G.probe_read_bw(64 << 20, 100)[0] for _ in range(3))
+    n_rows = 2 * 1_000_000
+    inner_us = tmx * 1e3 / max(1, inner_tot)
+    floor_us = n_rows * 36 / (l2 * 1e9) * 1e6
     return {"workload": "beam n_e=1e6 (n=2e6), m=8 (tip + 7 N(0,1), seed 4), 16 shifts "
-                        "logspace(-1,4), SPAI (QR) per shift",
+                        "logspace(-1,4), exact band-7 SPAI (normal equations) per shift",
+            "inner_iteration_l2": {
+                "l2_read_gbs_measured": round(l2, 1),
+                "bytes_per_row": 36,
+                "l2_floor_us": round(floor_us, 2),
+                "us_per_inner_iteration": round(inner_us, 2),
+                "frac_of_l2_floor": round(floor_us / inner_us, 3) if inner_us > 0 else None,
+                "note": "measured time per inner iteration includes the FP64 refinement "
+                        "residuals (an upper bound); the rest of the gap is the two grid "
+                        "barriers and their FP64 scalar chains per inner iteration"},
             "systems": nsol,
             "fp64_pcg": {"solves_per_s": round(ok64 / (t64 * 1e-3), 3), "converged": ok64,
                          "ms": round(t64, 3), "cg_iterations": it64_tot,

@@ -594,6 +594,16 @@ int airga_debug_force_pcg_kernel(int kind);
 int airga_probe_fp64_rate(int64_t iters, double *fma_per_clk_sm, double *tflops, double *ms,
                           void *stream);
 
+/* Measurement aid, no counterpart in the paper: read bandwidth of a device
+ * buffer of `bytes` (a multiple of 16 in [1 MiB, 16 GiB]; below the L2 size
+ * this is the L2 read bandwidth, above it DRAM's).  4 CTAs of 512 threads
+ * per SM stream 16-byte loads that bypass L1 over the buffer (from the
+ * library pool, filled first); one untimed pass warms the cache, then
+ * `passes` (1..1000) passes run in one timed launch.  *gbs (host) receives
+ * bytes x passes / time in GB/s, *ms (host, may be NULL) the time.
+ * SYNCHRONISES `stream`. */
+int airga_probe_read_bw(int64_t bytes, int32_t passes, double *gbs, double *ms, void *stream);
+
 /* Release the library's cached device memory (pool trim) on the current
  * device; outstanding handles stay valid. */
 int airga_trim(void);

@@ -41,7 +41,7 @@ EXPORTS = (
     "airga_debug_force_pcg_kernel", "airga_mat_is_banded", "airga_mat_nnz", "airga_mat_to_csr",
     "airga_precond_is_banded", "airga_precond_factor_nnz", "airga_precond_factor_csr",
     "airga_precond_from_csr", "airga_probe_fp64_rate", "airga_debug_pool_used",
-    "airga_debug_checked", "airga_debug_check_selftest",
+    "airga_debug_checked", "airga_debug_check_selftest", "airga_probe_read_bw",
 )
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
@@ -153,6 +153,7 @@ def lib():
         "airga_debug_set_fault": (C.c_int, [C.c_int]),
         "airga_debug_pool_used": (C.c_int, [C.POINTER(i64)]),
         "airga_debug_checked": (C.c_int, [C.POINTER(i64), C.POINTER(i32), C.POINTER(i64)]),
+        "airga_probe_read_bw": (C.c_int, [i64, i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]),
         "airga_debug_check_selftest": (C.c_int, [i64, i64, i32, vp]),
         "airga_debug_force_pcg_kernel": (C.c_int, [C.c_int]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
@@ -581,6 +582,15 @@ def probe_fp64_rate(iters: int = 1 << 16, stream=None):
     _check(lib().airga_probe_fp64_rate(int(iters), C.byref(f), C.byref(t), C.byref(ms),
                                        _stream(stream)), "probe_fp64_rate")
     return f.value, t.value, ms.value
+
+
+def probe_read_bw(nbytes: int, passes: int = 20, stream=None):
+    """(GB/s, ms) of streaming reads over a device buffer of `nbytes`
+    (below the L2 size: L2 read bandwidth; measurement aid)."""
+    g, ms = C.c_double(), C.c_double()
+    _check(lib().airga_probe_read_bw(int(nbytes), int(passes), C.byref(g), C.byref(ms),
+                                     _stream(stream)), "probe_read_bw")
+    return g.value, ms.value
 
 
 def debug_pool_used() -> int:

@@ -111,3 +111,71 @@ extern "C" int airga_probe_fp64_rate(int64_t iters, double *fma_per_clk_sm, doub
     if (ms) *ms = best_ms;
     return AIRGA_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Read bandwidth of a buffer of `bytes` (no counterpart in the paper): a
+// buffer below the L2 size measures L2 read bandwidth, a larger one DRAM.
+// Every thread streams 16-byte loads that bypass L1 (ld.global.cg) in a
+// grid-stride loop; one untimed pass warms the cache, then `passes` passes
+// are timed with events.  The XOR of everything read goes to `sink` only if
+// it has an impossible value, so the loads cannot be removed.
+// ---------------------------------------------------------------------------
+namespace airga {
+namespace {
+
+__global__ void __launch_bounds__(512)
+read_bw_kernel(const uint4 *__restrict__ buf, int64_t n16, int passes, unsigned *sink) {
+    unsigned acc = 0u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int p = 0; p < passes; ++p)
+        for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n16; i += stride) {
+            const uint4 v = __ldcg(buf + i);
+            acc ^= v.x ^ v.y ^ v.z ^ v.w;
+        }
+    if (acc == 0x9E3779B9u) sink[0] = acc;
+}
+
+}  // namespace
+}  // namespace airga
+
+extern "C" int airga_probe_read_bw(int64_t bytes, int32_t passes, double *gbs, double *ms,
+                                   void *stream) {
+    if (bytes < (1 << 20) || bytes > ((int64_t)16 << 30) || (bytes & 15))
+        return fail(AIRGA_E_INVALID_ARG, "bytes must be a multiple of 16 in [1 MiB, 16 GiB]");
+    if (passes < 1 || passes > 1000) return fail(AIRGA_E_INVALID_ARG, "passes must be in [1, 1000]");
+    if (!gbs) return fail(AIRGA_E_INVALID_ARG, "gbs is NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    AIRGA_CUDA(cudaGetDevice(&dev));
+    AIRGA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    void *buf = nullptr;
+    int st = dev_alloc(&buf, (size_t)bytes + 64, s);
+    if (st) return st;
+    unsigned *sink = (unsigned *)((char *)buf + bytes);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMemsetAsync(buf, 0x5A, (size_t)bytes, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const int64_t n16 = bytes / 16;
+    const unsigned grid = (unsigned)sms * 4u;
+    float t = 0.f;
+    if (e == cudaSuccess) {
+        read_bw_kernel<<<grid, 512, 0, s>>>((const uint4 *)buf, n16, 1, sink);   // warm
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+    if (e == cudaSuccess) {
+        read_bw_kernel<<<grid, 512, 0, s>>>((const uint4 *)buf, n16, passes, sink);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    dev_free(buf, s);
+    if (e != cudaSuccess) return cuda_fail(e, "read bandwidth probe");
+    *gbs = t > 0.f ? (double)bytes * passes / (t * 1e-3) / 1e9 : 0.0;
+    if (ms) *ms = t;
+    return AIRGA_OK;
+}
