@@ -249,7 +249,8 @@ constexpr int kMaxChain = 16;
 
 struct PcgPlan {
     int kind = 0;          // 0 generic (shared-memory state), 1 generic (global state), 2 node-pair,
-                           // 3 node-pair with r, p in shared memory and x, z/q in global memory
+                           // 3 node-pair with r, p in shared memory and x, z/q in global memory,
+                           // 4 the same on half an SM (two solves side by side)
     int grid = 0;          // CTAs (all co-resident)
     int threads = 0;
     int64_t rows = 0;      // rows per CTA (R)
@@ -300,18 +301,24 @@ cudaError_t injected_launch_error();
 
 // aligned16: A, the preconditioner band, b and x are 16-byte aligned (needed
 // by the node-pair kernel together with an even n)
-int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgPlan *plan);
+// share = 2: the solve may take at most half of each SM (plan kind 4 when it
+// applies), so that two solves on different streams run side by side
+int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgPlan *plan,
+             int share = 1);
 cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
 // test hook: 0 = automatic kernel choice, 1 = generic kernel with global
 // state, 2 = node-pair kernel with shared-memory state, 3 = node-pair kernel
-// with split state (whenever the forced kind is feasible)
+// with split state, 4 = node-pair kernel with split state on half an SM
+// (whenever the forced kind is feasible)
 int forced_pcg_kind();
 // node-pair kernel (pcg_pair.cu)
 size_t pcg_pair_smem(int64_t R);
 size_t pcg_pair_split_smem(int64_t R);       // r and p windows only
 size_t pcg_pair_split_slice(int64_t R);      // doubles of global workspace per CTA (z/q window)
 int pcg_pair_split_occupancy(int mode, size_t smem, int *per_sm);
-int pcg_pair_threads(int kind);   // threads per CTA of plan kind 2 or 3
+size_t pcg_pair_half_smem(int64_t R);        // split state at 256 threads
+int pcg_pair_half_occupancy(int mode, size_t smem, int *per_sm);
+int pcg_pair_threads(int kind);   // threads per CTA of plan kind 2, 3 or 4
 int pcg_pair_occupancy(int mode, size_t smem, int *per_sm);
 cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
 // batched node-pair kernel: systems `sys`, assignments asg (int4: system,

@@ -806,7 +806,7 @@ int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m
 }
 
 int airga_debug_force_pcg_kernel(int kind) {
-    if (kind < 0 || kind > 3) return fail(AIRGA_E_INVALID_ARG, "kernel kind must be 0..3");
+    if (kind < 0 || kind > 4) return fail(AIRGA_E_INVALID_ARG, "kernel kind must be 0..4");
     g_forced_kind.store(kind);
     return AIRGA_OK;
 }

@@ -439,11 +439,13 @@ int mode_of(int nf, bool psym_path) {
 
 }  // namespace
 
-int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgPlan *plan) {
+int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgPlan *plan,
+             int share) {
     const int mode = mode_of(nf, psym_path);
-    int sms = 0, optin = 0;
+    int sms = 0, optin = 0, smem_sm = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
     const int forced = forced_pcg_kind();
     // node-pair kernel: even n, aligned operands, no update chain; state in
     // shared memory (kind 2), or r and p in shared memory with x and z/q in
@@ -456,7 +458,28 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
         int64_t Rp = (n + grid_p - 1) / grid_p;
         Rp += Rp & 1;
         const size_t smem_p = pcg_pair_smem(Rp), smem_s = pcg_pair_split_smem(Rp);
-        bool ok2 = false, ok3 = false;
+        bool ok2 = false, ok3 = false, ok4 = false;
+        if (share == 2 || forced == 4) {
+            // half an SM: two CTAs of this kernel (two solves) per SM
+            const size_t smem_h = pcg_pair_half_smem(Rp);
+            if (2 * (smem_h + 1024) <= (size_t)smem_sm) {
+                int per_sm = 0;
+                int st = pcg_pair_half_occupancy(mode == kIdentity ? 0 : 1, smem_h, &per_sm);
+                if (st) return st;
+                ok4 = per_sm >= 2 && grid_p <= sms;
+            }
+            if (ok4) {
+                plan->kind = 4;
+                plan->threads = pcg_pair_threads(4);
+                plan->halo = 8;
+                plan->grid = grid_p;
+                plan->rows = Rp;
+                plan->smem_state = false;
+                plan->smem_bytes = smem_h;
+                plan->scratch_doubles = pcg_pair_split_slice(Rp) * (size_t)grid_p;
+                return AIRGA_OK;
+            }
+        }
         if (smem_p + 256 <= (size_t)optin) {
             int per_sm = 0;
             int st = pcg_pair_occupancy(mode == kIdentity ? 0 : 1, smem_p, &per_sm);

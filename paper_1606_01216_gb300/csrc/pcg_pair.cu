@@ -43,6 +43,10 @@ using namespace pcgdev;
 // upper-diagonal P_sym read; the split-state kernel, whose windows partly
 // live in L2, keeps 512 warps' worth of latency hiding
 constexpr int kThreadsFull = 384, kThreadsSplit = 512, kThreadsBatch = 384;
+// half-SM split-state kernel (SPLIT == 2): 256 threads and at most half an
+// SM's registers and shared memory, so that two solves on different streams
+// share every SM and each fills the other's barrier and scalar-chain gaps
+constexpr int kThreadsHalf = 256;
 constexpr int kThreadsMax = 512;   // sizes the shared-memory reduction buffer
 constexpr int HR = 8, HP = 12, HZ = 4;
 constexpr int kHaloPairs = HR;   // 4 pairs of r halo on each side
@@ -233,9 +237,10 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
     if (tid == 0) s_nb = 0.0;
 
     // SPLIT == 0: x, r, p, z/q windows all in shared memory.  SPLIT == 1 (n too
-    // large for four windows): r and p stay in shared memory, x is updated in
-    // place in the caller's X and the z/q window lives in this CTA's slice of
-    // the global workspace (L2 traffic of 48 B per row and iteration).
+    // large for four windows) and SPLIT == 2 (half an SM per CTA): r and p
+    // stay in shared memory, x is updated in place in the caller's X and the
+    // z/q window lives in this CTA's slice of the global workspace (L2
+    // traffic of 48 B per row and iteration).
     double *xs, *rs, *ps, *zq;
     if (SPLIT) {
         rs = smem;
@@ -578,7 +583,8 @@ finish:
 }
 
 template <int MODE, int SPLIT>
-__global__ void __launch_bounds__(SPLIT ? kThreadsSplit : kThreadsFull, 1)
+__global__ void __launch_bounds__(SPLIT == 2 ? kThreadsHalf : (SPLIT ? kThreadsSplit : kThreadsFull),
+                                  SPLIT == 2 ? 2 : 1)
 pcg_pair_kernel(PcgArgs a, int R) {
     extern __shared__ __align__(16) double smem[];
     __shared__ PairShared sh;
@@ -630,9 +636,22 @@ size_t pcg_pair_split_smem(int64_t R) {
     return (size_t)(2 * R + 2 * (HR + HZ) + 2 * kHaloPairs * kBand + 3 * kThreadsSplit) * sizeof(double);
 }
 
+size_t pcg_pair_half_smem(int64_t R) {
+    return (size_t)(2 * R + 2 * (HR + HZ) + 2 * kHaloPairs * kBand + 3 * kThreadsHalf) * sizeof(double);
+}
+
 size_t pcg_pair_split_slice(int64_t R) { return (size_t)(R + 2 * HZ); }
 
-int pcg_pair_threads(int kind) { return kind == 3 ? kThreadsSplit : kThreadsFull; }
+int pcg_pair_threads(int kind) {
+    return kind == 3 ? kThreadsSplit : (kind == 4 ? kThreadsHalf : kThreadsFull);
+}
+
+int pcg_pair_half_occupancy(int mode, size_t smem, int *per_sm) {
+    const void *kern = mode == 0 ? (const void *)pcg_pair_kernel<0, 2> : (const void *)pcg_pair_kernel<1, 2>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, kThreadsHalf, smem);
+    return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg pair half occupancy");
+}
 
 int pcg_pair_occupancy(int mode, size_t smem, int *per_sm) {
     cudaError_t e;
@@ -690,6 +709,10 @@ int pcg_pair_split_occupancy(int mode, size_t smem, int *per_sm) {
 }
 
 cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
+    if (plan.kind == 4) {
+        if (args.nf == 0) return launch_pair_mode<0, 2>(plan, args, s);
+        return launch_pair_mode<1, 2>(plan, args, s);
+    }
     if (plan.kind == 3) {
         if (args.nf == 0) return launch_pair_mode<0, 1>(plan, args, s);
         return launch_pair_mode<1, 1>(plan, args, s);
