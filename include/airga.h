@@ -574,13 +574,16 @@ int airga_debug_check_selftest(int64_t index, int64_t bound, int32_t site, void 
  * when even n fits, else the node-pair kernel with the r and p windows in
  * shared memory and x, z/q in global memory, else the generic kernel.
  * 1 = generic kernel with its state in global memory, 2 = node-pair kernel
- * with shared-memory state, 3 = node-pair kernel with split state.  A variant
- * that does not apply (odd n, unaligned operands, update chains, too little
- * shared memory) falls through to the next one as in automatic mode. */
+ * with shared-memory state, 3 = node-pair kernel with split state, 4 = the
+ * split-state kernel on half an SM (256 threads, two CTAs per SM: two solves
+ * on different streams share the SMs).  A variant that does not apply (odd
+ * n, unaligned operands, update chains, too little shared memory) falls
+ * through to the next one as in automatic mode. */
 #define AIRGA_PCG_KERNEL_AUTO 0
 #define AIRGA_PCG_KERNEL_GENERIC_GLOBAL 1
 #define AIRGA_PCG_KERNEL_PAIR 2
 #define AIRGA_PCG_KERNEL_PAIR_SPLIT 3
+#define AIRGA_PCG_KERNEL_PAIR_HALF 4
 int airga_debug_force_pcg_kernel(int kind);
 
 /* Measurement aid, no counterpart in the paper: the FP64 FMA issue rate of

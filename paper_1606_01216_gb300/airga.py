@@ -565,6 +565,7 @@ def true_residual(A: Mat, X: torch.Tensor, F: torch.Tensor, stream=None) -> torc
 
 FAULT_NONE, FAULT_SKIP_ARRIVAL, FAULT_ALLOC, FAULT_LAUNCH = 0, 1, 2, 3
 PCG_KERNEL_AUTO, PCG_KERNEL_GENERIC_GLOBAL, PCG_KERNEL_PAIR, PCG_KERNEL_PAIR_SPLIT = 0, 1, 2, 3
+PCG_KERNEL_PAIR_HALF = 4
 
 
 def debug_force_pcg_kernel(kind: int):

@@ -741,14 +741,16 @@ def test_literal_scaling_config1(G, s):
         assert int(res["status"][0]) == G.E_MAXIT and st_o == O.EMAXIT
 
 
-@pytest.mark.parametrize("kind", [1, 3])
+@pytest.mark.parametrize("kind", [1, 3, 4])
 @pytest.mark.parametrize("s", [0.1, 100.0])
 def test_pcg_forced_kernel_variants(G, kind, s):
     """Every CG kernel variant against the oracle on a small beam: the
-    generic kernel with global state (kind 1) and the node-pair kernel with
+    generic kernel with global state (kind 1), the node-pair kernel with
     the split state (kind 3, r and p in shared memory, x and z/q in global
     memory; chosen automatically only when n is too large for the
-    shared-memory state), with and without a preconditioner."""
+    shared-memory state) and the same on half an SM (kind 4, 256 threads,
+    two CTAs per SM: two solves side by side), with and without a
+    preconditioner."""
     beam, M, K = setup_beam(G, 1237)
     A = G.assemble_shifted(M, K, AL, BE, s)
     P = G.spai_build(A)
