@@ -565,7 +565,7 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
 cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s) {
     const cudaError_t fe = injected_launch_error();   // host-side test fault only
     if (fe != cudaSuccess) return fe;
-    if (plan.kind == 2 || plan.kind == 3) return launch_pcg_pair(plan, args, s);
+    if (plan.kind >= 2) return launch_pcg_pair(plan, args, s);       // node-pair kinds 2, 3, 4
     const int mode = mode_of(args.nf, args.psym != nullptr);
     if (plan.smem_state) {
         if (mode == kIdentity) return launch_mode<1, kIdentity>(plan, args, s);
