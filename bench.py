@@ -5,8 +5,12 @@ force, 8 real shifts log-spaced in [1e-1, 1e4], SPAI rebuilt per shift.
 One step = the whole plain path over the 8 shifts: for each shift
 assemble_shifted -> spai_build (exact fixed-pattern SPAI, least squares by
 the normal equations with the Householder fallback, + P_sym) -> pcg_solve
-(PCG to 1e-10 plus the true FP64 residual).  The Householder (QR) build is
-timed beside it in `detail`.  value = 8 solves / device time of a step
+(PCG to 1e-10 plus the true FP64 residual).  The shifts run on two streams,
+split longest-first by the CG iterations the first warm-up step measured,
+and every CG call takes half of each SM (options.sm_share = 2), so two
+solves share the SMs and fill each other's barrier gaps.  The Householder
+(QR) build and the whole-SM CG kernel are timed alone beside it in
+`detail`.  value = 8 solves / device time of a step
 (CUDA events on the launching stream; L2 flushed before every timed step by
 writing a 256 MiB buffer outside the timed interval).
 
@@ -53,6 +57,9 @@ PCG_DRAM_BYTES_PER_ROW_ITER = 0.641
 # (40 B) and the upper diagonals of P_sym (32 B); the vectors live in shared
 # memory
 PCG_L2_BYTES_PER_ROW_ITER = 72
+# DRAM bytes per row and iteration of the half-SM kernel (pcg_pair_kernel<1, 2>)
+# from its ncu capture on this workload; None until captured
+PCG_DRAM_BYTES_PER_ROW_ITER_HALF = None
 SPAI_FLOP_PER_COLUMN_MODEL = 1250  # algorithmic SPAI work per column (band-7 QR + solve)
 # FP64 instructions per interior column of the normal-equation SPAI build
 # as the bench runs it (no per-column residuals): Gram band 28 FMA; L D L^T
@@ -207,42 +214,70 @@ def gpu_arm(args, world, rank, local):
     n = beam.n
     M, K = G.beam_mats(beam)
     F = torch.from_numpy(W.loads(n)[:, 0]).cuda()
-    opts = G.options(tol=TOL, maxit=20000)
+    # two solves share the SMs: every CG call takes half of each SM
+    # (sm_share = 2) and the shifts run on two streams
+    opts = G.options(tol=TOL, maxit=20000, sm_share=2)
     spai_opts = spai_options(G)
     stream = torch.cuda.current_stream()
+    stream_b = torch.cuda.Stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    pcg_events = []       # (start, end, iters tensor) of every pcg_solve in timed steps
+    pcg_events = []       # (start, end, iters tensor, step start) of every pcg_solve in timed steps
     launches_per_step = 0
+    parts = [[0], list(range(1, len(SHIFTS)))]   # until a step has measured the shifts' costs
 
-    def step(record):
+    def step(record, t0=None):
         nonlocal launches_per_step
-        out = []
+        out = [None] * len(SHIFTS)
         cnt = 0
-        for s in SHIFTS:
-            A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
-            P = G.spai_build(A, spai_opts)
-            cnt += 5                      # assemble (also writes the packed beam stencil),
+        go = torch.cuda.Event()
+        go.record(stream)
+        stream_b.wait_event(go)
+        for st, idx in zip((stream, stream_b), parts):
+            with torch.cuda.stream(st):
+                for k in idx:
+                    A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, SHIFTS[k], stream=st)
+                    P = G.spai_build(A, spai_opts, stream=st)
+                    cnt += 5              # assemble (also writes the packed beam stencil),
                                           # Gram band, normal-equation columns, Householder
                                           # pass over the (empty) fallback list, symmetrize
-            if record:
-                e0 = torch.cuda.Event(enable_timing=True)
-                e1 = torch.cuda.Event(enable_timing=True)
-                e0.record(stream)
-            r = G.pcg_solve(A, P, F, opts)
-            cnt += 1                      # pcg (true residual in the PCG kernel's epilogue)
-            if record:
-                e1.record(stream)
-                pcg_events.append((e0, e1, r["iters"]))
-            out.append(r)
+                    if record:
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(st)
+                    r = G.pcg_solve(A, P, F, opts, stream=st)
+                    cnt += 1              # pcg (true residual in the PCG kernel's epilogue)
+                    if record:
+                        e1.record(st)
+                        pcg_events.append((e0, e1, r["iters"], t0))
+                    out[k] = (r, A, P)
+        done = torch.cuda.Event()
+        done.record(stream_b)
+        stream.wait_event(done)           # the step ends when both streams are done
         launches_per_step = cnt
-        return out
+        return [o[0] for o in out]
+
+    def balance(res):
+        """Split the shifts over the two streams, longest first (LPT), by the
+        cost a step measured: CG iterations x the per-iteration time of the
+        whole-GPU kernel plus one SPAI build (constants of this workload,
+        0.042 ms and 0.36 ms)."""
+        cost = [0.042 * int(r["iters"][0]) + 0.36 for r in res]
+        load, split = [0.0, 0.0], [[], []]
+        for k in sorted(range(len(cost)), key=lambda k: -cost[k]):
+            j = 0 if load[0] <= load[1] else 1
+            split[j].append(k)
+            load[j] += cost[k]
+        return [sorted(split[0]), sorted(split[1])]
 
     clocks = Clocks(local)
     clocks.start()
     time.sleep(0.5)                   # let the sampler start before the GPU work
-    for _ in range(args.warmup):
-        step(False)
+    for w in range(args.warmup):
+        res = step(False)
+        torch.cuda.synchronize()
+        if w == 0:
+            parts = balance(res)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -253,7 +288,7 @@ def gpu_arm(args, world, rank, local):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        results = step(True)
+        results = step(True, e0)
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
@@ -265,10 +300,28 @@ def gpu_arm(args, world, rank, local):
     relres = [float(r["true_relres"][0]) for r in results]
     ok = all(s == G.OK for s in status) and all(x <= 2 * TOL for x in relres)
 
-    # dominant kernel: the persistent PCG launch (events bracket pcg_solve)
-    pcg_ms = [a.elapsed_time(b) for a, b, _ in pcg_events]
-    pcg_it = [int(it[0]) for _, _, it in pcg_events]
-    tot_ms = sum(pcg_ms)
+    # dominant kernel: the persistent PCG launches.  Two run at once (one per
+    # stream), so one launch's own event time includes SM time it shares with
+    # the other; achieved = all PCG algorithmic flops of the timed steps / the
+    # wall time during which at least one PCG launch ran (the union of the
+    # launch intervals, from events on each launching stream measured from
+    # the step's start event)
+    pcg_it = [int(it[0]) for _, _, it, _ in pcg_events]
+    per_step = {}
+    for a, b, _, t0 in pcg_events:
+        per_step.setdefault(id(t0), (t0, []))[1].append((t0.elapsed_time(a), t0.elapsed_time(b)))
+    tot_ms = 0.0
+    for t0, iv in per_step.values():
+        iv.sort()
+        lo_, hi_ = iv[0]
+        for a_, b_ in iv[1:]:
+            if a_ > hi_:
+                tot_ms += hi_ - lo_
+                lo_, hi_ = a_, b_
+            else:
+                hi_ = max(hi_, b_)
+        tot_ms += hi_ - lo_
+    launch_ms = [a.elapsed_time(b) for a, b, _, _ in pcg_events]
     flops = sum(pcg_it) * n * PCG_FLOP_PER_ROW_ITER
     byts = sum(pcg_it) * n * PCG_BYTES_PER_ROW_ITER
     pk = peaks()
@@ -280,7 +333,9 @@ def gpu_arm(args, world, rank, local):
     achieved_gbs = byts / (tot_ms * 1e-3) / 1e9
 
     # per-shift split of one step and the method's arms (untimed diagnostics)
-    detail = None if args.profile else method_arms(G, torch, stream, M, K, F, SHIFTS, opts)
+    # (sequential, every CG call on whole SMs: the kernel timed alone)
+    opts_alone = G.options(tol=TOL, maxit=20000)
+    detail = None if args.profile else method_arms(G, torch, stream, M, K, F, SHIFTS, opts_alone)
     # the survey's solves/s counts PCG time only, SPAI reported beside it
     pcg_step_ms = tot_ms / max(1, args.steps)
     pcg_only = {"solves_per_s": round(len(SHIFTS) / (pcg_step_ms * 1e-3), 3),
@@ -304,6 +359,22 @@ def gpu_arm(args, world, rank, local):
                    "frac_fp64_peak_model": round(model_gf / (fp64_peak_tf * 1e3), 4),
                    "model": "1.25 kflop per column (Householder QR of the 12x7 block + solve, "
                             "full band); the kernel issues fewer (structural zeros skipped)"}}
+    # the whole-SM kernel timed alone (the detail's sequential solves) and the
+    # step's FP64 issue: PCG 18 and SPAI 182 FP64 instructions per row
+    kernel_alone = None
+    if detail is not None:
+        it_a = sum(r["iters"] for r in detail["rebuild"])
+        ms_a = sum(r["pcg_ms"] for r in detail["rebuild"])
+        tf_a = it_a * n * PCG_FLOP_PER_ROW_ITER / (ms_a * 1e-3) / 1e12
+        kernel_alone = {"kernel": "pcg_pair_kernel<1, 0> (whole SMs, sequential solves)",
+                        "achieved": round(tf_a, 4), "frac": round(tf_a / fp64_peak_tf, 4),
+                        "pcg_ms": round(ms_a, 3), "iterations": it_a}
+    instr = (PCG_FLOP_PER_ROW_ITER // 2) * sum(pcg_it) / max(1, args.steps) * n + \
+        len(SHIFTS) * n * SPAI_NE_FP64_INSTR_PER_COLUMN
+    step_fp64 = {"fp64_instr_per_step": round(instr),
+                 "frac": round(instr / (ms * 1e-3 * fp64_peak_tf * 1e12 / 2), 4),
+                 "note": "PCG 18 FP64 instructions per row and iteration + SPAI 182 per "
+                         "column, over the step time at the FP64 issue rate"}
     forms = None
     if not args.profile and not args.no_forms:
         del M, K
@@ -313,7 +384,7 @@ def gpu_arm(args, world, rank, local):
         forms = {k: makers[k](G, torch, stream) for k in args.forms.split(",") if k}
 
     # end to end through the public API with host buffers
-    e2e = e2e_arm(G, torch, beam, opts, args) if rank == 0 and not args.profile else None
+    e2e = e2e_arm(G, torch, beam, opts, args, parts) if rank == 0 and not args.profile else None
 
     return dict(ms=ms, iters=iters, status=status, relres=relres, ok=ok, clocks=ck,
                 launches=launches_per_step * args.steps, n=n,
@@ -324,11 +395,19 @@ def gpu_arm(args, world, rank, local):
                           "frac_20fma_model": round(achieved_tf * PCG_FLOP_PER_ROW_ITER_MODEL /
                                                     PCG_FLOP_PER_ROW_ITER / fp64_peak_tf, 4),
                           "fp64_probe": f64,
-                          "traffic": round(sum(pcg_it) * n * PCG_DRAM_BYTES_PER_ROW_ITER /
-                                           len(pcg_it)),
-                          "traffic_note": "ncu DRAM bytes per launch, 0.641 B/row/iter x the "
-                                          "mean row-iterations of a launch",
-                          "kernel": "pcg_pair_kernel (persistent row-pair PCG, FP64)",
+                          "traffic": (round(sum(pcg_it) * n * PCG_DRAM_BYTES_PER_ROW_ITER_HALF /
+                                            len(pcg_it))
+                                      if PCG_DRAM_BYTES_PER_ROW_ITER_HALF is not None else None),
+                          "traffic_note": "ncu DRAM bytes per launch of the half-SM kernel, "
+                                          "B/row/iter x the mean row-iterations of a launch",
+                          "kernel": "pcg_pair_kernel<1, 2> (persistent row-pair PCG, FP64, half "
+                                    "an SM per CTA: two launches share the SMs)",
+                          "method": "achieved = PCG algorithmic flops of the timed steps / the "
+                                    "union of the PCG launch intervals (two launches overlap; "
+                                    "events on each launching stream)",
+                          "launch_ms_mean_shared": round(sum(launch_ms) / len(launch_ms), 4),
+                          "kernel_alone": kernel_alone,
+                          "step_fp64_issue": step_fp64,
                           "hbm_achieved_gbs": round(achieved_gbs, 1),
                           "hbm_peak_gbs": pk["hbm_gbs"],
                           "hbm_frac": round(achieved_gbs / pk["hbm_gbs"], 4),
@@ -944,13 +1023,15 @@ def inner_loop_form(G, torch, stream):
             "speedup_fused": round(res["unfused"]["ms"] / res["fused"]["ms"], 3)}
 
 
-def e2e_arm(G, torch, beam, opts, args):
+def e2e_arm(G, torch, beam, opts, args, parts):
     """Same step through the public API with host inputs: CSR of M and K and
     F copied from pinned host memory, X of every shift copied back.  As a
     production caller would, the step overlaps transfers with compute: K's
     values and F travel on a copy stream while M is imported, and each
     shift's X returns on the copy stream while the next shift runs.  The
-    timed region covers every copy (it ends after a device synchronise)."""
+    shifts run on two compute streams split as in the device-timed step
+    (`parts`).  The timed region covers every copy (it ends after a device
+    synchronise)."""
     n = beam.n
     host = {k: torch.from_numpy(v).pin_memory() for k, v in
             dict(rp=beam.rowptr, ci=beam.col, mv=beam.m_val, kv=beam.k_val,
@@ -960,6 +1041,7 @@ def e2e_arm(G, torch, beam, opts, args):
     info_host = torch.empty((len(SHIFTS), 3), dtype=torch.float64).pin_memory()
     d2h = xs_host.numel() * 8 + info_host.numel() * 8
     stream = torch.cuda.current_stream()
+    stream_b = torch.cuda.Stream()
     copy = torch.cuda.Stream()
 
     def one():
@@ -972,20 +1054,25 @@ def e2e_arm(G, torch, beam, opts, args):
         M = G.mat_from_csr(n, dev["rp"], dev["ci"], dev["mv"])
         stream.wait_event(landed)
         K = G.mat_from_csr(n, dev["rp"], dev["ci"], dev["kv"])
+        ready = torch.cuda.Event()
+        ready.record(stream)
+        stream_b.wait_event(ready)
         keep = []
-        for i, s in enumerate(SHIFTS):
-            A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, s)
-            P = G.spai_build(A, spai_options(G))
-            r = G.pcg_solve(A, P, dev["f"], opts)
-            done = torch.cuda.Event()
-            done.record(stream)
-            copy.wait_event(done)
-            with torch.cuda.stream(copy):
-                xs_host[i].copy_(r["X"], non_blocking=True)
-                info = torch.stack([r["iters"][0].double(), r["status"][0].double(),
-                                    r["true_relres"][0]])
-                info_host[i].copy_(info, non_blocking=True)
-            keep.append((r, info))       # alive until the final synchronise
+        for st, idx in zip((stream, stream_b), parts):
+            for i in idx:
+                with torch.cuda.stream(st):
+                    A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, SHIFTS[i], stream=st)
+                    P = G.spai_build(A, spai_options(G), stream=st)
+                    r = G.pcg_solve(A, P, dev["f"], opts, stream=st)
+                    done = torch.cuda.Event()
+                    done.record(st)
+                copy.wait_event(done)
+                with torch.cuda.stream(copy):
+                    xs_host[i].copy_(r["X"], non_blocking=True)
+                    info = torch.stack([r["iters"][0].double(), r["status"][0].double(),
+                                        r["true_relres"][0]])
+                    info_host[i].copy_(info, non_blocking=True)
+                keep.append((r, info, A, P))   # alive until the final synchronise
         torch.cuda.synchronize()
 
     for _ in range(max(1, min(args.warmup, 2))):

@@ -99,6 +99,13 @@ typedef struct {
     int32_t mr_relative;        /* MR stop test: 0 = ||r|| <= mr_tol, the loop test of Algorithms 2 / 4
                                    (default); 1 = ||r|| <= mr_tol ||b_j||, b_j = e_j (build) or
                                    A_prev e_j (update) — the same for a build, scale-free for an update */
+    int32_t sm_share;           /* CG: 1 = a solve may take every SM whole (default); 2 = at most half
+                                   of each SM's registers and shared memory (the node-pair kernel with
+                                   r, p in shared memory and x, z/q in L2, 256 threads, where it
+                                   applies: even n, aligned operands, no update chain), so that two
+                                   solves issued on different streams run side by side and each fills
+                                   the other's barrier and scalar-chain gaps on the FP64 pipe */
+    int32_t reserved0;          /* 0 */
 } airga_options;
 
 void airga_options_default(airga_options *opt);

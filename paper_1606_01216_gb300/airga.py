@@ -62,6 +62,8 @@ class Options(C.Structure):
         ("inner_tol", C.c_double),
         ("max_outer", C.c_int32),
         ("mr_relative", C.c_int32),
+        ("sm_share", C.c_int32),
+        ("reserved0", C.c_int32),
     ]
 
 

@@ -145,6 +145,8 @@ static std::atomic<int> g_forced_kind{0};
 
 int forced_pcg_kind() { return g_forced_kind.load(); }
 
+static_assert(sizeof(airga_options) == 72, "airga_options layout (the Python binding mirrors it)");
+
 int check_options(const airga_options *o) {
     if (!(o->tol >= 0.0) || !std::isfinite(o->tol)) return fail(AIRGA_E_INVALID_ARG, "tol must be finite and >= 0");
     if (o->maxit < 0) return fail(AIRGA_E_INVALID_ARG, "maxit must be >= 0");
@@ -156,6 +158,7 @@ int check_options(const airga_options *o) {
     if (o->pattern_hbw < 0 || o->pattern_hbw > 3)
         return fail(AIRGA_E_INVALID_ARG, "pattern_hbw must be in 0..3");
     if (o->barrier_timeout_ms <= 0) return fail(AIRGA_E_INVALID_ARG, "barrier_timeout_ms must be > 0");
+    if (o->sm_share != 1 && o->sm_share != 2) return fail(AIRGA_E_INVALID_ARG, "sm_share must be 1 or 2");
     if (!(o->inner_tol > 0.0) || !(o->inner_tol < 1.0))
         return fail(AIRGA_E_INVALID_ARG, "inner_tol must be in (0, 1)");
     if (o->max_outer < 1) return fail(AIRGA_E_INVALID_ARG, "max_outer must be >= 1");
@@ -250,6 +253,8 @@ void airga_options_default(airga_options *o) {
     o->warm_start = 0;
     o->barrier_timeout_ms = 2000;
     o->want_colres = 1;
+    o->sm_share = 1;
+    o->reserved0 = 0;
     o->inner_tol = 3e-4;   // fewest FP32 + FP64 iterations on the beam workloads (measured)
     o->max_outer = 12;
     o->mr_relative = 0;    // the paper's ||r|| <= tol
@@ -670,7 +675,7 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
               (!mband || aligned16(mband));
     for (int f = 0; f < nf; ++f) al = al && aligned16(P->factors[f]->d);   // chain stencils: double2
     PcgPlan plan;
-    st = pcg_plan(n, nf, nf == 1 && o.symmetrize, al, dev, &plan);
+    st = pcg_plan(n, nf, nf == 1 && o.symmetrize, al, dev, &plan, o.sm_share);
     if (st) return st;
     cudaStream_t s = S(stream);
     const bool fused_rhs = Mrhs && plan.kind >= 2;

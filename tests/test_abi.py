@@ -46,6 +46,7 @@ def test_host_only_calls(G):
     assert o.tol == 1e-10 and o.maxit == 20000 and o.pattern_hbw == 3 and o.symmetrize == 1
     assert o.mr_tol == 0.01 and o.mr_kmax == 50 and o.spai_mode == G.SPAI_QR
     assert o.inner_tol == 3e-4 and o.max_outer == 12 and o.mr_relative == 0
+    assert o.want_colres == 1 and o.sm_share == 1 and o.reserved0 == 0
     assert G.status_string(G.E_UNSUPPORTED).startswith("operation not available")
     assert G.status_string(1234) == "unknown status"
 
@@ -82,7 +83,8 @@ def test_options_layout_matches_header(G):
     assert O.tol.offset == 0 and O.maxit.offset == 8 and O.mr_tol.offset == 16
     assert O.barrier_timeout_ms.offset == 40 and O.want_colres.offset == 44
     assert O.inner_tol.offset == 48
-    assert O.max_outer.offset == 56 and O.mr_relative.offset == 60 and C.sizeof(O) == 64
+    assert O.max_outer.offset == 56 and O.mr_relative.offset == 60
+    assert O.sm_share.offset == 64 and C.sizeof(O) == 72
 
 
 def test_product_path_does_not_import_oracle():

@@ -1,0 +1,125 @@
+"""Two CG solves side by side (options.sm_share = 2): each solve takes at most
+half of every SM (the node-pair split-state kernel at 256 threads), so two
+solves issued on different streams run concurrently.  Each must still be the
+CG solve of its own system: checked against the oracle's direct solve and
+iteration count (the parity tests' bars), with the other solve in flight."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1606_01216_gb300 import workloads as W
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+AL, BE = W.ALPHA, W.BETA
+
+
+@pytest.fixture(scope="module")
+def G():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1606_01216_gb300 import build
+    build.build()
+    from paper_1606_01216_gb300 import airga
+    airga.lib()
+    return airga
+
+
+def _solve_pair(G, beam, shifts, opts):
+    M, K = G.beam_mats(beam)
+    F = W.loads(beam.n, 2, seed=9)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    torch.cuda.synchronize()
+    out = []
+    for s, st, c in zip(shifts, streams, (0, 1)):
+        with torch.cuda.stream(st):
+            f = torch.from_numpy(np.ascontiguousarray(F[:, c])).cuda()
+            A = G.assemble_shifted(M, K, AL, BE, s, stream=st)
+            P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE), stream=st)
+            r = G.pcg_solve(A, P, f, opts, stream=st)
+            out.append((r, A, P, f))
+    torch.cuda.synchronize()
+    return out, F
+
+
+def band_of(D):
+    n = D.shape[0]
+    band = np.zeros((7, n))
+    for d in range(-3, 4):
+        i = np.arange(max(0, -d), min(n, n - d))
+        band[d + 3, i] = D[i, i + d]
+    return band
+
+
+def test_two_odd_band_solves_share(G):
+    """Odd n: the half-SM plan does not apply and the generic kernel runs;
+    sm_share = 2 still gives each system's CG solve."""
+    n = 4001
+    rp, ci = W.band_pattern(n, 3)
+    opts = G.options(tol=1e-10, maxit=20000, sm_share=2)
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    cases = []
+    for seed, st in zip((31, 32), streams):
+        rng = np.random.default_rng(seed)
+        D = np.zeros((n, n))
+        for d in range(1, 4):
+            i = np.arange(n - d)
+            v = rng.uniform(-1, 1, i.size)
+            D[i, i + d] = v
+            D[i + d, i] = v
+        D += np.diag(7.0 + rng.uniform(0, 1, n))
+        f = rng.standard_normal(n)
+        with torch.cuda.stream(st):
+            A = G.mat_from_band(torch.from_numpy(band_of(D).ravel()).cuda(), stream=st)
+            P = G.spai_build(A, stream=st)
+            r = G.pcg_solve(A, P, torch.from_numpy(f).cuda(), opts, stream=st)
+        cases.append((D, f, r, A, P))
+    torch.cuda.synchronize()
+    for D, f, r, _, _ in cases:
+        Ao = O.dense_to_csr(D, O.CSR(n, rp, ci, np.ones(ci.size)))
+        xd = O.chol_solve(Ao, f)[:, 0]
+        assert int(r["status"][0]) == G.OK
+        assert np.linalg.norm(r["X"].cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_two_solves_share_the_sms(G):
+    beam = W.beam(20000)
+    shifts = (0.1, 2.6827)
+    opts = G.options(tol=1e-10, maxit=20000, sm_share=2)
+    out, F = _solve_pair(G, beam, shifts, opts)
+    for (r, _, _, _), s, c in zip(out, shifts, (0, 1)):
+        Ao = O.shifted_csr(beam, AL, BE, s)
+        xd = O.chol_solve(Ao, F[:, c])[:, 0]
+        _, it_o, st_o, _ = O.pcg(Ao, F[:, c], [O.spai(Ao)], tol=1e-10, maxit=20000)
+        assert int(r["status"][0]) == G.OK and st_o == O.OK
+        assert np.linalg.norm(r["X"].cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
+        assert abs(int(r["iters"][0]) - it_o) <= max(2, it_o // 20)
+        assert float(r["true_relres"][0]) <= 2e-10
+
+
+def test_sm_share_matches_whole_sm_solve(G):
+    """The same system with sm_share 1 and 2: the same iteration count and
+    solutions equal to the CG tolerance (the half-SM kernel sums its
+    reductions over 256-thread blocks, so the rounding order differs)."""
+    beam = W.beam(30000)
+    M, K = G.beam_mats(beam)
+    A = G.assemble_shifted(M, K, AL, BE, 0.5179)
+    P = G.spai_build(A)
+    f = torch.from_numpy(np.ascontiguousarray(W.loads(beam.n)[:, 0])).cuda()
+    r1 = G.pcg_solve(A, P, f, G.options(sm_share=1))
+    r2 = G.pcg_solve(A, P, f, G.options(sm_share=2))
+    torch.cuda.synchronize()
+    assert int(r1["status"][0]) == G.OK and int(r2["status"][0]) == G.OK
+    assert abs(int(r1["iters"][0]) - int(r2["iters"][0])) <= 1
+    x1, x2 = r1["X"], r2["X"]
+    assert float((x1 - x2).norm()) <= 1e-8 * float(x1.norm())
+
+
+def test_sm_share_rejects_other_values(G):
+    beam = W.beam(10)
+    M, K = G.beam_mats(beam)
+    A = G.assemble_shifted(M, K, AL, BE, 1.0)
+    f = torch.ones(beam.n, dtype=torch.float64, device="cuda")
+    for bad in (0, 3):
+        with pytest.raises(G.AirgaError):
+            G.pcg_solve(A, None, f, G.options(sm_share=bad))
