@@ -230,17 +230,21 @@ def gpu_arm(args, world, rank, local):
         nonlocal launches_per_step
         out = [None] * len(SHIFTS)
         cnt = 0
-        go = torch.cuda.Event()
-        go.record(stream)
-        stream_b.wait_event(go)
         for st, idx in zip((stream, stream_b), parts):
             with torch.cuda.stream(st):
-                for k in idx:
+                for j, k in enumerate(idx):
                     A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, SHIFTS[k], stream=st)
                     P = G.spai_build(A, spai_opts, stream=st)
                     cnt += 5              # assemble (also writes the packed beam stencil),
                                           # Gram band, normal-equation columns, Householder
                                           # pass over the (empty) fallback list, symmetrize
+                    if st is stream and j == 0:
+                        # the second stream starts once the first solve's SPAI is
+                        # built: that solve's CTAs then find their half of every
+                        # SM free, and the second stream's work fills the rest
+                        held = torch.cuda.Event()
+                        held.record(stream)
+                        stream_b.wait_event(held)
                     if record:
                         e0 = torch.cuda.Event(enable_timing=True)
                         e1 = torch.cuda.Event(enable_timing=True)
@@ -1054,15 +1058,16 @@ def e2e_arm(G, torch, beam, opts, args, parts):
         M = G.mat_from_csr(n, dev["rp"], dev["ci"], dev["mv"])
         stream.wait_event(landed)
         K = G.mat_from_csr(n, dev["rp"], dev["ci"], dev["kv"])
-        ready = torch.cuda.Event()
-        ready.record(stream)
-        stream_b.wait_event(ready)
         keep = []
         for st, idx in zip((stream, stream_b), parts):
-            for i in idx:
+            for j, i in enumerate(idx):
                 with torch.cuda.stream(st):
                     A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, SHIFTS[i], stream=st)
                     P = G.spai_build(A, spai_options(G), stream=st)
+                    if st is stream and j == 0:          # as in the device-timed step
+                        held = torch.cuda.Event()
+                        held.record(stream)
+                        stream_b.wait_event(held)
                     r = G.pcg_solve(A, P, dev["f"], opts, stream=st)
                     done = torch.cuda.Event()
                     done.record(st)

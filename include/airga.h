@@ -104,7 +104,10 @@ typedef struct {
                                    r, p in shared memory and x, z/q in L2, 256 threads, where it
                                    applies: even n, aligned operands, no update chain), so that two
                                    solves issued on different streams run side by side and each fills
-                                   the other's barrier and scalar-chain gaps on the FP64 pipe */
+                                   the other's barrier and scalar-chain gaps on the FP64 pipe.  Start
+                                   the second stream's work once the first solve's inputs are ready
+                                   (an event after its preconditioner), so that the first solve's
+                                   CTAs find their half of every SM free */
     int32_t reserved0;          /* 0 */
 } airga_options;
 
