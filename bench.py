@@ -390,7 +390,11 @@ def gpu_arm(args, world, rank, local):
     # end to end through the public API with host buffers
     e2e = e2e_arm(G, torch, beam, opts, args, parts) if rank == 0 and not args.profile else None
 
+    step_spread = {"min": round(min(times), 3), "median": round(statistics.median(times), 3),
+                   "max": round(max(times), 3), "streams": [[float(SHIFTS[k]) for k in p]
+                                                            for p in parts]}
     return dict(ms=ms, iters=iters, status=status, relres=relres, ok=ok, clocks=ck,
+                step_ms=step_spread,
                 launches=launches_per_step * args.steps, n=n,
                 roofline={"bound": "alu", "achieved": round(achieved_tf, 4),
                           "peak": round(fp64_peak_tf, 4), "unit": "TFLOP/s",
@@ -1267,6 +1271,7 @@ def main():
             "config": config_dict(world),
             "converged": r["ok"], "iters": r["iters"], "true_relres": r["relres"],
             "roofline": r["roofline"], "gpu_launches": r["launches"], "clocks": r["clocks"],
+            "step_ms": r["step_ms"],
             "e2e": r["e2e"], "pcg_only": r["pcg_only"], "detail": r["detail"],
             "forms": r["forms"],
         }
