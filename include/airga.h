@@ -596,6 +596,13 @@ int airga_debug_check_selftest(int64_t index, int64_t bound, int32_t site, void 
 #define AIRGA_PCG_KERNEL_PAIR_HALF 4
 int airga_debug_force_pcg_kernel(int kind);
 
+/* Test hook: while `sm_of_cta` (device, at least as many int32 as the GPU
+ * has SMs) is set, every CG call that runs a node-pair kernel writes the SM
+ * index of each of its CTAs there, CTA rank k at sm_of_cta[k]; NULL (the
+ * default) turns it off.  The pointer is read when a call is made, so each
+ * of two concurrent solves can be given its own buffer. */
+int airga_debug_record_placement(int32_t *sm_of_cta);
+
 /* Measurement aid, no counterpart in the paper: the FP64 FMA issue rate of
  * the current device, the roofline of this library's FP64-bound kernels.
  * One CTA of 1024 threads per SM runs 8, 12 and then 16 independent FMA

@@ -42,6 +42,7 @@ EXPORTS = (
     "airga_precond_is_banded", "airga_precond_factor_nnz", "airga_precond_factor_csr",
     "airga_precond_from_csr", "airga_probe_fp64_rate", "airga_debug_pool_used",
     "airga_debug_checked", "airga_debug_check_selftest", "airga_probe_read_bw",
+    "airga_debug_record_placement",
 )
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
@@ -158,6 +159,7 @@ def lib():
         "airga_probe_read_bw": (C.c_int, [i64, i32, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]),
         "airga_debug_check_selftest": (C.c_int, [i64, i64, i32, vp]),
         "airga_debug_force_pcg_kernel": (C.c_int, [C.c_int]),
+        "airga_debug_record_placement": (C.c_int, [vp]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
         "airga_trim": (C.c_int, []),
@@ -594,6 +596,13 @@ def probe_read_bw(nbytes: int, passes: int = 20, stream=None):
     _check(lib().airga_probe_read_bw(int(nbytes), int(passes), C.byref(g), C.byref(ms),
                                      _stream(stream)), "probe_read_bw")
     return g.value, ms.value
+
+
+def debug_record_placement(buf=None):
+    """Make the next CG calls write each CTA's SM index into `buf` (an int32
+    device tensor with at least one entry per SM); None turns it off."""
+    _check(lib().airga_debug_record_placement(_ptr(buf, torch.int32) if buf is not None else None),
+           "debug_record_placement")
 
 
 def debug_pool_used() -> int:

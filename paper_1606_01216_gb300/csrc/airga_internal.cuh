@@ -290,6 +290,7 @@ struct PcgArgs {
     const double *rhs_M;           // node-pair kernel: b = rhs_scale M v formed on the fly (or null)
     const double *rhs_v;
     double rhs_scale;
+    int32_t *place = nullptr;      // test hook: node-pair kernels write each CTA's SM id here
 };
 
 // process-wide test fault consumed by the next pcg_solve (airga_debug_set_fault)
@@ -298,6 +299,9 @@ bool take_fault(int kind);
 // cudaErrorLaunchOutOfResources when AIRGA_FAULT_LAUNCH is armed (consumed),
 // else cudaSuccess: called where a solve or SPAI kernel is about to launch
 cudaError_t injected_launch_error();
+// test hook (airga_debug_record_placement): device buffer for the next CG
+// call's CTA placement, or null
+int32_t *placement_buffer();
 
 // aligned16: A, the preconditioner band, b and x are 16-byte aligned (needed
 // by the node-pair kernel together with an even n)

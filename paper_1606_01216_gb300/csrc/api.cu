@@ -144,6 +144,8 @@ cudaError_t injected_launch_error() {
 static std::atomic<int> g_forced_kind{0};
 
 int forced_pcg_kind() { return g_forced_kind.load(); }
+static std::atomic<int32_t *> g_place{nullptr};
+int32_t *placement_buffer() { return g_place.load(); }
 
 static_assert(sizeof(airga_options) == 72, "airga_options layout (the Python binding mirrors it)");
 
@@ -718,6 +720,7 @@ static int pcg_solve_impl(airga_mat A, airga_precond P, const double *F, airga_m
     a.warm = o.warm_start ? 1 : 0;
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
     a.fault_skip_arrival = take_fault(AIRGA_FAULT_SKIP_ARRIVAL) ? 1 : 0;
+    a.place = placement_buffer();
     a.pairz = A->pairz ? (const int32_t *)A->pairz.get() : nullptr;
     if (plan.kind >= 2 && A->pairz) {
         // packed beam entries for the row-pair stencil, made once per matrix
@@ -813,6 +816,11 @@ int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m
 int airga_debug_force_pcg_kernel(int kind) {
     if (kind < 0 || kind > 4) return fail(AIRGA_E_INVALID_ARG, "kernel kind must be 0..4");
     g_forced_kind.store(kind);
+    return AIRGA_OK;
+}
+
+int airga_debug_record_placement(int32_t *sm_of_cta) {
+    g_place.store(sm_of_cta);
     return AIRGA_OK;
 }
 

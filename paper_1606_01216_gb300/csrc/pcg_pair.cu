@@ -235,6 +235,11 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
     const int lo = rank * R < n ? rank * R : n;
     const int hi = lo + R < n ? lo + R : n;
     if (tid == 0) s_nb = 0.0;
+    if (a.place && tid == 0) {                     // test hook: where this CTA runs
+        unsigned sm;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+        a.place[rank] = (int32_t)sm;
+    }
 
     // SPLIT == 0: x, r, p, z/q windows all in shared memory.  SPLIT == 1 (n too
     // large for four windows) and SPLIT == 2 (half an SM per CTA): r and p
