@@ -7,8 +7,9 @@ assemble_shifted -> spai_build (exact fixed-pattern SPAI, least squares by
 the normal equations with the Householder fallback, + P_sym) -> pcg_solve
 (PCG to 1e-10 plus the true FP64 residual).  The shifts run on two streams,
 split longest-first by the CG iterations the first warm-up step measured,
-and every CG call takes half of each SM (options.sm_share = 2), so two
-solves share the SMs and fill each other's barrier gaps.  The Householder
+and every CG call takes half of each SM (options.sm_share: 2 for the first
+stream's solves, whose CTAs never double up on an SM; 3 for the second
+stream's), so two solves share every SM and fill each other's barrier gaps.  The Householder
 (QR) build and the whole-SM CG kernel are timed alone beside it in
 `detail`.  value = 8 solves / device time of a step
 (CUDA events on the launching stream; L2 flushed before every timed step by
@@ -61,6 +62,7 @@ PCG_L2_BYTES_PER_ROW_ITER = 72
 # from one ncu capture of the s = 0.1 launch on this workload (1286 MB read +
 # 236 MB written over 229 x 1e6 row-iterations; x and z/q travel through L2)
 PCG_DRAM_BYTES_PER_ROW_ITER_HALF = 6.65
+HOLD_US = 50                     # partner stream hold after the lead's SPAI (airga_stream_hold)
 SPAI_FLOP_PER_COLUMN_MODEL = 1250  # algorithmic SPAI work per column (band-7 QR + solve)
 # FP64 instructions per interior column of the normal-equation SPAI build
 # as the bench runs it (no per-column residuals): Gram band 28 FMA; L D L^T
@@ -215,9 +217,11 @@ def gpu_arm(args, world, rank, local):
     n = beam.n
     M, K = G.beam_mats(beam)
     F = torch.from_numpy(W.loads(n)[:, 0]).cuda()
-    # two solves share the SMs: every CG call takes half of each SM
-    # (sm_share = 2) and the shifts run on two streams
+    # two solves share the SMs: every CG call takes half of each SM, the first
+    # stream's solves as leads (sm_share = 2: never two of their CTAs on one
+    # SM), the second stream's as partners (sm_share = 3)
     opts = G.options(tol=TOL, maxit=20000, sm_share=2)
+    opts_b = G.options(tol=TOL, maxit=20000, sm_share=3)
     spai_opts = spai_options(G)
     stream = torch.cuda.current_stream()
     stream_b = torch.cuda.Stream()
@@ -241,16 +245,19 @@ def gpu_arm(args, world, rank, local):
                                           # pass over the (empty) fallback list, symmetrize
                     if st is stream and j == 0:
                         # the second stream starts once the first solve's SPAI is
-                        # built: that solve's CTAs then find their half of every
-                        # SM free, and the second stream's work fills the rest
+                        # built, and then only after a 50 us hold: every CTA of
+                        # that (lead) solve is placed first, one per SM, and the
+                        # second stream's (partner) work fills the rest
                         held = torch.cuda.Event()
                         held.record(stream)
                         stream_b.wait_event(held)
+                        G.stream_hold(HOLD_US, stream_b)
+                        cnt += 1
                     if record:
                         e0 = torch.cuda.Event(enable_timing=True)
                         e1 = torch.cuda.Event(enable_timing=True)
                         e0.record(st)
-                    r = G.pcg_solve(A, P, F, opts, stream=st)
+                    r = G.pcg_solve(A, P, F, opts if st is stream else opts_b, stream=st)
                     cnt += 1              # pcg (true residual in the PCG kernel's epilogue)
                     if record:
                         e1.record(st)
@@ -389,7 +396,7 @@ def gpu_arm(args, world, rank, local):
         forms = {k: makers[k](G, torch, stream) for k in args.forms.split(",") if k}
 
     # end to end through the public API with host buffers
-    e2e = e2e_arm(G, torch, beam, opts, args, parts) if rank == 0 and not args.profile else None
+    e2e = e2e_arm(G, torch, beam, (opts, opts_b), args, parts) if rank == 0 and not args.profile else None
 
     step_spread = {"min": round(min(times), 3), "median": round(statistics.median(times), 3),
                    "max": round(max(times), 3), "streams": [[float(SHIFTS[k]) for k in p]
@@ -1073,7 +1080,8 @@ def e2e_arm(G, torch, beam, opts, args, parts):
                         held = torch.cuda.Event()
                         held.record(stream)
                         stream_b.wait_event(held)
-                    r = G.pcg_solve(A, P, dev["f"], opts, stream=st)
+                        G.stream_hold(HOLD_US, stream_b)
+                    r = G.pcg_solve(A, P, dev["f"], opts[0] if st is stream else opts[1], stream=st)
                     done = torch.cuda.Event()
                     done.record(st)
                 copy.wait_event(done)

@@ -99,15 +99,20 @@ typedef struct {
     int32_t mr_relative;        /* MR stop test: 0 = ||r|| <= mr_tol, the loop test of Algorithms 2 / 4
                                    (default); 1 = ||r|| <= mr_tol ||b_j||, b_j = e_j (build) or
                                    A_prev e_j (update) — the same for a build, scale-free for an update */
-    int32_t sm_share;           /* CG: 1 = a solve may take every SM whole (default); 2 = at most half
-                                   of each SM's registers and shared memory (the node-pair kernel with
-                                   r, p in shared memory and x, z/q in L2, 256 threads, where it
-                                   applies: even n, aligned operands, no update chain), so that two
-                                   solves issued on different streams run side by side and each fills
-                                   the other's barrier and scalar-chain gaps on the FP64 pipe.  Start
-                                   the second stream's work once the first solve's inputs are ready
-                                   (an event after its preconditioner), so that the first solve's
-                                   CTAs find their half of every SM free */
+    int32_t sm_share;           /* CG: 1 = a solve may take every SM whole (default).  2 (lead) and
+                                   3 (partner): the solve takes half of each SM's registers and shared
+                                   memory (the node-pair kernel with r, p in shared memory and x, z/q
+                                   in L2, 256 threads, where it applies: even n, aligned operands, no
+                                   update chain, n up to about 1.03e6 on GB300), so that a lead and a
+                                   partner issued on different streams run side by side, one CTA of
+                                   each per SM, and each fills the other's barrier and scalar-chain
+                                   gaps on the FP64 pipe.  A lead reserves just over half of an SM's
+                                   shared memory, so two of its CTAs never share an SM: an SM holding
+                                   two CTAs of one solve would pace that solve's every barrier.  Give
+                                   the longer solve 2 and launch it first; run the others as 3 on a
+                                   second stream that waits for an event after the lead's
+                                   preconditioner and then for airga_stream_hold (about 50 us), so
+                                   that every lead CTA is placed before partner work takes SM room */
     int32_t reserved0;          /* 0 */
 } airga_options;
 
@@ -602,6 +607,15 @@ int airga_debug_force_pcg_kernel(int kind);
  * default) turns it off.  The pointer is read when a call is made, so each
  * of two concurrent solves can be given its own buffer. */
 int airga_debug_record_placement(int32_t *sm_of_cta);
+
+/* Scheduling aid for lead / partner solves (options.sm_share 2 and 3), no
+ * counterpart in the paper: queue on `stream` one warp that sleeps for
+ * `microseconds` (0..1000) by the GPU's global timer.  Placed on the
+ * partners' stream after the event that releases it, it keeps partner work
+ * off the SMs while the lead's CTAs are placed (a cooperative grid is placed
+ * CTA by CTA, so partner CTAs arriving meanwhile can take the room of a lead
+ * CTA, which then waits for them at the lead's first barrier). */
+int airga_stream_hold(int32_t microseconds, void *stream);
 
 /* Measurement aid, no counterpart in the paper: the FP64 FMA issue rate of
  * the current device, the roofline of this library's FP64-bound kernels.

@@ -42,7 +42,7 @@ EXPORTS = (
     "airga_precond_is_banded", "airga_precond_factor_nnz", "airga_precond_factor_csr",
     "airga_precond_from_csr", "airga_probe_fp64_rate", "airga_debug_pool_used",
     "airga_debug_checked", "airga_debug_check_selftest", "airga_probe_read_bw",
-    "airga_debug_record_placement",
+    "airga_debug_record_placement", "airga_stream_hold",
 )
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
@@ -160,6 +160,7 @@ def lib():
         "airga_debug_check_selftest": (C.c_int, [i64, i64, i32, vp]),
         "airga_debug_force_pcg_kernel": (C.c_int, [C.c_int]),
         "airga_debug_record_placement": (C.c_int, [vp]),
+        "airga_stream_hold": (C.c_int, [i32, vp]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
         "airga_trim": (C.c_int, []),
@@ -603,6 +604,11 @@ def debug_record_placement(buf=None):
     device tensor with at least one entry per SM); None turns it off."""
     _check(lib().airga_debug_record_placement(_ptr(buf, torch.int32) if buf is not None else None),
            "debug_record_placement")
+
+
+def stream_hold(microseconds: int, stream=None):
+    """Queue a bounded sleep of `microseconds` on `stream` (see sm_share)."""
+    _check(lib().airga_stream_hold(int(microseconds), _stream(stream)), "stream_hold")
 
 
 def debug_pool_used() -> int:

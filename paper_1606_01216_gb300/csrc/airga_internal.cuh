@@ -305,8 +305,10 @@ int32_t *placement_buffer();
 
 // aligned16: A, the preconditioner band, b and x are 16-byte aligned (needed
 // by the node-pair kernel together with an even n)
-// share = 2: the solve may take at most half of each SM (plan kind 4 when it
-// applies), so that two solves on different streams run side by side
+// share = 2 (lead) / 3 (partner): the solve takes half of each SM (plan
+// kind 4 when it applies), so that two solves on different streams run side
+// by side; a lead's CTAs reserve just over half an SM's shared memory, so two
+// of them never share an SM, while one partner CTA fits beside each
 int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgPlan *plan,
              int share = 1);
 cudaError_t launch_pcg(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
@@ -321,6 +323,7 @@ size_t pcg_pair_split_smem(int64_t R);       // r and p windows only
 size_t pcg_pair_split_slice(int64_t R);      // doubles of global workspace per CTA (z/q window)
 int pcg_pair_split_occupancy(int mode, size_t smem, int *per_sm);
 size_t pcg_pair_half_smem(int64_t R);        // split state at 256 threads
+size_t pcg_pair_half_static_smem(int mode);  // the half-SM kernel's static shared memory
 int pcg_pair_half_occupancy(int mode, size_t smem, int *per_sm);
 int pcg_pair_threads(int kind);   // threads per CTA of plan kind 2, 3 or 4
 int pcg_pair_occupancy(int mode, size_t smem, int *per_sm);

@@ -160,7 +160,7 @@ int check_options(const airga_options *o) {
     if (o->pattern_hbw < 0 || o->pattern_hbw > 3)
         return fail(AIRGA_E_INVALID_ARG, "pattern_hbw must be in 0..3");
     if (o->barrier_timeout_ms <= 0) return fail(AIRGA_E_INVALID_ARG, "barrier_timeout_ms must be > 0");
-    if (o->sm_share != 1 && o->sm_share != 2) return fail(AIRGA_E_INVALID_ARG, "sm_share must be 1 or 2");
+    if (o->sm_share < 1 || o->sm_share > 3) return fail(AIRGA_E_INVALID_ARG, "sm_share must be 1, 2 or 3");
     if (!(o->inner_tol > 0.0) || !(o->inner_tol < 1.0))
         return fail(AIRGA_E_INVALID_ARG, "inner_tol must be in (0, 1)");
     if (o->max_outer < 1) return fail(AIRGA_E_INVALID_ARG, "max_outer must be >= 1");

@@ -459,14 +459,35 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
         Rp += Rp & 1;
         const size_t smem_p = pcg_pair_smem(Rp), smem_s = pcg_pair_split_smem(Rp);
         bool ok2 = false, ok3 = false, ok4 = false;
-        if (share == 2 || forced == 4) {
-            // half an SM: two CTAs of this kernel (two solves) per SM
+        if (share == 2 || share == 3 || forced == 4) {
+            // half an SM: one CTA of each of two solves per SM.  Footprint of a
+            // CTA = dynamic + static shared memory + the per-block reservation.
+            // A lead (share 2) pads its dynamic request so that its footprint is
+            // just over half the SM: two lead CTAs never share an SM, so the
+            // dispatcher has to spread a lead one CTA per SM even when other
+            // work holds some SMs at its launch (a doubled-up SM would pace the
+            // whole solve).  A partner (share 3, or the test hook) must fit in
+            // the rest of every SM.
+            const int md = mode == kIdentity ? 0 : 1;
             const size_t smem_h = pcg_pair_half_smem(Rp);
-            if (2 * (smem_h + 1024) <= (size_t)smem_sm) {
+            int reserved = 0;
+            cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+            const size_t stat = pcg_pair_half_static_smem(md) + (size_t)reserved;
+            const size_t half_sm = (size_t)smem_sm / 2;
+            const size_t lead = half_sm + 64 > stat ? half_sm + 64 - stat : smem_h;
+            size_t smem_use = smem_h;
+            if (smem_h + stat + 64 <= half_sm && lead + 256 <= (size_t)optin) {
                 int per_sm = 0;
-                int st = pcg_pair_half_occupancy(mode == kIdentity ? 0 : 1, smem_h, &per_sm);
-                if (st) return st;
-                ok4 = per_sm >= 2 && grid_p <= sms;
+                if (share == 2) {
+                    int st = pcg_pair_half_occupancy(md, lead, &per_sm);
+                    if (st) return st;
+                    ok4 = per_sm == 1 && grid_p <= sms;
+                    smem_use = lead;
+                } else {
+                    int st = pcg_pair_half_occupancy(md, smem_h, &per_sm);
+                    if (st) return st;
+                    ok4 = per_sm >= 2 && grid_p <= sms;
+                }
             }
             if (ok4) {
                 plan->kind = 4;
@@ -475,7 +496,7 @@ int pcg_plan(int64_t n, int nf, bool psym_path, bool aligned16, int device, PcgP
                 plan->grid = grid_p;
                 plan->rows = Rp;
                 plan->smem_state = false;
-                plan->smem_bytes = smem_h;
+                plan->smem_bytes = smem_use;
                 plan->scratch_doubles = pcg_pair_split_slice(Rp) * (size_t)grid_p;
                 return AIRGA_OK;
             }

@@ -623,6 +623,14 @@ cudaError_t launch_pair_mode(const PcgPlan &plan, const PcgArgs &args, cudaStrea
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)plan.smem_bytes);
     if (e != cudaSuccess) return e;
+    if (SPLIT == 2) {
+        // the SMs must be configured for the largest shared-memory carveout:
+        // a lead CTA alone would otherwise get a smaller one (more L1), and a
+        // partner CTA would find no room beside it
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+        if (e != cudaSuccess) return e;
+    }
     PcgArgs a = args;
     int R = (int)plan.rows;
     void *kargs[] = {(void *)&a, (void *)&R};
@@ -651,9 +659,17 @@ int pcg_pair_threads(int kind) {
     return kind == 3 ? kThreadsSplit : (kind == 4 ? kThreadsHalf : kThreadsFull);
 }
 
+size_t pcg_pair_half_static_smem(int mode) {
+    cudaFuncAttributes fa;
+    const void *kern = mode == 0 ? (const void *)pcg_pair_kernel<0, 2> : (const void *)pcg_pair_kernel<1, 2>;
+    return cudaFuncGetAttributes(&fa, kern) == cudaSuccess ? fa.sharedSizeBytes : 256;
+}
+
 int pcg_pair_half_occupancy(int mode, size_t smem, int *per_sm) {
     const void *kern = mode == 0 ? (const void *)pcg_pair_kernel<0, 2> : (const void *)pcg_pair_kernel<1, 2>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                         cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, kThreadsHalf, smem);
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg pair half occupancy");
 }
@@ -729,3 +745,34 @@ cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream
 }  // namespace airga
 
 AIRGA_CHECK_READER(pcg_pair)
+
+// ---------------------------------------------------------------------------
+// Stream hold for lead / partner solves (options.sm_share 2 and 3): one warp
+// that sleeps for a bounded time on the global timer.  Queued on the
+// partners' stream right after the lead's inputs are ready, it keeps partner
+// work off the SMs while the lead's CTAs are dispatched (a cooperative grid
+// is placed CTA by CTA; an SM taken by partner work at that moment would
+// leave one lead CTA waiting for it at the lead's first barrier).
+// ---------------------------------------------------------------------------
+namespace airga {
+namespace {
+__global__ void stream_hold_kernel(long long ns) {
+    if (threadIdx.x != 0) return;
+    unsigned long long t0, t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    do {
+        __nanosleep(1000);
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    } while ((long long)(t - t0) < ns);
+}
+}  // namespace
+}  // namespace airga
+
+extern "C" int airga_stream_hold(int32_t microseconds, void *stream) {
+    if (microseconds < 0 || microseconds > 1000)
+        return airga::fail(AIRGA_E_INVALID_ARG, "microseconds must be in [0, 1000]");
+    if (microseconds == 0) return AIRGA_OK;
+    airga::stream_hold_kernel<<<1, 32, 0, (cudaStream_t)stream>>>((long long)microseconds * 1000);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? AIRGA_OK : airga::cuda_fail(e, "stream hold");
+}

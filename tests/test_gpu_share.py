@@ -1,6 +1,6 @@
-"""Two CG solves side by side (options.sm_share = 2): each solve takes at most
-half of every SM (the node-pair split-state kernel at 256 threads), so two
-solves issued on different streams run concurrently.  Each must still be the
+"""Two CG solves side by side (options.sm_share = 2 for the lead, 3 for the
+partner): each solve takes half of every SM (the node-pair split-state kernel
+at 256 threads), so two solves issued on different streams run concurrently.  Each must still be the
 CG solve of its own system: checked against the oracle's direct solve and
 iteration count (the parity tests' bars), with the other solve in flight."""
 import numpy as np
@@ -25,18 +25,23 @@ def G():
     return airga
 
 
-def _solve_pair(G, beam, shifts, opts):
+def _solve_pair(G, beam, shifts, share):
     M, K = G.beam_mats(beam)
     F = W.loads(beam.n, 2, seed=9)
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     torch.cuda.synchronize()
     out = []
-    for s, st, c in zip(shifts, streams, (0, 1)):
+    for s, st, c, sh in zip(shifts, streams, (0, 1), share):
         with torch.cuda.stream(st):
             f = torch.from_numpy(np.ascontiguousarray(F[:, c])).cuda()
             A = G.assemble_shifted(M, K, AL, BE, s, stream=st)
             P = G.spai_build(A, G.options(spai_mode=G.SPAI_NE), stream=st)
-            r = G.pcg_solve(A, P, f, opts, stream=st)
+            if c == 0:                        # the second stream starts after the lead's
+                ready = torch.cuda.Event()    # inputs, then after a short hold
+                ready.record(st)
+                streams[1].wait_event(ready)
+                G.stream_hold(50, streams[1])
+            r = G.pcg_solve(A, P, f, G.options(tol=1e-10, maxit=20000, sm_share=sh), stream=st)
             out.append((r, A, P, f))
     torch.cuda.synchronize()
     return out, F
@@ -56,10 +61,10 @@ def test_two_odd_band_solves_share(G):
     sm_share = 2 still gives each system's CG solve."""
     n = 4001
     rp, ci = W.band_pattern(n, 3)
-    opts = G.options(tol=1e-10, maxit=20000, sm_share=2)
     streams = [torch.cuda.Stream(), torch.cuda.Stream()]
     cases = []
-    for seed, st in zip((31, 32), streams):
+    for seed, st, sh in zip((31, 32), streams, (2, 3)):
+        opts = G.options(tol=1e-10, maxit=20000, sm_share=sh)
         rng = np.random.default_rng(seed)
         D = np.zeros((n, n))
         for d in range(1, 4):
@@ -82,11 +87,13 @@ def test_two_odd_band_solves_share(G):
         assert np.linalg.norm(r["X"].cpu().numpy() - xd) <= 1e-8 * np.linalg.norm(xd)
 
 
-def test_two_solves_share_the_sms(G):
+@pytest.mark.parametrize("share", [(2, 3), (3, 3), (2, 2)], ids=["lead+partner", "two partners", "two leads"])
+def test_two_solves_share_the_sms(G, share):
+    # two leads cannot share an SM (their second launch waits for SMs): still
+    # each its own solve
     beam = W.beam(20000)
     shifts = (0.1, 2.6827)
-    opts = G.options(tol=1e-10, maxit=20000, sm_share=2)
-    out, F = _solve_pair(G, beam, shifts, opts)
+    out, F = _solve_pair(G, beam, shifts, share)
     for (r, _, _, _), s, c in zip(out, shifts, (0, 1)):
         Ao = O.shifted_csr(beam, AL, BE, s)
         xd = O.chol_solve(Ao, F[:, c])[:, 0]
@@ -97,9 +104,10 @@ def test_two_solves_share_the_sms(G):
         assert float(r["true_relres"][0]) <= 2e-10
 
 
-def test_sm_share_matches_whole_sm_solve(G):
-    """The same system with sm_share 1 and 2: the same iteration count and
-    solutions equal to the CG tolerance (the half-SM kernel sums its
+@pytest.mark.parametrize("share", [2, 3])
+def test_sm_share_matches_whole_sm_solve(G, share):
+    """The same system with sm_share 1 and 2 or 3: the same iteration count
+    and solutions equal to the CG tolerance (the half-SM kernel sums its
     reductions over 256-thread blocks, so the rounding order differs)."""
     beam = W.beam(30000)
     M, K = G.beam_mats(beam)
@@ -107,7 +115,7 @@ def test_sm_share_matches_whole_sm_solve(G):
     P = G.spai_build(A)
     f = torch.from_numpy(np.ascontiguousarray(W.loads(beam.n)[:, 0])).cuda()
     r1 = G.pcg_solve(A, P, f, G.options(sm_share=1))
-    r2 = G.pcg_solve(A, P, f, G.options(sm_share=2))
+    r2 = G.pcg_solve(A, P, f, G.options(sm_share=share))
     torch.cuda.synchronize()
     assert int(r1["status"][0]) == G.OK and int(r2["status"][0]) == G.OK
     assert abs(int(r1["iters"][0]) - int(r2["iters"][0])) <= 1
@@ -115,11 +123,25 @@ def test_sm_share_matches_whole_sm_solve(G):
     assert float((x1 - x2).norm()) <= 1e-8 * float(x1.norm())
 
 
+def test_stream_hold(G):
+    st = torch.cuda.Stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    G.stream_hold(300, st)
+    e1.record(st)
+    torch.cuda.synchronize()
+    assert 0.3 <= e0.elapsed_time(e1) < 50.0        # ms: at least the hold, and bounded
+    G.stream_hold(0, st)                             # nothing queued
+    for bad in (-1, 1001):
+        with pytest.raises(G.AirgaError):
+            G.stream_hold(bad, st)
+
+
 def test_sm_share_rejects_other_values(G):
     beam = W.beam(10)
     M, K = G.beam_mats(beam)
     A = G.assemble_shifted(M, K, AL, BE, 1.0)
     f = torch.ones(beam.n, dtype=torch.float64, device="cuda")
-    for bad in (0, 3):
+    for bad in (0, 4):
         with pytest.raises(G.AirgaError):
             G.pcg_solve(A, None, f, G.options(sm_share=bad))
