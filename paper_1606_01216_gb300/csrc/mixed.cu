@@ -37,9 +37,6 @@ namespace {
 using namespace pcgdev;
 
 constexpr int kThreads = 512;
-// paired launches (two columns in one launch, one CTA of each per SM): 256
-// threads and at most half an SM's registers and shared memory per CTA
-constexpr int kThreadsDual = 256;
 constexpr int HR = 8, HP = 12, HZ = 4, kHaloPairs = 8;
 
 // ---------------------------------------------------------------------------
@@ -78,7 +75,6 @@ struct Args32 {
     int32_t *outer_iters; // out: refinement steps taken
     int32_t *inner_iters; // out: FP32 CG iterations, all steps
     int32_t *status;      // out
-    float *state = nullptr; // paired launches: per-CTA slices of the inner d and the z/q window
 };
 
 // Warm L2 with the 8-byte rows of `count` FP32 band arrays at pair i (no
@@ -230,38 +226,27 @@ __device__ void block_partials_tree_f(float (&v)[NV], float *red, double *partia
     }
 }
 
-// The whole refinement of one column by CTA `rank` of the G CTAs of that
-// column (rows [rank R, rank R + R)).  SPLIT == 0: every FP32 window in
-// shared memory.  SPLIT == 1 (paired launches, half an SM per CTA): the r and
-// p windows in shared memory, the inner solution d (own rows) and the z/q
-// window in this CTA's slice of the global workspace.
-template <int MODE, int SPLIT>   // MODE 0: identity, 1: band preconditioner, 2: symmetric (upper diagonals)
-__device__ __forceinline__ void mixed_body(const Args32 &a, int R, int G, int rank) {
+template <int MODE>   // 0: identity, 1: band preconditioner, 2: symmetric (upper diagonals)
+__global__ void __launch_bounds__(kThreads, 1)
+mixed_pair_kernel(Args32 a, int R) {
     extern __shared__ __align__(16) double smem64[];
     __shared__ double tot[8];
     __shared__ int s_flag;
     __shared__ int s_dec;
 
+    const int G = gridDim.x;
     const int n = a.n;
     const int tid = threadIdx.x, nt = blockDim.x;
-    const int lo = rank * R < n ? rank * R : n;
+    const int lo = blockIdx.x * R < n ? blockIdx.x * R : n;
     const int hi = lo + R < n ? lo + R : n;
 
     double *red = smem64;                                        // 3 * nt doubles
     float *redf = reinterpret_cast<float *>(red);                // the inner loop's FP32 trees
-    float *xs, *rs, *ps, *zq;
-    if (SPLIT) {
-        rs = reinterpret_cast<float *>(red + 3 * nt);
-        ps = rs + (R + 2 * HR);
-        xs = a.state + (size_t)rank * (size_t)(2 * R + 2 * HZ);
-        zq = xs + R;
-    } else {
-        xs = reinterpret_cast<float *>(red + 3 * nt);
-        rs = xs + R;
-        ps = rs + (R + 2 * HR);
-        zq = ps + (R + 2 * HZ);
-    }
-    float2 *ah = reinterpret_cast<float2 *>(ps + (R + 2 * HZ) + (SPLIT ? 0 : R + 2 * HZ));   // A rows of the r halo
+    float *xs = reinterpret_cast<float *>(red + 3 * nt);
+    float *rs = xs + R;
+    float *ps = rs + (R + 2 * HR);
+    float *zq = ps + (R + 2 * HZ);
+    float2 *ah = reinterpret_cast<float2 *>(zq + (R + 2 * HZ));  // A rows of the r halo
     const int xbase = lo, rbase = lo - HR, pbase = lo - HZ, zbase = lo - HZ;
     const int lenR = R + 2 * HR, lenZ = R + 2 * HZ;      // window lengths (r; p and z/q)
     (void)lenR;
@@ -276,12 +261,8 @@ __device__ __forceinline__ void mixed_body(const Args32 &a, int R, int G, int ra
     const bool hvalid = halo_thread && hpair >= 0 && hpair < n;
 
     {
-        // zero every window (out-of-matrix slots must read as 0)
-        const int total = SPLIT ? 2 * R + 2 * (HR + HZ) : 4 * R + 2 * (HR + 2 * HZ);
-        float *w0 = SPLIT ? rs : xs;
-        for (int k = tid; k < total; k += nt) w0[k] = 0.0f;
-        if (SPLIT)
-            for (int k = tid; k < 2 * R + 2 * HZ; k += nt) xs[k] = 0.0f;
+        const int total = 4 * R + 2 * (HR + 2 * HZ);
+        for (int k = tid; k < total; k += nt) xs[k] = 0.0f;
         if (hvalid) {
             float2 t[kBand];
             load_band_pair_f(a.A, n, hpair, t);
@@ -350,7 +331,7 @@ __device__ __forceinline__ void mixed_body(const Args32 &a, int R, int G, int ra
                 if (i >= lo && i < hi) rr = fma(r, r, rr);
             }
             double v[1] = {rr};
-            block_partials_tree<1>(v, red, a.partials, bar_no & 1, G, rank);
+            block_partials_tree<1>(v, red, a.partials, bar_no & 1, G, blockIdx.x);
         }
         if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
             status = AIRGA_E_TIMEOUT;
@@ -381,7 +362,7 @@ __device__ __forceinline__ void mixed_body(const Args32 &a, int R, int G, int ra
         {
             float v2[2] = {0.0f, 0.0f};
             apply_M(zlo, zhi, v2);
-            block_partials_tree_f<2>(v2, redf, a.partials, bar_no & 1, G, rank);
+            block_partials_tree_f<2>(v2, redf, a.partials, bar_no & 1, G, blockIdx.x);
         }
         if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
             status = AIRGA_E_TIMEOUT;
@@ -443,9 +424,9 @@ __device__ __forceinline__ void mixed_body(const Args32 &a, int R, int G, int ra
                     prefetch_pair_f(a.M, n, zlo + 2 * tid, MODE == 2 ? 4 : kBand);
                 {
                     float vv[1] = {vq};
-                    block_partials_tree_f<1>(vv, redf, a.partials, bar_no & 1, G, rank);
+                    block_partials_tree_f<1>(vv, redf, a.partials, bar_no & 1, G, blockIdx.x);
                 }
-                const bool arrive = !(a.fault_skip_arrival && ko == 0 && k == 1 && rank == 0);
+                const bool arrive = !(a.fault_skip_arrival && ko == 0 && k == 1 && blockIdx.x == 0);
                 if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
                                   arrive)) {
                     istatus = AIRGA_E_TIMEOUT;
@@ -517,7 +498,7 @@ __device__ __forceinline__ void mixed_body(const Args32 &a, int R, int G, int ra
                     if (packed) prefetch_pair_f(a.Apk, n, lo + 2 * tid, 5);
                     else prefetch_pair_f(a.A, n, lo + 2 * tid, kBand);
                 }
-                block_partials_tree_f<2>(v2, redf, a.partials, bar_no & 1, G, rank);
+                block_partials_tree_f<2>(v2, redf, a.partials, bar_no & 1, G, blockIdx.x);
                 if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
                     istatus = AIRGA_E_TIMEOUT;
                     iters = k;
@@ -562,7 +543,7 @@ __device__ __forceinline__ void mixed_body(const Args32 &a, int R, int G, int ra
         }
         ++bar_no;
     }
-    if (rank == 0 && tid == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
         *a.relres = relres;
         *a.outer_iters = outer;
         *a.inner_iters = inner_total;
@@ -570,76 +551,9 @@ __device__ __forceinline__ void mixed_body(const Args32 &a, int R, int G, int ra
     }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kThreads, 1)
-mixed_pair_kernel(Args32 a, int R) {
-    mixed_body<MODE, 0>(a, R, gridDim.x, blockIdx.x);
-}
-
-// Two columns in one launch of 2 G CTAs, two per SM.  Each CTA takes its
-// column from its arrival slot on its SM (first: column 0, second: column 1)
-// and its rank from a per-column counter; a column that already has G CTAs
-// sends the CTA to the other one, so each column gets exactly G.  On a launch
-// of 2 x (SM count) CTAs every SM therefore holds one CTA of each column, and
-// each column's barrier and scalar-chain gaps are filled by the other's work.
-// roles: [0], [1] per-column counters, [2 + s] arrivals on SM s (zeroed
-// before the launch).
-template <int MODE>
-__global__ void __launch_bounds__(kThreadsDual, 2)
-mixed_dual_kernel(Args32 a0, Args32 a1, int R, unsigned *roles) {
-    __shared__ int s_role[2];
-    const int G = (int)(gridDim.x / 2);
-    if (threadIdx.x == 0) {
-        unsigned sm;
-        asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
-        const unsigned slot = atomicAdd(&roles[2 + (sm & 1023u)], 1u);
-        int c = (int)(slot & 1u);
-        unsigned r = atomicAdd(&roles[c], 1u);
-        if ((int)r >= G) {
-            c ^= 1;
-            r = atomicAdd(&roles[c], 1u);
-        }
-        s_role[0] = c;
-        s_role[1] = (int)r;
-    }
-    __syncthreads();
-    const int c = s_role[0], rank = s_role[1];
-    if (!AIRGA_CK(rank, 0, G, 613)) return;
-    mixed_body<MODE, 1>(c ? a1 : a0, R, G, rank);
-}
-
 size_t mixed_smem(int64_t R) {
     return (size_t)3 * kThreads * sizeof(double) +
            (size_t)(4 * R + 2 * (HR + 2 * HZ) + 2 * kHaloPairs * kBand) * sizeof(float);
-}
-
-size_t mixed_dual_smem(int64_t R) {
-    return (size_t)3 * kThreadsDual * sizeof(double) +
-           (size_t)(2 * R + 2 * (HR + HZ) + 2 * kHaloPairs * kBand) * sizeof(float);
-}
-
-template <int MODE>
-cudaError_t launch_mixed_dual(int grid2, int64_t R, size_t smem, const Args32 &a0,
-                              const Args32 &a1, unsigned *roles, cudaStream_t s) {
-    auto kern = mixed_dual_kernel<MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    Args32 x0 = a0, x1 = a1;
-    int r = (int)R;
-    void *kargs[] = {(void *)&x0, (void *)&x1, (void *)&r, (void *)&roles};
-    return cudaLaunchCooperativeKernel((const void *)kern, dim3(grid2), dim3(kThreadsDual), kargs, smem, s);
-}
-
-template <int MODE>
-int occupancy_mixed_dual(size_t smem, int *per_sm) {
-    auto kern = mixed_dual_kernel<MODE>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                         cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, kThreadsDual, smem);
-    return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "paired mixed-precision kernel occupancy");
 }
 
 template <int MODE>
@@ -716,30 +630,15 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
                    : (mode ? occupancy_mixed<1>(smem, &per_sm) : occupancy_mixed<0>(smem, &per_sm));
     if (st) return st;
     if (per_sm < 1 || grid > per_sm * sms) return fail(AIRGA_E_INVALID_ARG, "mixed solve: grid not co-resident");
-    // paired launches: two columns per launch, one CTA of each per SM, when
-    // there are two columns and half an SM holds a CTA's r and p windows
-    const size_t smem_d = mixed_dual_smem(R);
-    bool dual = false;
-    if (m >= 2 && smem_d + 256 <= (size_t)optin) {
-        int pd = 0;
-        st = mode == 2 ? occupancy_mixed_dual<2>(smem_d, &pd)
-                       : (mode ? occupancy_mixed_dual<1>(smem_d, &pd) : occupancy_mixed_dual<0>(smem_d, &pd));
-        if (st) return st;
-        dual = pd >= 2 && grid <= sms;
-    }
 
     cudaStream_t s = (cudaStream_t)stream;
-    // workspace: FP32 A band (7n), FP32 packed (5n), FP32 M band (7n), pbuf32 (n
-    // per column of a launch), paired launches' per-CTA slices (d and z/q) as
-    // floats; partials (per column of a launch), control words, role counters
+    // workspace: FP32 A band (7n), FP32 packed (5n), FP32 M band (7n), pbuf32 (n)
+    // as floats; partials, control
     const size_t nf = (size_t)n;
     const size_t mfl = mode == 2 ? 4 * nf : (mode ? 7 * nf : 0);
-    const size_t slice = (size_t)(2 * R + 2 * HZ);
-    const size_t slices = dual ? slice * (size_t)grid : 0;
-    const size_t floats = 7 * nf + 5 * nf + mfl + nf + (dual ? nf + 2 * slices : 0);
-    const size_t doubles = (size_t)16 * grid + 4;
-    const size_t ctl_words = 4 + 2 + 1024;
-    const size_t bytes = floats * sizeof(float) + 256 + doubles * sizeof(double) + ctl_words * sizeof(unsigned) + 256;
+    const size_t floats = 7 * nf + 5 * nf + mfl + nf;
+    const size_t doubles = (size_t)8 * grid + 4;
+    const size_t bytes = floats * sizeof(float) + 256 + doubles * sizeof(double) + 256;
     void *ws = nullptr;
     st = dev_alloc(&ws, bytes, s);
     if (st) return st;
@@ -748,14 +647,9 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     float *Apk32 = A32 + 7 * nf;
     float *M32 = Apk32 + 5 * nf;
     float *pbuf = M32 + mfl;
-    float *pbuf1 = pbuf + nf;                        // paired launches only
-    float *state0 = pbuf1 + (dual ? nf : 0);
-    float *state1 = state0 + slices;
-    double *dbase = (double *)(((uintptr_t)(state1 + slices) + 255) & ~(uintptr_t)255);
+    double *dbase = (double *)(((uintptr_t)(pbuf + nf) + 255) & ~(uintptr_t)255);
     double *partials = dbase;
-    double *partials1 = partials + 8 * grid;
-    unsigned *ctl = (unsigned *)(partials1 + 8 * grid);   // bar0, abort0, bar1, abort1
-    unsigned *roles = ctl + 4;                             // 2 column counters, 1024 per-SM
+    unsigned *ctl = (unsigned *)(partials + 8 * grid);
 
     cudaError_t e = cudaSuccess;
     const int gconv = grid_for(7 * n);
@@ -796,41 +690,19 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
     a.max_outer = o.max_outer;
     a.timeout_ns = (long long)o.barrier_timeout_ms * 1000000ll;
     const int fault = take_fault(AIRGA_FAULT_SKIP_ARRIVAL) ? 1 : 0;
-    auto column = [&](Args32 &x, int32_t c) {
-        x.f = F + (size_t)c * nf;
-        x.x64 = X + (size_t)c * nf;
-        x.relres = true_relres + c;
-        x.outer_iters = outer_iters + c;
-        x.inner_iters = inner_iters + c;
-        x.status = status + c;
-        x.fault_skip_arrival = c == 0 ? fault : 0;
-    };
-    // one launch runs a column's whole refinement, or two columns' side by side
-    for (int32_t c = 0; c < m && e == cudaSuccess;) {
-        if (dual && c + 1 < m) {
-            Args32 a0 = a, a1 = a;
-            column(a0, c);
-            column(a1, c + 1);
-            a0.state = state0;
-            a1.pbuf = pbuf1;
-            a1.partials = partials1;
-            a1.bar = ctl + 2;
-            a1.abort_flag = (int *)(ctl + 3);
-            a1.state = state1;
-            e = cudaMemsetAsync(ctl, 0, ctl_words * sizeof(unsigned), s);
-            if (e == cudaSuccess)
-                e = mode == 2 ? launch_mixed_dual<2>(2 * grid, R, smem_d, a0, a1, roles, s)
-                              : (mode ? launch_mixed_dual<1>(2 * grid, R, smem_d, a0, a1, roles, s)
-                                      : launch_mixed_dual<0>(2 * grid, R, smem_d, a0, a1, roles, s));
-            c += 2;
-        } else {
-            column(a, c);
-            e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
-            if (e == cudaSuccess)
-                e = mode == 2 ? launch_mixed<2>(grid, R, smem, a, s)
-                              : (mode ? launch_mixed<1>(grid, R, smem, a, s) : launch_mixed<0>(grid, R, smem, a, s));
-            c += 1;
-        }
+    // one launch per column runs its whole refinement
+    for (int32_t c = 0; c < m && e == cudaSuccess; ++c) {
+        a.f = F + (size_t)c * nf;
+        a.x64 = X + (size_t)c * nf;
+        a.relres = true_relres + c;
+        a.outer_iters = outer_iters + c;
+        a.inner_iters = inner_iters + c;
+        a.status = status + c;
+        a.fault_skip_arrival = c == 0 ? fault : 0;
+        e = cudaMemsetAsync(ctl, 0, 2 * sizeof(unsigned), s);
+        if (e == cudaSuccess)
+            e = mode == 2 ? launch_mixed<2>(grid, R, smem, a, s)
+                          : (mode ? launch_mixed<1>(grid, R, smem, a, s) : launch_mixed<0>(grid, R, smem, a, s));
     }
     dev_free(ws, s);
     if (e != cudaSuccess) return cuda_fail(e, "mixed solve launch");
