@@ -10,12 +10,14 @@ The batched launch needs choices the library cannot know in advance:
     right-hand sides of one shift — either scheduled one by one wherever CTAs
     free up, or as one job back to back on one CTA group, so that they reuse
     the bands while these sit in L2;
+  * CTAs per SM: one CTA slot per SM (sm_share 1), or two with half an SM
+    each (sm_share 2), whose systems fill each other's barrier gaps;
   * the cost of each system (rows x CG iterations decides the list schedule).
 The tuner measures instead of guessing:
 
   1. plan with cost = rows and the default rows per CTA, solve once, read the
      CG iterations of every system;
-  2. for each (rows per CTA, grouping) candidate, plan with cost = rows x
+  2. for each (CTAs per SM, rows per CTA, grouping) candidate, plan with cost = rows x
      iterations and time the solve on the device (CUDA events, best of
      `reps`);
   3. keep the fastest plan.
@@ -30,6 +32,7 @@ from . import airga as G
 
 DEFAULT_CANDIDATES = (512, 1024, 2048, 4096, 5120, 6144, 8192)
 GROUPING = (False, True)
+SHARES = (1, 2)
 
 
 def _time_solve(batch, stream, reps):
@@ -55,8 +58,17 @@ def rhs_groups(systems):
     return out
 
 
+def _with_share(opts, share):
+    o = G.options()
+    if opts is not None:
+        for name, _ in G.Options._fields_:
+            setattr(o, name, getattr(opts, name))
+    o.sm_share = share
+    return o
+
+
 def tune(systems, opts=None, candidates=DEFAULT_CANDIDATES, grouping=GROUPING, reps=2,
-         stream=None):
+         stream=None, shares=SHARES):
     """Return (best Batch, report).  systems: list of (A, P, f, x)."""
     stream = stream or torch.cuda.current_stream()
     first = G.Batch(systems, opts=opts, stream=stream)
@@ -68,21 +80,30 @@ def tune(systems, opts=None, candidates=DEFAULT_CANDIDATES, grouping=GROUPING, r
     groups = rhs_groups(systems)
     report = []
     best, best_ms, best_key = None, float("inf"), None
-    for grouped in grouping:
-        for rows in candidates:
-            b = G.Batch(systems, opts=opts, cost=cost, rows_per_cta=rows, stream=stream,
-                        group=groups if grouped else None)
-            ms = _time_solve(b, stream, reps)
-            info = b.info()
-            report.append(dict(rows_per_cta=rows, rhs_grouped=grouped, ms=round(ms, 4),
-                               rows_max=info["rows_max"], est_makespan=info["makespan"]))
-            if ms < best_ms:
-                best, best_ms, best_key = b, ms, (rows, grouped)
-            else:
-                del b
-    cap = max(r["rows_max"] for r in report)
+    caps = {}
+    for share in shares:
+        o = _with_share(opts, share)
+        for grouped in grouping:
+            prev = None
+            for rows in candidates:
+                b = G.Batch(systems, opts=o, cost=cost, rows_per_cta=rows, stream=stream,
+                            group=groups if grouped else None)
+                info = b.info()
+                if info["rows_target"] == prev:
+                    del b          # past the shared-memory cap: the same plan as the cap
+                    continue
+                prev = info["rows_target"]
+                caps[share] = max(caps.get(share, 0), info["rows_target"])
+                ms = _time_solve(b, stream, reps)
+                report.append(dict(sm_share=share, rows_per_cta=rows, rhs_grouped=grouped,
+                                   ms=round(ms, 4), rows_max=info["rows_max"],
+                                   grid=info["grid"], est_makespan=info["makespan"]))
+                if ms < best_ms:
+                    best, best_ms, best_key = b, ms, (rows, grouped, share)
+                else:
+                    del b
     return best, dict(candidates=report, best_rows_per_cta=best.info()["rows_target"],
-                      best_rhs_grouped=best_key[1], best_ms=round(best_ms, 4),
-                      rows_cap=cap, rhs_groups=max(groups) + 1,
-                      note="targets at or above the shared-memory cap give the same plan "
-                           "(rows_max = %d): the sweep ends there" % cap)
+                      best_rhs_grouped=best_key[1], best_sm_share=best_key[2],
+                      best_ms=round(best_ms, 4), rows_cap=caps, rhs_groups=max(groups) + 1,
+                      note="targets above the shared-memory cap give the cap's plan and are "
+                           "not timed again")

@@ -27,6 +27,7 @@ struct airga_batch_s {
     int64_t rows_target = 0;
     int64_t rows_max = 0;       // largest rows per CTA in the schedule
     size_t smem = 0;
+    bool half = false;          // two CTAs per SM (options.sm_share 2 or 3)
     double makespan = 0.0;      // estimated, in cost units per CTA
     std::shared_ptr<void> ws;   // device workspace (PcgArgs, assignments, buffers)
     airga::PcgArgs *sys = nullptr;
@@ -67,16 +68,27 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
         if (mode < 0) mode = m_s;
         if (mode != m_s) return fail(AIRGA_E_INVALID_ARG, "all systems need a preconditioner or none");
     }
-    int dev = 0, sms = 0, optin = 0;
+    int dev = 0, sms = 0, optin = 0, smem_sm = 0, reserved = 0;
     AIRGA_CUDA(cudaGetDevice(&dev));
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    // sm_share 2 or 3: two CTA slots per SM, each with half an SM (the slots
+    // of different systems fill each other's barrier gaps)
+    const bool half = o.sm_share >= 2;
+    const size_t stat = pcg_pair_batch_static_smem(half) + (size_t)reserved;
     // rows per CTA the shared memory can hold
+    auto fits = [&](int64_t r) {
+        const size_t sm = pcg_pair_batch_smem(r, half);
+        return half ? 2 * (sm + stat) <= (size_t)smem_sm && sm + 256 <= (size_t)optin
+                    : sm + 512 <= (size_t)optin;
+    };
     int64_t rmax = 2;
-    while (pcg_pair_smem(rmax + 2) + 512 <= (size_t)optin) rmax += 2;
+    while (fits(rmax + 2)) rmax += 2;
     int64_t target = rows_per_cta > 0 ? rows_per_cta : 4096;
     target = std::min<int64_t>(std::max<int64_t>(target, 16), rmax);
-    const int G = sms;
+    const int G = half ? 2 * sms : sms;
 
     // group sizes
     std::vector<int> g(nsys);
@@ -96,7 +108,7 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
         c[s] = cost ? std::max(cost[s], 1.0) : (double)n;
     }
     const int64_t rbig = *std::max_element(R.begin(), R.end());
-    const size_t smem = pcg_pair_smem(rbig);
+    const size_t smem = pcg_pair_batch_smem(rbig, half);
     // jobs: one system each, or (group given) the systems of one group id with
     // the same group size, placed back to back on one CTA group so that the
     // right-hand sides of one (A, P) reuse its bands while they are in L2
@@ -242,17 +254,18 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
         delete B;
         return cuda_fail(e, "batch upload");
     }
-    st = pcg_pair_batch_prepare(mode, smem);
+    st = pcg_pair_batch_prepare(mode, smem, half);
     if (st) {
         delete B;
         return st;
     }
     int per_sm = 0;
-    st = pcg_pair_batch_occupancy(mode, smem, &per_sm);
-    if (st || per_sm < 1) {
+    st = pcg_pair_batch_occupancy(mode, smem, &per_sm, half);
+    if (st || per_sm < (half ? 2 : 1)) {
         delete B;
         return st ? st : fail(AIRGA_E_INVALID_ARG, "batch kernel cannot be resident");
     }
+    B->half = half;
     B->nsys = nsys;
     B->grid = G;
     B->mode = mode;
@@ -274,7 +287,7 @@ int airga_batch_solve(airga_batch B, void *stream) {
     const bool fault = take_fault(AIRGA_FAULT_SKIP_ARRIVAL);
     int *flag0 = &B->sys[0].fault_skip_arrival;
     if (fault) AIRGA_CUDA(cudaMemcpyAsync(flag0, &kOne, sizeof(int), cudaMemcpyHostToDevice, cs));
-    AIRGA_CUDA(launch_pcg_pair_batch(B->mode, B->grid, B->smem, B->sys, B->asg, B->off, cs));
+    AIRGA_CUDA(launch_pcg_pair_batch(B->mode, B->grid, B->smem, B->sys, B->asg, B->off, B->half, cs));
     if (fault) AIRGA_CUDA(cudaMemcpyAsync(flag0, &kZero, sizeof(int), cudaMemcpyHostToDevice, cs));
     return AIRGA_OK;
 }

@@ -602,8 +602,10 @@ pcg_pair_kernel(PcgArgs a, int R) {
 // CTA.  Assignments are appended in one global order of systems, so a CTA
 // waiting at a group barrier only waits for CTAs that are at the same or an
 // earlier system in that order: the schedule cannot deadlock.
-template <int MODE>
-__global__ void __launch_bounds__(kThreadsBatch, 1)
+// THREADS == kThreadsHalf: two CTAs per SM (options.sm_share 2 or 3), each
+// with at most half an SM's registers and shared memory
+template <int MODE, int THREADS>
+__global__ void __launch_bounds__(THREADS, THREADS == kThreadsHalf ? 2 : 1)
 pcg_pair_batch_kernel(const PcgArgs *__restrict__ sys, const int4 *__restrict__ asg,
                       const int *__restrict__ off) {
     extern __shared__ __align__(16) double smem[];
@@ -690,27 +692,48 @@ int pcg_pair_occupancy(int mode, size_t smem, int *per_sm) {
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "pcg pair occupancy");
 }
 
-int pcg_pair_batch_prepare(int mode, size_t smem) {
-    cudaError_t e = mode ? cudaFuncSetAttribute(pcg_pair_batch_kernel<1>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                         : cudaFuncSetAttribute(pcg_pair_batch_kernel<0>,
-                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+static const void *batch_kernel(int mode, bool half) {
+    if (half)
+        return mode ? (const void *)pcg_pair_batch_kernel<1, kThreadsHalf>
+                    : (const void *)pcg_pair_batch_kernel<0, kThreadsHalf>;
+    return mode ? (const void *)pcg_pair_batch_kernel<1, kThreadsBatch>
+                : (const void *)pcg_pair_batch_kernel<0, kThreadsBatch>;
+}
+
+int pcg_pair_batch_threads(bool half) { return half ? kThreadsHalf : kThreadsBatch; }
+
+size_t pcg_pair_batch_smem(int64_t R, bool half) {
+    return (size_t)(4 * R + 2 * (HR + 2 * HZ) + 2 * kHaloPairs * kBand +
+                    3 * pcg_pair_batch_threads(half)) * sizeof(double);
+}
+
+size_t pcg_pair_batch_static_smem(bool half) {
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, batch_kernel(1, half)) == cudaSuccess ? fa.sharedSizeBytes : 256;
+}
+
+int pcg_pair_batch_prepare(int mode, size_t smem, bool half) {
+    const void *kern = batch_kernel(mode, half);
+    cudaError_t e = cudaSuccess;
+    if (half)   // two CTAs per SM need the largest shared-memory carveout
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "batch smem");
 }
 
-int pcg_pair_batch_occupancy(int mode, size_t smem, int *per_sm) {
-    cudaError_t e = mode ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_batch_kernel<1>,
-                                                                         kThreadsBatch, smem)
-                         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, pcg_pair_batch_kernel<0>,
-                                                                         kThreadsBatch, smem);
+int pcg_pair_batch_occupancy(int mode, size_t smem, int *per_sm, bool half) {
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, batch_kernel(mode, half),
+                                                                  pcg_pair_batch_threads(half), smem);
     return e == cudaSuccess ? AIRGA_OK : cuda_fail(e, "batch occupancy");
 }
 
 cudaError_t launch_pcg_pair_batch(int mode, int grid, size_t smem, const PcgArgs *sys,
-                                  const int4 *asg, const int *off, cudaStream_t s) {
+                                  const int4 *asg, const int *off, bool half, cudaStream_t s) {
     void *kargs[] = {(void *)&sys, (void *)&asg, (void *)&off};
-    const void *kern = mode ? (const void *)pcg_pair_batch_kernel<1> : (const void *)pcg_pair_batch_kernel<0>;
-    return cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(kThreadsBatch), kargs, smem, s);
+    return cudaLaunchCooperativeKernel(batch_kernel(mode, half), dim3(grid),
+                                       dim3(pcg_pair_batch_threads(half)), kargs, smem, s);
 }
 
 int pcg_pair_split_occupancy(int mode, size_t smem, int *per_sm) {

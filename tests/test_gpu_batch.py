@@ -46,13 +46,14 @@ def make_systems(G, spec, seed=3):
 SPEC = [(37, [0.3, 20.0], 1), (900, [0.1, 2.0, 500.0], 2), (5000, [1.0], 3), (12, [5.0], 1)]
 
 
+@pytest.mark.parametrize("share", [1, 2], ids=["cta_per_sm", "two_ctas_per_sm"])
 @pytest.mark.parametrize("grouped", [False, True], ids=["single", "rhs_grouped"])
 @pytest.mark.parametrize("rows", [0, 64, 700])
-def test_batch_matches_oracle(G, rows, grouped):
+def test_batch_matches_oracle(G, rows, grouped, share):
     from paper_1606_01216_gb300 import autotune
     systems, ref, keep = make_systems(G, SPEC)
     group = autotune.rhs_groups(systems) if grouped else None
-    B = G.Batch(systems, rows_per_cta=rows, group=group)
+    B = G.Batch(systems, G.options(sm_share=share), rows_per_cta=rows, group=group)
     info = B.info()
     assert info["grid"] >= 1 and info["rows_max"] % 2 == 0
     B.solve()
