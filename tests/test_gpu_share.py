@@ -145,3 +145,43 @@ def test_sm_share_rejects_other_values(G):
     for bad in (0, 4):
         with pytest.raises(G.AirgaError):
             G.pcg_solve(A, None, f, G.options(sm_share=bad))
+
+
+def test_lead_ctas_never_share_an_sm(G):
+    """A lead solve (sm_share = 2) reserves just over half an SM's shared
+    memory, so no two of its CTAs can sit on one SM: the placement hook must
+    show every CTA on its own SM, whatever else runs.  A partner launched
+    beside it on another stream still solves its own system."""
+    beam = W.beam(500000)                       # n = 1e6: 152 CTAs of 6580 rows
+    M, K = G.beam_mats(beam)
+    f = torch.from_numpy(np.ascontiguousarray(W.loads(beam.n)[:, 0])).cuda()
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    place_a = torch.full((1024,), -1, dtype=torch.int32, device="cuda")
+    place_b = torch.full((1024,), -1, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(sa):
+        Aa = G.assemble_shifted(M, K, AL, BE, 2.6827, stream=sa)
+        Pa = G.spai_build(Aa, G.options(spai_mode=G.SPAI_NE), stream=sa)
+        ready = torch.cuda.Event()
+        ready.record(sa)
+        G.debug_record_placement(place_a)
+        ra = G.pcg_solve(Aa, Pa, f, G.options(sm_share=2), stream=sa)
+    sb.wait_event(ready)
+    G.stream_hold(50, sb)
+    with torch.cuda.stream(sb):
+        Ab = G.assemble_shifted(M, K, AL, BE, 13.895, stream=sb)
+        Pb = G.spai_build(Ab, G.options(spai_mode=G.SPAI_NE), stream=sb)
+        G.debug_record_placement(place_b)
+        rb = G.pcg_solve(Ab, Pb, f, G.options(sm_share=3), stream=sb)
+    G.debug_record_placement(None)
+    torch.cuda.synchronize()
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    pa = place_a.cpu().numpy()
+    grid = int((pa >= 0).sum())
+    assert 1 <= grid <= sms
+    assert np.all(pa[:grid] >= 0) and np.all(pa[:grid] < 1024) and np.all(pa[grid:] == -1)
+    assert len(set(pa[:grid].tolist())) == grid          # one lead CTA per SM
+    pb = place_b.cpu().numpy()
+    assert int((pb >= 0).sum()) == grid
+    for r in (ra, rb):
+        assert int(r["status"][0]) == G.OK and float(r["true_relres"][0]) <= 2e-10
