@@ -180,3 +180,17 @@ def test_ne_without_column_residuals(G):
     # the Householder solver keeps its by-product residuals either way
     Pq = G.spai_build(A, G.options(want_colres=0))
     assert not np.any(np.isnan(G.precond_status(Pq)[1].cpu().numpy()))
+
+
+@pytest.mark.parametrize("s", [0.1, 4.0, 1e4])
+def test_ne_update_same_matrix_is_identity(G, s):
+    """Sec. 3.2 with A_prev = A_next: the update's least-squares problem is
+    solved exactly by Q = I.  Through the normal equations m = G^{-1} G e_c,
+    so the error is the Gram block's rounding (cond(G) <= 4.6e5 on the beam)."""
+    beam = W.beam(300)
+    M, K = G.beam_mats(beam)
+    A = G.assemble_shifted(M, K, AL, BE, s)
+    Q = G.precond_factor(G.spai_update(G.spai_build(A, ne(G)), A, A, ne(G)), 1).cpu().numpy()
+    Q = Q.reshape(7, -1)
+    assert np.abs(Q[3] - 1.0).max() <= 1e-9
+    assert np.abs(np.delete(Q, 3, axis=0)).max() <= 1e-9
