@@ -451,6 +451,11 @@ def method_arms(G, torch, stream, M, K, F, shifts, opts):
     the chain restarts there.  Every phase is timed on the device (CUDA
     events); totals are preconditioner + CG time, as in Table 8."""
     def timed(fn):
+        # device time of one call: a 200 us hold queued first keeps the device
+        # busy while the host enqueues the call, so the host's launch latency
+        # falls before the start event instead of inside the interval
+        torch.cuda.synchronize()
+        G.stream_hold(200, stream)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
