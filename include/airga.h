@@ -326,9 +326,13 @@ int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
  * back to back on one CTA group, e.g. the right-hand sides of one (A, P),
  * which then reuse its bands while they sit in L2; NULL schedules every
  * system on its own.  opt->sm_share 1 (default) plans one CTA slot per SM;
- * 2 or 3 plans two per SM (256 threads, at most half an SM's registers and
- * shared memory each, about 3,300 rows per CTA at most), so that the CTAs of
- * different systems on one SM fill each other's barrier gaps.  Requirements: every n even, F[s] and X[s]
+ * 2 or 3 plans two lanes of one slot per SM each (256 threads, at most half
+ * an SM's registers and shared memory per CTA; x updated in place and the
+ * z/q window in a per-slot device slice, about 6,700 rows per CTA at most).
+ * A system's CTA group lies within one lane, so its CTAs sit on distinct SMs,
+ * and the two CTAs on an SM belong to different systems, which fill each
+ * other's barrier gaps; each job goes to the lane where it can start first.
+ * Requirements: every n even, F[s] and X[s]
  * (device, n-vectors) 16-byte aligned, either every P[s] a single factor of
  * matching size or P NULL / every P[s] NULL.  Results of each solve go to the
  * caller's device arrays iters[s], status[s] and relres[s] (true residual).

@@ -329,15 +329,19 @@ int pcg_pair_threads(int kind);   // threads per CTA of plan kind 2, 3 or 4
 int pcg_pair_occupancy(int mode, size_t smem, int *per_sm);
 cudaError_t launch_pcg_pair(const PcgPlan &plan, const PcgArgs &args, cudaStream_t s);
 // batched node-pair kernel: systems `sys`, assignments asg (int4: system,
-// group size, rank, rows per CTA) per CTA from off[c] to off[c+1].  half:
-// two CTAs per SM (256 threads, at most half an SM each) instead of one
+// group size, rank, rows per CTA) per CTA slot from off[c] to off[c+1].
+// half: two lanes of CTA slots, two CTAs per SM (256 threads, half an SM
+// each, split state: the z/q window in a per-slot slice of slice_len doubles;
+// roles: 2 + 1024 zeroed words) instead of one CTA per SM
 int pcg_pair_batch_threads(bool half);
 size_t pcg_pair_batch_smem(int64_t R, bool half);
+size_t pcg_pair_batch_slice(int64_t R);
 size_t pcg_pair_batch_static_smem(bool half);
 int pcg_pair_batch_prepare(int mode, size_t smem, bool half);
 int pcg_pair_batch_occupancy(int mode, size_t smem, int *per_sm, bool half);
 cudaError_t launch_pcg_pair_batch(int mode, int grid, size_t smem, const PcgArgs *sys,
-                                  const int4 *asg, const int *off, bool half, cudaStream_t s);
+                                  const int4 *asg, const int *off, bool half, unsigned *roles,
+                                  double *slices, int slice_len, cudaStream_t s);
 
 }  // namespace airga
 

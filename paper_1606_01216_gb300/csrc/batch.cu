@@ -10,6 +10,9 @@
 // CTAs follow that single global order, which makes the group barriers
 // deadlock free (see pcg_pair_batch_kernel).  Each system has a private
 // barrier counter, abort flag, partials block and p boundary buffer.
+// With options.sm_share 2 or 3 the CTA slots form two lanes of one slot per
+// SM each; a system's group lies within one lane (so its CTAs sit on distinct
+// SMs) and each job goes to the lane where it can start first.
 //
 // The solve call enqueues one memset and one cooperative launch and
 // allocates nothing, so it can be captured in a CUDA graph and replayed.
@@ -27,7 +30,7 @@ struct airga_batch_s {
     int64_t rows_target = 0;
     int64_t rows_max = 0;       // largest rows per CTA in the schedule
     size_t smem = 0;
-    bool half = false;          // two CTAs per SM (options.sm_share 2 or 3)
+    bool half = false;          // two lanes, two CTAs per SM (options.sm_share 2 or 3)
     double makespan = 0.0;      // estimated, in cost units per CTA
     std::shared_ptr<void> ws;   // device workspace (PcgArgs, assignments, buffers)
     airga::PcgArgs *sys = nullptr;
@@ -35,6 +38,9 @@ struct airga_batch_s {
     int *off = nullptr;
     void *ctl = nullptr;
     size_t ctl_bytes = 0;
+    unsigned *roles = nullptr;  // lane counters and per-SM arrivals (inside ctl)
+    double *slices = nullptr;   // z/q slice per CTA slot (lanes only)
+    int slice_len = 0;
 };
 
 using namespace airga;
@@ -88,7 +94,9 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
     while (fits(rmax + 2)) rmax += 2;
     int64_t target = rows_per_cta > 0 ? rows_per_cta : 4096;
     target = std::min<int64_t>(std::max<int64_t>(target, 16), rmax);
-    const int G = half ? 2 * sms : sms;
+    const int G = half ? 2 * sms : sms;          // CTA slots
+    const int L = sms;                           // slots per lane (one per SM)
+    const int nl = half ? 2 : 1;
 
     // group sizes
     std::vector<int> g(nsys);
@@ -98,9 +106,9 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
         const int64_t n = A[s]->n;
         int64_t gs = (n + target - 1) / target;
         if (gs < 1) gs = 1;
-        if (gs > G) gs = G;                                  // more rows per CTA instead
+        if (gs > L) gs = L;                                  // more rows per CTA instead
         if ((n + gs - 1) / gs > rmax) gs = (n + rmax - 1) / rmax;
-        if (gs > G) return fail(AIRGA_E_INVALID_ARG, "a batch system is larger than the GPU's shared memory");
+        if (gs > L) return fail(AIRGA_E_INVALID_ARG, "a batch system is larger than the GPU's shared memory");
         g[s] = (int)gs;
         int64_t rs = (n + gs - 1) / gs;
         rs += rs & 1;
@@ -139,29 +147,38 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jc[a] > jc[b]; });
     std::vector<double> avail(G, 0.0);
     std::vector<std::vector<int4>> lists(G);
-    std::vector<int> idx(G);
+    std::vector<int> idx(L), pick(L);
     for (int j : order) {
         const int gj = g[jobs[j][0]];
-        std::iota(idx.begin(), idx.end(), 0);
-        std::partial_sort(idx.begin(), idx.begin() + gj, idx.end(), [&](int a, int b) {
-            return avail[a] < avail[b] || (avail[a] == avail[b] && a < b);
-        });
-        std::sort(idx.begin(), idx.begin() + gj);
         double start = 0.0;
-        for (int k = 0; k < gj; ++k) start = std::max(start, avail[idx[k]]);
+        for (int l = 0; l < nl; ++l) {                   // the lane where the job starts first
+            std::iota(idx.begin(), idx.end(), l * L);
+            std::partial_sort(idx.begin(), idx.begin() + gj, idx.end(), [&](int a, int b) {
+                return avail[a] < avail[b] || (avail[a] == avail[b] && a < b);
+            });
+            double st_l = 0.0;
+            for (int k = 0; k < gj; ++k) st_l = std::max(st_l, avail[idx[k]]);
+            if (l == 0 || st_l < start) {
+                start = st_l;
+                std::copy(idx.begin(), idx.begin() + gj, pick.begin());
+            }
+        }
+        std::sort(pick.begin(), pick.begin() + gj);
+        const std::vector<int> &sel = pick;
         // members in one global order: every CTA of the group appends them in
         // the same sequence, which keeps the group barriers deadlock free
         for (int s : jobs[j]) {
             const double end = start + c[s] / gj;
-            for (int k = 0; k < gj; ++k) lists[idx[k]].push_back(make_int4(s, gj, k, (int)R[s]));
+            for (int k = 0; k < gj; ++k) lists[sel[k]].push_back(make_int4(s, gj, k, (int)R[s]));
             start = end;
         }
-        for (int k = 0; k < gj; ++k) avail[idx[k]] = start;
+        for (int k = 0; k < gj; ++k) avail[sel[k]] = start;
     }
     const double makespan = *std::max_element(avail.begin(), avail.end());
 
     // workspace: PcgArgs[nsys] | int4 asg[total] | int off[G+1] | control (2 ints per
-    // system) | partials (8 g doubles per system) | pbuf (n doubles per system)
+    // system; lanes: + 2 + 1024 role counters) | partials (8 g doubles per
+    // system) | pbuf (n doubles per system) | lanes: z/q slice per CTA slot
     size_t total_asg = 0;
     for (auto &l : lists) total_asg += l.size();
     size_t nb_pbuf = 0, nb_part = 0;
@@ -171,11 +188,14 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
     }
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     const size_t b_sys = al(sizeof(PcgArgs) * nsys), b_asg = al(sizeof(int4) * total_asg),
-                 b_off = al(sizeof(int) * (G + 1)), b_ctl = al(sizeof(unsigned) * 2 * nsys),
+                 b_off = al(sizeof(int) * (G + 1)), b_bar = al(sizeof(unsigned) * 2 * nsys),
+                 b_ctl = b_bar + (half ? al(sizeof(unsigned) * (2 + 1024)) : 0),
                  b_part = al(sizeof(double) * nb_part), b_pbuf = al(sizeof(double) * nb_pbuf);
+    const size_t slice_len = pcg_pair_batch_slice(rbig);
+    const size_t b_slc = half ? al(sizeof(double) * slice_len * (size_t)G) : 0;
     cudaStream_t cs = (cudaStream_t)stream;
     auto *B = new airga_batch_s;
-    st = make_buf(b_sys + b_asg + b_off + b_ctl + b_part + b_pbuf, cs, &B->ws);
+    st = make_buf(b_sys + b_asg + b_off + b_ctl + b_part + b_pbuf + b_slc, cs, &B->ws);
     if (st) {
         delete B;
         return st;
@@ -188,6 +208,11 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
     B->ctl_bytes = b_ctl;
     double *part = (double *)(base + b_sys + b_asg + b_off + b_ctl);
     double *pbuf = (double *)(base + b_sys + b_asg + b_off + b_ctl + b_part);
+    if (half) {
+        B->roles = (unsigned *)((char *)B->ctl + b_bar);
+        B->slices = (double *)(base + b_sys + b_asg + b_off + b_ctl + b_part + b_pbuf);
+        B->slice_len = (int)slice_len;
+    }
 
     // per-system arguments (host copy, then one upload)
     std::vector<PcgArgs> hs(nsys);
@@ -287,7 +312,8 @@ int airga_batch_solve(airga_batch B, void *stream) {
     const bool fault = take_fault(AIRGA_FAULT_SKIP_ARRIVAL);
     int *flag0 = &B->sys[0].fault_skip_arrival;
     if (fault) AIRGA_CUDA(cudaMemcpyAsync(flag0, &kOne, sizeof(int), cudaMemcpyHostToDevice, cs));
-    AIRGA_CUDA(launch_pcg_pair_batch(B->mode, B->grid, B->smem, B->sys, B->asg, B->off, B->half, cs));
+    AIRGA_CUDA(launch_pcg_pair_batch(B->mode, B->grid, B->smem, B->sys, B->asg, B->off, B->half,
+                                     B->roles, B->slices, B->slice_len, cs));
     if (fault) AIRGA_CUDA(cudaMemcpyAsync(flag0, &kZero, sizeof(int), cudaMemcpyHostToDevice, cs));
     return AIRGA_OK;
 }

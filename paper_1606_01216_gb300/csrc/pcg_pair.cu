@@ -223,7 +223,9 @@ struct PairShared {
 // the whole grid as the group, the batched kernel once per assignment.
 // SYMU: read P_sym through its upper diagonals (pair_sym; every kernel that
 // has P_sym does)
-template <int MODE, int SPLIT = 0, bool SYMU = true>   // MODE 0: identity, 1: one symmetric band
+// SLOT_SLICE (batch lanes): a.state is this CTA's own z/q slice, not the base
+// of the group's slices
+template <int MODE, int SPLIT = 0, bool SYMU = true, bool SLOT_SLICE = false>   // MODE 0: identity, 1: one symmetric band
 __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem,
                           PairShared &sh) {
     double *tot = sh.tot;
@@ -251,7 +253,7 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
         rs = smem;
         ps = rs + (R + 2 * HR);
         xs = a.x + lo;
-        zq = a.state + (size_t)rank * (size_t)(R + 2 * HZ);
+        zq = a.state + (SLOT_SLICE ? (size_t)0 : (size_t)rank * (size_t)(R + 2 * HZ));
     } else {
         xs = smem;
         rs = xs + R;
@@ -602,19 +604,53 @@ pcg_pair_kernel(PcgArgs a, int R) {
 // CTA.  Assignments are appended in one global order of systems, so a CTA
 // waiting at a group barrier only waits for CTAs that are at the same or an
 // earlier system in that order: the schedule cannot deadlock.
-// THREADS == kThreadsHalf: two CTAs per SM (options.sm_share 2 or 3), each
-// with at most half an SM's registers and shared memory
-template <int MODE, int THREADS>
-__global__ void __launch_bounds__(THREADS, THREADS == kThreadsHalf ? 2 : 1)
+//
+// LANES (options.sm_share 2 or 3): two lanes of gridDim.x / 2 CTA slots,
+// two CTAs per SM (256 threads, half an SM each, r and p windows in shared
+// memory, x in place, z/q in the slot's own global slice).  A CTA takes its
+// lane from its arrival on its SM (first: lane 0, second: lane 1; a full lane
+// sends it to the other), so every SM holds one CTA of each lane, and the
+// systems of the two lanes fill each other's barrier gaps.  Each system's
+// group lies within one lane; each lane's lists follow one global order.
+// roles: [0], [1] lane counters, [2 + s] arrivals on SM s (zeroed per solve).
+template <int MODE, int LANES>
+__global__ void __launch_bounds__(LANES ? kThreadsHalf : kThreadsBatch, LANES ? 2 : 1)
 pcg_pair_batch_kernel(const PcgArgs *__restrict__ sys, const int4 *__restrict__ asg,
-                      const int *__restrict__ off) {
+                      const int *__restrict__ off, unsigned *roles, double *slices,
+                      int slice_len) {
     extern __shared__ __align__(16) double smem[];
     __shared__ PairShared sh;
-    const int b = off[blockIdx.x], e = off[blockIdx.x + 1];
+    __shared__ int s_slot;
+    int slot = blockIdx.x;
+    if (LANES) {
+        const int L = (int)(gridDim.x / 2);
+        if (threadIdx.x == 0) {
+            unsigned sm;
+            asm volatile("mov.u32 %0, %%smid;" : "=r"(sm));
+            int lane = (int)(atomicAdd(&roles[2 + (sm & 1023u)], 1u) & 1u);
+            unsigned r = atomicAdd(&roles[lane], 1u);
+            if ((int)r >= L) {
+                lane ^= 1;
+                r = atomicAdd(&roles[lane], 1u);
+            }
+            s_slot = lane * L + (int)r;
+        }
+        __syncthreads();
+        slot = s_slot;
+        if (!AIRGA_CK(slot, 0, 2 * L, 116)) return;
+    }
+    const int b = off[slot], e = off[slot + 1];
     for (int k = b; k < e; ++k) {
         const int4 w = asg[k];                       // (system, group size, rank, rows per CTA)
-        const PcgArgs a = sys[w.x];
-        if ((MODE == 1) == (a.nf == 1)) pair_body<MODE, 0, true>(a, w.w, w.y, w.z, smem, sh);
+        PcgArgs a = sys[w.x];
+        if ((MODE == 1) == (a.nf == 1)) {
+            if (LANES) {
+                a.state = slices + (size_t)slot * (size_t)slice_len;
+                pair_body<MODE, 2, true, true>(a, w.w, w.y, w.z, smem, sh);
+            } else {
+                pair_body<MODE, 0, true>(a, w.w, w.y, w.z, smem, sh);
+            }
+        }
         __syncthreads();
     }
 }
@@ -694,18 +730,19 @@ int pcg_pair_occupancy(int mode, size_t smem, int *per_sm) {
 
 static const void *batch_kernel(int mode, bool half) {
     if (half)
-        return mode ? (const void *)pcg_pair_batch_kernel<1, kThreadsHalf>
-                    : (const void *)pcg_pair_batch_kernel<0, kThreadsHalf>;
-    return mode ? (const void *)pcg_pair_batch_kernel<1, kThreadsBatch>
-                : (const void *)pcg_pair_batch_kernel<0, kThreadsBatch>;
+        return mode ? (const void *)pcg_pair_batch_kernel<1, 1> : (const void *)pcg_pair_batch_kernel<0, 1>;
+    return mode ? (const void *)pcg_pair_batch_kernel<1, 0> : (const void *)pcg_pair_batch_kernel<0, 0>;
 }
 
 int pcg_pair_batch_threads(bool half) { return half ? kThreadsHalf : kThreadsBatch; }
 
 size_t pcg_pair_batch_smem(int64_t R, bool half) {
-    return (size_t)(4 * R + 2 * (HR + 2 * HZ) + 2 * kHaloPairs * kBand +
-                    3 * pcg_pair_batch_threads(half)) * sizeof(double);
+    if (half) return pcg_pair_half_smem(R);                 // lanes: the split state
+    return (size_t)(4 * R + 2 * (HR + 2 * HZ) + 2 * kHaloPairs * kBand + 3 * kThreadsBatch) *
+           sizeof(double);
 }
+
+size_t pcg_pair_batch_slice(int64_t R) { return (size_t)(R + 2 * HZ); }
 
 size_t pcg_pair_batch_static_smem(bool half) {
     cudaFuncAttributes fa;
@@ -730,8 +767,10 @@ int pcg_pair_batch_occupancy(int mode, size_t smem, int *per_sm, bool half) {
 }
 
 cudaError_t launch_pcg_pair_batch(int mode, int grid, size_t smem, const PcgArgs *sys,
-                                  const int4 *asg, const int *off, bool half, cudaStream_t s) {
-    void *kargs[] = {(void *)&sys, (void *)&asg, (void *)&off};
+                                  const int4 *asg, const int *off, bool half, unsigned *roles,
+                                  double *slices, int slice_len, cudaStream_t s) {
+    void *kargs[] = {(void *)&sys, (void *)&asg, (void *)&off, (void *)&roles, (void *)&slices,
+                     (void *)&slice_len};
     return cudaLaunchCooperativeKernel(batch_kernel(mode, half), dim3(grid),
                                        dim3(pcg_pair_batch_threads(half)), kargs, smem, s);
 }
