@@ -185,3 +185,67 @@ def test_lead_ctas_never_share_an_sm(G):
     assert int((pb >= 0).sum()) == grid
     for r in (ra, rb):
         assert int(r["status"][0]) == G.OK and float(r["true_relres"][0]) <= 2e-10
+
+
+def _band_from_csr(C):
+    """(7, n) band of a CSR factor on the band-7 pattern: band[d + 3, i] = C[i, i + d]."""
+    rows = np.repeat(np.arange(C.n), np.diff(C.rowptr))
+    band = np.zeros((7, C.n))
+    band[C.col - rows + 3, rows] = C.val
+    return band
+
+
+def _band_col_errors(bg, bo):
+    """max_j ||f_gpu(:, j) - f_ora(:, j)|| / ||f_ora(:, j)|| on two (7, n) bands."""
+    n = bo.shape[1]
+    num, den = np.zeros(n), np.zeros(n)
+    for d in range(-3, 4):
+        i = np.arange(max(0, -d), min(n, n - d))
+        num[i + d] += (bg[d + 3, i] - bo[d + 3, i]) ** 2
+        den[i + d] += bo[d + 3, i] ** 2
+    return np.sqrt(num) / np.where(den > 0, np.sqrt(den), 1.0)
+
+
+def test_full_size_step_configuration(G):
+    """The measured configuration at full size: the n = 1e6 beam, SPAI by the
+    normal equations without per-column residuals, the s = 0.1 solve as a
+    lead (sm_share = 2) and the s = 0.518 solve as a partner (sm_share = 3)
+    on a second stream that starts 50 us after the lead's inputs, both solves
+    in flight together.  Every SPAI column against the oracle's Householder
+    solve, each solution against the oracle's banded Cholesky solve, each
+    iteration count against the oracle's PCG."""
+    beam = W.beam(500000)
+    M, K = G.beam_mats(beam)
+    F = W.loads(beam.n)[:, 0]
+    f = torch.from_numpy(np.ascontiguousarray(F)).cuda()
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    so = G.options(spai_mode=G.SPAI_NE, want_colres=0)
+    torch.cuda.synchronize()
+    out = []
+    for s, st, share in ((0.1, sa, 2), (0.5179474679231212, sb, 3)):
+        with torch.cuda.stream(st):
+            A = G.assemble_shifted(M, K, AL, BE, s, stream=st)
+            P = G.spai_build(A, so, stream=st)
+            if st is sa:
+                ready = torch.cuda.Event()
+                ready.record(sa)
+                sb.wait_event(ready)
+                G.stream_hold(50, sb)
+            r = G.pcg_solve(A, P, f, G.options(tol=1e-10, maxit=20000, sm_share=share), stream=st)
+            out.append((s, A, P, r))
+    torch.cuda.synchronize()
+    for s, A, P, r in out:
+        Ao = O.shifted_csr(beam, AL, BE, s)
+        Po = O.spai(Ao)
+        err = _band_col_errors(G.precond_factor(P, 0).cpu().numpy().reshape(7, -1),
+                               _band_from_csr(Po))
+        assert err.max() <= 1e-10, (s, float(err.max()))
+        x = r["X"].cpu().numpy().reshape(-1)
+        xd = O.chol_solve(Ao, F)[:, 0]
+        assert int(r["status"][0]) == G.OK
+        assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+        true = np.linalg.norm(F - O.spmv(Ao, x)) / np.linalg.norm(F)
+        assert true <= 2e-10
+        assert abs(true - float(r["true_relres"][0])) <= 1e-3 * true + 1e-12
+        _, it_o, _, _ = O.pcg(Ao, F, [Po], tol=1e-10, maxit=20000)
+        assert abs(int(r["iters"][0]) - it_o) <= max(2, it_o // 20), (s, int(r["iters"][0]), it_o)
