@@ -388,12 +388,14 @@ def gpu_arm(args, world, rank, local):
                  "note": "PCG 18 FP64 instructions per row and iteration + SPAI 182 per "
                          "column, over the step time at the FP64 issue rate"}
     forms = None
-    if not args.profile and not args.no_forms:
+    # under --profile the forms run only when --forms names them
+    if not args.no_forms and (not args.profile or args.forms is not None):
         del M, K
         makers = {"c1": c1_form, "c2": c2_form, "precision": precision_form,
                   "batching": batching_form, "learned": learned_form,
                   "inner_loop": inner_loop_form}
-        forms = {k: makers[k](G, torch, stream) for k in args.forms.split(",") if k}
+        names = args.forms if args.forms is not None else DEFAULT_FORMS
+        forms = {k: makers[k](G, torch, stream) for k in names.split(",") if k}
 
     # end to end through the public API with host buffers
     e2e = e2e_arm(G, torch, beam, (opts, opts_b), args, parts) if rank == 0 and not args.profile else None
@@ -731,13 +733,15 @@ def precision_error_vs_oracle():
 def batching_form(G, torch, stream):
     """Batching workload: 32 beams, element counts log-uniform in
     [5e3, 5e5] (seed 20261203), 4..16 shifts log-spaced in [1e-1, 1e4] each,
-    m in {1, 4} right-hand sides (tip + N(0,1) loads); SPAI (QR) per
-    (beam, shift).  All systems are solved (a) one pcg_solve call per
+    m in {1, 4} right-hand sides (tip + N(0,1) loads); SPAI (normal
+    equations) per (beam, shift).  --batch-beams K keeps the first K beams
+    (fewer only to profile).  The timed graph replays sit in the NVTX range
+    "batched_graph", which a profiler can filter on.  All systems are solved (a) one pcg_solve call per
     (beam, shift) in sequence and (b) in ONE persistent batched launch,
     schedule chosen by the autotuner, captured in a CUDA graph and replayed.
     Both report solves/s (systems at FP64 relative residual <= 1e-10)."""
     from paper_1606_01216_gb300 import autotune
-    spec = W.batched_beams()
+    spec = W.batched_beams(count=BATCH_BEAMS)
     opts = G.options(tol=TOL, maxit=20000)
     keep, systems, per_shift = [], [], []
     for cfg in spec:
@@ -785,6 +789,7 @@ def batching_form(G, torch, stream):
     graph.replay()
     torch.cuda.synchronize()
     times = []
+    torch.cuda.nvtx.range_push("batched_graph")
     for _ in range(3):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -793,14 +798,16 @@ def batching_form(G, torch, stream):
         e1.record(stream)
         torch.cuda.synchronize()
         times.append(e0.elapsed_time(e1))
+    torch.cuda.nvtx.range_pop()
     bat_ms = min(times)
     bat_ok = int(((batch.status == G.OK) & (batch.relres <= 2 * TOL)).sum())
     # FP64 work of the batch in the model count (20 FMA per row and iteration)
     row_iters = float(sum(s[0].n * int(it) for s, it in zip(systems, batch.iters.cpu().tolist())))
     pk = peaks()
     fp64_peak_tf = fp64_peak(G, pk["sm_max_mhz"])["tflops"]
-    return {"workload": "32 beams n_e log-uniform [5e3, 5e5] (seed 20261203), 4..16 shifts "
-                        "logspace(-1,4) each, m in {1,4}; SPAI (QR) per (beam, shift)",
+    return {"workload": "%d beams n_e log-uniform [5e3, 5e5] (seed 20261203), 4..16 shifts "
+                        "logspace(-1,4) each, m in {1,4}; SPAI (normal equations) per "
+                        "(beam, shift)" % len(spec),
             "systems": nsys, "rows_total": rows,
             "sequential_pcg": {"solves_per_s": round(seq_ok / (seq_ms * 1e-3), 2),
                                "converged": seq_ok, "ms": round(seq_ms, 3),
@@ -818,6 +825,8 @@ def batching_form(G, torch, stream):
 
 MLP_FLOP_PER_SAMPLE_FWD = 2 * (16 * 64 + 64 * 64 + 64 * 16)   # 12288 (MACs x 2)
 LEARNED_TRAIN_STEPS = 30_000     # --learned-train-steps (shorter only for profiling runs)
+BATCH_BEAMS = 32                 # --batch-beams (fewer only for profiling runs)
+DEFAULT_FORMS = "c1,c2,precision,batching,learned,inner_loop"
 
 
 def learned_form(G, torch, stream):
@@ -1261,23 +1270,28 @@ def reference_arm(args, world, rank):
 
 
 def main():
-    global LEARNED_TRAIN_STEPS
+    global LEARNED_TRAIN_STEPS, BATCH_BEAMS
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--forms", default="c1,c2,precision,batching,learned,inner_loop",
-                    help="comma-separated growth forms to run after the timed steps")
+    ap.add_argument("--forms", default=None,
+                    help="comma-separated growth forms to run after the timed steps "
+                         "(default: all of %s; under --profile none unless named)" % DEFAULT_FORMS)
+    ap.add_argument("--batch-beams", type=int, default=BATCH_BEAMS,
+                    help="beams of the batching form (default 32; fewer only to profile)")
     ap.add_argument("--learned-train-steps", type=int, default=LEARNED_TRAIN_STEPS,
                     help="Adam steps of the learned form (default 30000; fewer only to profile)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the growth-form measurements (precision, batching)")
     ap.add_argument("--profile", action="store_true",
-                    help="timed steps only (no per-phase split, e2e or CPU legs): for ncu")
+                    help="timed steps only (no per-phase split, e2e or CPU legs; growth forms "
+                         "only when --forms names them): for ncu")
     args = ap.parse_args()
     LEARNED_TRAIN_STEPS = max(1, args.learned_train_steps)
+    BATCH_BEAMS = min(32, max(1, args.batch_beams))
     if args.warmup < 3 and args.impl != "reference":
         args.warmup = 3
     world, rank, local = dist_env()
