@@ -442,7 +442,8 @@ def gpu_arm(args, world, rank, local):
 
 def method_arms(G, torch, stream, M, K, F, shifts, opts):
     """The paper's comparison on one beam and shift list (Tables 2-5 and 8):
-      rebuild      assemble -> SPAI (QR) -> PCG per shift;
+      rebuild      assemble -> SPAI (normal equations; the Householder build
+                   of the same matrix timed beside it) -> PCG per shift;
       update_qr    the exact-LS update Q of Sec. 3.2 from the previous shift,
                    chained (Algorithm 5, horizontal);
       mr_absolute  the paper's MR iteration (Algorithms 2 / 4) stopping at
@@ -605,7 +606,7 @@ def c2_form(G, torch, stream):
 def precision_form(G, torch, stream):
     """Precision workload: 1,000,000 elements (n = 2e6), m = 8 right-hand sides
     (tip force + 7 seeded N(0,1) loads, seed 4), 16 shifts log-spaced in
-    [1e-1, 1e4]; SPAI (QR) per shift.  The same matrices and preconditioners
+    [1e-1, 1e4]; SPAI (normal equations) per shift.  The same matrices and preconditioners
     are solved by the plain FP64 PCG and by the FP32-inner / FP64-refinement
     solve; each reports solves/s (shift x RHS systems at FP64 relative residual
     <= 1e-10 per second of solve time) and the largest FP64 true residual.  The

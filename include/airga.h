@@ -612,7 +612,10 @@ int airga_debug_force_pcg_kernel(int kind);
  * has SMs) is set, every CG call that runs a node-pair kernel writes the SM
  * index of each of its CTAs there, CTA rank k at sm_of_cta[k]; NULL (the
  * default) turns it off.  The pointer is read when a call is made, so each
- * of two concurrent solves can be given its own buffer. */
+ * of two concurrent solves can be given its own buffer.  airga_batch_create
+ * reads it too: every solve of a plan created while it is set writes system
+ * s's CTA rank k at sm_of_cta[s * 1024 + k] (the buffer then needs 1024 int32
+ * per system). */
 int airga_debug_record_placement(int32_t *sm_of_cta);
 
 /* Scheduling aid for lead / partner solves (options.sm_share 2 and 3), no

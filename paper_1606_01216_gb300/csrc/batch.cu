@@ -215,6 +215,7 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
     }
 
     // per-system arguments (host copy, then one upload)
+    int32_t *place = placement_buffer();      // test hook: system s records at place[s * 1024 + rank]
     std::vector<PcgArgs> hs(nsys);
     size_t po = 0, pp = 0;
     for (int s = 0; s < nsys; ++s) {
@@ -256,6 +257,7 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
         h.bar = (unsigned *)B->ctl + 2 * s;
         h.abort_flag = (int *)((unsigned *)B->ctl + 2 * s + 1);
         h.fault_skip_arrival = 0;
+        h.place = place ? place + (size_t)s * 1024 : nullptr;
         h.pairz = a->pairz ? (const int32_t *)a->pairz.get() : nullptr;
         h.Apk = a->packed ? (const double *)a->packed.get() : nullptr;
         h.relres = relres + s;

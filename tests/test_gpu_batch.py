@@ -112,6 +112,38 @@ def test_batch_graph_replay_and_cost_replan(G):
         assert float((s[3] - x0).norm()) <= 1e-8 * float(x0.norm())
 
 
+@pytest.mark.parametrize("share", [1, 2], ids=["cta_per_sm", "two_lanes"])
+def test_batch_groups_sit_on_distinct_sms(G, share):
+    """A system's CTA group never puts two of its CTAs on one SM: with one
+    CTA per SM trivially, with two lanes (sm_share = 2) because a CTA takes
+    its lane from its arrival order on its SM (one CTA of each lane per SM)
+    and a group stays within one lane.  rows_per_cta = 64 gives the
+    n = 10,002 systems the largest group a lane allows (one CTA per SM).  The
+    placement hook records each system's CTA ranks on every solve."""
+    systems, ref, keep = make_systems(G, [(5000, [1.0, 20.0], 2), (900, [0.1], 1), (12, [5.0], 1)])
+    nsys = len(systems)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    place = torch.full((nsys * 1024,), -1, dtype=torch.int32, device="cuda")
+    G.debug_record_placement(place)
+    try:
+        B = G.Batch(systems, G.options(sm_share=share), rows_per_cta=64)
+    finally:
+        G.debug_record_placement(None)
+    B.solve()
+    torch.cuda.synchronize()
+    pl = place.view(nsys, 1024).cpu().numpy()
+    sizes = []
+    for s in range(nsys):
+        row = pl[s]
+        g = int((row >= 0).sum())
+        assert 1 <= g <= sms
+        assert np.all(row[:g] >= 0) and np.all(row[:g] < 1024) and np.all(row[g:] == -1)
+        assert len(set(row[:g].tolist())) == g, s          # distinct SMs within the group
+        assert int(B.status[s]) == G.OK
+        sizes.append(g)
+    assert max(sizes) == sms                               # the n = 10,002 systems span every SM
+
+
 def test_batch_rejects(G):
     beam = W.beam(10)
     M, K = G.beam_mats(beam)
