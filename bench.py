@@ -995,7 +995,7 @@ def learned_form(G, torch, stream):
             "device_ms": {k: round(v[0], 3) for k, v in tot.items()},
             "updated_shifts": len(shifts) - 1,
             "learned_fallbacks": fallbacks,
-            "build_ms_median": {"exact_spai_qr": round(statistics.median(build_ms["exact"]), 4),
+            "build_ms_median": {"exact_spai_ne": round(statistics.median(build_ms["exact"]), 4),
                                 "learned_spai": round(lb, 4)},
             "learned_build_tflops_model": round(n * 1.06 * MLP_FLOP_PER_SAMPLE_FWD / (lb * 1e-3) / 1e12, 4),
             "speedup_learned_vs_exact": round(tot["exact"][0] / tot["learned"][0], 3),
