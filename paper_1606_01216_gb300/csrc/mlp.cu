@@ -97,7 +97,9 @@ __device__ __forceinline__ bool wait_mma(uint64_t *mbar, uint32_t &phase, int *e
     if (threadIdx.x == 0) {
         const uint32_t addr = tc::smem_u32(mbar);
         const long long t0 = gtime();
-        while (true) {
+        // bounded by the timer and, should the timer stall, by a round count
+        // (each round takes well over a nanosecond)
+        for (long long round = 0; round < kWaitNs; ++round) {
             asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                          "selp.u32 %0, 1, 0, p;\n}"
                          : "=r"(done)

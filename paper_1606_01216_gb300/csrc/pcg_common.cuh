@@ -32,11 +32,14 @@ __device__ bool grid_barrier(unsigned *bar, int *abort_flag, unsigned target,
         if (arrive) asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar) : "memory");
         int ok = 1;
         unsigned long long t0 = global_ns();
-        unsigned spins = 0;
+        // bounded by the timer and, should the timer stall, by a poll count
+        // (each poll is an L2 round trip, far longer than 16 ns)
+        const unsigned long long max_spins = (unsigned long long)(timeout_ns > 0 ? timeout_ns : 0) / 16 + 64;
+        unsigned long long spins = 0;
         while (ld_acquire(bar) < target) {
             if ((++spins & 63u) == 0) {
                 if (*(volatile int *)abort_flag) { ok = 0; break; }
-                if ((long long)(global_ns() - t0) > timeout_ns) {
+                if ((long long)(global_ns() - t0) > timeout_ns || spins > max_spins) {
                     atomicExch(abort_flag, 1);
                     ok = 0;
                     break;

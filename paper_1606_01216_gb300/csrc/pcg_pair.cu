@@ -818,14 +818,18 @@ AIRGA_CHECK_READER(pcg_pair)
 // ---------------------------------------------------------------------------
 namespace airga {
 namespace {
+// Sleeps until the global timer has advanced `ns`; the loop is also capped at
+// `ns` rounds (each round takes well over a nanosecond), so it ends even if
+// the timer were to stall.
 __global__ void stream_hold_kernel(long long ns) {
     if (threadIdx.x != 0) return;
     unsigned long long t0, t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    do {
+    for (long long round = 0; round < ns; ++round) {
         __nanosleep(1000);
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    } while ((long long)(t - t0) < ns);
+        if ((long long)(t - t0) >= ns) break;
+    }
 }
 }  // namespace
 }  // namespace airga
