@@ -652,6 +652,34 @@ int airga_probe_read_bw(int64_t bytes, int32_t passes, double *gbs, double *ms, 
  * device; outstanding handles stay valid. */
 int airga_trim(void);
 
+/* Call tracing, no counterpart in the paper.  While enabled, each traced
+ * call (matrix import, assemble_shifted, spmv, spai_build, spai_update,
+ * precond_apply, the pcg_solve family except the allocation-free one,
+ * true_residual, batch_solve, mlp_train, mlp_forward, mlp_spai) records a
+ * CUDA event on its stream before it enqueues work and another when it
+ * returns; the elapsed device time between them covers the work that call
+ * enqueued (and any work queued before it on the same stream that was still
+ * running).  Calls on a stream under graph capture are not traced.
+ *
+ * airga_trace_enable(capacity): capacity 1..2^24 turns tracing on and keeps
+ * at most that many unread records (later calls are counted as dropped);
+ * 0 turns it off and discards unread records.  Host-side state, shared by
+ * every thread of the process. */
+typedef struct {
+    const char *name;   /* the entry point's name (static storage) */
+    double ms;          /* device time between the call's two events */
+    void *stream;       /* the call's stream */
+} airga_trace_record;
+int airga_trace_enable(int32_t capacity);
+
+/* Move up to `max_records` of the oldest unread records into `out` (host
+ * array), oldest first; *count (host) receives how many.  Waits for each
+ * record's end event.  *dropped (host, may be NULL) receives the number of
+ * calls not recorded for lack of capacity since the previous read, and that
+ * count restarts at 0. */
+int airga_trace_read(airga_trace_record *out, int32_t max_records, int32_t *count,
+                     int64_t *dropped);
+
 #ifdef __cplusplus
 }
 #endif

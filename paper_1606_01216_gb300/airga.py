@@ -42,10 +42,15 @@ EXPORTS = (
     "airga_precond_is_banded", "airga_precond_factor_nnz", "airga_precond_factor_csr",
     "airga_precond_from_csr", "airga_probe_fp64_rate", "airga_debug_pool_used",
     "airga_debug_checked", "airga_debug_check_selftest", "airga_probe_read_bw",
-    "airga_debug_record_placement", "airga_stream_hold",
+    "airga_debug_record_placement", "airga_stream_hold", "airga_trace_enable", "airga_trace_read",
 )
 
 MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_NPARAM = 16, 64, 16, 6288
+
+
+class TraceRecord(C.Structure):
+    """airga_trace_record: one traced C-ABI call."""
+    _fields_ = [("name", C.c_char_p), ("ms", C.c_double), ("stream", C.c_void_p)]
 
 
 class Options(C.Structure):
@@ -161,6 +166,8 @@ def lib():
         "airga_debug_force_pcg_kernel": (C.c_int, [C.c_int]),
         "airga_debug_record_placement": (C.c_int, [vp]),
         "airga_stream_hold": (C.c_int, [i32, vp]),
+        "airga_trace_enable": (C.c_int, [i32]),
+        "airga_trace_read": (C.c_int, [C.POINTER(TraceRecord), i32, C.POINTER(i32), C.POINTER(i64)]),
         "airga_pcg_solve_noalloc": (C.c_int, [i64, vp, vp, vp, i32, C.POINTER(Options), vp, vp,
                                               vp, vp, vp, vp]),
         "airga_trim": (C.c_int, []),
@@ -604,6 +611,23 @@ def debug_record_placement(buf=None):
     device tensor with at least one entry per SM); None turns it off."""
     _check(lib().airga_debug_record_placement(_ptr(buf, torch.int32) if buf is not None else None),
            "debug_record_placement")
+
+
+def trace_enable(capacity: int = 4096):
+    """Turn call tracing on, keeping at most `capacity` unread records (0
+    turns it off and discards them)."""
+    _check(lib().airga_trace_enable(int(capacity)), "trace_enable")
+
+
+def trace_read(max_records: int = 4096):
+    """The oldest unread trace records (waits for their end events):
+    (list of dicts {name, ms, stream}, calls dropped for lack of capacity
+    since the previous read)."""
+    buf = (TraceRecord * max(1, int(max_records)))()
+    n, dropped = C.c_int32(), C.c_int64()
+    _check(lib().airga_trace_read(buf, int(max_records), C.byref(n), C.byref(dropped)), "trace_read")
+    return ([dict(name=buf[k].name.decode(), ms=buf[k].ms, stream=buf[k].stream or 0)
+             for k in range(n.value)], dropped.value)
 
 
 def stream_hold(microseconds: int, stream=None):

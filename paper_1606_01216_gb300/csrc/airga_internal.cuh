@@ -303,6 +303,22 @@ cudaError_t injected_launch_error();
 // call's CTA placement, or null
 int32_t *placement_buffer();
 
+// Call tracing (airga_trace_enable): declare one at the top of a traced
+// C-ABI call; it records an event on `stream` now and another when the call
+// returns, when tracing is on and the stream is not being captured.
+class TraceScope {
+  public:
+    TraceScope(const char *name, void *stream);
+    ~TraceScope();
+    TraceScope(const TraceScope &) = delete;
+    TraceScope &operator=(const TraceScope &) = delete;
+
+  private:
+    const char *name_;
+    void *stream_;
+    void *e0_;
+};
+
 // aligned16: A, the preconditioner band, b and x are 16-byte aligned (needed
 // by the node-pair kernel together with an even n)
 // share = 2 (lead) / 3 (partner): the solve takes half of each SM (plan

@@ -287,6 +287,7 @@ int airga_version(void) { return 100; }
 // ---------------------------------------------------------------------------
 int airga_mat_from_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *col,
                        const double *val, void *stream, airga_mat *out) {
+    TraceScope trace_("airga_mat_from_csr", stream);
     if (!out) return fail(AIRGA_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > (int64_t)INT32_MAX) return fail(AIRGA_E_INVALID_ARG, "n must be in [1, 2^31)");
@@ -324,6 +325,7 @@ int airga_mat_from_csr(int64_t n, int64_t nnz, const int64_t *rowptr, const int3
 }
 
 int airga_mat_from_band(int64_t n, const double *band, void *stream, airga_mat *out) {
+    TraceScope trace_("airga_mat_from_band", stream);
     if (!out) return fail(AIRGA_E_INVALID_ARG, "out is NULL");
     *out = nullptr;
     if (n < 1 || n > (int64_t)INT32_MAX || !band) return fail(AIRGA_E_INVALID_ARG, "bad band input");
@@ -363,6 +365,7 @@ void airga_mat_free(airga_mat A) { delete A; }
 // ---------------------------------------------------------------------------
 int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, double s,
                            void *stream, airga_mat *A_out) {
+    TraceScope trace_("airga_assemble_shifted", stream);
     if (!A_out) return fail(AIRGA_E_INVALID_ARG, "A_out is NULL");
     *A_out = nullptr;
     int st = check_any(M, "M");
@@ -403,6 +406,7 @@ int airga_assemble_shifted(airga_mat M, airga_mat K, double alpha, double beta, 
 }
 
 int airga_spmv(airga_mat A, const double *X, double *Y, int32_t m, void *stream) {
+    TraceScope trace_("airga_spmv", stream);
     int st = check_any(A, "A");
     if (st) return st;
     if (m < 0 || (m > 0 && (!X || !Y))) return fail(AIRGA_E_INVALID_ARG, "bad spmv operands");
@@ -414,6 +418,7 @@ int airga_spmv(airga_mat A, const double *X, double *Y, int32_t m, void *stream)
 
 int airga_spai_build(airga_mat A, airga_mat pattern, const airga_options *opt, void *stream,
                      airga_precond *P_out) {
+    TraceScope trace_("airga_spai_build", stream);
     if (!P_out) return fail(AIRGA_E_INVALID_ARG, "P_out is NULL");
     *P_out = nullptr;
     int st = check_any(A, "A");
@@ -459,6 +464,7 @@ int airga_spai_build(airga_mat A, airga_mat pattern, const airga_options *opt, v
 
 int airga_spai_update(airga_precond P_prev, airga_mat A_prev, airga_mat A_next,
                       const airga_options *opt, void *stream, airga_precond *P_out) {
+    TraceScope trace_("airga_spai_update", stream);
     if (!P_out) return fail(AIRGA_E_INVALID_ARG, "P_out is NULL");
     *P_out = nullptr;
     if (!P_prev || (P_prev->factors.empty() && P_prev->cfactors.empty()))
@@ -501,6 +507,7 @@ int airga_spai_update(airga_precond P_prev, airga_mat A_prev, airga_mat A_next,
 
 int airga_precond_apply(airga_precond P, const double *r, double *z, int32_t symmetrize,
                         void *stream) {
+    TraceScope trace_("airga_precond_apply", stream);
     if (!P || (P->factors.empty() && P->cfactors.empty()) || !r || !z)
         return fail(AIRGA_E_INVALID_ARG, "bad apply operands");
     cudaStream_t s = S(stream);
@@ -778,6 +785,7 @@ extern "C" {
 int airga_pcg_solve(airga_mat A, airga_precond P, const double *F, int32_t m,
                     const airga_options *opt, double *X, double *res_hist, int32_t *iters,
                     int32_t *status, double *true_relres, void *stream) {
+    TraceScope trace_("airga_pcg_solve", stream);
     if (!F) return fail(AIRGA_E_INVALID_ARG, "F is required");
     return pcg_solve_impl(A, P, F, nullptr, nullptr, 1.0, m, opt, X, res_hist, iters, status,
                           true_relres, stream);
@@ -787,6 +795,7 @@ int airga_pcg_solve_mv(airga_mat A, airga_precond P, airga_mat M, const double *
                        double rhs_scale, int32_t m, const airga_options *opt, double *X,
                        double *res_hist, int32_t *iters, int32_t *status, double *true_relres,
                        void *stream) {
+    TraceScope trace_("airga_pcg_solve_mv", stream);
     int st = check_any(M, "M");
     if (st) return st;
     if (!V) return fail(AIRGA_E_INVALID_ARG, "V is required");
@@ -797,6 +806,7 @@ int airga_pcg_solve_mv(airga_mat A, airga_precond P, airga_mat M, const double *
 
 int airga_true_residual(airga_mat A, const double *X, const double *F, int32_t m,
                         double *relres, void *stream) {
+    TraceScope trace_("airga_true_residual", stream);
     int st = check_any(A, "A");
     if (st) return st;
     if (m < 0 || (m > 0 && (!X || !F || !relres))) return fail(AIRGA_E_INVALID_ARG, "bad residual operands");

@@ -305,6 +305,7 @@ int airga_batch_create(int32_t nsys, const airga_mat *A, const airga_precond *P,
 }
 
 int airga_batch_solve(airga_batch B, void *stream) {
+    TraceScope trace_("airga_batch_solve", stream);
     if (!B) return fail(AIRGA_E_INVALID_ARG, "batch is NULL");
     cudaStream_t cs = (cudaStream_t)stream;
     AIRGA_CUDA(cudaMemsetAsync(B->ctl, 0, B->ctl_bytes, cs));

@@ -595,6 +595,7 @@ extern "C" int airga_pcg_solve_mixed(airga_mat A, airga_precond P, const double 
                                      const airga_options *opt, double *X, int32_t *outer_iters,
                                      int32_t *inner_iters, int32_t *status, double *true_relres,
                                      void *stream) {
+    TraceScope trace_("airga_pcg_solve_mixed", stream);
     int st = check_mat(A, "A");
     if (st) return st;
     if (m < 0) return fail(AIRGA_E_INVALID_ARG, "m must be >= 0");

@@ -1079,6 +1079,7 @@ int airga_mlp_features(airga_mat A, airga_precond P, double s, double alpha, dou
 }
 
 int airga_mlp_forward(airga_mlp net, const float *X, int64_t count, float *Y, void *stream) {
+    TraceScope trace_("airga_mlp_forward", stream);
     int st = check_net(net);
     if (st) return st;
     if (count < 0 || (count > 0 && (!X || !Y))) return fail(AIRGA_E_INVALID_ARG, "bad forward buffers");
@@ -1123,6 +1124,7 @@ int airga_mlp_grad(airga_mlp net, const float *X, const float *T, const uint8_t 
 int airga_mlp_train(airga_mlp net, const float *X, const float *T, const uint8_t *mask, int64_t count,
                     int32_t steps, const airga_mlp_train_options *opt, const int32_t *idx,
                     float *loss_hist, void *stream) {
+    TraceScope trace_("airga_mlp_train", stream);
     int st = check_net(net);
     if (st) return st;
     airga_mlp_train_options o;
@@ -1165,6 +1167,7 @@ int airga_mlp_train(airga_mlp net, const float *X, const float *T, const uint8_t
 
 int airga_mlp_spai(airga_mlp net, airga_mat A, double s, double alpha, double beta, void *stream,
                    airga_precond *P_out) {
+    TraceScope trace_("airga_mlp_spai", stream);
     if (!P_out) return fail(AIRGA_E_INVALID_ARG, "P_out is NULL");
     *P_out = nullptr;
     int st = check_net(net);

@@ -51,6 +51,23 @@ def test_host_only_calls(G):
     assert G.status_string(1234) == "unknown status"
 
 
+def test_trace_host_side(G):
+    """Tracing state is host-side: enabling, reading an empty trace and
+    turning it off need no GPU; bad arguments are rejected."""
+    G.trace_enable(8)
+    try:
+        recs, dropped = G.trace_read()
+        assert recs == [] and dropped == 0
+        with pytest.raises(G.AirgaError):
+            G.trace_enable(-1)
+        n = C.c_int32()
+        assert G.lib().airga_trace_read(None, -1, C.byref(n), None) == G.E_INVALID_ARG
+        assert G.lib().airga_trace_read(None, 4, C.byref(n), None) == G.E_INVALID_ARG
+        assert G.lib().airga_trace_read(None, 0, C.byref(n), None) == G.OK and n.value == 0
+    finally:
+        G.trace_enable(0)
+
+
 def test_argument_checks_need_no_gpu(G):
     L = G.lib()
     out = C.c_void_p()
