@@ -1072,7 +1072,8 @@ def e2e_arm(G, torch, beam, opts, args, parts):
     F copied from pinned host memory, X of every shift copied back.  As a
     production caller would, the step overlaps transfers with compute: K's
     values and F travel on a copy stream while M is imported, and each
-    shift's X returns on the copy stream while the next shift runs.  The
+    shift's X returns, on a copy stream of its compute stream, while the
+    other shifts run.  The
     shifts run on two compute streams split as in the device-timed step
     (`parts`).  The timed region covers every copy (it ends after a device
     synchronise)."""
@@ -1087,6 +1088,9 @@ def e2e_arm(G, torch, beam, opts, args, parts):
     stream = torch.cuda.current_stream()
     stream_b = torch.cuda.Stream()
     copy = torch.cuda.Stream()
+    # results return on one copy stream per compute stream: on a shared one the
+    # partner's copies would queue behind the lead's, which finishes last
+    copy_back = {id(stream): copy, id(stream_b): torch.cuda.Stream()}
 
     def one():
         dev = {k: host[k].to("cuda", non_blocking=True) for k in ("rp", "ci", "mv")}
@@ -1112,8 +1116,9 @@ def e2e_arm(G, torch, beam, opts, args, parts):
                     r = G.pcg_solve(A, P, dev["f"], opts[0] if st is stream else opts[1], stream=st)
                     done = torch.cuda.Event()
                     done.record(st)
-                copy.wait_event(done)
-                with torch.cuda.stream(copy):
+                back = copy_back[id(st)]
+                back.wait_event(done)
+                with torch.cuda.stream(back):
                     xs_host[i].copy_(r["X"], non_blocking=True)
                     info = torch.stack([r["iters"][0].double(), r["status"][0].double(),
                                         r["true_relres"][0]])
