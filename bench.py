@@ -44,8 +44,8 @@ SHIFTS = W.log_shifts(-1, 4, 8)
 TOL = 1e-10
 FP64_FMA_PER_CLK_SM = 2          # GB300 FP64 pipe (nominal; the bench measures it)
 # FP64 work the PCG kernel issues per row and iteration: 18 FMA = A's five
-# beam nonzeros + P_sym's seven + 3 dots + 3 axpys (the survey's 20-FMA model
-# counts A's two structural zeros too)
+# beam nonzeros + P_sym's seven + 3 dots + 3 axpys (the 20-FMA algorithmic
+# model counts the full band-7 of A, two of whose entries are structural zeros)
 PCG_FLOP_PER_ROW_ITER = 36
 PCG_FLOP_PER_ROW_ITER_MODEL = 40
 PCG_BYTES_PER_ROW_ITER = 160     # A 56 + P_sym 56 + x, r, p read+write 48
@@ -349,7 +349,7 @@ def gpu_arm(args, world, rank, local):
     # (sequential, every CG call on whole SMs: the kernel timed alone)
     opts_alone = G.options(tol=TOL, maxit=20000)
     detail = None if args.profile else method_arms(G, torch, stream, M, K, F, SHIFTS, opts_alone)
-    # the survey's solves/s counts PCG time only, SPAI reported beside it
+    # PCG-only solves/s: the PCG time alone, the SPAI build reported beside it
     pcg_step_ms = tot_ms / max(1, args.steps)
     pcg_only = {"solves_per_s": round(len(SHIFTS) / (pcg_step_ms * 1e-3), 3),
                 "pcg_ms_per_step": round(pcg_step_ms, 4)}
