@@ -23,9 +23,14 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
 // Bounded grid barrier.  Returns false (in every thread) if this CTA gave up.
 // `arrive` is false only under the test fault injection (a CTA that never
 // arrives, so every wait runs into its bound).
+// `grid_size` 1 (a group of one CTA; 0 = not stated): the CTA barrier alone
+// orders the CTA's writes before its own later reads, so the counter round
+// trip is skipped (unless the test fault withholds the arrival).
 __device__ bool grid_barrier(unsigned *bar, int *abort_flag, unsigned target,
-                             long long timeout_ns, int *s_flag, bool arrive = true) {
+                             long long timeout_ns, int *s_flag, bool arrive = true,
+                             int grid_size = 0) {
     __syncthreads();
+    if (grid_size == 1 && arrive) return true;
     if (threadIdx.x == 0) {
         // release-reduction: orders this CTA's writes (gathered by the CTA
         // barrier above) before the arrival, without a separate fence

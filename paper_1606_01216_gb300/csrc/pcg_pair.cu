@@ -365,7 +365,7 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
         }
         block_partials_tree<3>(v, red, a.partials, bar_no & 1, G, rank);
     }
-    if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+    if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag, true, G)) {
         status = AIRGA_E_TIMEOUT;
         goto finish;
     }
@@ -438,7 +438,7 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
                 else prefetch_pair(Pb, n, zlo + 2 * tid, kBand);
             }
             block_partials_tree<1>(vq, red, a.partials, bar_no & 1, G, rank);
-            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag, true, G)) {
                 status = AIRGA_E_TIMEOUT;
                 iters = k - 1;
                 goto finish;
@@ -515,7 +515,7 @@ __device__ void pair_body(const PcgArgs &a, int R, int G, int rank, double *smem
             block_partials_tree<2>(v2, red, a.partials, bar_no & 1, G, rank);
             const bool arrive = !(a.fault_skip_arrival && k == 1 && rank == 0);
             if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag,
-                              arrive)) {
+                              arrive, G)) {
                 status = AIRGA_E_TIMEOUT;
                 iters = k;
                 goto finish;
@@ -565,7 +565,7 @@ finish:
     if (a.relres && status != AIRGA_E_TIMEOUT) {
         // true residual ||b - A x|| / ||b|| of the final x, in FP64: the group
         // exchanges x through global memory (one barrier), each CTA sums its rows
-        if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) return;
+        if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag, true, G)) return;
         ++bar_no;
         double v[2] = {0.0, 0.0};
         for (int i = lo + tid; i < hi; i += nt) {
@@ -580,7 +580,7 @@ finish:
             v[1] = fma(bi, bi, v[1]);
         }
         block_partials_tree<2>(v, red, a.partials, bar_no & 1, G, rank);
-        if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) return;
+        if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag, true, G)) return;
         if (rank == 0 && tid < 32) {
             double t[2];
             warp0_totals<2>(a.partials, bar_no & 1, G, t);
