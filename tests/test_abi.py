@@ -51,6 +51,24 @@ def test_host_only_calls(G):
     assert G.status_string(1234) == "unknown status"
 
 
+def test_header_is_plain_c(tmp_path):
+    """include/airga.h compiles as strict C99 (no C++ or CUDA types leak in)."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "airga.h"\n'
+                   "int main(void) { airga_options o; airga_trace_record r; (void)o; (void)r;\n"
+                   "  return 0; }\n")
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", inc,
+                        "-c", str(src), "-o", str(tmp_path / "use_header.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_trace_host_side(G):
     """Tracing state is host-side: enabling, reading an empty trace and
     turning it off need no GPU; bad arguments are rejected."""
