@@ -66,9 +66,12 @@ PCG_DRAM_BYTES_PER_ROW_ITER_HALF = 10.21
 HOLD_US = 50                     # partner stream hold after the lead's SPAI (airga_stream_hold)
 SPAI_FLOP_PER_COLUMN_MODEL = 1250  # algorithmic SPAI work per column (band-7 QR + solve)
 # FP64 instructions per interior column of the normal-equation SPAI build
-# as the bench runs it (no per-column residuals): Gram band 28 FMA; L D L^T
-# 35 + 21 FMA, 21 MUL, 7 x 4 for the reciprocals; solves 42 FMA + 7 MUL
-SPAI_NE_FP64_INSTR_PER_COLUMN = 182
+# as the bench runs it on the beam (no per-column residuals; products with a
+# stored zero of the beam structure skipped): Gram band 15 FMA (17 on even,
+# 13 on odd columns); L D L^T 98 (35 + 21 FMA and 21 MUL less the 7 through
+# the zero corner of the Gram block, 7 x 4 for the reciprocals); solves 47
+# (42 FMA + 7 MUL less 2 through the corner)
+SPAI_NE_FP64_INSTR_PER_COLUMN = 160
 
 
 def spai_options(G):
@@ -373,7 +376,7 @@ def gpu_arm(args, world, rank, local):
                    "model": "1.25 kflop per column (Householder QR of the 12x7 block + solve, "
                             "full band); the kernel issues fewer (structural zeros skipped)"}}
     # the whole-SM kernel timed alone (the detail's sequential solves) and the
-    # step's FP64 issue: PCG 18 and SPAI 182 FP64 instructions per row
+    # step's FP64 issue: PCG 18 and SPAI 160 FP64 instructions per row
     kernel_alone = None
     if detail is not None:
         it_a = sum(r["iters"] for r in detail["rebuild"])
@@ -386,8 +389,9 @@ def gpu_arm(args, world, rank, local):
         len(SHIFTS) * n * SPAI_NE_FP64_INSTR_PER_COLUMN
     step_fp64 = {"fp64_instr_per_step": round(instr),
                  "frac": round(instr / (ms * 1e-3 * fp64_peak_tf * 1e12 / 2), 4),
-                 "note": "PCG 18 FP64 instructions per row and iteration + SPAI 182 per "
-                         "column, over the step time at the FP64 issue rate"}
+                 "note": "PCG 18 FP64 instructions per row and iteration + SPAI %d per "
+                         "column, over the step time at the FP64 issue rate"
+                         % SPAI_NE_FP64_INSTR_PER_COLUMN}
     forms = None
     # under --profile the forms run only when --forms names them
     if not args.no_forms and (not args.profile or args.forms is not None):

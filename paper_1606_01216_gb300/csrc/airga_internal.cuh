@@ -189,9 +189,11 @@ cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_
 // steps[j] = 1 (steps zeroed by the caller).  fb: n + 1 int32 of scratch.
 // want_colres false: the NE columns' colres entries are set to NaN instead
 // of forming the residual (the Householder columns still write theirs).
+// zA (device, may be null): A's beam-structure flag; when set the column
+// kernel skips the Gram block's zero corner.
 cudaError_t launch_spai_ne(int64_t n, const double *A, const double *A_old, double *F,
                            double *colres, bool want_colres, int32_t *rank_flag, int32_t *steps,
-                           double *U, int32_t *fb, cudaStream_t s);
+                           double *U, int32_t *fb, const int32_t *zA, cudaStream_t s);
 
 // ---------------------------------------------------------------------------
 // general sparse storage (csr_kernels.cu, spai_csr.cu, pcg_csr.cu)

@@ -209,7 +209,8 @@ static int spai_factor(airga_mat A, airga_mat A_old, const airga_options &o, cud
         int32_t *fb = (int32_t *)(U + 7 * (size_t)n);
         const cudaError_t e = launch_spai_ne(n, A->band->d, Aold, (*F)->d, (double *)out->col_res.get(),
                                              o.want_colres != 0, (int32_t *)out->rank_flag.get(),
-                                             (int32_t *)out->col_steps.get(), U, fb, s);
+                                             (int32_t *)out->col_steps.get(), U, fb,
+                                             (const int32_t *)A->pairz.get(), s);
         dev_free(tmp, s);
         if (e != cudaSuccess) return cuda_fail(e, "spai NE launch");
         return AIRGA_OK;

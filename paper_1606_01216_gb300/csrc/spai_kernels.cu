@@ -506,12 +506,47 @@ spai_mr_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
 // ---------------------------------------------------------------------------
 constexpr int kGramRows = 128;
 constexpr int kGramStage = kGramRows + 8;   // band rows i0-3 .. i0+kGramRows+4
+static_assert(kGramRows % 64 == 0, "parity-mapped warp pairs cover 64 columns");
 
-// U[d n + i] = (A^T A)(i, i + d), d = 0..6 (0 where i + d >= n), summed over
-// the rows k common to both columns in increasing k.  A CTA stages the band
-// rows its columns touch in shared memory (rows outside [0, n) as zeros).
+// Beam zero structure (checked at import, the pairz flag, on every row but
+// the last two): on an even row k the band entries at offsets -3 and +1 are
+// stored zeros, on an odd row those at +3 and -1.  P is the parity of row
+// k - t.
+template <int P>
+__device__ constexpr bool beam_zero(int t, int off) {
+    return (((P + t) & 1) == 0) ? (off == -3 || off == 1) : (off == 3 || off == -1);
+}
+
+// Column i of the Gram band: U[d n + i] = (A^T A)(i, i + d), d = 0..6, summed
+// over the rows k = i + t common to both columns in increasing k.  BEAM with
+// row parity P: the products with a stored-zero factor are skipped (each
+// would add an exact zero), 18 FMA instead of 28.
+template <bool BEAM, int P>
+__device__ __forceinline__ void gram_column(int64_t n, int64_t i, int li,
+                                            const double (&sb)[kBand][kGramStage],
+                                            double *__restrict__ U) {
+#pragma unroll
+    for (int d = 0; d < kBand; ++d) {
+        double acc = 0.0;
+#pragma unroll
+        for (int t = d - 3; t <= 3; ++t) {                 // k = i + t
+            if (BEAM && (beam_zero<P>(t, -t) || beam_zero<P>(t, d - t))) continue;
+            acc = fma(sb[3 - t][li + t], sb[d + 3 - t][li + t], acc);
+        }
+        if (AIRGA_CK((int64_t)d * n + i, 0, 7 * n, 507))
+            U[(int64_t)d * n + i] = i + d < n ? acc : 0.0;
+    }
+}
+
+// U[d n + i] = (A^T A)(i, i + d), d = 0..6 (0 where i + d >= n).  A CTA
+// stages the band rows its columns touch in shared memory (rows outside
+// [0, n) as zeros).  zA (device, may be null): A's beam-structure flag; with
+// it set the warps are parity-mapped (a warp pair covers 64 consecutive
+// columns, the even warp the even ones) so that each warp skips the same
+// zero products.
 __global__ void __launch_bounds__(kGramRows)
-gram_band_kernel(int64_t n, const double *__restrict__ A, double *__restrict__ U) {
+gram_band_kernel(int64_t n, const double *__restrict__ A, double *__restrict__ U,
+                 const int32_t *__restrict__ zA) {
     __shared__ double sb[kBand][kGramStage];
     const int64_t i0 = (int64_t)blockIdx.x * kGramRows;
     const int64_t k0 = i0 - 3;                             // band row of stage slot 0
@@ -521,18 +556,20 @@ gram_band_kernel(int64_t n, const double *__restrict__ A, double *__restrict__ U
         sb[d][q] = (k >= 0 && k < n) ? __ldg(A + (int64_t)d * n + k) : 0.0;
     }
     __syncthreads();
-    const int64_t i = i0 + threadIdx.x;
-    if (i >= n) return;
     // A(k, c) = band[(c - k + 3) n + k] = sb[c - k + 3][k - k0]
-    const int li = (int)(i - k0);                          // stage slot of row i
-#pragma unroll
-    for (int d = 0; d < kBand; ++d) {
-        double acc = 0.0;
-#pragma unroll
-        for (int t = d - 3; t <= 3; ++t)                   // k = i + t
-            acc = fma(sb[3 - t][li + t], sb[d + 3 - t][li + t], acc);
-        if (AIRGA_CK((int64_t)d * n + i, 0, 7 * n, 507))
-            U[(int64_t)d * n + i] = i + d < n ? acc : 0.0;
+    if (zA && *zA) {
+        const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+        const int par = w & 1;
+        const int64_t i = i0 + 64 * (w >> 1) + 2 * l + par;
+        if (i >= n) return;
+        const int li = (int)(i - k0);
+        if (i + 3 >= n - 2) gram_column<false, 0>(n, i, li, sb, U);   // touches the last rows
+        else if (par == 0) gram_column<true, 0>(n, i, li, sb, U);
+        else gram_column<true, 1>(n, i, li, sb, U);
+    } else {
+        const int64_t i = i0 + threadIdx.x;
+        if (i >= n) return;
+        gram_column<false, 0>(n, i, (int)(i - k0), sb, U);
     }
 }
 
@@ -554,13 +591,20 @@ __device__ __forceinline__ double bhat(const double *__restrict__ Aold, int64_t 
     return AIRGA_CK(at, 0, 7 * n, 509) ? __ldg(Aold + at) : 0.0;
 }
 
-template <int UPD>
-__global__ void __launch_bounds__(kThreadsSpai)
-spai_ne_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
-               const double *__restrict__ U, double *__restrict__ F, double *__restrict__ colres,
-               int want_colres, int32_t *__restrict__ fb_count, int32_t *__restrict__ fb_list) {
-    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (j >= n) return;
+// BEAM: A has the beam's zero structure (checked at import on every row but
+// the last two: offsets -3 and +1 vanish on even rows, +3 and -1 on odd
+// rows), so the Gram block's corner G(j-3, j+3) = A(j, j-3) A(j, j+3) is
+// exactly zero wherever it lies inside the matrix (j + 3 < n, so row j is
+// checked; one factor is a stored zero) and the L D L^T terms through it are
+// skipped: L(6, 0) = 0 exactly, and the skipped products would each add a
+// zero.
+template <int UPD, bool BEAM>
+__device__ __forceinline__ void ne_column(int64_t n, int64_t j, const double *__restrict__ A,
+                                          const double *__restrict__ Aold,
+                                          const double *__restrict__ U, double *__restrict__ F,
+                                          double *__restrict__ colres, int want_colres,
+                                          int32_t *__restrict__ fb_count,
+                                          int32_t *__restrict__ fb_list) {
     bool in[7];
 #pragma unroll
     for (int c = 0; c < 7; ++c) in[c] = j - 3 + c >= 0 && j - 3 + c < n;
@@ -595,9 +639,15 @@ spai_ne_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
         double w[7];
 #pragma unroll
         for (int k = 0; k < i; ++k) {
+            if (BEAM && i == 6 && k == 0) {               // the zero corner
+                w[0] = 0.0;
+                L[6][0] = 0.0;
+                continue;
+            }
             double s = (in[i] && in[k]) ? __ldg(U + (int64_t)(i - k) * n + (j - 3 + k)) : 0.0;
 #pragma unroll
-            for (int p = 0; p < k; ++p) s = fma(-w[p], L[k][p], s);
+            for (int p = 0; p < k; ++p)
+                if (!(BEAM && i == 6 && p == 0)) s = fma(-w[p], L[k][p], s);
             w[k] = s;
             L[i][k] = s * rinv[k];
         }
@@ -607,7 +657,8 @@ spai_ne_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
             dmax = db > dmax ? db : dmax;
         }
 #pragma unroll
-        for (int p = 0; p < i; ++p) d = fma(-w[p], L[i][p], d);
+        for (int p = 0; p < i; ++p)
+            if (!(BEAM && i == 6 && p == 0)) d = fma(-w[p], L[i][p], d);
         if (in[i]) {
             const unsigned long long pb = lean::bits_of(d);
             pos = pos && (pb >> 63) == 0ull && pb != 0ull;
@@ -627,7 +678,8 @@ spai_ne_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
     for (int i = 0; i < 7; ++i) {
         double s = g[i];
 #pragma unroll
-        for (int k = 0; k < i; ++k) s = fma(-L[i][k], y[k], s);
+        for (int k = 0; k < i; ++k)
+            if (!(BEAM && i == 6 && k == 0)) s = fma(-L[i][k], y[k], s);
         y[i] = s;
     }
 #pragma unroll
@@ -635,7 +687,8 @@ spai_ne_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
         const int i = 6 - ii;
         double s = y[i] * rinv[i];
 #pragma unroll
-        for (int k = i + 1; k < 7; ++k) s = fma(-L[k][i], m[k], s);
+        for (int k = i + 1; k < 7; ++k)
+            if (!(BEAM && k == 6 && i == 0)) s = fma(-L[k][i], m[k], s);
         m[i] = s;
     }
     if (colres && !want_colres) {
@@ -654,6 +707,21 @@ spai_ne_kernel(int64_t n, const double *__restrict__ A, const double *__restrict
         colres[j] = rr * lean::rsqrt1(rr);
     }
     store_column<3>(n, j, m, F);
+}
+
+// zA (device, may be null): A's beam-structure flag
+template <int UPD>
+__global__ void __launch_bounds__(kThreadsSpai)
+spai_ne_kernel(int64_t n, const double *__restrict__ A, const double *__restrict__ Aold,
+               const double *__restrict__ U, double *__restrict__ F, double *__restrict__ colres,
+               int want_colres, int32_t *__restrict__ fb_count, int32_t *__restrict__ fb_list,
+               const int32_t *__restrict__ zA) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    if (zA && *zA)
+        ne_column<UPD, true>(n, j, A, Aold, U, F, colres, want_colres, fb_count, fb_list);
+    else
+        ne_column<UPD, false>(n, j, A, Aold, U, F, colres, want_colres, fb_count, fb_list);
 }
 
 // The columns the normal-equation kernel left to the Householder solve (a
@@ -752,21 +820,21 @@ cudaError_t launch_spai_mr(int64_t n, int hbw, const double *A, const double *A_
 
 cudaError_t launch_spai_ne(int64_t n, const double *A, const double *A_old, double *F,
                            double *colres, bool want_colres, int32_t *rank_flag, int32_t *steps,
-                           double *U, int32_t *fb, cudaStream_t s) {
+                           double *U, int32_t *fb, const int32_t *zA, cudaStream_t s) {
     const int want = want_colres ? 1 : 0;
     const cudaError_t fe = injected_launch_error();   // host-side test fault only
     if (fe != cudaSuccess) return fe;
     const int64_t gb = (n + kGramRows - 1) / kGramRows;
-    gram_band_kernel<<<(unsigned)gb, kGramRows, 0, s>>>(n, A, U);
+    gram_band_kernel<<<(unsigned)gb, kGramRows, 0, s>>>(n, A, U, zA);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     e = cudaMemsetAsync(fb, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const int64_t blocks = (n + kThreadsSpai - 1) / kThreadsSpai;
     if (A_old)
-        spai_ne_kernel<1><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, A_old, U, F, colres, want, fb, fb + 1);
+        spai_ne_kernel<1><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, A_old, U, F, colres, want, fb, fb + 1, zA);
     else
-        spai_ne_kernel<0><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, nullptr, U, F, colres, want, fb, fb + 1);
+        spai_ne_kernel<0><<<(unsigned)blocks, kThreadsSpai, 0, s>>>(n, A, nullptr, U, F, colres, want, fb, fb + 1, zA);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     // the Householder pass over the listed columns: one resident wave
