@@ -186,19 +186,25 @@ class SparseCSR:
     meta: dict = field(default_factory=dict)
 
 
-def _coo_to_csr(n, rows, cols, vals):
-    """Sorted CSR with duplicates summed (input assembly, no method arithmetic)."""
-    order = np.lexsort((cols, rows))
-    r, c, v = rows[order], cols[order], vals[order]
-    key = r.astype(np.int64) * n + c
+def _coo_to_csr(n, rows, cols, *vals):
+    """Sorted CSR with duplicates summed (input assembly, no method arithmetic),
+    one value array per matrix on the same (rows, cols) list: returns rowptr,
+    col and the summed values of each.  Entries are ordered by (row, col),
+    stably, and duplicates are summed in their input order."""
+    key = rows.astype(np.int64) * n + cols
+    order = np.argsort(key, kind="stable")
+    key = key[order]
     first = np.ones(key.size, dtype=bool)
     first[1:] = key[1:] != key[:-1]
     idx = np.cumsum(first) - 1
-    val = np.zeros(int(first.sum()))
-    np.add.at(val, idx, v)
+    nu = int(idx[-1]) + 1 if idx.size else 0
+    r = rows[order][first]
     rowptr = np.zeros(n + 1, dtype=np.int64)
-    np.cumsum(np.bincount(r[first], minlength=n), out=rowptr[1:])
-    return rowptr, c[first].astype(np.int32), val
+    np.cumsum(np.bincount(r, minlength=n), out=rowptr[1:])
+    col = cols[order][first].astype(np.int32)
+    # bincount adds the weights in index order, as a sequential sum would
+    summed = [np.bincount(idx, weights=v[order], minlength=nu) for v in vals]
+    return (rowptr, col, *summed)
 
 
 def membrane(nx: int, ny: int, seed: int = 0, lumped_mass: bool = False,
@@ -219,25 +225,24 @@ def membrane(nx: int, ny: int, seed: int = 0, lumped_mass: bool = False,
     # grid nodes (i, j), i = 0..nx along x, j = 0..ny; nodes with i = 0 clamped
     free = np.arange(nx * (ny + 1))
     perm = rng.permutation(free.size) if permute else free
-    def dof(i, j):
-        return perm[(i - 1) * (ny + 1) + j] if i > 0 else -1
     E = rng.uniform(0.5, 2.0, (nx, ny))
     rho = rng.uniform(0.5, 2.0, (nx, ny))
-    rows, cols, kv, mv = [], [], [], []
-    for ex in range(nx):
-        for ey in range(ny):
-            nodes = [dof(ex, ey), dof(ex + 1, ey), dof(ex + 1, ey + 1), dof(ex, ey + 1)]
-            for a in range(4):
-                for b in range(4):
-                    if nodes[a] < 0 or nodes[b] < 0:
-                        continue
-                    rows.append(nodes[a]); cols.append(nodes[b])
-                    kv.append(E[ex, ey] * ke[a, b]); mv.append(rho[ex, ey] * me[a, b])
+    # element (ex, ey) has nodes (ex, ey), (ex+1, ey), (ex+1, ey+1), (ex, ey+1);
+    # entries in element order, then a, then b (the order duplicates are summed in)
+    ex, ey = np.meshgrid(np.arange(nx), np.arange(ny), indexing="ij")
+    ni = np.stack([ex, ex + 1, ex + 1, ex], axis=-1)          # (nx, ny, 4) node i
+    nj = np.stack([ey, ey, ey + 1, ey + 1], axis=-1)
+    nodes = np.where(ni > 0, perm[np.maximum(ni - 1, 0) * (ny + 1) + nj], -1)
+    ra = np.broadcast_to(nodes[:, :, :, None], (nx, ny, 4, 4))
+    cb = np.broadcast_to(nodes[:, :, None, :], (nx, ny, 4, 4))
+    keep = (ra >= 0) & (cb >= 0)
+    rows = ra[keep].astype(np.int64)
+    cols = cb[keep].astype(np.int64)
+    kv = (E[:, :, None, None] * ke[None, None])[keep]
+    mv = (rho[:, :, None, None] * me[None, None])[keep]
     n = free.size
-    rows = np.array(rows, dtype=np.int64)
-    cols = np.array(cols, dtype=np.int64)
-    krp, kci, kva = _coo_to_csr(n, rows, cols, np.array(kv))
-    mrp, mci, mva = _coo_to_csr(n, rows, cols, np.array(mv))
+    krp, kci, kva, mva = _coo_to_csr(n, rows, cols, kv, mv)
+    mrp, mci = krp, kci
     if lumped_mass:
         diag = np.zeros(n)
         np.add.at(diag, np.repeat(np.arange(n), np.diff(mrp)), mva)

@@ -123,3 +123,52 @@ def test_membrane_element_sums():
     # the clamp-side column keeps nodes 1 and 2 of each element: 12/36 of it
     expected = rho[1:].sum() + rho[0].sum() * 12.0 / 36.0
     assert abs(w.m_val.sum() - expected) <= 1e-13 * expected
+
+
+def _membrane_by_loops(nx, ny, seed, lumped_mass=False, permute=True):
+    """The membrane's assembly written element by element with dense
+    accumulation, as a reference for the vectorised generator (small sizes)."""
+    rng = np.random.default_rng(seed)
+    ke = np.array([[4, -1, -2, -1], [-1, 4, -1, -2], [-2, -1, 4, -1], [-1, -2, -1, 4]]) / 6.0
+    me = np.array([[4, 2, 1, 2], [2, 4, 2, 1], [1, 2, 4, 2], [2, 1, 2, 4]]) / 36.0
+    n = nx * (ny + 1)
+    perm = rng.permutation(n) if permute else np.arange(n)
+    E = rng.uniform(0.5, 2.0, (nx, ny))
+    rho = rng.uniform(0.5, 2.0, (nx, ny))
+    K = np.zeros((n, n))
+    M = np.zeros((n, n))
+    present = np.zeros((n, n), dtype=bool)
+    for ex in range(nx):
+        for ey in range(ny):
+            corners = [(ex, ey), (ex + 1, ey), (ex + 1, ey + 1), (ex, ey + 1)]
+            nodes = [perm[(i - 1) * (ny + 1) + j] if i > 0 else -1 for i, j in corners]
+            for a in range(4):
+                for b in range(4):
+                    if nodes[a] >= 0 and nodes[b] >= 0:
+                        K[nodes[a], nodes[b]] += E[ex, ey] * ke[a, b]
+                        M[nodes[a], nodes[b]] += rho[ex, ey] * me[a, b]
+                        present[nodes[a], nodes[b]] = True
+    if lumped_mass:
+        M = np.diag(M.sum(axis=1))
+    return K, M, present
+
+
+@pytest.mark.parametrize("args", [(3, 2, 0, False, True), (7, 5, 4, False, True),
+                                  (6, 4, 9, True, True), (5, 6, 2, False, False)])
+def test_membrane_matches_element_loop(args):
+    nx, ny, seed, lumped, permute = args
+    w = W.membrane(nx, ny, seed=seed, lumped_mass=lumped, permute=permute)
+    K, M, present = _membrane_by_loops(nx, ny, seed, lumped, permute)
+    for rowptr, col, val, ref, pat in ((w.k_rowptr, w.k_col, w.k_val, K, present),
+                                       (w.m_rowptr, w.m_col, w.m_val, M, np.diag(np.diag(M)) != 0
+                                        if lumped else present)):
+        rows = np.repeat(np.arange(w.n), np.diff(rowptr))
+        got = np.zeros_like(ref)
+        got[rows, col] = val
+        assert np.allclose(got, ref, rtol=1e-14, atol=1e-15)
+        stored = np.zeros_like(pat)
+        stored[rows, col] = True
+        assert np.array_equal(stored, pat)                      # the pattern, explicit zeros kept
+        for r in range(w.n):                                     # sorted, no duplicates
+            c = col[rowptr[r]:rowptr[r + 1]]
+            assert np.all(np.diff(c) > 0)
