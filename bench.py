@@ -398,7 +398,7 @@ def gpu_arm(args, world, rank, local):
         del M, K
         makers = {"c1": c1_form, "c2": c2_form, "precision": precision_form,
                   "batching": batching_form, "learned": learned_form,
-                  "inner_loop": inner_loop_form}
+                  "inner_loop": inner_loop_form, "csr": csr_form}
         names = args.forms if args.forms is not None else DEFAULT_FORMS
         forms = {k: makers[k](G, torch, stream) for k in names.split(",") if k}
 
@@ -832,7 +832,7 @@ def batching_form(G, torch, stream):
 MLP_FLOP_PER_SAMPLE_FWD = 2 * (16 * 64 + 64 * 64 + 64 * 16)   # 12288 (MACs x 2)
 LEARNED_TRAIN_STEPS = 30_000     # --learned-train-steps (shorter only for profiling runs)
 BATCH_BEAMS = 32                 # --batch-beams (fewer only for profiling runs)
-DEFAULT_FORMS = "c1,c2,precision,batching,learned,inner_loop"
+DEFAULT_FORMS = "c1,c2,precision,batching,learned,inner_loop,csr"
 
 
 def learned_form(G, torch, stream):
@@ -1013,6 +1013,84 @@ def learned_form(G, torch, stream):
                      "break_even_sweeps": (round(train_ms / (tot["exact"][0] - tot["learned"][0]), 1)
                                            if tot["exact"][0] > tot["learned"][0] else None),
                      "sweep": "the 16 evaluation shifts of the n = 1e6 beam"}}
+
+
+# general sparse PCG (pcg_csr_kernel) per row and iteration on a 9-point
+# matrix: A and P_sym entries (value 8 B + column 4 B, 9 each) and the
+# vectors r, z, q, p (twice) and x through L2; 9 + 9 FMA + 3 dots + 3 axpys
+CSR_BYTES_PER_ROW_ITER_9PT = (9 + 9) * 12 + 72
+CSR_FLOP_PER_ROW_ITER_9PT = 2 * (9 + 9 + 6)
+
+
+def csr_form(G, torch, stream):
+    """General sparse workload (the CSR path of the boundary, matrices kept
+    as CSR): a 700 x 700 membrane of bilinear quadrilaterals (n = 490,700,
+    9-point rows, free nodes renumbered by a seeded permutation so that no
+    band exists; seed 20), shifts logspace(-1, 2, 4), right-hand side N(0,1)
+    (seed 21); SPAI on A's pattern (Householder per column, general-pattern
+    kernel), PCG to 1e-10.  Per shift: SPAI and PCG device time, CG
+    iterations; PCG solves/s, time per iteration, and the model bytes and
+    flops per row and iteration against the measured L2 read bandwidth and
+    the FP64 rate."""
+    w = W.membrane(700, 700, seed=20)
+    n = w.n
+
+    def dev(x, dt):
+        return torch.from_numpy(np.ascontiguousarray(x)).to(dtype=dt).cuda()
+
+    M = G.mat_from_csr(n, dev(w.m_rowptr, torch.int64), dev(w.m_col, torch.int32),
+                       dev(w.m_val, torch.float64))
+    K = G.mat_from_csr(n, dev(w.k_rowptr, torch.int64), dev(w.k_col, torch.int32),
+                       dev(w.k_val, torch.float64))
+    F = dev(np.random.default_rng(21).standard_normal(n), torch.float64)
+    shifts = W.log_shifts(-1, 2, 4)
+    opts = G.options(tol=TOL, maxit=20000)
+    rows = []
+    for rep in range(2):                       # the first pass warms the kernels and pool
+        rows = []
+        for sh in shifts:
+            A = G.assemble_shifted(M, K, W.ALPHA, W.BETA, float(sh))
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e2 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P = G.spai_build(A)
+            e1.record(stream)
+            r = G.pcg_solve(A, P, F, opts)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            rows.append({"s": float(sh), "spai_ms": round(e0.elapsed_time(e1), 4),
+                         "pcg_ms": round(e1.elapsed_time(e2), 4), "iters": int(r["iters"][0]),
+                         "status": int(r["status"][0]),
+                         "true_relres": float(r["true_relres"][0])})
+    pcg_ms = sum(x["pcg_ms"] for x in rows)
+    its = sum(x["iters"] for x in rows)
+    ok = sum(1 for x in rows if x["status"] == G.OK and x["true_relres"] <= 2 * TOL)
+    bw = read_bw(G)
+    pk = peaks()
+    tf = fp64_peak(G, pk["sm_max_mhz"])["tflops"]
+    gbs = its * n * CSR_BYTES_PER_ROW_ITER_9PT / (pcg_ms * 1e-3) / 1e9
+    tflops = its * n * CSR_FLOP_PER_ROW_ITER_9PT / (pcg_ms * 1e-3) / 1e12
+    nnz_k = int(w.k_rowptr[-1])
+    return {"workload": "membrane 700 x 700 bilinear quads (n = %d, %d stored entries per "
+                        "matrix, 9-point rows, random node numbering, seed 20), shifts "
+                        "logspace(-1,2,4), RHS N(0,1) seed 21; SPAI (Householder, A's pattern), "
+                        "PCG to 1e-10, matrices kept as CSR" % (n, nnz_k),
+            "per_shift": rows, "converged": ok,
+            "pcg_solves_per_s": round(len(rows) / (pcg_ms * 1e-3), 2),
+            "precond_plus_cg_ms": round(sum(x["spai_ms"] + x["pcg_ms"] for x in rows), 3),
+            "us_per_iteration": round(pcg_ms * 1e3 / max(1, its), 2),
+            "model": {"bytes_per_row_iter": CSR_BYTES_PER_ROW_ITER_9PT,
+                      "flop_per_row_iter": CSR_FLOP_PER_ROW_ITER_9PT,
+                      "achieved_gbs": round(gbs, 1),
+                      "frac_of_l2_read": round(gbs / bw["l2_read_gbs"], 4),
+                      "frac_of_dram_read": round(gbs / bw["dram_read_gbs"], 4),
+                      "achieved_tflops": round(tflops, 4),
+                      "frac_fp64_peak": round(tflops / tf, 4),
+                      "note": "the 106 MB of A and P_sym entries stay mostly in L2; three grid "
+                              "barriers per iteration"},
+            "read_bw": bw}
 
 
 def inner_loop_form(G, torch, stream):
