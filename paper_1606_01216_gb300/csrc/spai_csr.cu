@@ -288,15 +288,19 @@ spai_csr_kernel(SpaiCsrArgs a, int max_j) {
                     const double nx = sqrt(nx2);
                     const double xk = ak[k];
                     const double sg = xk >= 0.0 ? 1.0 : -1.0;
-                    double vv = 0.0;
 #pragma unroll
                     for (int q = 0; q < R; ++q) {
                         const int r = lane + 32 * q;
                         if (r == k) x[q] += sg * nx;     // x now holds v
-                        vv = fma(x[q], x[q], vv);
                     }
-                    vv = wsum(vv);
+                    // ||v||^2 = ||x||^2 - x_k^2 + (x_k + sg ||x||)^2 = 2 ||x|| (||x|| + |x_k|):
+                    // no second warp reduction.  Each warp-wide FP64 instruction holds a
+                    // sub-partition's FP64 pipe for ~64 cycles whatever the active lanes,
+                    // so the reductions and divisions, not the FMAs, set this kernel's
+                    // time: one reciprocal per reflector instead of a division per column.
+                    const double vv = 2.0 * nx * (nx + fabs(xk));
                     if (vv == 0.0) continue;             // zero column: R_kk = 0, caught below
+                    const double tau = 2.0 / vv;
                     for (int t = k; t <= nj; ++t) {      // t == nj: the right-hand side
                         double *col = t < nj ? Ah + t * kLd : bv;
                         double sdot = 0.0;
@@ -305,7 +309,7 @@ spai_csr_kernel(SpaiCsrArgs a, int max_j) {
                             const int r = lane + 32 * q;
                             if (r >= k && r < ni) sdot = fma(x[q], col[r], sdot);
                         }
-                        sdot = 2.0 * wsum(sdot) / vv;
+                        sdot = wsum(sdot) * tau;
 #pragma unroll
                         for (int q = 0; q < R; ++q) {
                             const int r = lane + 32 * q;
