@@ -219,7 +219,7 @@ spai_csr_kernel(SpaiCsrArgs a, int max_j) {
     double *Ah = reinterpret_cast<double *>(wbase);
     double *bv = Ah + (size_t)max_j * kLd;
     double *xs = bv + kLd;                       // solution / MR iterate m
-    double *dv = xs + kSpaiMaxJ;                 // MR direction
+    double *dv = xs + kSpaiMaxJ;                 // MR direction; QR: 1 / R_kk
     double *bout = dv + kSpaiMaxJ;               // b at rows J_c outside I_j
     int32_t *Irow = reinterpret_cast<int32_t *>(bout + kSpaiMaxJ);
     int32_t *Jcol = Irow + kLd;
@@ -328,11 +328,17 @@ spai_csr_kernel(SpaiCsrArgs a, int max_j) {
             if (rank_bad) {
                 if (lane == 0) atomicOr(a.flag, 1);
                 if (lane < nj) xs[lane] = 0.0;
-            } else if (lane == 0) {
-                for (int k = nj - 1; k >= 0; --k) {      // R x = (Q^T b)(0:nj)
-                    double s = bv[k];
-                    for (int t = k + 1; t < nj; ++t) s = fma(-Ah[t * kLd + k], xs[t], s);
-                    xs[k] = s / Ah[k * kLd + k];
+            } else {
+                // the reciprocals of R's diagonal in one warp-wide division (lane k
+                // takes R_kk), then the back substitution R x = (Q^T b)(0:nj) by lane 0
+                if (lane < nj) dv[lane] = 1.0 / Ah[lane * kLd + lane];
+                __syncwarp();
+                if (lane == 0) {
+                    for (int k = nj - 1; k >= 0; --k) {
+                        double s = bv[k];
+                        for (int t = k + 1; t < nj; ++t) s = fma(-Ah[t * kLd + k], xs[t], s);
+                        xs[k] = s * dv[k];
+                    }
                 }
             }
             __syncwarp();
