@@ -61,7 +61,7 @@ PCG_L2_BYTES_PER_ROW_ITER = 72
 # DRAM bytes per row and iteration of the half-SM kernel (pcg_pair_kernel<1, 2>)
 # from one ncu capture of the s = 0.1 launch on this workload, launched as a
 # lead (1297 MB read + 237 MB written over 229 x 1e6 row-iterations; x and
-# z/q travel through L2; another box's capture read 10.2 B)
+# z/q travel through L2; a capture on another GB300 read 10.2 B)
 PCG_DRAM_BYTES_PER_ROW_ITER_HALF = 6.70
 HOLD_US = 50                     # partner stream hold after the lead's SPAI (airga_stream_hold)
 SPAI_FLOP_PER_COLUMN_MODEL = 1250  # algorithmic SPAI work per column (band-7 QR + solve)
