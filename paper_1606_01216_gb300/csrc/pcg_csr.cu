@@ -6,15 +6,15 @@
 // One cooperative launch per right-hand side; thread t of the grid owns rows
 // t, t + T, t + 2T, ... for the whole solve.  A CSR row may reach any other
 // row, so vectors are exchanged through global memory (L2) at grid barriers:
+//   B0  after p = z + beta p                -> p visible to all
 //   B1  after q = A p and (p, q)            -> alpha
 //   B2  after x += alpha p, r -= alpha q    -> ||r||, r visible to all
 //       [one barrier per further factor of an update chain]
 //   B3  after z = M r and (r, z)            -> beta, z visible to all
-// p is never exchanged: q_i = sum_c A(i,c) (z_c + beta p_c) is formed from
-// z and the previous p directly, every CTA evaluating p_c with the same
-// instruction as its owner, so the result equals A applied to the stored p.
-// The previous and the new p live in two buffers (iteration parity), so no
-// CTA overwrites a p another CTA still reads.
+// (Forming p_c = z_c + beta p_c inside q's gather instead of exchanging p
+// saves B0 but doubles the gathers and adds an FMA per entry; with two CTAs
+// per SM the barrier is the cheaper of the two.)  The previous and the new p
+// live in two buffers (iteration parity).
 #include <cstring>
 
 #include "csr_common.cuh"
@@ -158,7 +158,15 @@ __global__ void __launch_bounds__(kThreads) pcg_csr_kernel(CsrPcgArgs a) {
         for (int k = 1; k <= a.maxit; ++k) {
             double *pc = (k & 1) ? a.p[1] : a.p[0];
             const double *pp = (k & 1) ? a.p[0] : a.p[1];
-            // ---- q = A p, p = z + beta p_prev formed per entry ----
+            // ---- p = z + beta p_prev on own rows, exchanged at a barrier ----
+            for (int64_t i = g0; i < n; i += gs) pc[i] = k == 1 ? a.z[i] : fma(beta, pp[i], a.z[i]);
+            if (!grid_barrier(a.bar, a.abort_flag, (bar_no + 1) * (unsigned)G, tmo, &s_flag)) {
+                status = AIRGA_E_TIMEOUT;
+                iters = k - 1;
+                goto finish;
+            }
+            ++bar_no;
+            // ---- q = A p, (p, q) ----
             double vq[1] = {0.0};
             for (int64_t i = g0; i < n; i += gs) {
                 int64_t rb, re;
@@ -167,11 +175,9 @@ __global__ void __launch_bounds__(kThreads) pcg_csr_kernel(CsrPcgArgs a) {
                 for (int64_t e = rb; e < re; ++e) {
                     const int64_t c = rv_col(a.A, e);
                     if (c < 0) continue;
-                    const double pcv = k == 1 ? __ldcg(a.z + c) : fma(beta, __ldcg(pp + c), __ldcg(a.z + c));
-                    acc = fma(rv_val(a.A, e), pcv, acc);
+                    acc = fma(rv_val(a.A, e), __ldcg(pc + c), acc);
                 }
-                const double pi = k == 1 ? a.z[i] : fma(beta, pp[i], a.z[i]);
-                pc[i] = pi;
+                const double pi = pc[i];
                 a.q[i] = acc;
                 vq[0] = fma(pi, acc, vq[0]);
             }
