@@ -1088,7 +1088,7 @@ def csr_form(G, torch, stream):
                       "frac_of_dram_read": round(gbs / bw["dram_read_gbs"], 4),
                       "achieved_tflops": round(tflops, 4),
                       "frac_fp64_peak": round(tflops / tf, 4),
-                      "note": "the 106 MB of A and P_sym entries stay mostly in L2; three grid "
+                      "note": "the 106 MB of A and P_sym entries stay mostly in L2; four grid "
                               "barriers per iteration"},
             "read_bw": bw}
 
